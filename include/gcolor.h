@@ -1,0 +1,165 @@
+/*
+ * gcolor.h -- C ABI of the GB300 (sm_103a) graph-colouring library.
+ *
+ * The library computes the two data-parallel steps of JP-ADG from Besta et
+ * al., "High-Performance Parallel Graph Coloring with Strong Guarantees on
+ * Work, Depth, and Quality" (SC'20):
+ *
+ *   ADG     (Algorithm 1, Section 3): the approximate degeneracy ordering.
+ *           Round after round it removes every remaining vertex whose degree
+ *           in the remaining subgraph is at most (1+eps) times that
+ *           subgraph's average degree; the round number is the vertex's batch.
+ *   JP-ADG  (Algorithm 3, Section 4.1): Jones-Plassmann colouring with the
+ *           priority rho(v) = <rho_ADG(v), rho_R(v)>, where rho_R is a seeded
+ *           random tie-break.
+ *
+ * Graph model (Section 2.1): an undirected simple graph in CSR.  Both
+ * directions of every edge are stored, rows are sorted ascending, there are
+ * no self-loops and no duplicate edges.  Vertex ids are 0..n-1.
+ *
+ * Conventions for every call below:
+ *  - Pointers documented "device" must be device memory of the context's GPU
+ *    (cudaMalloc, or a PyTorch CUDA tensor's data pointer); "host" pointers
+ *    are ordinary or page-locked host memory.  The CALLER owns every input
+ *    and output buffer.  The context owns only its scratch memory, which it
+ *    grows on demand and frees in gc_destroy().
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *    stream-ordered.  Calls that return host scalars (num_rounds, num_colors)
+ *    synchronise the stream before returning, so those scalars and the device
+ *    outputs are ready when the call returns.
+ *  - Exact integer arithmetic throughout: eps = eps_p / eps_q with
+ *    eps_q >= 1, eps_p >= 0 and eps_p, eps_q <= 2^20 (GC_ERR_INVALID_ARG
+ *    otherwise).  The ADG test "D[u] <= (1+eps) * Sigma/|U|" is evaluated as
+ *    D[u] <= floor((q+p)*Sigma / (q*|U|)) without floating point.
+ *  - Output numbering: batch ids start at 1 (Algorithm 1 starts its round
+ *    counter at 1); colours start at 1 (Algorithm 3: 0 means uncoloured).
+ *  - Results are deterministic: for a fixed seed the batches are unique and
+ *    the colouring equals the sequential Greedy colouring in decreasing
+ *    priority order (with vertex id as the final tie-break), whatever the
+ *    thread schedule.
+ *  - No call aborts, traps or hangs: every device-side wait is bounded and a
+ *    wait that runs out is reported as GC_ERR_TIMEOUT.  After any error the
+ *    context stays usable; device outputs are then unspecified.
+ *  - A context may be used by one host thread at a time.
+ */
+#ifndef GCOLOR_H_
+#define GCOLOR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GC_OK = 0,
+  GC_ERR_INVALID_ARG = 1,   /* null pointer, bad size, eps out of range      */
+  GC_ERR_INVALID_GRAPH = 2, /* CSR breaks the graph model (gc_validate_csr)  */
+  GC_ERR_OOM = 3,           /* device or pinned-host allocation failed       */
+  GC_ERR_CUDA = 4,          /* a CUDA runtime call failed                    */
+  GC_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out            */
+  GC_ERR_OVERFLOW = 6       /* a count would not fit the documented range    */
+} gc_status;
+
+/* Same type as cudaStream_t, spelled without the CUDA headers. */
+typedef struct CUstream_st *gc_stream;
+
+typedef struct gc_context gc_context;
+
+/* A CSR graph resident on the device: row_ptr has n+1 int64 entries with
+ * row_ptr[0] = 0 and row_ptr[n] = nnz; col_idx has nnz int32 entries.
+ * n <= 2^31 - 2; nnz = 2m (both directions of each undirected edge). */
+typedef struct {
+  int64_t n;
+  int64_t nnz;
+  const int64_t *row_ptr; /* device */
+  const int32_t *col_idx; /* device */
+} gc_csr;
+
+/* Per-call statistics of the last completed call on a context. */
+typedef struct {
+  int32_t adg_rounds;      /* rho-bar: number of ADG rounds                    */
+  int32_t num_colors;      /* largest colour used                              */
+  int64_t sum_U;           /* sum over rounds of |U_l| (partition work)        */
+  int64_t sum_decrements;  /* degree decrements performed by ADG's UPDATE      */
+  int64_t jp_spins;        /* polls of uncoloured predecessors (diagnostic)    */
+  float ms_adg;            /* device time of the ADG phase (0 if not timed)    */
+  float ms_jp;             /* device time of the JP phase (0 if not timed)     */
+} gc_stats;
+
+/* Human-readable name of a status code (static storage). */
+const char *gc_status_str(gc_status s);
+
+/* Create a context bound to CUDA device `device`.  Allocates nothing large
+ * until the first call needs scratch.  *ctx is NULL on failure. */
+gc_status gc_create(gc_context **ctx, int device);
+
+/* Release the context's scratch memory and the context itself (NULL ok). */
+void gc_destroy(gc_context *ctx);
+
+/* Statistics of the last successful colouring call on `ctx`. */
+gc_status gc_get_stats(const gc_context *ctx, gc_stats *out);
+
+/* When `enable` is non-zero, later calls time their ADG and JP phases with
+ * CUDA events on their stream (reported in gc_stats); default off. */
+gc_status gc_set_timing(gc_context *ctx, int enable);
+
+/* Check that `g` satisfies the graph model of Section 2.1: row_ptr starts at
+ * 0, is non-decreasing and ends at nnz; every id is in [0, n); rows are
+ * strictly increasing (sorted, no duplicates); no self-loops; and the graph
+ * is symmetric (w in N(u) <=> u in N(w)).  Returns GC_OK or
+ * GC_ERR_INVALID_GRAPH.  O(nnz log Delta) work on the device.  The other
+ * calls assume a valid graph and do not re-check it. */
+gc_status gc_validate_csr(gc_context *ctx, const gc_csr *g, gc_stream stream);
+
+/* ADG, Algorithm 1 (Section 3).  Writes batch_out[v] = rho_ADG(v) in
+ * 1..num_rounds for every vertex (device, n int32) and the number of rounds
+ * to *num_rounds_out (host).  Degrees are maintained by push-style UPDATE
+ * (atomic decrements of the neighbours of each removed vertex) and the degree
+ * sum is carried from round to round by subtracting the removed degrees and
+ * the cut (Section 5, "Caching Sums of Degrees"). */
+gc_status gc_adg_partition(gc_context *ctx, const gc_csr *g, uint32_t eps_p, uint32_t eps_q,
+                           int32_t *batch_out, int32_t *num_rounds_out, gc_stream stream);
+
+/* JP-ADG priority (Section 4.1): key_out[v] = (batch[v] << 32) | h_seed(v)
+ * (device, n uint64), where h_seed(v) is the upper 32 bits of the (v+1)-th
+ * output of the SplitMix64 generator (Steele, Lea & Flood, OOPSLA 2014)
+ * started from state `seed`.  batch is device, n int32, values >= 0. */
+gc_status gc_make_priority(gc_context *ctx, int64_t n, const int32_t *batch, uint64_t seed,
+                           uint64_t *key_out, gc_stream stream);
+
+/* JP colouring, Algorithm 3 (Section 4.1), for an arbitrary priority:
+ * vertex u precedes v (u is a predecessor of v in the DAG G_rho) iff
+ * (priority[u], u) > (priority[v], v) lexicographically, so any array gives
+ * a total order.  color_out[v] >= 1 (device, n int32) is the smallest colour
+ * not used by v's predecessors; *num_colors_out (host) is the largest colour. */
+gc_status gc_jp_color(gc_context *ctx, const gc_csr *g, const uint64_t *priority,
+                      int32_t *color_out, int32_t *num_colors_out, gc_stream stream);
+
+/* JP-ADG end to end: ADG with eps = eps_p/eps_q, then JP with the priority
+ * of gc_make_priority(batch, seed), computed on the fly.  color_out (device,
+ * n int32) is required; batch_out (device, n int32) may be NULL.  Both host
+ * scalars may be NULL.  Same result as gc_adg_partition + gc_make_priority +
+ * gc_jp_color. */
+gc_status gc_color_graph(gc_context *ctx, const gc_csr *g, uint32_t eps_p, uint32_t eps_q,
+                         uint64_t seed, int32_t *color_out, int32_t *batch_out,
+                         int32_t *num_colors_out, int32_t *num_rounds_out, gc_stream stream);
+
+/* gc_color_graph for a graph in HOST memory: copies row_ptr (n+1 int64) and
+ * col_idx (nnz int32) to device buffers that the context owns and keeps for
+ * reuse, colours the graph, and copies the colours (and, if batch_out is not
+ * NULL, the batches) back to the host arrays of n int32.  Page-locked host
+ * buffers make the copies asynchronous.  Returns after the results are on
+ * the host. */
+gc_status gc_color_graph_host(gc_context *ctx, int64_t n, int64_t nnz, const int64_t *row_ptr,
+                              const int32_t *col_idx, uint32_t eps_p, uint32_t eps_q,
+                              uint64_t seed, int32_t *color_out, int32_t *batch_out,
+                              int32_t *num_colors_out, int32_t *num_rounds_out,
+                              gc_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GCOLOR_H_ */

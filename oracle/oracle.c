@@ -1,0 +1,419 @@
+/*
+ * oracle.c -- plain, slow, obviously correct CPU reference for ADG and JP-ADG
+ * (Besta et al., "High-Performance Parallel Graph Coloring with Strong
+ * Guarantees on Work, Depth, and Quality", SC'20).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg may load this file.  The CUDA library shares
+ * no code, header, table or constant with it: the priority hash below is
+ * written here from SplitMix64's published definition, independently of the
+ * GPU side's own version.
+ *
+ * Single-threaded, exact integer arithmetic throughout.  Graph input is the
+ * paper's CSR model (Section 2.1, "Graph Model and Representation"): n vertices, int64 row offsets row_ptr[n+1],
+ * int32 neighbour ids col_idx[row_ptr[n]], undirected (both directions stored),
+ * simple, rows sorted.
+ *
+ * Readings of the paper taken here:
+ *  - R test uses "<=" (Algorithm 1, the definition of R; the proof of the
+ *    round bound in Section 3 also uses <=), evaluated exactly in integers:
+ *    D[u] <= (1+eps) * Sigma/|U|  with eps = p/q  <=>  q*|U|*D[u] <= (q+p)*Sigma
+ *    <=> D[u] <= floor((q+p)*Sigma / (q*|U|)), computed in 128 bits.
+ *  - Batch ids start at 1 (Algorithm 1 sets l = 1); 0 never appears in output.
+ *  - Priority rho(v) = <rho_ADG(v), rho_R(v)> (Section 4.1), made a total
+ *    order by the vertex id: key(v) = (batch(v), h_seed(v), v), compared
+ *    lexicographically; a HIGHER key is coloured first (pred(v) = neighbours
+ *    with higher rho, Algorithm 3).
+ *  - h_seed(v) = upper 32 bits of the (v+1)-th output of SplitMix64 seeded
+ *    with `seed` (Steele, Lea & Flood, OOPSLA 2014): the paper only says the
+ *    tie-break is random.
+ *  - Colours start at 1 (Algorithm 3 initialises C to 0 = uncoloured and
+ *    GetColor draws from {1, ..., |pred|+1}).
+ *  - JP with a total order produces exactly the sequential Greedy colouring
+ *    in decreasing priority (Algorithm 3: GetColor of v reads only the colours
+ *    of pred(v), which are all final when v is coloured).  So the colour
+ *    oracle is Greedy (Section 1) in that order.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------- */
+/* Priority tie-break: SplitMix64.                                            */
+/* The generator's state advances by the odd constant 0x9e3779b97f4a7c15 and */
+/* each output is the state passed through the 64-bit finaliser with shifts   */
+/* 30, 27, 31 and multipliers 0xbf58476d1ce4e5b9, 0x94d049bb133111eb.          */
+/* ------------------------------------------------------------------------- */
+
+uint64_t oracle_splitmix64_output(uint64_t seed, uint64_t k)
+{
+    /* k-th output (k >= 1) of SplitMix64 started from state `seed` */
+    uint64_t z = seed + k * 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    z = z ^ (z >> 31);
+    return z;
+}
+
+uint32_t oracle_tiebreak(uint64_t seed, int64_t v)
+{
+    return (uint32_t)(oracle_splitmix64_output(seed, (uint64_t)v + 1) >> 32);
+}
+
+/* ------------------------------------------------------------------------- */
+/* ADG, Algorithm 1 (Section 3), step by step.                                */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * Inputs: CSR, eps = eps_p / eps_q.
+ * Output: batch[v] = rho_ADG(v) in 1..num_rounds.
+ * Optional per-round records (NULL to skip; at most max_log rounds written):
+ *   log_U[l-1] = |U_l|, log_R[l-1] = |R_l|, log_sigma[l-1] = sum_{u in U_l} D[u],
+ *   log_T[l-1] = floor((q+p)*Sigma / (q*|U|)).
+ * Returns 0 on success, 1 on bad arguments, 2 on allocation failure.
+ */
+int oracle_adg(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+               uint32_t eps_p, uint32_t eps_q, int32_t *batch, int32_t *num_rounds,
+               int64_t *log_U, int64_t *log_R, int64_t *log_sigma, int64_t *log_T,
+               int64_t max_log)
+{
+    if (n < 0 || eps_q == 0) return 1;
+    int64_t *D = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    char *inU = (char *)malloc((size_t)(n > 0 ? n : 1));
+    char *inR = (char *)malloc((size_t)(n > 0 ? n : 1));
+    if (!D || !inU || !inR) { free(D); free(inU); free(inR); return 2; }
+
+    /* D = [deg(v_1) ... deg(v_n)];  l = 1;  U = V */
+    for (int64_t v = 0; v < n; ++v) {
+        D[v] = row_ptr[v + 1] - row_ptr[v];
+        inU[v] = 1;
+        batch[v] = 0;
+    }
+    int64_t sizeU = n;
+    int32_t l = 1;
+
+    while (sizeU > 0) {
+        /* |U| = Count(U);  cnt = Reduce(U) = sum of D over U (a fresh sum) */
+        int64_t count = 0, cnt = 0;
+        for (int64_t v = 0; v < n; ++v)
+            if (inU[v]) { count += 1; cnt += D[v]; }
+
+        /* R = {u in U : D[u] <= (1+eps) * cnt/|U|}, exactly in integers */
+        unsigned __int128 num = (unsigned __int128)(eps_q + (uint64_t)eps_p) * (uint64_t)cnt;
+        unsigned __int128 den = (unsigned __int128)eps_q * (uint64_t)count;
+        unsigned __int128 T = num / den;
+        int64_t sizeR = 0;
+        for (int64_t v = 0; v < n; ++v) {
+            inR[v] = (char)(inU[v] && (unsigned __int128)D[v] <= T);
+            sizeR += inR[v];
+        }
+
+        if (l - 1 < max_log) {
+            if (log_U) log_U[l - 1] = count;
+            if (log_R) log_R[l - 1] = sizeR;
+            if (log_sigma) log_sigma[l - 1] = cnt;
+            if (log_T) log_T[l - 1] = T > (unsigned __int128)INT64_MAX ? INT64_MAX : (int64_t)T;
+        }
+
+        /* UPDATE(U, R, D): for v in R, for u in N_U(v): DecrementAndFetch(D[u]).
+         * U still contains R here, as in the listing. */
+        for (int64_t v = 0; v < n; ++v) {
+            if (!inR[v]) continue;
+            for (int64_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) {
+                int32_t u = col_idx[k];
+                if (inU[u]) D[u] -= 1;
+            }
+        }
+
+        /* U = U \ R;  rho_ADG(v) = l for v in R;  l = l + 1 */
+        for (int64_t v = 0; v < n; ++v) {
+            if (inR[v]) {
+                inU[v] = 0;
+                batch[v] = l;
+            }
+        }
+        sizeU -= sizeR;
+        if (sizeR == 0) { free(D); free(inU); free(inR); return 3; } /* cannot happen: min degree <= average */
+        l += 1;
+    }
+    *num_rounds = l - 1;
+    free(D);
+    free(inU);
+    free(inR);
+    return 0;
+}
+
+/*
+ * A second, deliberately naive ADG: every round recomputes each remaining
+ * vertex's degree inside G[U] from scratch, D[u] = |N(u) cap U| (the quantity
+ * Algorithm 1's UPDATE maintains).  O(rounds * nnz); tiny graphs only.
+ */
+int oracle_adg_naive(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                     uint32_t eps_p, uint32_t eps_q, int32_t *batch, int32_t *num_rounds)
+{
+    if (n < 0 || eps_q == 0) return 1;
+    int64_t *deg = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    if (!deg) return 2;
+    for (int64_t v = 0; v < n; ++v) batch[v] = 0;
+    int64_t left = n;
+    int32_t l = 0;
+    while (left > 0) {
+        ++l;
+        int64_t sum = 0;
+        for (int64_t v = 0; v < n; ++v) {
+            deg[v] = 0;
+            if (batch[v] != 0) continue;
+            for (int64_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k)
+                if (batch[col_idx[k]] == 0) deg[v] += 1;
+            sum += deg[v];
+        }
+        /* threshold comparison by cross-multiplication, no division */
+        int64_t removed = 0;
+        for (int64_t v = 0; v < n; ++v) {
+            if (batch[v] != 0) continue;
+            unsigned __int128 lhs = (unsigned __int128)eps_q * (uint64_t)left * (uint64_t)deg[v];
+            unsigned __int128 rhs = (unsigned __int128)(eps_q + (uint64_t)eps_p) * (uint64_t)sum;
+            if (lhs <= rhs) deg[v] = -1; /* mark for removal */
+        }
+        for (int64_t v = 0; v < n; ++v)
+            if (batch[v] == 0 && deg[v] == -1) { batch[v] = l; ++removed; }
+        left -= removed;
+        if (removed == 0) { free(deg); return 3; }
+    }
+    *num_rounds = l;
+    free(deg);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Greedy colouring in a given order (Section 1: each vertex in turn takes   */
+/* the smallest colour not used by an already coloured neighbour).           */
+/* ------------------------------------------------------------------------- */
+
+int oracle_greedy(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                  const int64_t *order, int32_t *color, int32_t *num_colors)
+{
+    int64_t maxdeg = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        color[v] = 0;
+        if (row_ptr[v + 1] - row_ptr[v] > maxdeg) maxdeg = row_ptr[v + 1] - row_ptr[v];
+    }
+    /* used[c] == stamp  <=>  colour c is taken by a coloured neighbour */
+    int64_t *used = (int64_t *)calloc((size_t)(maxdeg + 2), sizeof(int64_t));
+    if (!used) return 2;
+    int32_t maxc = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t v = order[i];
+        int64_t stamp = i + 1;
+        for (int64_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) {
+            int32_t c = color[col_idx[k]];
+            if (c > 0 && c <= maxdeg + 1) used[c] = stamp;
+        }
+        int32_t c = 1;
+        while (used[c] == stamp) ++c;
+        color[v] = c;
+        if (c > maxc) maxc = c;
+    }
+    *num_colors = maxc;
+    free(used);
+    return 0;
+}
+
+/* ---- priority order: key(v) = (primary(v), secondary(v), v), descending ---- */
+
+typedef struct {
+    uint64_t primary;
+    uint64_t secondary;
+    int64_t v;
+} okey;
+
+static int okey_desc(const void *a, const void *b)
+{
+    const okey *x = (const okey *)a, *y = (const okey *)b;
+    if (x->primary != y->primary) return x->primary > y->primary ? -1 : 1;
+    if (x->secondary != y->secondary) return x->secondary > y->secondary ? -1 : 1;
+    if (x->v != y->v) return x->v > y->v ? -1 : 1;
+    return 0;
+}
+
+/* order[] = vertices sorted by (primary, secondary, id) descending */
+static int order_desc(int64_t n, const uint64_t *primary, const uint64_t *secondary, int64_t *order)
+{
+    okey *k = (okey *)malloc(sizeof(okey) * (size_t)(n > 0 ? n : 1));
+    if (!k) return 2;
+    for (int64_t v = 0; v < n; ++v) {
+        k[v].primary = primary ? primary[v] : 0;
+        k[v].secondary = secondary ? secondary[v] : 0;
+        k[v].v = v;
+    }
+    qsort(k, (size_t)n, sizeof(okey), okey_desc);
+    for (int64_t i = 0; i < n; ++i) order[i] = k[i].v;
+    free(k);
+    return 0;
+}
+
+/* JP-ADG priority key as one 64-bit word: (batch << 32) | h_seed(v); ties on
+ * the word are broken by the larger vertex id. */
+void oracle_priority(int64_t n, const int32_t *batch, uint64_t seed, uint64_t *key)
+{
+    for (int64_t v = 0; v < n; ++v)
+        key[v] = ((uint64_t)(uint32_t)batch[v] << 32) | (uint64_t)oracle_tiebreak(seed, v);
+}
+
+/* JP colouring (Algorithm 3) for an arbitrary priority array, via its
+ * equivalent Greedy in decreasing (priority, id) order. */
+int oracle_jp_color(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                    const uint64_t *priority, int32_t *color, int32_t *num_colors)
+{
+    int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    if (!order) return 2;
+    int rc = order_desc(n, priority, NULL, order);
+    if (rc == 0) rc = oracle_greedy(n, row_ptr, col_idx, order, color, num_colors);
+    free(order);
+    return rc;
+}
+
+/* Full JP-ADG: ADG batches, then colouring in (batch, h_seed, id) order. */
+int oracle_jp_adg(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                  uint32_t eps_p, uint32_t eps_q, uint64_t seed,
+                  int32_t *batch, int32_t *color, int32_t *num_rounds, int32_t *num_colors)
+{
+    int rc = oracle_adg(n, row_ptr, col_idx, eps_p, eps_q, batch, num_rounds,
+                        NULL, NULL, NULL, NULL, 0);
+    if (rc) return rc;
+    uint64_t *key = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
+    if (!key) return 2;
+    oracle_priority(n, batch, seed, key);
+    rc = oracle_jp_color(n, row_ptr, col_idx, key, color, num_colors);
+    free(key);
+    return rc;
+}
+
+/* |pred(v)| = number of neighbours with a higher (priority, id) (Algorithm 3,
+ * Part 1: count[v] = |pred[v]|). */
+void oracle_pred_count(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                       const uint64_t *priority, int32_t *count)
+{
+    for (int64_t v = 0; v < n; ++v) {
+        int32_t c = 0;
+        for (int64_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) {
+            int64_t w = col_idx[k];
+            if (priority[w] > priority[v] || (priority[w] == priority[v] && w > v)) ++c;
+        }
+        count[v] = c;
+    }
+}
+
+/* Longest path (in vertices) of the DAG G_rho whose edges run from higher to
+ * lower (priority, id); depth[v] = 1 + max depth over pred(v).  Returns the
+ * maximum: the number of dependency steps JP needs. */
+int64_t oracle_jp_depth(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                        const uint64_t *priority, int32_t *depth)
+{
+    int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    if (!order) return -1;
+    if (order_desc(n, priority, NULL, order)) { free(order); return -1; }
+    int64_t best = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t v = order[i];
+        int32_t dv = 1;
+        for (int64_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) {
+            int64_t w = col_idx[k];
+            if (priority[w] > priority[v] || (priority[w] == priority[v] && w > v))
+                if (depth[w] + 1 > dv) dv = depth[w] + 1;
+        }
+        depth[v] = dv;
+        if (dv > best) best = dv;
+    }
+    free(order);
+    return best;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Exact degeneracy by smallest-last peeling (Matula & Beck; Section 2.2):   */
+/* repeatedly remove a vertex of minimum remaining degree.  d is the largest */
+/* degree seen at removal; order[] is the removal sequence (first removed    */
+/* first).  Bucket queue, O(n + m).                                          */
+/* ------------------------------------------------------------------------- */
+
+int64_t oracle_degeneracy(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, int64_t *order)
+{
+    if (n == 0) return 0;
+    int64_t maxdeg = 0;
+    int64_t *deg = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    for (int64_t v = 0; v < n; ++v) {
+        deg[v] = row_ptr[v + 1] - row_ptr[v];
+        if (deg[v] > maxdeg) maxdeg = deg[v];
+    }
+    /* doubly linked bucket lists */
+    int64_t *head = (int64_t *)malloc(sizeof(int64_t) * (size_t)(maxdeg + 1));
+    int64_t *next = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *prev = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    char *gone = (char *)calloc((size_t)n, 1);
+    for (int64_t d = 0; d <= maxdeg; ++d) head[d] = -1;
+    for (int64_t v = 0; v < n; ++v) {
+        prev[v] = -1;
+        next[v] = head[deg[v]];
+        if (head[deg[v]] >= 0) prev[head[deg[v]]] = v;
+        head[deg[v]] = v;
+    }
+    int64_t d = 0, cur = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (cur > 0) cur -= 1; /* the minimum can drop by at most one per removal */
+        while (head[cur] < 0) ++cur;
+        int64_t v = head[cur];
+        /* unlink v */
+        head[cur] = next[v];
+        if (next[v] >= 0) prev[next[v]] = -1;
+        gone[v] = 1;
+        order[i] = v;
+        if (cur > d) d = cur;
+        for (int64_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) {
+            int64_t w = col_idx[k];
+            if (gone[w]) continue;
+            /* move w from bucket deg[w] to deg[w]-1 */
+            if (prev[w] >= 0) next[prev[w]] = next[w]; else head[deg[w]] = next[w];
+            if (next[w] >= 0) prev[next[w]] = prev[w];
+            deg[w] -= 1;
+            prev[w] = -1;
+            next[w] = head[deg[w]];
+            if (head[deg[w]] >= 0) prev[head[deg[w]]] = w;
+            head[deg[w]] = w;
+        }
+    }
+    free(deg); free(head); free(next); free(prev); free(gone);
+    return d;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Chromatic number by exhaustive backtracking (n <= 16), a lower bound for  */
+/* every proper colouring (Section 1).                                        */
+/* ------------------------------------------------------------------------- */
+
+static int try_color(int64_t v, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                     int32_t k, int32_t *c)
+{
+    if (v == n) return 1;
+    for (int32_t col = 1; col <= k; ++col) {
+        int ok = 1;
+        for (int64_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e)
+            if (col_idx[e] < v && c[col_idx[e]] == col) { ok = 0; break; }
+        if (!ok) continue;
+        c[v] = col;
+        if (try_color(v + 1, n, row_ptr, col_idx, k, c)) return 1;
+    }
+    c[v] = 0;
+    return 0;
+}
+
+int32_t oracle_chromatic_number(int64_t n, const int64_t *row_ptr, const int32_t *col_idx)
+{
+    if (n == 0) return 0;
+    if (n > 16) return -1;
+    int32_t c[16];
+    for (int32_t k = 1; k <= (int32_t)n; ++k) {
+        memset(c, 0, sizeof(c));
+        if (try_color(0, n, row_ptr, col_idx, k, c)) return k;
+    }
+    return (int32_t)n;
+}

@@ -1,0 +1,402 @@
+"""Pins for the CPU oracle: each check is fixed by the paper's statements or
+by mathematics, not by the oracle itself.
+
+- closed forms of ADG and JP-ADG on graph families (worked in the fixtures and
+  docstrings below from Algorithm 1's integer threshold);
+- the invariants that the paper proves for ADG (Section 3: the round-bound
+  lemma and its recurrence, the work lemma, the average-degree lemma and the
+  2(1+eps)-approximation lemma) and for JP-ADG (Section 4.1: the colour bound
+  kd+1 and the corollary 2(1+eps)d+1);
+- an independent event-driven simulation of Algorithm 3 (JP with counters
+  and Join) that must equal the oracle's Greedy-in-priority-order colouring;
+- a second, naive ADG that recomputes degrees from scratch;
+- exhaustive degeneracy and chromatic number on tiny graphs;
+- published SplitMix64 test vectors for the priority tie-break.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from _fixtures import (case_graph, complete, complete_bipartite, cycle, empty, ints, neighbours,
+                       path, petersen, random_small, read_cases, star, wheel)
+
+EPS = (1, 100)
+
+
+# ---------------------------------------------------------------- tie-break hash
+
+def test_splitmix64_published_vectors():
+    # Reference outputs of SplitMix64: state 0 -> first output 0xe220a8397b1dcdaf;
+    # state 1234567 -> the five outputs below.
+    assert oracle.splitmix64_output(0, 1) == 0xE220A8397B1DCDAF
+    want = [6457827717110365317, 3203168211198807973, 9817491932198370423,
+            4593380528125082431, 16408922859458223821]
+    assert [oracle.splitmix64_output(1234567, k) for k in range(1, 6)] == want
+
+
+def test_tiebreak_is_upper_half_of_output_v_plus_1():
+    for seed in (0, 42, 2**63 + 5):
+        for v in (0, 1, 17, 2**31 - 2):
+            assert oracle.tiebreak(seed, v) == oracle.splitmix64_output(seed, v + 1) >> 32
+
+
+def test_tiebreak_spread():
+    # 2^16 consecutive ids: upper-32-bit values should collide only at the
+    # birthday rate (expected ~0.5 collisions) and fill all 16 top-bit buckets.
+    vals = np.array([oracle.tiebreak(42, v) for v in range(1 << 16)], dtype=np.uint64)
+    assert len(np.unique(vals)) >= (1 << 16) - 4
+    hist = np.bincount((vals >> np.uint64(28)).astype(np.int64), minlength=16)
+    assert hist.min() > 0.8 * (1 << 12) and hist.max() < 1.2 * (1 << 12)
+
+
+# ---------------------------------------------------------------- hand-worked fixtures
+
+def test_golden_lollipop_adg():
+    (case,) = read_cases("lollipop_adg.txt")
+    g = case_graph(case)
+    batch, rounds, log = oracle.adg(g, int(case["eps_p"]), int(case["eps_q"]), log=True)
+    assert rounds == int(case["rounds"])
+    assert np.array_equal(batch, ints(case["batch"]))
+    for key in ("U", "R", "sigma", "T"):
+        assert np.array_equal(log[key], ints(case[key])), key
+    _, color, _, nc = oracle.jp_adg(g, 1, 100, 42)
+    assert sorted(color[:5].tolist()) == [1, 2, 3, 4, 5]
+
+
+@pytest.mark.parametrize("case", read_cases("jp_adg_small.txt"), ids=lambda c: c["name"])
+def test_golden_jp_adg_small(case):
+    g = case_graph(case)
+    for seed in (0, 42, 7):
+        batch, color, rounds, nc = oracle.jp_adg(g, *EPS, seed)
+        assert rounds == int(case["rounds"])
+        assert np.array_equal(batch, ints(case["batch"]))
+        assert np.array_equal(color, ints(case["color"]))
+
+
+# ---------------------------------------------------------------- closed forms
+
+def test_empty_graph_one_round_colour_one():
+    g = empty(9)
+    batch, color, rounds, nc = oracle.jp_adg(g, *EPS, 42)
+    assert rounds == 1 and (batch == 1).all() and (color == 1).all() and nc == 1
+
+
+def test_zero_vertices():
+    g = empty(0)
+    batch, color, rounds, nc = oracle.jp_adg(g, *EPS, 42)
+    assert rounds == 0 and nc == 0 and batch.size == 0
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 17])
+def test_complete_graph(n):
+    # every degree equals the average: one round; colours are a permutation
+    batch, color, rounds, nc = oracle.jp_adg(complete(n), *EPS, 42)
+    assert rounds == 1 and (batch == 1).all()
+    assert sorted(color.tolist()) == list(range(1, n + 1)) and nc == n
+
+
+@pytest.mark.parametrize("k", [2, 3, 10, 150])
+def test_star(k):
+    # Sigma = 2k, |U| = k+1: T = floor(101*2k / (100(k+1))) = 1 for k >= 2
+    batch, color, rounds, nc = oracle.jp_adg(star(k), *EPS, 42)
+    assert rounds == 2 and batch[0] == 2 and (batch[1:] == 1).all()
+    assert color[0] == 1 and (color[1:] == 2).all()
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 9, 50, 99, 100])
+def test_path_short_peels_from_both_ends(n):
+    # |U| = k <= 100 with degree sum 2(k-1): T = floor(202(k-1)/(100k)) = 1, so
+    # only the two end points leave each round (worked in fixture path7)
+    g = path(n)
+    for seed in (1, 42):
+        batch, color, rounds, nc = oracle.jp_adg(g, *EPS, seed)
+        i = np.arange(n)
+        assert rounds == (n + 1) // 2
+        assert np.array_equal(batch, np.minimum(i, n - 1 - i) + 1)
+        assert nc == 2
+        if n % 2 == 1:  # centre first, colours alternate outward
+            c = n // 2
+            assert np.array_equal(color, np.where((i - c) % 2 == 0, 1, 2))
+
+
+@pytest.mark.parametrize("n", [101, 102, 500])
+def test_path_long_single_round(n):
+    # T = floor(202(n-1)/(100n)) = 2 iff 202(n-1) >= 200n iff n >= 101
+    batch, color, rounds, nc = oracle.jp_adg(path(n), *EPS, 42)
+    assert rounds == 1 and (batch == 1).all() and nc <= 3
+
+
+@pytest.mark.parametrize("n", [3, 4, 7, 1000])
+def test_cycle_single_round(n):
+    batch, color, rounds, nc = oracle.jp_adg(cycle(n), *EPS, 42)
+    assert rounds == 1 and (batch == 1).all() and 2 <= nc <= 3
+
+
+@pytest.mark.parametrize("a,b", [(2, 5), (3, 4), (10, 11), (7, 50)])
+def test_complete_bipartite_unbalanced(a, b):
+    # b > (1+2 eps) a: only the b-side passes the first threshold
+    assert b * 100 > 102 * a
+    batch, color, rounds, nc = oracle.jp_adg(complete_bipartite(a, b), *EPS, 42)
+    assert rounds == 2
+    assert (batch[:a] == 2).all() and (batch[a:] == 1).all()
+    assert (color[:a] == 1).all() and (color[a:] == 2).all()
+
+
+def test_complete_bipartite_balanced_one_round():
+    batch, color, rounds, nc = oracle.jp_adg(complete_bipartite(50, 51), *EPS, 42)
+    assert rounds == 1 and nc == 2
+
+
+@pytest.mark.parametrize("k,single", [(100, False), (101, True), (150, True)])
+def test_grid2d_single_round_iff_k_at_least_101(k, single):
+    batch, rounds = oracle.adg(gg.grid(k, k), *EPS)
+    assert (rounds == 1) == single
+
+
+@pytest.mark.parametrize("k,single", [(100, False), (101, True)])
+def test_grid3d_single_round_iff_k_at_least_101(k, single):
+    # 6k^2(k-1) degree sum over k^3 vertices: 101*6(k-1) >= 600k iff k >= 101
+    batch, rounds = oracle.adg(gg.grid(k, k, k), *EPS)
+    assert (rounds == 1) == single
+
+
+def test_grid3d_256_threshold_arithmetic():
+    # the 256^3 workload is one round: 100 * 6 * 256^3 <= 101 * nnz
+    k = 256
+    nnz = 2 * 3 * k * k * (k - 1)
+    assert nnz == 100_270_080
+    assert 100 * 6 * k**3 <= 101 * nnz
+
+
+# ---------------------------------------------------------------- invariants
+
+def _graphs():
+    yield gg.erdos_renyi(16384, 81920, 1)
+    yield gg.erdos_renyi(3000, 30000, 5)
+    yield gg.rmat(12, 16, seed=3)
+    yield gg.rmat(14, 8, seed=4)
+    yield gg.barabasi_albert(5000, 4, 2)
+    yield gg.grid(40, 30)
+    yield gg.grid(12, 10, 9, perm_seed=9)
+    yield petersen()
+
+
+GRAPHS = list(_graphs())
+EPSES = [(1, 100), (1, 10), (1, 2), (0, 1), (3, 1)]
+
+
+def _geq_counts(g, batch):
+    src = np.repeat(np.arange(g.n), g.degrees())
+    return np.bincount(src, weights=(batch[g.col_idx] >= batch[src]), minlength=g.n).astype(np.int64)
+
+
+@pytest.mark.parametrize("g", GRAPHS, ids=lambda g: g.name)
+@pytest.mark.parametrize("p,q", EPSES)
+def test_adg_invariants(g, p, q):
+    d, _ = oracle.degeneracy(g)
+    batch, rounds, log = oracle.adg(g, p, q, log=True)
+    U, R, S, T = log["U"], log["R"], log["sigma"], log["T"]
+    assert batch.min() == 1 and batch.max() == rounds
+    assert np.array_equal(np.bincount(batch, minlength=rounds + 1)[1:], R)
+    # U shrinks by R each round and ends empty
+    assert U[0] == g.n and np.array_equal(U[1:], U[:-1] - R[:-1]) and U[-1] == R[-1]
+    # at least an eps/(1+eps) fraction leaves each round: (q+p)|U_{l+1}| < q|U_l|
+    Unext = np.append(U[1:], 0)
+    assert np.all((q + p) * Unext < q * U)
+    if p > 0:  # rounds <= ceil(log n / log(1+eps)) + 1, checked exactly
+        assert rounds == 1 or (q + p) ** (rounds - 1) < q ** (rounds - 1) * g.n
+    # average-degree lemma: the degree sum of G[U_l] is at most 2d(|U_l|-1)
+    assert np.all(S <= 2 * d * (U - 1))
+    # Sigma of round 1 is the full degree sum
+    assert S[0] == g.nnz
+    # each vertex has at most T_{batch(v)} neighbours ranked equal or higher,
+    # hence at most floor(2(1+eps)d) (partial 2(1+eps)-approximate ordering)
+    geq = _geq_counts(g, batch)
+    assert np.all(geq <= T[batch - 1])
+    assert geq.max() <= (2 * (q + p) * d) // q
+    # the sum of |U_l| is bounded by (1+eps)/eps * n (work lemma)
+    if p > 0:
+        assert p * U.sum() <= (q + p) * g.n
+
+
+@pytest.mark.parametrize("g", GRAPHS, ids=lambda g: g.name)
+def test_degree_sum_cache_rule(g):
+    # Sigma_{l+1} = Sigma_l - sum_{v in R_l} D_l[v] - cut(R_l, U_{l+1}), where
+    # D_l[v] = deg inside G[U_l]; checked against the oracle's fresh sums.
+    batch, rounds, log = oracle.adg(g, *EPS, log=True)
+    src = np.repeat(np.arange(g.n), g.degrees())
+    dst = g.col_idx
+    for l in range(1, rounds):
+        inU = batch >= l
+        inR = batch == l
+        D_R = np.sum(inR[src] & inU[dst])
+        cut = np.sum(inR[src] & (batch[dst] > l))
+        assert log["sigma"][l] == log["sigma"][l - 1] - D_R - cut
+
+
+@pytest.mark.parametrize("g", GRAPHS, ids=lambda g: g.name)
+@pytest.mark.parametrize("p,q", [(1, 100), (1, 2)])
+def test_colour_invariants(g, p, q):
+    d, _ = oracle.degeneracy(g)
+    batch, color, rounds, nc = oracle.jp_adg(g, p, q, 42)
+    src = np.repeat(np.arange(g.n), g.degrees())
+    assert np.all(color >= 1) and color.max() == nc
+    assert np.all(color[src] != color[g.col_idx])                  # proper
+    prio = oracle.priority(batch, 42)
+    npred = oracle.pred_count(g, prio)
+    assert np.all(color <= npred + 1)                               # GetColor palette
+    assert nc <= (2 * (q + p) * d) // q + 1                         # corollary bound
+    # each colour is the smallest one absent from the predecessors
+    higher = (prio[g.col_idx] > prio[src]) | ((prio[g.col_idx] == prio[src]) & (g.col_idx > src))
+    for v in range(0, g.n, max(1, g.n // 500)):
+        sel = higher[g.row_ptr[v]:g.row_ptr[v + 1]]
+        used = set(color[neighbours(g, v)[sel]].tolist())
+        c = 1
+        while c in used:
+            c += 1
+        assert color[v] == c
+
+
+def test_priority_layout():
+    batch = np.array([0, 1, 5, 2**31 - 1], dtype=np.int32)
+    key = oracle.priority(batch, 42)
+    for v in range(4):
+        assert int(key[v]) >> 32 == int(batch[v])
+        assert int(key[v]) & 0xFFFFFFFF == oracle.tiebreak(42, v)
+
+
+# ---------------------------------------------------------------- JP == Greedy
+
+def _jp_simulate(g, prio, rng):
+    """Algorithm 3 executed literally: Part 1 builds pred/succ/count; Part 2
+    colours pred-free vertices, then Join decrements successors' counters and
+    colours a successor when its counter reaches 0.  The ready vertices are
+    taken in a random order, standing in for an arbitrary parallel schedule."""
+    n = g.n
+    key = [(int(prio[v]), v) for v in range(n)]
+    pred = [[int(w) for w in neighbours(g, v) if key[w] > key[v]] for v in range(n)]
+    succ = [[int(w) for w in neighbours(g, v) if key[w] < key[v]] for v in range(n)]
+    count = [len(p) for p in pred]
+    C = [0] * n
+    ready = [v for v in range(n) if count[v] == 0]
+    while ready:
+        v = ready.pop(rng.integers(len(ready)))
+        palette = set(range(1, len(pred[v]) + 2)) - {C[u] for u in pred[v]}
+        C[v] = min(palette)
+        for u in succ[v]:
+            count[u] -= 1
+            if count[u] == 0:
+                ready.append(u)
+    return np.array(C, dtype=np.int32)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_jp_simulation_equals_oracle(seed):
+    rng = np.random.default_rng(seed)
+    for g in (random_small(40, 0.2, seed), gg.erdos_renyi(300, 1500, seed + 1),
+              gg.barabasi_albert(300, 3, seed + 1), petersen()):
+        batch, color, rounds, nc = oracle.jp_adg(g, *EPS, seed)
+        prio = oracle.priority(batch, seed)
+        assert np.array_equal(_jp_simulate(g, prio, rng), color)
+        # arbitrary priorities too (many ties: the id breaks them)
+        prio2 = rng.integers(0, 4, size=g.n).astype(np.uint64)
+        c2, _ = oracle.jp_color(g, prio2)
+        assert np.array_equal(_jp_simulate(g, prio2, rng), c2)
+
+
+# ---------------------------------------------------------------- naive ADG
+
+@pytest.mark.parametrize("p,q", EPSES)
+def test_adg_equals_naive(p, q):
+    for s in range(4):
+        for g in (random_small(60, 0.1, s), gg.erdos_renyi(500, 2000, s + 3),
+                  gg.rmat(9, 8, seed=s + 1), gg.barabasi_albert(400, 2, s + 1)):
+            b1, r1 = oracle.adg(g, p, q)
+            b2, r2 = oracle.adg_naive(g, p, q)
+            assert r1 == r2 and np.array_equal(b1, b2)
+
+
+# ---------------------------------------------------------------- degeneracy, chi
+
+def _brute_degeneracy(g):
+    n = g.n
+    adj = [set(neighbours(g, v).tolist()) for v in range(n)]
+    best = 0
+    for mask in range(1, 1 << n):
+        S = [v for v in range(n) if mask >> v & 1]
+        best = max(best, min(len(adj[v] & set(S)) for v in S))
+    return best
+
+
+@pytest.mark.parametrize("g,d", [(complete(6), 5), (path(9), 1), (cycle(8), 2), (star(7), 1),
+                                 (complete_bipartite(3, 5), 3), (petersen(), 3), (empty(4), 0),
+                                 (wheel(6), 3)])
+def test_degeneracy_known(g, d):
+    assert oracle.degeneracy(g)[0] == d
+
+
+def test_degeneracy_grids():
+    assert oracle.degeneracy(gg.grid(20, 20))[0] == 2
+    assert oracle.degeneracy(gg.grid(8, 8, 8))[0] == 3
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_degeneracy_brute_force(seed):
+    g = random_small(11, 0.35, seed)
+    assert oracle.degeneracy(g)[0] == _brute_degeneracy(g)
+
+
+@pytest.mark.parametrize("g", GRAPHS, ids=lambda g: g.name)
+def test_smallest_last_greedy_uses_at_most_d_plus_1(g):
+    d, order = oracle.degeneracy(g)
+    _, nc = oracle.greedy(g, order[::-1].copy())   # last removed coloured first
+    assert nc <= d + 1
+    assert d * (d + 1) // 2 <= g.m                 # the d-core has >= d+1 vertices
+
+
+@pytest.mark.parametrize("g,chi", [(complete(5), 5), (cycle(7), 3), (cycle(8), 2), (petersen(), 3),
+                                   (complete_bipartite(3, 4), 2), (empty(5), 1), (wheel(5), 4),
+                                   (wheel(6), 3), (path(2), 2)])
+def test_chromatic_number_known(g, chi):
+    assert oracle.chromatic_number(g) == chi
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_colours_at_least_chromatic_number(seed):
+    g = random_small(10 + seed % 3, 0.45, seed)
+    chi = oracle.chromatic_number(g)
+    for p, q in [(1, 100), (1, 2), (0, 1)]:
+        _, color, _, nc = oracle.jp_adg(g, p, q, seed)
+        assert nc >= chi
+
+
+# ---------------------------------------------------------------- generator sanity
+
+@pytest.mark.parametrize("g", GRAPHS, ids=lambda g: g.name)
+def test_generated_csr_is_canonical(g):
+    src = np.repeat(np.arange(g.n), g.degrees())
+    dst = g.col_idx.astype(np.int64)
+    assert np.all(src != dst)
+    same_row = src[1:] == src[:-1]
+    assert np.all(dst[1:][same_row] > dst[:-1][same_row])
+    fwd = set(zip(src.tolist(), dst.tolist()))
+    assert all((b, a) in fwd for a, b in fwd)
+
+
+def test_er_exact_edge_count_and_determinism():
+    g1 = gg.erdos_renyi(16384, 81920, 1)
+    g2 = gg.erdos_renyi(16384, 81920, 1)
+    assert g1.m == 81920 and np.array_equal(g1.col_idx, g2.col_idx)
+
+
+def test_grid_edge_counts():
+    assert gg.grid(7, 5).m == 6 * 5 + 7 * 4
+    assert gg.grid(4, 3, 2).m == 3 * 3 * 2 + 4 * 2 * 2 + 4 * 3 * 1
+    g = gg.grid(6, 6, 6, perm_seed=1)
+    assert g.m == 3 * 6 * 6 * 5 and g.degrees().max() == 6

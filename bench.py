@@ -1,0 +1,356 @@
+#!/usr/bin/env python3
+"""JP-ADG benchmark: undirected edges coloured per second (ADG + JP) on GB300.
+
+One step = one gc_color_graph call on a graph resident in HBM: every ADG
+round (partition, UPDATE, threshold) and the whole JP colouring, with the
+batch ids and colours written to device buffers.  `value` is m * steps / time
+over the timed region (CUDA events on the launching stream, max over ranks).
+`e2e` is the same metric through gc_color_graph_host with the graph in
+page-locked host memory: the host->device copy of the CSR and the
+device->host copy of the colours are inside every timed step.
+
+Default workload: R-MAT scale 24, edge factor 16, (a,b,c,d) =
+(.57,.19,.19,.05), duplicates and self-loops removed, eps = 1/100, tie-break
+seed 42.  The CSR (2 GB of col_idx) is larger than the 129 MB L2, so no L2
+flush is needed between steps.
+
+--impl reference times the CPU oracle (plain single-threaded C: ADG with
+fresh degree sums, then Greedy in priority order) on a bounded sample of the
+same family.  With --gpus N > 1 each rank colours its own replica (the
+single-graph path has no exchange step here): weak scaling, no collective on
+the data path; a barrier and a max-reduction of the elapsed time bracket the
+timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "undirected edges colored/s (ADG+JP) and HBM GB/s vs peak; graphs/s batched vs per-graph"
+
+WORKLOADS = {
+    "rmat24": dict(kind="rmat", scale=24, ef=16, gen_seed=1, eps=(1, 100), seed=42,
+                   desc="R-MAT scale 24, edge factor 16, (a,b,c,d)=(.57,.19,.19,.05), dedup, "
+                        "no self-loops, eps=1/100, tie-break seed 42"),
+    "rmat20": dict(kind="rmat", scale=20, ef=16, gen_seed=1, eps=(1, 100), seed=42,
+                   desc="R-MAT scale 20, edge factor 16, (a,b,c,d)=(.57,.19,.19,.05), eps=1/100, seed 42"),
+    "grid256": dict(kind="grid3", k=256, perm_seed=7, eps=(1, 100), seed=42,
+                    desc="3D 7-point grid 256^3, seeded vertex permutation, eps=1/100, seed 42"),
+    "er": dict(kind="er", n=16384, m=81920, gen_seed=1, eps=(1, 100), seed=42,
+               desc="Erdos-Renyi G(n=16384, m=81920), eps=1/100, seed 42"),
+}
+
+# JP colouring kernel, algorithmic bytes: per vertex row_ptr pair (16 B), own
+# batch (4 B), list entry (4 B) and colour write (4 B); per directed edge the
+# neighbour id (4 B) and its batch (4 B); per predecessor edge (half of them)
+# its colour (4 B).
+def jp_kernel_bytes(n, nnz):
+    return 28 * n + 8 * nnz + 4 * (nnz // 2)
+
+
+# Whole path (ADG + JP), algorithmic bytes: ADG reads D and writes the
+# survivor list per vertex-round (8 * sum|U|), writes the batch (4n), reads the
+# row offsets of removed vertices (16n), streams col_idx (4 nnz), reads the
+# neighbour's batch (4 nnz) and decrements survivors (4 per decrement); JP as
+# above.
+def path_bytes(n, nnz, sum_u, decrements):
+    adg = 8 * sum_u + 4 * n + 16 * n + 4 * nnz + 4 * nnz + 4 * decrements
+    return adg + jp_kernel_bytes(n, nnz)
+
+
+# DRAM traffic per launch of the JP colouring kernel from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), by workload; None until a
+# capture of the current kernel exists.
+JP_KERNEL_TRAFFIC = {}
+
+
+def load_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def make_graph(w, pinned=False):
+    import graphgen as gg
+    if w["kind"] == "rmat":
+        return gg.rmat(w["scale"], w["ef"], seed=w["gen_seed"], pinned=pinned)
+    if w["kind"] == "grid3":
+        k = w["k"]
+        return gg.grid(k, k, k, perm_seed=w["perm_seed"], pinned=pinned)
+    if w["kind"] == "er":
+        return gg.erdos_renyi(w["n"], w["m"], w["gen_seed"], pinned=pinned)
+    raise ValueError(w["kind"])
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id: str):
+        self.proc = None
+        self.device_id = device_id
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", self.device_id],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sms, maxs, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                maxs.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxs), "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def cpu_baseline(w_name, seconds_target=10.0):
+    """The oracle as it stands, single-threaded, on a bounded sample of the
+    same family (R-MAT scale 22 for the R-MAT workloads)."""
+    import graphgen as gg
+    import oracle
+    w = WORKLOADS[w_name]
+    if w["kind"] == "rmat":
+        sample = dict(w, scale=min(w["scale"], 22))
+        g = make_graph(sample)
+        desc = f"R-MAT scale {sample['scale']} edge factor {w['ef']} (same a,b,c,d), eps=1/100"
+    elif w["kind"] == "grid3":
+        g = gg.grid(128, 128, 128, perm_seed=w["perm_seed"])
+        desc = "3D grid 128^3, seeded permutation, eps=1/100"
+    else:
+        g = make_graph(w)
+        desc = w["desc"]
+    p, q = w["eps"]
+    reps, total = 0, 0.0
+    while total < seconds_target and reps < 50:
+        t0 = time.perf_counter()
+        oracle.jp_adg(g, p, q, w["seed"])
+        total += time.perf_counter() - t0
+        reps += 1
+    return {"value": g.m * reps / total, "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "sample": f"{desc}: n={g.n}, m={g.m}, {reps} run(s) of ADG + Greedy, {total:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import graphgen as gg  # noqa: F401
+    import oracle
+    w = WORKLOADS[args.workload]
+    # each step: the oracle on a bounded sample (R-MAT scale 20 for R-MAT)
+    if w["kind"] == "rmat":
+        sample = dict(w, scale=min(w["scale"], 20))
+        desc = f"R-MAT scale {sample['scale']} edge factor {w['ef']}"
+    elif w["kind"] == "grid3":
+        sample = dict(w, k=min(w["k"], 96))
+        desc = f"3D grid {sample['k']}^3 permuted"
+    else:
+        sample = w
+        desc = w["desc"]
+    g = make_graph(sample)
+    p, q = w["eps"]
+    for _ in range(args.warmup):
+        oracle.jp_adg(g, p, q, w["seed"])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.jp_adg(g, p, q, w["seed"])
+    dt = time.perf_counter() - t0
+    value = g.m * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": w["desc"], "sample": f"{desc}: n={g.n}, m={g.m}"},
+            "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{desc}: n={g.n}, m={g.m}, ADG + Greedy per step"},
+            "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat24")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: --warmup below 3 is outside the timing rules", file=sys.stderr)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2008_11321_gb300 import _build
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    import paper_2008_11321_gb300 as gcp
+
+    w = WORKLOADS[args.workload]
+    p, q = w["eps"]
+    seed = w["seed"]
+    g = make_graph(w, pinned=True)
+    n, nnz, m = g.n, g.nnz, g.m
+    dg = gcp.DeviceGraph(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col_idx).to(dev))
+    color = torch.empty(n, dtype=torch.int32, device=dev)
+    batch = torch.empty(n, dtype=torch.int32, device=dev)
+    ctx = gcp.Context(local)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        nc, nr = ctx.gc_color_graph(dg, p, q, seed, color, batch)
+    ctx.gc_set_timing(True)
+
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        dev_id = uuid if uuid.startswith("GPU-") else f"GPU-{uuid}"
+    except Exception:
+        dev_id = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]
+    sampler = ClockSampler(dev_id)
+    sampler.start()
+    time.sleep(0.3)
+
+    steps = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        nc, nr = ctx.gc_color_graph(dg, p, q, seed, color, batch)
+        st = ctx.gc_get_stats()
+        steps.append((st.ms_adg, st.ms_jp, st.ms_jp_color, st.launches, st.sum_U, st.sum_decrements,
+                      st.jp_spins))
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    value = m * args.steps * world / t_max
+
+    # end to end through the public host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        hcolor = torch.empty(n, dtype=torch.int32, pin_memory=True).numpy()
+        ctx.gc_set_timing(False)
+        ctx.gc_color_graph_host(g.row_ptr, g.col_idx, p, q, seed, hcolor)  # grows buffers once
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.gc_color_graph_host(g.row_ptr, g.col_idx, p, q, seed, hcolor)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        te = torch.tensor([e0.elapsed_time(e1) / 1e3], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        assert (hcolor == color.cpu().numpy()).all(), "host entry point disagrees with device path"
+        e2e = {"value": m * args.steps * world / float(te.item()), "unit": "edges/s",
+               "h2d_bytes_per_step": 8 * (n + 1) + 4 * nnz, "d2h_bytes_per_step": 4 * n}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    ms_adg = statistics.mean(s[0] for s in steps)
+    ms_jp = statistics.mean(s[1] for s in steps)
+    ms_jpk = statistics.mean(s[2] for s in steps)
+    launches = sum(s[3] for s in steps)
+    sum_u, dec = steps[-1][4], steps[-1][5]
+    peak, peak_kind = load_peak()
+    kbytes = jp_kernel_bytes(n, nnz)
+    achieved = kbytes / (ms_jpk / 1e3) / 1e9
+    pbytes = path_bytes(n, nnz, sum_u, dec)
+    path_gbs = pbytes / (t_max / args.steps) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": w["desc"], "n": n, "m": m, "eps": f"{p}/{q}", "seed": seed,
+                   "adg_rounds": nr, "num_colors": nc, "sum_U": sum_u, "decrements": dec,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": f"inputs larger than L2 (col_idx {4 * nnz / 1e9:.2f} GB), no flush"},
+        "roofline": {"bound": "hbm", "kernel": "jp_color_kernel", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": JP_KERNEL_TRAFFIC.get(args.workload),
+                     "algorithmic_bytes_per_launch": kbytes, "ms_per_launch": ms_jpk},
+        "path": {"algorithmic_bytes_per_step": pbytes, "gbs": path_gbs, "frac": path_gbs / peak,
+                 "ms_adg": ms_adg, "ms_jp": ms_jp, "ms_jp_color": ms_jpk},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -86,6 +86,8 @@ typedef struct {
   int64_t jp_spins;        /* polls of uncoloured predecessors (diagnostic)    */
   float ms_adg;            /* device time of the ADG phase (0 if not timed)    */
   float ms_jp;             /* device time of the JP phase (0 if not timed)     */
+  float ms_jp_color;       /* device time of the JP colouring kernel alone     */
+  int32_t launches;        /* kernels this library launched in the last call   */
 } gc_stats;
 
 /* Human-readable name of a status code (static storage). */

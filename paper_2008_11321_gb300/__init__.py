@@ -1,0 +1,12 @@
+"""GB300-native (sm_103a) ADG + JP-ADG graph colouring.
+
+The computation lives in ``libgcolor.so`` (CUDA kernels behind the C ABI of
+include/gcolor.h); ``gcolor`` is its thin ctypes binding.  Importing the
+package does not load the library: the first call does, and fails loudly if
+it is missing.
+"""
+from .gcolor import (Context, DeviceGraph, GcError, GC_ERR_CUDA, GC_ERR_INVALID_ARG,  # noqa: F401
+                     GC_ERR_INVALID_GRAPH, GC_ERR_OOM, GC_ERR_OVERFLOW, GC_ERR_TIMEOUT, GC_OK,
+                     EXPORTS, LIB_PATH, load, status_str)
+
+__all__ = ["Context", "DeviceGraph", "GcError", "load", "status_str", "EXPORTS", "LIB_PATH"]

@@ -1,0 +1,246 @@
+// ADG, Algorithm 1 (Section 3), as three kernels per round:
+//
+//   partition  R = {u in U : D[u] <= T}  (T = floor((q+p)*Sigma / (q*|U|)),
+//              the exact integer form of D[u] <= (1+eps)*Sigma/|U|);
+//              batch[R] = l; U' = U \ R compacted into the other U buffer
+//              (the contiguous [R | U] layout of Section 5.1, kept as a list);
+//              each removed vertex's adjacency is cut into UPDATE tasks of at
+//              most kChunk edges; Sigma_R = sum of D over R is reduced.
+//   update     push-style UPDATE: for every task edge (v, w) with w still in
+//              U' (batch[w] == 0) an atomic decrement of D[w]
+//              (DecrementAndFetch, Section 2.4); the number of decrements is
+//              the cut (R, U').  Edges are spread over the lanes of a warp
+//              across 32 tasks at a time, so short and long rows mix.
+//   finalize   Sigma' = Sigma - Sigma_R - cut (Section 5, "Caching Sums of
+//              Degrees"), |U| = |U'|, next T, l = l + 1.
+//
+// Round 1 reads U = V implicitly (no list) and writes D only for survivors.
+// The host reads |U| after every round to stop; the number of rounds is
+// O(log n) (the round-bound lemma of Section 3) and is single-digit on the
+// power-law workloads, so the read-back is not on the bulk path.
+#include <climits>
+#include <cstring>
+
+#include "gc_internal.cuh"
+
+namespace gc {
+namespace {
+
+constexpr int kAdgThreads = 256;
+
+__device__ __forceinline__ int adg_threshold(unsigned long long sigma, int size_u, unsigned p,
+                                             unsigned q) {
+  if (size_u <= 0) return 0;
+  unsigned __int128 num = static_cast<unsigned __int128>(static_cast<unsigned long long>(q) + p) * sigma;
+  unsigned __int128 den = static_cast<unsigned __int128>(q) * static_cast<unsigned>(size_u);
+  unsigned __int128 t = num / den;
+  return t > static_cast<unsigned __int128>(INT_MAX) ? INT_MAX : static_cast<int>(t);
+}
+
+__global__ void adg_init_kernel(AdgCtl* ctl, long long n, long long nnz, unsigned p, unsigned q) {
+  AdgCtl c{};
+  c.sigma = static_cast<unsigned long long>(nnz);
+  c.size_U = static_cast<int>(n);
+  c.round = 1;
+  c.p = p;
+  c.q = q;
+  c.T = adg_threshold(c.sigma, c.size_U, p, q);
+  *ctl = c;
+}
+
+__global__ void __launch_bounds__(kAdgThreads)
+adg_partition_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row_ptr,
+                     int* __restrict__ D, int* __restrict__ batch, const int* __restrict__ u_in,
+                     int* __restrict__ u_out, long long* __restrict__ task_start,
+                     int* __restrict__ task_len, int first_round_n) {
+  const int round = ctl->round;
+  const int T = ctl->T;
+  const long long size_u = first_round_n > 0 ? first_round_n : ctl->size_U;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+  unsigned long long sum_r = 0;
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  for (long long base = static_cast<long long>(blockIdx.x) * blockDim.x; base < size_u; base += stride) {
+    const long long i = base + threadIdx.x;
+    const bool active = i < size_u;
+    int u = 0, d = 0;
+    long long rs = 0, re = 0;
+    if (active) {
+      if (first_round_n > 0) {
+        u = static_cast<int>(i);
+        rs = row_ptr[u];
+        re = row_ptr[u + 1];
+        d = static_cast<int>(re - rs);
+      } else {
+        u = u_in[i];
+        d = D[u];
+      }
+    }
+    const bool in_r = active && d <= T;
+    const bool keep = active && !in_r;
+    // survivors -> U'
+    const unsigned km = __ballot_sync(kFull, keep);
+    int kbase = 0;
+    if (lane == 0 && km) kbase = atomicAdd(&ctl->size_Unext, __popc(km));
+    kbase = __shfl_sync(kFull, kbase, 0);
+    if (keep) {
+      u_out[kbase + __popc(km & lt)] = u;
+      if (first_round_n > 0) D[u] = d;
+    }
+    // removed -> batch id and UPDATE tasks
+    int nt = 0;
+    if (in_r) {
+      batch[u] = round;
+      sum_r += static_cast<unsigned long long>(d);
+      if (first_round_n == 0) {
+        rs = row_ptr[u];
+        re = row_ptr[u + 1];
+      }
+      nt = static_cast<int>((re - rs + kChunk - 1) / kChunk);
+    }
+    const int incl = warp_inclusive_scan(nt);
+    const int tot = __shfl_sync(kFull, incl, 31);
+    unsigned long long tbase = 0;
+    if (lane == 31 && tot) tbase = atomicAdd(&ctl->ntasks, static_cast<unsigned long long>(tot));
+    tbase = __shfl_sync(kFull, tbase, 31);
+    if (nt) {
+      unsigned long long t = tbase + static_cast<unsigned>(incl - nt);
+      for (int j = 0; j < nt; ++j) {
+        long long st = rs + static_cast<long long>(j) * kChunk;
+        long long len = re - st < kChunk ? re - st : kChunk;
+        task_start[t + j] = st;
+        task_len[t + j] = static_cast<int>(len);
+      }
+    }
+  }
+  sum_r = warp_sum(sum_r);
+  if (lane == 0 && sum_r) atomicAdd(&ctl->sum_R, sum_r);
+}
+
+__global__ void __launch_bounds__(kAdgThreads)
+adg_update_kernel(AdgCtl* __restrict__ ctl, const int* __restrict__ col, int* __restrict__ D,
+                  const int* __restrict__ batch, const long long* __restrict__ task_start,
+                  const int* __restrict__ task_len) {
+  const unsigned long long ntasks = ctl->ntasks;
+  const int lane = threadIdx.x & 31;
+  const unsigned long long gwarp = (static_cast<unsigned long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long nwarps = (static_cast<unsigned long long>(gridDim.x) * blockDim.x) >> 5;
+  unsigned long long cut = 0;
+  for (unsigned long long tile = gwarp; tile * 32 < ntasks; tile += nwarps) {
+    const unsigned long long t = tile * 32 + lane;
+    long long st = 0;
+    int len = 0;
+    if (t < ntasks) {
+      st = task_start[t];
+      len = task_len[t];
+    }
+    const int incl = warp_inclusive_scan(len);
+    const int total = __shfl_sync(kFull, incl, 31);
+    const int excl = incl - len;
+    for (int b = 0; b < total; b += 32) {
+      const int e = b + lane;
+      // owner task: the largest lane j with excl_j <= e
+      int j = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        int c = j + step;
+        int ex = __shfl_sync(kFull, excl, c);
+        if (ex <= e) j = c;
+      }
+      const long long k = __shfl_sync(kFull, st, j) + (e - __shfl_sync(kFull, excl, j));
+      if (e < total) {
+        const int w = col[k];
+        if (batch[w] == 0) {
+          atomicSub(&D[w], 1);
+          ++cut;
+        }
+      }
+    }
+  }
+  cut = warp_sum(cut);
+  if (lane == 0 && cut) atomicAdd(&ctl->cut, cut);
+}
+
+__global__ void adg_finalize_kernel(AdgCtl* ctl) {
+  AdgCtl c = *ctl;
+  c.total_U += static_cast<unsigned long long>(c.size_U);
+  c.total_dec += c.cut;
+  c.sigma = c.sigma - c.sum_R - c.cut;
+  c.size_U = c.size_Unext;
+  c.round += 1;
+  c.T = adg_threshold(c.sigma, c.size_U, c.p, c.q);
+  c.sum_R = 0;
+  c.cut = 0;
+  c.ntasks = 0;
+  c.size_Unext = 0;
+  *ctl = c;
+}
+
+}  // namespace
+
+size_t adg_scratch_bytes(long long n, long long nnz) {
+  const long long ntask = n + nnz / kChunk + 1;
+  return 3 * (static_cast<size_t>(n) * 4 + 256) + static_cast<size_t>(ntask) * 12 + 2048;
+}
+
+gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigned q, int* batch,
+                  int* rounds_out, cudaStream_t s) {
+  const long long n = g->n, nnz = g->nnz;
+  *rounds_out = 0;
+  ctx->stats.adg_rounds = 0;
+  if (n == 0) return GC_OK;
+  AdgCtl* ctl = a.take<AdgCtl>(1);
+  int* D = a.take<int>(n);
+  int* ubuf[2] = {a.take<int>(n), a.take<int>(n)};
+  const long long ntask = n + nnz / kChunk + 1;
+  long long* task_start = a.take<long long>(ntask);
+  int* task_len = a.take<int>(ntask);
+  if (!ctl || !D || !ubuf[0] || !ubuf[1] || !task_start || !task_len) return GC_ERR_OOM;
+
+  GC_TRY_CUDA(cudaMemsetAsync(batch, 0, sizeof(int) * n, s));
+  adg_init_kernel<<<1, 1, 0, s>>>(ctl, n, nnz, p, q);
+  ++g_launches;
+  GC_TRY_CUDA(cudaGetLastError());
+
+  const int max_blocks = ctx->num_sms * 8;
+  long long size_u = n;
+  int cur = 0;
+  int* pinned = static_cast<int*>(ctx->pinned);
+  int round = 0;
+  while (size_u > 0) {
+    ++round;
+    long long want = (size_u + kAdgThreads - 1) / kAdgThreads;
+    int blocks = static_cast<int>(want < max_blocks ? want : max_blocks);
+    adg_partition_kernel<<<blocks, kAdgThreads, 0, s>>>(
+        ctl, row_ptr_of(g), D, batch, round == 1 ? nullptr : ubuf[cur ^ 1], ubuf[cur], task_start,
+        task_len, round == 1 ? static_cast<int>(n) : 0);
+    ++g_launches;
+    GC_TRY_CUDA(cudaGetLastError());
+    adg_update_kernel<<<max_blocks, kAdgThreads, 0, s>>>(ctl, g->col_idx, D, batch, task_start,
+                                                          task_len);
+    ++g_launches;
+    GC_TRY_CUDA(cudaGetLastError());
+    adg_finalize_kernel<<<1, 1, 0, s>>>(ctl);
+    ++g_launches;
+    GC_TRY_CUDA(cudaGetLastError());
+    GC_TRY_CUDA(cudaMemcpyAsync(pinned, &ctl->size_U, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GC_TRY_CUDA(cudaStreamSynchronize(s));
+    long long next = *pinned;
+    if (next >= size_u) return GC_ERR_CUDA;  // cannot happen: every round removes a vertex
+    size_u = next;
+    cur ^= 1;
+  }
+  // statistics
+  unsigned long long tot[2];
+  GC_TRY_CUDA(cudaMemcpyAsync(pinned, &ctl->total_U, 2 * sizeof(unsigned long long),
+                              cudaMemcpyDeviceToHost, s));
+  GC_TRY_CUDA(cudaStreamSynchronize(s));
+  memcpy(tot, pinned, sizeof(tot));
+  ctx->stats.sum_U = static_cast<int64_t>(tot[0]);
+  ctx->stats.sum_decrements = static_cast<int64_t>(tot[1]);
+  ctx->stats.adg_rounds = round;
+  *rounds_out = round;
+  return GC_OK;
+}
+
+}  // namespace gc

@@ -1,0 +1,384 @@
+// C ABI entry points (gcolor.h): context management, argument checks, CSR
+// validation, and the orchestration of the ADG and JP kernels.
+#include <climits>
+#include <cstring>
+#include <new>
+
+#include "gc_internal.cuh"
+
+namespace gc {
+thread_local int g_launches = 0;
+}  // namespace gc
+
+namespace {
+
+constexpr uint32_t kEpsMax = 1u << 20;
+
+// Per-call bookkeeping: resets the launch counter on entry and stores it in
+// the context's statistics on exit.
+struct CallScope {
+  gc_context* ctx;
+  explicit CallScope(gc_context* c) : ctx(c) { gc::g_launches = 0; }
+  ~CallScope() {
+    if (ctx) ctx->stats.launches = gc::g_launches;
+  }
+};
+
+// Make the context's device current for the scope, restore the caller's after.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    ok = prev == dev || cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+gc_status check_graph_args(const gc_csr* g) {
+  if (!g) return GC_ERR_INVALID_ARG;
+  if (g->n < 0 || g->nnz < 0 || g->n > static_cast<int64_t>(INT_MAX) - 1) return GC_ERR_INVALID_ARG;
+  if (g->n > 0 && !row_ptr_of(g)) return GC_ERR_INVALID_ARG;
+  if (g->nnz > 0 && !g->col_idx) return GC_ERR_INVALID_ARG;
+  return GC_OK;
+}
+
+gc_status check_eps(uint32_t p, uint32_t q) {
+  if (q == 0 || q > kEpsMax || p > kEpsMax) return GC_ERR_INVALID_ARG;
+  return GC_OK;
+}
+
+// ---- CSR validation kernels ------------------------------------------------
+
+__global__ void validate_rows_kernel(const long long* __restrict__ row_ptr, long long n, long long nnz,
+                                     int* bad) {
+  for (long long u = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; u <= n;
+       u += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long r = row_ptr[u];
+    if (u == 0 && r != 0) atomicExch(bad, 1);
+    if (u == n && r != nnz) atomicExch(bad, 1);
+    if (u < n) {
+      const long long r1 = row_ptr[u + 1];
+      if (r1 < r || r1 > nnz || r < 0) atomicExch(bad, 1);
+    }
+  }
+}
+
+__device__ bool row_contains(const int* col, long long s, long long e, int key) {
+  while (s < e) {
+    long long mid = s + ((e - s) >> 1);
+    int x = col[mid];
+    if (x == key) return true;
+    if (x < key)
+      s = mid + 1;
+    else
+      e = mid;
+  }
+  return false;
+}
+
+// One warp per row: ids in range, no self-loop, strictly increasing rows,
+// and the reverse edge present.  Runs only after validate_rows_kernel passed.
+__global__ void validate_edges_kernel(const long long* __restrict__ row_ptr, const int* __restrict__ col,
+                                      long long n, int* bad) {
+  const int lane = threadIdx.x & 31;
+  const long long gwarp = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
+  for (long long u = gwarp; u < n; u += nwarps) {
+    const long long s = row_ptr[u], e = row_ptr[u + 1];
+    for (long long k = s + lane; k < e; k += 32) {
+      const int w = col[k];
+      bool ok = w >= 0 && w < n && w != u;
+      if (ok && k + 1 < e) ok = col[k + 1] > w;
+      if (ok) ok = row_contains(col, row_ptr[w], row_ptr[w + 1], static_cast<int>(u));
+      if (!ok) atomicExch(bad, 1);
+    }
+  }
+}
+
+gc_status timing_begin(gc_context* ctx, int idx, cudaStream_t s) {
+  if (!ctx->timing) return GC_OK;
+  GC_TRY_CUDA(cudaEventRecord(ctx->ev[idx], s));
+  return GC_OK;
+}
+
+float timing_ms(gc_context* ctx, int a, int b) {
+  float ms = 0.f;
+  if (!ctx->timing) return 0.f;
+  if (cudaEventElapsedTime(&ms, ctx->ev[a], ctx->ev[b]) != cudaSuccess) return 0.f;
+  return ms;
+}
+
+// Shared body of gc_color_graph and gc_color_graph_host.
+gc_status color_graph_device(gc_context* ctx, const gc_csr* g, uint32_t p, uint32_t q, uint64_t seed,
+                             int32_t* color, int32_t* batch, int32_t* ncol, int32_t* nrounds,
+                             cudaStream_t s) {
+  const long long n = g->n;
+  const size_t batch_bytes = batch ? 0 : (static_cast<size_t>(n) * 4 + 256);
+  const size_t adg = gc::adg_scratch_bytes(n, g->nnz);
+  const size_t jp = gc::jp_scratch_bytes(n);
+  GC_TRY(ctx->reserve(batch_bytes + (adg > jp ? adg : jp)));
+  gc::Arena a = ctx->arena();
+  int* b = batch ? batch : a.take<int>(n > 0 ? n : 1);
+  if (!b) return GC_ERR_OOM;
+  int rounds = 0, colors = 0;
+  GC_TRY(timing_begin(ctx, 0, s));
+  GC_TRY(gc::adg_run(ctx, a, g, p, q, b, &rounds, s));
+  GC_TRY(timing_begin(ctx, 1, s));
+  GC_TRY(gc::jp_run_fused(ctx, a, g, b, seed, color, &colors, s));
+  GC_TRY(timing_begin(ctx, 2, s));
+  if (ctx->timing) {
+    GC_TRY_CUDA(cudaEventSynchronize(ctx->ev[2]));
+    ctx->stats.ms_adg = timing_ms(ctx, 0, 1);
+    ctx->stats.ms_jp = timing_ms(ctx, 1, 2);
+  }
+  if (ncol) *ncol = colors;
+  if (nrounds) *nrounds = rounds;
+  return GC_OK;
+}
+
+}  // namespace
+
+gc_status gc_context::reserve(size_t bytes) {
+  if (bytes <= scratch_bytes) return GC_OK;
+  if (scratch) {
+    cudaFree(scratch);
+    scratch = nullptr;
+    scratch_bytes = 0;
+  }
+  size_t want = bytes + bytes / 8;
+  cudaError_t e = cudaMalloc(&scratch, want);
+  if (e != cudaSuccess) {
+    scratch = nullptr;
+    cudaGetLastError();
+    return GC_ERR_OOM;
+  }
+  scratch_bytes = want;
+  return GC_OK;
+}
+
+extern "C" {
+
+const char* gc_status_str(gc_status s) {
+  switch (s) {
+    case GC_OK: return "GC_OK";
+    case GC_ERR_INVALID_ARG: return "GC_ERR_INVALID_ARG";
+    case GC_ERR_INVALID_GRAPH: return "GC_ERR_INVALID_GRAPH";
+    case GC_ERR_OOM: return "GC_ERR_OOM";
+    case GC_ERR_CUDA: return "GC_ERR_CUDA";
+    case GC_ERR_TIMEOUT: return "GC_ERR_TIMEOUT";
+    case GC_ERR_OVERFLOW: return "GC_ERR_OVERFLOW";
+  }
+  return "GC_ERR_UNKNOWN";
+}
+
+gc_status gc_create(gc_context** out, int device) {
+  if (!out) return GC_ERR_INVALID_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess) {
+    cudaGetLastError();
+    return GC_ERR_CUDA;
+  }
+  if (device < 0 || device >= count) return GC_ERR_INVALID_ARG;
+  DeviceGuard guard(device);
+  if (!guard.ok) return GC_ERR_CUDA;
+  gc_context* ctx = new (std::nothrow) gc_context();
+  if (!ctx) return GC_ERR_OOM;
+  ctx->device = device;
+  if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess) {
+    delete ctx;
+    return GC_ERR_CUDA;
+  }
+  if (cudaMallocHost(&ctx->pinned, 256) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return GC_ERR_OOM;
+  }
+  for (auto& ev : ctx->ev) {
+    if (cudaEventCreate(&ev) != cudaSuccess) {
+      gc_destroy(ctx);
+      return GC_ERR_CUDA;
+    }
+  }
+  *out = ctx;
+  return GC_OK;
+}
+
+void gc_destroy(gc_context* ctx) {
+  if (!ctx) return;
+  DeviceGuard guard(ctx->device);
+  if (ctx->scratch) cudaFree(ctx->scratch);
+  if (ctx->h_graph) cudaFree(ctx->h_graph);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  for (auto& ev : ctx->ev)
+    if (ev) cudaEventDestroy(ev);
+  delete ctx;
+}
+
+gc_status gc_get_stats(const gc_context* ctx, gc_stats* out) {
+  if (!ctx || !out) return GC_ERR_INVALID_ARG;
+  *out = ctx->stats;
+  return GC_OK;
+}
+
+gc_status gc_set_timing(gc_context* ctx, int enable) {
+  if (!ctx) return GC_ERR_INVALID_ARG;
+  ctx->timing = enable != 0;
+  return GC_OK;
+}
+
+gc_status gc_validate_csr(gc_context* ctx, const gc_csr* g, gc_stream stream) {
+  if (!ctx) return GC_ERR_INVALID_ARG;
+  GC_TRY(check_graph_args(g));
+  DeviceGuard guard(ctx->device);
+  CallScope scope(ctx);
+  if (!guard.ok) return GC_ERR_CUDA;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (g->n == 0) return g->nnz == 0 ? GC_OK : GC_ERR_INVALID_GRAPH;
+  GC_TRY(ctx->reserve(256));
+  int* bad = static_cast<int*>(ctx->scratch);
+  int* pin = static_cast<int*>(ctx->pinned);
+  GC_TRY_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  validate_rows_kernel<<<ctx->num_sms * 8, 256, 0, s>>>(row_ptr_of(g), g->n, g->nnz, bad);
+  ++gc::g_launches;
+  GC_TRY_CUDA(cudaGetLastError());
+  GC_TRY_CUDA(cudaMemcpyAsync(pin, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GC_TRY_CUDA(cudaStreamSynchronize(s));
+  if (*pin) return GC_ERR_INVALID_GRAPH;
+  if (g->nnz == 0) return GC_OK;
+  validate_edges_kernel<<<ctx->num_sms * 8, 256, 0, s>>>(row_ptr_of(g), g->col_idx, g->n, bad);
+  ++gc::g_launches;
+  GC_TRY_CUDA(cudaGetLastError());
+  GC_TRY_CUDA(cudaMemcpyAsync(pin, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GC_TRY_CUDA(cudaStreamSynchronize(s));
+  return *pin ? GC_ERR_INVALID_GRAPH : GC_OK;
+}
+
+gc_status gc_adg_partition(gc_context* ctx, const gc_csr* g, uint32_t eps_p, uint32_t eps_q,
+                           int32_t* batch_out, int32_t* num_rounds_out, gc_stream stream) {
+  if (!ctx || !num_rounds_out) return GC_ERR_INVALID_ARG;
+  GC_TRY(check_graph_args(g));
+  GC_TRY(check_eps(eps_p, eps_q));
+  if (g->n > 0 && !batch_out) return GC_ERR_INVALID_ARG;
+  DeviceGuard guard(ctx->device);
+  CallScope scope(ctx);
+  if (!guard.ok) return GC_ERR_CUDA;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  GC_TRY(ctx->reserve(gc::adg_scratch_bytes(g->n, g->nnz)));
+  int rounds = 0;
+  GC_TRY(timing_begin(ctx, 0, s));
+  GC_TRY(gc::adg_run(ctx, ctx->arena(), g, eps_p, eps_q, batch_out, &rounds, s));
+  GC_TRY(timing_begin(ctx, 1, s));
+  if (ctx->timing) {
+    GC_TRY_CUDA(cudaEventSynchronize(ctx->ev[1]));
+    ctx->stats.ms_adg = timing_ms(ctx, 0, 1);
+  }
+  *num_rounds_out = rounds;
+  return GC_OK;
+}
+
+gc_status gc_make_priority(gc_context* ctx, int64_t n, const int32_t* batch, uint64_t seed,
+                           uint64_t* key_out, gc_stream stream) {
+  if (!ctx || n < 0 || n > static_cast<int64_t>(INT_MAX) - 1) return GC_ERR_INVALID_ARG;
+  if (n > 0 && (!batch || !key_out)) return GC_ERR_INVALID_ARG;
+  DeviceGuard guard(ctx->device);
+  CallScope scope(ctx);
+  if (!guard.ok) return GC_ERR_CUDA;
+  GC_TRY_CUDA(gc::make_priority(batch, n, seed, reinterpret_cast<unsigned long long*>(key_out),
+                                ctx->num_sms, reinterpret_cast<cudaStream_t>(stream)));
+  return GC_OK;
+}
+
+gc_status gc_jp_color(gc_context* ctx, const gc_csr* g, const uint64_t* priority, int32_t* color_out,
+                      int32_t* num_colors_out, gc_stream stream) {
+  if (!ctx) return GC_ERR_INVALID_ARG;
+  GC_TRY(check_graph_args(g));
+  if (g->n > 0 && (!priority || !color_out)) return GC_ERR_INVALID_ARG;
+  DeviceGuard guard(ctx->device);
+  CallScope scope(ctx);
+  if (!guard.ok) return GC_ERR_CUDA;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  GC_TRY(ctx->reserve(gc::jp_scratch_bytes(g->n)));
+  int colors = 0;
+  GC_TRY(timing_begin(ctx, 1, s));
+  GC_TRY(gc::jp_run_given(ctx, ctx->arena(), g, reinterpret_cast<const unsigned long long*>(priority),
+                          color_out, &colors, s));
+  GC_TRY(timing_begin(ctx, 2, s));
+  if (ctx->timing) {
+    GC_TRY_CUDA(cudaEventSynchronize(ctx->ev[2]));
+    ctx->stats.ms_jp = timing_ms(ctx, 1, 2);
+  }
+  if (num_colors_out) *num_colors_out = colors;
+  return GC_OK;
+}
+
+gc_status gc_color_graph(gc_context* ctx, const gc_csr* g, uint32_t eps_p, uint32_t eps_q,
+                         uint64_t seed, int32_t* color_out, int32_t* batch_out,
+                         int32_t* num_colors_out, int32_t* num_rounds_out, gc_stream stream) {
+  if (!ctx) return GC_ERR_INVALID_ARG;
+  GC_TRY(check_graph_args(g));
+  GC_TRY(check_eps(eps_p, eps_q));
+  if (g->n > 0 && !color_out) return GC_ERR_INVALID_ARG;
+  DeviceGuard guard(ctx->device);
+  CallScope scope(ctx);
+  if (!guard.ok) return GC_ERR_CUDA;
+  return color_graph_device(ctx, g, eps_p, eps_q, seed, color_out, batch_out, num_colors_out,
+                            num_rounds_out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+gc_status gc_color_graph_host(gc_context* ctx, int64_t n, int64_t nnz, const int64_t* row_ptr,
+                              const int32_t* col_idx, uint32_t eps_p, uint32_t eps_q, uint64_t seed,
+                              int32_t* color_out, int32_t* batch_out, int32_t* num_colors_out,
+                              int32_t* num_rounds_out, gc_stream stream) {
+  if (!ctx || n < 0 || nnz < 0 || n > static_cast<int64_t>(INT_MAX) - 1) return GC_ERR_INVALID_ARG;
+  if (!row_ptr || (nnz > 0 && !col_idx) || (n > 0 && !color_out)) return GC_ERR_INVALID_ARG;
+  GC_TRY(check_eps(eps_p, eps_q));
+  DeviceGuard guard(ctx->device);
+  CallScope scope(ctx);
+  if (!guard.ok) return GC_ERR_CUDA;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // context-owned device copies: row_ptr | col_idx | color | batch
+  const size_t b_rp = (static_cast<size_t>(n + 1) * 8 + 255) & ~size_t(255);
+  const size_t b_ci = (static_cast<size_t>(nnz) * 4 + 255) & ~size_t(255);
+  const size_t b_v = (static_cast<size_t>(n) * 4 + 255) & ~size_t(255);
+  const size_t need = b_rp + b_ci + 2 * b_v + 256;
+  if (need > ctx->h_graph_bytes) {
+    if (ctx->h_graph) cudaFree(ctx->h_graph);
+    ctx->h_graph = nullptr;
+    ctx->h_graph_bytes = 0;
+    if (cudaMalloc(&ctx->h_graph, need) != cudaSuccess) {
+      cudaGetLastError();
+      return GC_ERR_OOM;
+    }
+    ctx->h_graph_bytes = need;
+  }
+  char* base = static_cast<char*>(ctx->h_graph);
+  gc_csr g;
+  g.n = n;
+  g.nnz = nnz;
+  g.row_ptr = reinterpret_cast<const int64_t*>(base);
+  g.col_idx = reinterpret_cast<const int32_t*>(base + b_rp);
+  int32_t* d_color = reinterpret_cast<int32_t*>(base + b_rp + b_ci);
+  int32_t* d_batch = reinterpret_cast<int32_t*>(base + b_rp + b_ci + b_v);
+  GC_TRY_CUDA(cudaMemcpyAsync(const_cast<int64_t*>(g.row_ptr), row_ptr, static_cast<size_t>(n + 1) * 8,
+                              cudaMemcpyHostToDevice, s));
+  if (nnz > 0)
+    GC_TRY_CUDA(cudaMemcpyAsync(const_cast<int32_t*>(g.col_idx), col_idx, static_cast<size_t>(nnz) * 4,
+                                cudaMemcpyHostToDevice, s));
+  GC_TRY(color_graph_device(ctx, &g, eps_p, eps_q, seed, d_color, d_batch, num_colors_out,
+                            num_rounds_out, s));
+  if (n > 0) {
+    GC_TRY_CUDA(cudaMemcpyAsync(color_out, d_color, static_cast<size_t>(n) * 4, cudaMemcpyDeviceToHost, s));
+    if (batch_out)
+      GC_TRY_CUDA(cudaMemcpyAsync(batch_out, d_batch, static_cast<size_t>(n) * 4, cudaMemcpyDeviceToHost, s));
+  }
+  GC_TRY_CUDA(cudaStreamSynchronize(s));
+  return GC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,239 @@
+// Internal declarations of the GB300 colouring library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "gcolor.h"
+
+namespace gc {
+
+constexpr int kWarp = 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Edges per UPDATE task: a removed vertex of degree d becomes ceil(d / kChunk)
+// tasks, so one hub cannot hold a warp for long.
+constexpr int kChunk = 1024;
+// Vertices of degree <= kSmallDeg are coloured one per lane, larger ones one
+// per warp (at most kSmallDeg predecessors -> the colour fits a 64-bit mask).
+constexpr int kSmallDeg = 32;
+// Colour window of the warp path: a 1024-bit shared-memory bitmap per warp.
+constexpr int kColorWin = 1024;
+// Pending (still uncoloured) predecessors a lane of the warp path remembers.
+constexpr int kPendCap = 16;
+
+// Device-side error codes (written to a control block, mapped to gc_status).
+enum DevErr : int { kDevOk = 0, kDevTimeout = 1, kDevOverflow = 2 };
+
+// How long any device-side wait may spin before it gives up (nanoseconds of
+// %globaltimer).
+constexpr unsigned long long kWaitLimitNs = 4000000000ull;
+
+// Control block of one ADG run (device memory, in the context's scratch).
+struct AdgCtl {
+  unsigned long long sigma;      // sum of D over U in the current round
+  unsigned long long sum_R;      // this round: sum of D over R
+  unsigned long long cut;        // this round: decrements (edges R -> U\R)
+  unsigned long long ntasks;     // this round: UPDATE tasks appended
+  unsigned long long total_U;    // sum over rounds of |U|
+  unsigned long long total_dec;  // sum over rounds of the cut
+  int size_U;                    // |U| of the current round
+  int size_Unext;                // this round: survivors appended
+  int T;                         // threshold of the current round (clamped)
+  int round;                     // l (1-based) of the current round
+  unsigned p, q;                 // eps = p / q
+  int err;
+  int pad;
+};
+
+// Control block of one JP run.
+struct JpCtl {
+  unsigned long long big_cursor;
+  unsigned long long small_cursor;
+  unsigned long long key_or;     // OR over the sort keys (constant digits)
+  unsigned long long key_and;    // AND over the sort keys
+  unsigned long long spins;      // polls that found an uncoloured predecessor
+  unsigned long long nbig;       // vertices in the warp path list
+  int max_color;
+  int err;
+};
+
+// Bump allocator over the context's scratch arena (256-byte aligned slices).
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t count) {
+    size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+    if (off + bytes > cap) return nullptr;
+    T* p = reinterpret_cast<T*>(base + off);
+    off += bytes;
+    return p;
+  }
+};
+
+// Device-wide exclusive scan helpers (gc_scan.cu).  `temp` needs
+// scan_temp_elems(count) elements.
+size_t scan_temp_elems(long long count);
+cudaError_t exclusive_scan_i64(const long long* in, long long* out, long long count,
+                               long long* temp, cudaStream_t s);
+
+// Stable LSD radix sort of (key, value) pairs, ascending by key (gc_sort.cu).
+// Only the 8-bit digits set in `digit_mask` are sorted (bit i = digit i).
+// Returns the buffer index (0 or 1) that holds the result.
+struct SortBufs {
+  unsigned long long* keys[2];
+  int* vals[2];
+  long long* hist;   // 256 * ntiles
+  long long* temp;   // scan temp
+};
+size_t sort_hist_elems(long long n);
+int radix_sort_pairs(SortBufs& b, long long n, unsigned digit_mask, cudaStream_t s,
+                     cudaError_t* err);
+
+// ADG rounds on the device (gc_adg.cu).  Scratch sized by adg_scratch_bytes.
+size_t adg_scratch_bytes(long long n, long long nnz);
+gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigned q, int* batch,
+                  int* rounds_out, cudaStream_t s);
+
+// JP colouring by predecessor polling (gc_jp.cu).
+size_t jp_scratch_bytes(long long n);
+gc_status jp_run_fused(gc_context* ctx, Arena a, const gc_csr* g, const int* batch,
+                       unsigned long long seed, int* color, int* num_colors_out, cudaStream_t s);
+gc_status jp_run_given(gc_context* ctx, Arena a, const gc_csr* g, const unsigned long long* prio,
+                       int* color, int* num_colors_out, cudaStream_t s);
+cudaError_t make_priority(const int* batch, long long n, unsigned long long seed,
+                          unsigned long long* key, int num_sms, cudaStream_t s);
+
+}  // namespace gc
+
+// The opaque context.
+struct gc_context {
+  int device = 0;
+  int num_sms = 0;
+  int coop = 0;
+  int timing = 0;
+  // scratch arena (device)
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  // small page-locked host buffer for scalar read-back
+  void* pinned = nullptr;
+  // buffers owned for gc_color_graph_host
+  void* h_graph = nullptr;
+  size_t h_graph_bytes = 0;
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  gc_stats stats{};
+
+  gc_status reserve(size_t bytes);
+  gc::Arena arena() const {
+    gc::Arena a;
+    a.base = static_cast<char*>(scratch);
+    a.cap = scratch_bytes;
+    return a;
+  }
+};
+
+// int64_t is `long` on LP64 Linux while the kernels use `long long`.
+inline const long long* row_ptr_of(const gc_csr* g) {
+  return reinterpret_cast<const long long*>(g->row_ptr);
+}
+
+namespace gc {
+// Kernels launched by the current entry-point call on this host thread.
+extern thread_local int g_launches;
+}  // namespace gc
+
+// Map a CUDA error to a status (and leave no sticky state behind).
+inline gc_status gc_cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return GC_OK;
+  if (e == cudaErrorMemoryAllocation) return GC_ERR_OOM;
+  return GC_ERR_CUDA;
+}
+
+#define GC_TRY_CUDA(expr)                              \
+  do {                                                 \
+    cudaError_t e_ = (expr);                           \
+    if (e_ != cudaSuccess) return gc_cuda_status(e_);  \
+  } while (0)
+
+#define GC_TRY(expr)                 \
+  do {                               \
+    gc_status s_ = (expr);           \
+    if (s_ != GC_OK) return s_;      \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Device helpers shared by the kernels of this library.
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+namespace gc {
+
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_relaxed(int* p, int v) {
+  asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    T u = __shfl_xor_sync(kFull, v, o);
+    v = u > v ? u : v;
+  }
+  return v;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_inclusive_scan(T v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T u = __shfl_up_sync(kFull, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
+}
+
+// Random tie-break rho_R of the JP-ADG priority (Section 4.1): the upper 32
+// bits of the (v+1)-th output of SplitMix64 (Steele, Lea & Flood, OOPSLA
+// 2014) started from state `seed`.  The state advances by the golden-ratio
+// increment 0x9e3779b97f4a7c15 and each output is mixed by the finaliser
+// z ^= z>>30; z *= 0xbf58476d1ce4e5b9; z ^= z>>27; z *= 0x94d049bb133111eb;
+// z ^= z>>31.
+__device__ __forceinline__ unsigned tie_hash(unsigned long long seed, unsigned v) {
+  unsigned long long z = seed + (static_cast<unsigned long long>(v) + 1ull) * 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  z ^= z >> 31;
+  return static_cast<unsigned>(z >> 32);
+}
+
+}  // namespace gc
+#endif

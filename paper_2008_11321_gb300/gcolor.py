@@ -1,0 +1,223 @@
+"""Python binding of the C ABI in include/gcolor.h (argument marshalling only).
+
+Every function here forwards to the same-named entry point of libgcolor.so
+through ctypes.  Device buffers are PyTorch CUDA tensors (their data
+pointers are passed; PyTorch is used for device memory and streams only) and
+the stream defaults to the caller's current PyTorch stream.  All computation
+happens in the library's CUDA kernels; there is no fallback: if the library
+cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgcolor.so")
+
+GC_OK, GC_ERR_INVALID_ARG, GC_ERR_INVALID_GRAPH, GC_ERR_OOM = 0, 1, 2, 3
+GC_ERR_CUDA, GC_ERR_TIMEOUT, GC_ERR_OVERFLOW = 4, 5, 6
+
+# Every symbol declared in include/gcolor.h.
+EXPORTS = ("gc_status_str", "gc_create", "gc_destroy", "gc_get_stats", "gc_set_timing",
+           "gc_validate_csr", "gc_adg_partition", "gc_make_priority", "gc_jp_color",
+           "gc_color_graph", "gc_color_graph_host")
+
+
+class GcError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_str(status)}")
+
+
+class gc_csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p)]
+
+
+class gc_stats(ctypes.Structure):
+    _fields_ = [("adg_rounds", ctypes.c_int32), ("num_colors", ctypes.c_int32),
+                ("sum_U", ctypes.c_int64), ("sum_decrements", ctypes.c_int64),
+                ("jp_spins", ctypes.c_int64), ("ms_adg", ctypes.c_float), ("ms_jp", ctypes.c_float),
+                ("ms_jp_color", ctypes.c_float), ("launches", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libgcolor.so (build it first with __graft_entry__.build() or
+    paper_2008_11321_gb300._build.build()).  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libgcolor.so not built at {path}; run paper_2008_11321_gb300._build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, u32, u64 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                              ctypes.c_uint64)
+    P = ctypes.POINTER
+    lib.gc_status_str.restype = ctypes.c_char_p
+    lib.gc_status_str.argtypes = [ctypes.c_int]
+    lib.gc_create.restype = ctypes.c_int
+    lib.gc_create.argtypes = [P(vp), ctypes.c_int]
+    lib.gc_destroy.restype = None
+    lib.gc_destroy.argtypes = [vp]
+    lib.gc_get_stats.restype = ctypes.c_int
+    lib.gc_get_stats.argtypes = [vp, P(gc_stats)]
+    lib.gc_set_timing.restype = ctypes.c_int
+    lib.gc_set_timing.argtypes = [vp, ctypes.c_int]
+    lib.gc_validate_csr.restype = ctypes.c_int
+    lib.gc_validate_csr.argtypes = [vp, P(gc_csr), vp]
+    lib.gc_adg_partition.restype = ctypes.c_int
+    lib.gc_adg_partition.argtypes = [vp, P(gc_csr), u32, u32, vp, P(i32), vp]
+    lib.gc_make_priority.restype = ctypes.c_int
+    lib.gc_make_priority.argtypes = [vp, i64, vp, u64, vp, vp]
+    lib.gc_jp_color.restype = ctypes.c_int
+    lib.gc_jp_color.argtypes = [vp, P(gc_csr), vp, vp, P(i32), vp]
+    lib.gc_color_graph.restype = ctypes.c_int
+    lib.gc_color_graph.argtypes = [vp, P(gc_csr), u32, u32, u64, vp, vp, P(i32), P(i32), vp]
+    lib.gc_color_graph_host.restype = ctypes.c_int
+    lib.gc_color_graph_host.argtypes = [vp, i64, i64, vp, vp, u32, u32, u64, vp, vp, P(i32), P(i32), vp]
+    _lib = lib
+    return lib
+
+
+def status_str(status: int) -> str:
+    return load().gc_status_str(status).decode()
+
+
+def _check(status: int, what: str):
+    if status != GC_OK:
+        raise GcError(status, what)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+@dataclass
+class DeviceGraph:
+    """A CSR graph held in CUDA tensors (int64 row_ptr[n+1], int32 col_idx)."""
+    row_ptr: "object"
+    col_idx: "object"
+
+    @property
+    def n(self) -> int:
+        return int(self.row_ptr.shape[0]) - 1
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col_idx.shape[0])
+
+    def csr(self) -> gc_csr:
+        return gc_csr(self.n, self.nnz, self.row_ptr.data_ptr(),
+                      self.col_idx.data_ptr() if self.nnz else None)
+
+    @classmethod
+    def from_host(cls, g, device="cuda"):
+        import torch
+        rp = torch.from_numpy(np.ascontiguousarray(g.row_ptr, dtype=np.int64)).to(device)
+        ci = torch.from_numpy(np.ascontiguousarray(g.col_idx, dtype=np.int32)).to(device)
+        return cls(rp, ci)
+
+
+class Context:
+    """Owns a gc_context (scratch memory on one device)."""
+
+    def __init__(self, device: int = 0):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        _check(self._lib.gc_create(ctypes.byref(h), device), "gc_create")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            self._lib.gc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- the C ABI, one method per entry point ------------------------------
+    def gc_set_timing(self, enable: bool):
+        _check(self._lib.gc_set_timing(self.handle, int(enable)), "gc_set_timing")
+
+    def gc_get_stats(self) -> gc_stats:
+        st = gc_stats()
+        _check(self._lib.gc_get_stats(self.handle, ctypes.byref(st)), "gc_get_stats")
+        return st
+
+    def gc_validate_csr(self, g: DeviceGraph, stream=None) -> int:
+        """Returns GC_OK or GC_ERR_INVALID_GRAPH (other errors raise)."""
+        c = g.csr()
+        st = self._lib.gc_validate_csr(self.handle, ctypes.byref(c), _stream(stream))
+        if st not in (GC_OK, GC_ERR_INVALID_GRAPH):
+            _check(st, "gc_validate_csr")
+        return st
+
+    def gc_adg_partition(self, g: DeviceGraph, eps_p: int, eps_q: int, batch_out, stream=None) -> int:
+        c = g.csr()
+        rounds = ctypes.c_int32(0)
+        _check(self._lib.gc_adg_partition(self.handle, ctypes.byref(c), eps_p, eps_q, _ptr(batch_out),
+                                          ctypes.byref(rounds), _stream(stream)), "gc_adg_partition")
+        return rounds.value
+
+    def gc_make_priority(self, n: int, batch, seed: int, key_out, stream=None):
+        _check(self._lib.gc_make_priority(self.handle, n, _ptr(batch), seed, _ptr(key_out),
+                                          _stream(stream)), "gc_make_priority")
+
+    def gc_jp_color(self, g: DeviceGraph, priority, color_out, stream=None) -> int:
+        c = g.csr()
+        nc = ctypes.c_int32(0)
+        _check(self._lib.gc_jp_color(self.handle, ctypes.byref(c), _ptr(priority), _ptr(color_out),
+                                     ctypes.byref(nc), _stream(stream)), "gc_jp_color")
+        return nc.value
+
+    def gc_color_graph(self, g: DeviceGraph, eps_p: int, eps_q: int, seed: int, color_out,
+                       batch_out=None, stream=None):
+        """Returns (num_colors, num_rounds)."""
+        c = g.csr()
+        nc, nr = ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(self._lib.gc_color_graph(self.handle, ctypes.byref(c), eps_p, eps_q, seed,
+                                        _ptr(color_out), _ptr(batch_out), ctypes.byref(nc),
+                                        ctypes.byref(nr), _stream(stream)), "gc_color_graph")
+        return nc.value, nr.value
+
+    def gc_color_graph_host(self, row_ptr: np.ndarray, col_idx: np.ndarray, eps_p: int, eps_q: int,
+                            seed: int, color_out: np.ndarray, batch_out: np.ndarray | None = None,
+                            stream=None):
+        """Host arrays in and out (numpy, ideally in page-locked memory).
+        Returns (num_colors, num_rounds)."""
+        n = row_ptr.shape[0] - 1
+        nnz = col_idx.shape[0]
+        assert row_ptr.dtype == np.int64 and col_idx.dtype == np.int32 and color_out.dtype == np.int32
+        nc, nr = ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(self._lib.gc_color_graph_host(
+            self.handle, n, nnz, row_ptr.ctypes.data, col_idx.ctypes.data if nnz else None,
+            eps_p, eps_q, seed, color_out.ctypes.data if n else None,
+            batch_out.ctypes.data if batch_out is not None and n else None,
+            ctypes.byref(nc), ctypes.byref(nr), _stream(stream)), "gc_color_graph_host")
+        return nc.value, nr.value

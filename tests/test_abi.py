@@ -1,0 +1,59 @@
+"""The C-ABI library builds, loads and exports every symbol that
+include/gcolor.h declares (no GPU needed: only calls that make no CUDA
+compute call are exercised)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2008_11321_gb300 as gcp
+from paper_2008_11321_gb300 import _build
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "gcolor.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(gc_\w+)\s*\(", text, re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return gcp.load()
+
+
+def test_header_declares_expected_calls():
+    assert set(_declared()) == set(gcp.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+        assert isinstance(getattr(lib, name), ctypes._CFuncPtr)
+
+
+def test_status_strings(lib):
+    assert gcp.status_str(gcp.GC_OK) == "GC_OK"
+    assert gcp.status_str(gcp.GC_ERR_TIMEOUT) == "GC_ERR_TIMEOUT"
+    assert gcp.status_str(99) == "GC_ERR_UNKNOWN"
+
+
+def test_null_arguments_rejected_without_device_work(lib):
+    rounds = ctypes.c_int32(0)
+    csr = gcp.gcolor.gc_csr(10, 0, None, None)
+    assert lib.gc_adg_partition(None, ctypes.byref(csr), 1, 100, None, ctypes.byref(rounds), None) == \
+        gcp.GC_ERR_INVALID_ARG
+    assert lib.gc_color_graph(None, None, 1, 100, 42, None, None, None, None, None) == gcp.GC_ERR_INVALID_ARG
+    assert lib.gc_create(None, 0) == gcp.GC_ERR_INVALID_ARG
+    st = gcp.gcolor.gc_stats()
+    assert lib.gc_get_stats(None, ctypes.byref(st)) == gcp.GC_ERR_INVALID_ARG
+    lib.gc_destroy(None)  # a no-op
+
+
+def test_library_links_cuda_sm103a_only(lib):
+    # the build compiles for exactly one real architecture
+    assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]

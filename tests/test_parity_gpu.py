@@ -1,0 +1,249 @@
+"""CUDA path vs the CPU oracle, bit for bit, through the C ABI.
+
+Batch ids, round counts, colours and colour counts are integers, so the bar
+is exact equality.  Graphs span several thread blocks and ragged tails,
+vertices above the lane/warp split (degree 32), UPDATE tasks split at 1024
+edges, colours above the 1024-colour window, and the degenerate cases of the
+method (no vertices, no edges, isolated vertices, cliques, stars, paths).
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from _fixtures import (case_graph, complete, complete_bipartite, cycle, empty, ints, path, petersen,
+                       random_small, read_cases, star)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2008_11321_gb300 as gcp  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2008_11321_gb300 import _build
+    _build.build()
+    c = gcp.Context(0)
+    yield c
+    c.close()
+
+
+def dev(g):
+    return gcp.DeviceGraph.from_host(g, "cuda:0")
+
+
+def color_graph(ctx, g, p, q, seed):
+    dg = dev(g)
+    color = torch.full((g.n,), -7, dtype=torch.int32, device="cuda:0")
+    batch = torch.full((g.n,), -7, dtype=torch.int32, device="cuda:0")
+    nc, nr = ctx.gc_color_graph(dg, p, q, seed, color, batch)
+    torch.cuda.synchronize()
+    return batch.cpu().numpy(), color.cpu().numpy(), nr, nc
+
+
+def assert_same_as_oracle(ctx, g, p=1, q=100, seed=42):
+    b, c, nr, nc = color_graph(ctx, g, p, q, seed)
+    ob, oc, onr, onc = oracle.jp_adg(g, p, q, seed)
+    assert nr == onr, (g.name, nr, onr)
+    assert np.array_equal(b, ob), g.name
+    assert nc == onc, (g.name, nc, onc)
+    assert np.array_equal(c, oc), g.name
+    return b, c
+
+
+SMALL = [empty(1), empty(100), complete(2), complete(5), complete(33), complete(40), star(3),
+         star(31), star(32), star(33), star(5000), path(7), path(100), path(101), cycle(1000),
+         complete_bipartite(7, 50), complete_bipartite(40, 41), petersen(),
+         random_small(60, 0.3, 1), random_small(200, 0.05, 2)]
+
+
+@pytest.mark.parametrize("g", SMALL, ids=lambda g: g.name)
+def test_small_families(ctx, g):
+    assert_same_as_oracle(ctx, g)
+
+
+@pytest.mark.parametrize("case", read_cases("jp_adg_small.txt") + read_cases("lollipop_adg.txt"),
+                         ids=lambda c: c.get("name", "lollipop"))
+def test_golden_fixtures(ctx, case):
+    g = case_graph(case)
+    b, c = assert_same_as_oracle(ctx, g)
+    assert np.array_equal(b, ints(case["batch"]))
+    if "color" in case:
+        assert np.array_equal(c, ints(case["color"]))
+
+
+def test_zero_vertices(ctx):
+    g = empty(0)
+    dg = dev(g)
+    color = torch.empty(0, dtype=torch.int32, device="cuda:0")
+    assert ctx.gc_color_graph(dg, 1, 100, 42, color) == (0, 0)
+
+
+def test_clique_beyond_colour_window(ctx):
+    # K_1100: colours 1..1100 exceed one 1024-colour window of the warp path
+    g = complete(1100)
+    b, c = assert_same_as_oracle(ctx, g)
+    assert sorted(c.tolist()) == list(range(1, 1101))
+
+
+def test_er_config(ctx):
+    # Erdos-Renyi G(n=16384, m=81920), eps = 1/100, tie-break seed 42
+    assert_same_as_oracle(ctx, gg.erdos_renyi(16384, 81920, 1), 1, 100, 42)
+
+
+@pytest.mark.parametrize("p,q", [(1, 100), (1, 10), (1, 2), (0, 1), (3, 1), (7, 1000)])
+def test_eps_sweep(ctx, p, q):
+    for g in (gg.rmat(14, 16, seed=3), gg.erdos_renyi(20000, 100000, 4), gg.barabasi_albert(8000, 6, 5)):
+        assert_same_as_oracle(ctx, g, p, q, 42)
+
+
+@pytest.mark.parametrize("scale,ef", [(8, 4), (10, 16), (12, 8), (15, 16), (16, 4)])
+def test_rmat_ragged(ctx, scale, ef):
+    assert_same_as_oracle(ctx, gg.rmat(scale, ef, seed=scale), 1, 100, scale)
+
+
+@pytest.mark.parametrize("g", [gg.grid(100, 100), gg.grid(101, 101), gg.grid(33, 47, perm_seed=3),
+                               gg.grid(24, 24, 24, perm_seed=5), gg.barabasi_albert(30000, 4, 9),
+                               gg.barabasi_albert(3000, 40, 9)], ids=lambda g: g.name)
+def test_grids_and_ba(ctx, g):
+    assert_same_as_oracle(ctx, g)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2**63 + 11])
+def test_seeds(ctx, seed):
+    assert_same_as_oracle(ctx, gg.rmat(13, 16, seed=7), 1, 100, seed)
+
+
+@pytest.mark.parametrize("p,q", [(1, 100), (1, 10), (1, 2)])
+def test_rmat20_config(ctx, p, q):
+    # R-MAT scale 20, edge factor 16, (a,b,c,d) = (.57,.19,.19,.05)
+    assert_same_as_oracle(ctx, gg.rmat(20, 16, seed=1), p, q, 42)
+
+
+def test_adg_partition_and_stats(ctx):
+    g = gg.rmat(16, 16, seed=2)
+    dg = dev(g)
+    batch = torch.empty(g.n, dtype=torch.int32, device="cuda:0")
+    rounds = ctx.gc_adg_partition(dg, 1, 100, batch)
+    ob, onr, log = oracle.adg(g, 1, 100, log=True)
+    assert rounds == onr and np.array_equal(batch.cpu().numpy(), ob)
+    st = ctx.gc_get_stats()
+    assert st.adg_rounds == onr
+    assert st.sum_U == int(log["U"].sum())
+    src = np.repeat(np.arange(g.n), g.degrees())
+    assert st.sum_decrements == int(np.sum(ob[g.col_idx] > ob[src]))
+
+
+def test_make_priority(ctx):
+    n = 100003
+    rng = np.random.default_rng(1)
+    b = rng.integers(0, 2**31 - 1, size=n).astype(np.int32)
+    bt = torch.from_numpy(b).cuda()
+    key = torch.empty(n, dtype=torch.int64, device="cuda:0")
+    ctx.gc_make_priority(n, bt, 987654321, key)
+    torch.cuda.synchronize()
+    assert np.array_equal(key.cpu().numpy().view(np.uint64), oracle.priority(b, 987654321))
+
+
+@pytest.mark.parametrize("kind", ["ties", "full64", "adg"])
+def test_jp_color_given_priority(ctx, kind):
+    g = gg.rmat(14, 16, seed=11)
+    rng = np.random.default_rng(5)
+    if kind == "ties":
+        prio = rng.integers(0, 3, size=g.n).astype(np.uint64)
+    elif kind == "full64":
+        prio = rng.integers(0, 2**63, size=g.n, dtype=np.uint64) * np.uint64(2) + \
+            rng.integers(0, 2, size=g.n).astype(np.uint64)
+    else:
+        prio = oracle.priority(oracle.adg(g, 1, 100)[0], 42)
+    dg = dev(g)
+    pt = torch.from_numpy(prio.view(np.int64)).cuda()
+    color = torch.empty(g.n, dtype=torch.int32, device="cuda:0")
+    nc = ctx.gc_jp_color(dg, pt, color)
+    oc, onc = oracle.jp_color(g, prio)
+    assert nc == onc and np.array_equal(color.cpu().numpy(), oc)
+
+
+def test_three_calls_equal_one(ctx):
+    # adg_partition + make_priority + jp_color == color_graph
+    g = gg.barabasi_albert(20000, 5, 3)
+    dg = dev(g)
+    batch = torch.empty(g.n, dtype=torch.int32, device="cuda:0")
+    ctx.gc_adg_partition(dg, 1, 10, batch)
+    key = torch.empty(g.n, dtype=torch.int64, device="cuda:0")
+    ctx.gc_make_priority(g.n, batch, 77, key)
+    c1 = torch.empty(g.n, dtype=torch.int32, device="cuda:0")
+    ctx.gc_jp_color(dg, key, c1)
+    c2 = torch.empty(g.n, dtype=torch.int32, device="cuda:0")
+    ctx.gc_color_graph(dg, 1, 10, 77, c2)
+    assert torch.equal(c1, c2)
+
+
+def test_host_entry_point(ctx):
+    g = gg.rmat(15, 16, seed=4)
+    color = np.zeros(g.n, dtype=np.int32)
+    batch = np.zeros(g.n, dtype=np.int32)
+    nc, nr = ctx.gc_color_graph_host(g.row_ptr, g.col_idx, 1, 100, 42, color, batch)
+    ob, oc, onr, onc = oracle.jp_adg(g, 1, 100, 42)
+    assert (nc, nr) == (onc, onr)
+    assert np.array_equal(batch, ob) and np.array_equal(color, oc)
+
+
+def test_scratch_regrow_and_reuse(ctx):
+    for g in (gg.rmat(10, 8, seed=1), gg.rmat(17, 16, seed=2), gg.rmat(11, 8, seed=3)):
+        assert_same_as_oracle(ctx, g)
+
+
+def test_user_stream(ctx):
+    g = gg.rmat(14, 8, seed=6)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        dg = dev(g)
+        color = torch.empty(g.n, dtype=torch.int32, device="cuda:0")
+        ctx.gc_color_graph(dg, 1, 100, 42, color, stream=s)
+    s.synchronize()
+    assert np.array_equal(color.cpu().numpy(), oracle.jp_adg(g, 1, 100, 42)[1])
+
+
+# ------------------------------------------------------------------ validation
+
+def _raw(n, row_ptr, col_idx):
+    rp = torch.tensor(row_ptr, dtype=torch.int64, device="cuda:0")
+    ci = torch.tensor(col_idx if col_idx else [0], dtype=torch.int32, device="cuda:0")
+    if not col_idx:
+        ci = ci[:0]
+    return gcp.DeviceGraph(rp, ci)
+
+
+def test_validate_accepts_generated(ctx):
+    for g in (gg.rmat(12, 16), gg.grid(5, 5, 5, perm_seed=2), empty(3), empty(0)):
+        assert ctx.gc_validate_csr(dev(g)) == gcp.GC_OK
+
+
+@pytest.mark.parametrize("name,rp,ci", [
+    ("asymmetric", [0, 1, 1], [1]),
+    ("self_loop", [0, 1, 2], [0, 0]),
+    ("unsorted", [0, 2, 3, 4], [2, 1, 0, 0]),
+    ("duplicate", [0, 2, 4], [1, 1, 0, 0]),
+    ("id_out_of_range", [0, 1, 2], [5, 0]),
+    ("negative_id", [0, 1, 2], [-1, 0]),
+    ("row_ptr_decreasing", [0, 2, 1, 2], [1, 2]),
+    ("row_ptr_bad_end", [0, 1, 3], [1, 0]),
+])
+def test_validate_rejects(ctx, name, rp, ci):
+    g = _raw(len(rp) - 1, rp, ci)
+    assert ctx.gc_validate_csr(g) == gcp.GC_ERR_INVALID_GRAPH
+
+
+def test_invalid_eps_rejected(ctx):
+    g = dev(path(5))
+    color = torch.empty(5, dtype=torch.int32, device="cuda:0")
+    for p, q in [(1, 0), (1, 2**20 + 1), (2**20 + 1, 1)]:
+        with pytest.raises(gcp.GcError) as e:
+            ctx.gc_color_graph(g, p, q, 42, color)
+        assert e.value.status == gcp.GC_ERR_INVALID_ARG

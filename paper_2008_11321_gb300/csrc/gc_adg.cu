@@ -83,10 +83,11 @@ adg_partition_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row
     int kbase = 0;
     if (lane == 0 && km) kbase = atomicAdd(&ctl->size_Unext, __popc(km));
     kbase = __shfl_sync(kFull, kbase, 0);
-    if (keep) {
-      u_out[kbase + __popc(km & lt)] = u;
-      if (first_round_n > 0) D[u] = d;
-    }
+    if (keep) u_out[kbase + __popc(km & lt)] = u;
+    // D[u] is written for every vertex in round 1; for a removed vertex it then
+    // keeps its degree at removal, |{w in N(u) : batch(w) >= batch(u)}|, which
+    // bounds u's predecessor count in JP.
+    if (active && first_round_n > 0) D[u] = d;
     // removed -> batch id and UPDATE tasks
     int nt = 0;
     if (in_r) {
@@ -134,28 +135,12 @@ adg_update_kernel(AdgCtl* __restrict__ ctl, const int* __restrict__ col, int* __
       st = task_start[t];
       len = task_len[t];
     }
-    const int incl = warp_inclusive_scan(len);
-    const int total = __shfl_sync(kFull, incl, 31);
-    const int excl = incl - len;
-    for (int b = 0; b < total; b += 32) {
-      const int e = b + lane;
-      // owner task: the largest lane j with excl_j <= e
-      int j = 0;
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        int c = j + step;
-        int ex = __shfl_sync(kFull, excl, c);
-        if (ex <= e) j = c;
+    sweep_tile(st, len, 0, col, [&](int w, int) {
+      if (__ldg(batch + w) == 0) {
+        atomicSub(&D[w], 1);
+        ++cut;
       }
-      const long long k = __shfl_sync(kFull, st, j) + (e - __shfl_sync(kFull, excl, j));
-      if (e < total) {
-        const int w = col[k];
-        if (batch[w] == 0) {
-          atomicSub(&D[w], 1);
-          ++cut;
-        }
-      }
-    }
+    });
   }
   cut = warp_sum(cut);
   if (lane == 0 && cut) atomicAdd(&ctl->cut, cut);
@@ -178,19 +163,19 @@ __global__ void adg_finalize_kernel(AdgCtl* ctl) {
 
 }  // namespace
 
+// Excludes D (n ints), which the caller provides.
 size_t adg_scratch_bytes(long long n, long long nnz) {
   const long long ntask = n + nnz / kChunk + 1;
-  return 3 * (static_cast<size_t>(n) * 4 + 256) + static_cast<size_t>(ntask) * 12 + 2048;
+  return 2 * (static_cast<size_t>(n) * 4 + 256) + static_cast<size_t>(ntask) * 12 + 2048;
 }
 
 gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigned q, int* batch,
-                  int* rounds_out, cudaStream_t s) {
+                  int* D, int* rounds_out, cudaStream_t s) {
   const long long n = g->n, nnz = g->nnz;
   *rounds_out = 0;
   ctx->stats.adg_rounds = 0;
   if (n == 0) return GC_OK;
   AdgCtl* ctl = a.take<AdgCtl>(1);
-  int* D = a.take<int>(n);
   int* ubuf[2] = {a.take<int>(n), a.take<int>(n)};
   const long long ntask = n + nnz / kChunk + 1;
   long long* task_start = a.take<long long>(ntask);

@@ -117,18 +117,17 @@ gc_status color_graph_device(gc_context* ctx, const gc_csr* g, uint32_t p, uint3
                              int32_t* color, int32_t* batch, int32_t* ncol, int32_t* nrounds,
                              cudaStream_t s) {
   const long long n = g->n;
-  const size_t batch_bytes = batch ? 0 : (static_cast<size_t>(n) * 4 + 256);
-  const size_t adg = gc::adg_scratch_bytes(n, g->nnz);
-  const size_t jp = gc::jp_scratch_bytes(n);
-  GC_TRY(ctx->reserve(batch_bytes + (adg > jp ? adg : jp)));
-  gc::Arena a = ctx->arena();
-  int* b = batch ? batch : a.take<int>(n > 0 ? n : 1);
-  if (!b) return GC_ERR_OOM;
+  const size_t vb = static_cast<size_t>(n > 0 ? n : 1) * 4 + 256;
+  GC_TRY(ctx->reserve_vert(2 * vb));
+  int* D = static_cast<int*>(ctx->vbuf);
+  int* b = batch ? batch : reinterpret_cast<int*>(static_cast<char*>(ctx->vbuf) + vb);
+  GC_TRY(ctx->reserve(gc::adg_scratch_bytes(n, g->nnz)));
   int rounds = 0, colors = 0;
   GC_TRY(timing_begin(ctx, 0, s));
-  GC_TRY(gc::adg_run(ctx, a, g, p, q, b, &rounds, s));
+  GC_TRY(gc::adg_run(ctx, ctx->arena(), g, p, q, b, D, &rounds, s));
   GC_TRY(timing_begin(ctx, 1, s));
-  GC_TRY(gc::jp_run_fused(ctx, a, g, b, seed, color, &colors, s));
+  GC_TRY(ctx->reserve(gc::jpadg_scratch_bytes(n, g->nnz, rounds)));
+  GC_TRY(gc::jp_run_fused(ctx, ctx->arena(), g, b, D, rounds, seed, color, &colors, s));
   GC_TRY(timing_begin(ctx, 2, s));
   if (ctx->timing) {
     GC_TRY_CUDA(cudaEventSynchronize(ctx->ev[2]));
@@ -142,23 +141,27 @@ gc_status color_graph_device(gc_context* ctx, const gc_csr* g, uint32_t p, uint3
 
 }  // namespace
 
-gc_status gc_context::reserve(size_t bytes) {
-  if (bytes <= scratch_bytes) return GC_OK;
-  if (scratch) {
-    cudaFree(scratch);
-    scratch = nullptr;
-    scratch_bytes = 0;
-  }
-  size_t want = bytes + bytes / 8;
-  cudaError_t e = cudaMalloc(&scratch, want);
-  if (e != cudaSuccess) {
-    scratch = nullptr;
+namespace {
+// Grow a device buffer to at least `bytes` (contents are not kept).
+gc_status grow(void** buf, size_t* cap, size_t bytes) {
+  if (bytes <= *cap) return GC_OK;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  const size_t want = bytes + bytes / 8;
+  if (cudaMalloc(buf, want) != cudaSuccess) {
+    *buf = nullptr;
     cudaGetLastError();
     return GC_ERR_OOM;
   }
-  scratch_bytes = want;
+  *cap = want;
   return GC_OK;
 }
+}  // namespace
+
+gc_status gc_context::reserve(size_t bytes) { return grow(&scratch, &scratch_bytes, bytes); }
+gc_status gc_context::reserve_vert(size_t bytes) { return grow(&vbuf, &vbuf_bytes, bytes); }
+gc_status gc_context::reserve_aux(size_t bytes) { return grow(&aux, &aux_bytes, bytes); }
 
 extern "C" {
 
@@ -213,6 +216,8 @@ void gc_destroy(gc_context* ctx) {
   if (!ctx) return;
   DeviceGuard guard(ctx->device);
   if (ctx->scratch) cudaFree(ctx->scratch);
+  if (ctx->vbuf) cudaFree(ctx->vbuf);
+  if (ctx->aux) cudaFree(ctx->aux);
   if (ctx->h_graph) cudaFree(ctx->h_graph);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   for (auto& ev : ctx->ev)
@@ -270,9 +275,11 @@ gc_status gc_adg_partition(gc_context* ctx, const gc_csr* g, uint32_t eps_p, uin
   if (!guard.ok) return GC_ERR_CUDA;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   GC_TRY(ctx->reserve(gc::adg_scratch_bytes(g->n, g->nnz)));
+  GC_TRY(ctx->reserve_vert(static_cast<size_t>(g->n > 0 ? g->n : 1) * 4 + 256));
   int rounds = 0;
   GC_TRY(timing_begin(ctx, 0, s));
-  GC_TRY(gc::adg_run(ctx, ctx->arena(), g, eps_p, eps_q, batch_out, &rounds, s));
+  GC_TRY(gc::adg_run(ctx, ctx->arena(), g, eps_p, eps_q, batch_out, static_cast<int*>(ctx->vbuf),
+                     &rounds, s));
   GC_TRY(timing_begin(ctx, 1, s));
   if (ctx->timing) {
     GC_TRY_CUDA(cudaEventSynchronize(ctx->ev[1]));

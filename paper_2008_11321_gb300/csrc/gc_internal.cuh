@@ -13,9 +13,12 @@ namespace gc {
 constexpr int kWarp = 32;
 constexpr unsigned kFull = 0xffffffffu;
 
-// Edges per UPDATE task: a removed vertex of degree d becomes ceil(d / kChunk)
-// tasks, so one hub cannot hold a warp for long.
-constexpr int kChunk = 1024;
+// Edges per task of the edge sweeps (ADG's UPDATE, JP's core extraction): a
+// vertex of degree d becomes ceil(d / kChunk) tasks, so one hub cannot hold a
+// warp for long and hub-heavy rounds still spread over every warp.
+constexpr int kChunk = 256;
+// Independent edges each lane keeps in flight in the edge sweeps.
+constexpr int kSweepUnroll = 4;
 // Vertices of degree <= kSmallDeg are coloured one per lane, larger ones one
 // per warp (at most kSmallDeg predecessors -> the colour fits a 64-bit mask).
 constexpr int kSmallDeg = 32;
@@ -48,17 +51,26 @@ struct AdgCtl {
   int pad;
 };
 
-// Control block of one JP run.
+// Control block of one JP run (must fit the context's 256-byte pinned buffer).
 struct JpCtl {
   unsigned long long big_cursor;
   unsigned long long small_cursor;
   unsigned long long key_or;     // OR over the sort keys (constant digits)
   unsigned long long key_and;    // AND over the sort keys
   unsigned long long spins;      // polls that found an uncoloured predecessor
-  unsigned long long nbig;       // vertices in the warp path list
+  unsigned long long nbig;       // vertices in the warp-path list
+  unsigned long long nsmall;     // vertices in the lane-path list
+  unsigned long long ncore;      // vertices coloured by the core block
+  unsigned long long base0;      // warp-path offset of the first bulk bucket
+  unsigned long long base1;      // lane-path offset of the first bulk bucket
+  long long bstar;               // last core bucket (-1: no core)
   int max_color;
   int err;
 };
+static_assert(sizeof(JpCtl) <= 256, "JpCtl must fit the pinned read-back buffer");
+
+// Largest core coloured by the single shared-memory block (16-bit colours).
+constexpr long long kCoreTarget = 49152;
 
 // Bump allocator over the context's scratch arena (256-byte aligned slices).
 struct Arena {
@@ -96,13 +108,17 @@ int radix_sort_pairs(SortBufs& b, long long n, unsigned digit_mask, cudaStream_t
 
 // ADG rounds on the device (gc_adg.cu).  Scratch sized by adg_scratch_bytes.
 size_t adg_scratch_bytes(long long n, long long nnz);
+// D (n ints) receives each vertex's degree at removal.
 gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigned q, int* batch,
-                  int* rounds_out, cudaStream_t s);
+                  int* D, int* rounds_out, cudaStream_t s);
 
 // JP colouring by predecessor polling (gc_jp.cu).
 size_t jp_scratch_bytes(long long n);
-gc_status jp_run_fused(gc_context* ctx, Arena a, const gc_csr* g, const int* batch,
-                       unsigned long long seed, int* color, int* num_colors_out, cudaStream_t s);
+size_t jpadg_scratch_bytes(long long n, long long nnz, int rounds);
+// batch: ADG batches; D: degree at removal (from adg_run); rounds: ADG rounds.
+gc_status jp_run_fused(gc_context* ctx, Arena a, const gc_csr* g, const int* batch, const int* D,
+                       int rounds, unsigned long long seed, int* color, int* num_colors_out,
+                       cudaStream_t s);
 gc_status jp_run_given(gc_context* ctx, Arena a, const gc_csr* g, const unsigned long long* prio,
                        int* color, int* num_colors_out, cudaStream_t s);
 cudaError_t make_priority(const int* batch, long long n, unsigned long long seed,
@@ -121,13 +137,21 @@ struct gc_context {
   size_t scratch_bytes = 0;
   // small page-locked host buffer for scalar read-back
   void* pinned = nullptr;
+  // per-vertex state that outlives one phase (D, an internal batch array)
+  void* vbuf = nullptr;
+  size_t vbuf_bytes = 0;
+  // predecessor lists of the JP core
+  void* aux = nullptr;
+  size_t aux_bytes = 0;
   // buffers owned for gc_color_graph_host
   void* h_graph = nullptr;
   size_t h_graph_bytes = 0;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   gc_stats stats{};
 
-  gc_status reserve(size_t bytes);
+  gc_status reserve(size_t bytes);      // scratch arena
+  gc_status reserve_vert(size_t bytes); // vbuf
+  gc_status reserve_aux(size_t bytes);  // aux
   gc::Arena arena() const {
     gc::Arena a;
     a.base = static_cast<char*>(scratch);
@@ -219,6 +243,41 @@ __device__ __forceinline__ T warp_inclusive_scan(T v) {
     if (lane >= o) v += u;
   }
   return v;
+}
+
+// Edge sweep over 32 tasks held one per lane (task start `st`, length `len`,
+// a caller value `tag`): the tasks' edges are numbered 0..total-1 in lane
+// order and handed out 32 * kSweepUnroll at a time, each lane taking
+// kSweepUnroll edges.  fn(w, tag) is called with the neighbour w = col_idx[k]
+// of each edge and the tag of the task owning it; all kSweepUnroll col_idx
+// loads of a lane are issued before any fn runs, so their latencies overlap.
+template <class Fn>
+__device__ __forceinline__ void sweep_tile(long long st, int len, int tag, const int* __restrict__ col,
+                                           Fn fn) {
+  const int lane = threadIdx.x & 31;
+  const int incl = warp_inclusive_scan(len);
+  const int total = __shfl_sync(kFull, incl, 31);
+  const int excl = incl - len;
+  for (int b = 0; b < total; b += 32 * kSweepUnroll) {
+    int w[kSweepUnroll], own[kSweepUnroll];
+#pragma unroll
+    for (int u = 0; u < kSweepUnroll; ++u) {
+      const int e = b + u * 32 + lane;
+      int j = 0;  // owner: the largest lane j with excl_j <= e
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int c = j + step;
+        if (__shfl_sync(kFull, excl, c) <= e) j = c;
+      }
+      const long long k = __shfl_sync(kFull, st, j) + (e - __shfl_sync(kFull, excl, j));
+      const int tg = __shfl_sync(kFull, tag, j);
+      own[u] = e < total ? tg : -1;
+      w[u] = e < total ? __ldg(col + k) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < kSweepUnroll; ++u)
+      if (w[u] >= 0) fn(w[u], own[u]);
+  }
 }
 
 // Random tie-break rho_R of the JP-ADG priority (Section 4.1): the upper 32

@@ -55,7 +55,8 @@ adg_partition_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row
                      int* __restrict__ task_len, int first_round_n) {
   const int round = ctl->round;
   const int T = ctl->T;
-  const long long size_u = first_round_n > 0 ? first_round_n : ctl->size_U;
+  const bool first = first_round_n > 0;
+  const long long size_u = first ? first_round_n : ctl->size_U;
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
   unsigned long long sum_r = 0;
@@ -66,7 +67,7 @@ adg_partition_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row
     int u = 0, d = 0;
     long long rs = 0, re = 0;
     if (active) {
-      if (first_round_n > 0) {
+      if (first) {
         u = static_cast<int>(i);
         rs = row_ptr[u];
         re = row_ptr[u + 1];
@@ -87,30 +88,39 @@ adg_partition_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row
     // D[u] is written for every vertex in round 1; for a removed vertex it then
     // keeps its degree at removal, |{w in N(u) : batch(w) >= batch(u)}|, which
     // bounds u's predecessor count in JP.
-    if (active && first_round_n > 0) D[u] = d;
-    // removed -> batch id and UPDATE tasks
-    int nt = 0;
+    if (active && first) D[u] = d;
     if (in_r) {
       batch[u] = round;
       sum_r += static_cast<unsigned long long>(d);
-      if (first_round_n == 0) {
-        rs = row_ptr[u];
-        re = row_ptr[u + 1];
-      }
+    }
+    if (first) continue;  // round 1's UPDATE sweeps vertex tiles, no task list
+    // removed -> UPDATE tasks of at most kChunk edges, written by the warp
+    int nt = 0;
+    if (in_r) {
+      rs = row_ptr[u];
+      re = row_ptr[u + 1];
       nt = static_cast<int>((re - rs + kChunk - 1) / kChunk);
     }
     const int incl = warp_inclusive_scan(nt);
     const int tot = __shfl_sync(kFull, incl, 31);
+    const int excl = incl - nt;
     unsigned long long tbase = 0;
     if (lane == 31 && tot) tbase = atomicAdd(&ctl->ntasks, static_cast<unsigned long long>(tot));
     tbase = __shfl_sync(kFull, tbase, 31);
-    if (nt) {
-      unsigned long long t = tbase + static_cast<unsigned>(incl - nt);
-      for (int j = 0; j < nt; ++j) {
-        long long st = rs + static_cast<long long>(j) * kChunk;
-        long long len = re - st < kChunk ? re - st : kChunk;
-        task_start[t + j] = st;
-        task_len[t + j] = static_cast<int>(len);
+    for (int b = 0; b < tot; b += 32) {
+      const int x = b + lane;
+      int j = 0;  // owner: the largest lane j with excl_j <= x
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int c = j + step;
+        if (__shfl_sync(kFull, excl, c) <= x) j = c;
+      }
+      const long long st = __shfl_sync(kFull, rs, j) +
+                           static_cast<long long>(x - __shfl_sync(kFull, excl, j)) * kChunk;
+      const long long rej = __shfl_sync(kFull, re, j);
+      if (x < tot) {
+        task_start[tbase + x] = st;
+        task_len[tbase + x] = static_cast<int>(rej - st < kChunk ? rej - st : kChunk);
       }
     }
   }
@@ -118,11 +128,18 @@ adg_partition_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row
   if (lane == 0 && sum_r) atomicAdd(&ctl->sum_R, sum_r);
 }
 
+// Round 1 (vertex_tiles != 0): lane l of a warp owns vertex 32*tile + l and
+// sweeps its row if it was removed in round 1 (degree <= T_1, no chunking
+// needed since T_1 is the average degree bound).  Later rounds sweep the task
+// list written by the partition.
 __global__ void __launch_bounds__(kAdgThreads)
-adg_update_kernel(AdgCtl* __restrict__ ctl, const int* __restrict__ col, int* __restrict__ D,
-                  const int* __restrict__ batch, const long long* __restrict__ task_start,
-                  const int* __restrict__ task_len) {
-  const unsigned long long ntasks = ctl->ntasks;
+adg_update_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row_ptr,
+                  const int* __restrict__ col, int* __restrict__ D, const int* __restrict__ batch,
+                  const long long* __restrict__ task_start, const int* __restrict__ task_len,
+                  long long vertex_tiles_n) {
+  const int round = ctl->round;
+  const unsigned long long ntasks =
+      vertex_tiles_n > 0 ? static_cast<unsigned long long>(vertex_tiles_n) : ctl->ntasks;
   const int lane = threadIdx.x & 31;
   const unsigned long long gwarp = (static_cast<unsigned long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const unsigned long long nwarps = (static_cast<unsigned long long>(gridDim.x) * blockDim.x) >> 5;
@@ -132,13 +149,20 @@ adg_update_kernel(AdgCtl* __restrict__ ctl, const int* __restrict__ col, int* __
     long long st = 0;
     int len = 0;
     if (t < ntasks) {
-      st = task_start[t];
-      len = task_len[t];
+      if (vertex_tiles_n > 0) {
+        if (batch[t] == round) {
+          st = row_ptr[t];
+          len = static_cast<int>(row_ptr[t + 1] - st);
+        }
+      } else {
+        st = task_start[t];
+        len = task_len[t];
+      }
     }
     sweep_tile(st, len, 0, col, [&](int w, int) {
-      if (__ldg(batch + w) == 0) {
-        atomicSub(&D[w], 1);
+      if (__ldg(batch + w) == 0) {  // w is still in U
         ++cut;
+        atomicSub(&D[w], 1);
       }
     });
   }
@@ -182,7 +206,7 @@ gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigne
   int* task_len = a.take<int>(ntask);
   if (!ctl || !D || !ubuf[0] || !ubuf[1] || !task_start || !task_len) return GC_ERR_OOM;
 
-  GC_TRY_CUDA(cudaMemsetAsync(batch, 0, sizeof(int) * n, s));
+  GC_TRY_CUDA(cudaMemsetAsync(batch, 0, sizeof(int) * n, s));  // batch 0 = still in U
   adg_init_kernel<<<1, 1, 0, s>>>(ctl, n, nnz, p, q);
   ++g_launches;
   GC_TRY_CUDA(cudaGetLastError());
@@ -201,8 +225,8 @@ gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigne
         task_len, round == 1 ? static_cast<int>(n) : 0);
     ++g_launches;
     GC_TRY_CUDA(cudaGetLastError());
-    adg_update_kernel<<<max_blocks, kAdgThreads, 0, s>>>(ctl, g->col_idx, D, batch, task_start,
-                                                          task_len);
+    adg_update_kernel<<<max_blocks, kAdgThreads, 0, s>>>(ctl, row_ptr_of(g), g->col_idx, D, batch,
+                                                          task_start, task_len, round == 1 ? n : 0);
     ++g_launches;
     GC_TRY_CUDA(cudaGetLastError());
     adg_finalize_kernel<<<1, 1, 0, s>>>(ctl);

@@ -1,6 +1,7 @@
 // C ABI entry points (gcolor.h): context management, argument checks, CSR
 // validation, and the orchestration of the ADG and JP kernels.
 #include <climits>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -192,6 +193,7 @@ gc_status gc_create(gc_context** out, int device) {
   gc_context* ctx = new (std::nothrow) gc_context();
   if (!ctx) return GC_ERR_OOM;
   ctx->device = device;
+  if (const char* env = getenv("GC_CORE_TARGET")) ctx->core_target = atoll(env);
   if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
       cudaDeviceGetAttribute(&ctx->coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess) {
     delete ctx;

@@ -18,7 +18,7 @@ constexpr unsigned kFull = 0xffffffffu;
 // warp for long and hub-heavy rounds still spread over every warp.
 constexpr int kChunk = 256;
 // Independent edges each lane keeps in flight in the edge sweeps.
-constexpr int kSweepUnroll = 4;
+constexpr int kSweepUnroll = 8;
 // Vertices of degree <= kSmallDeg are coloured one per lane, larger ones one
 // per warp (at most kSmallDeg predecessors -> the colour fits a 64-bit mask).
 constexpr int kSmallDeg = 32;
@@ -69,8 +69,11 @@ struct JpCtl {
 };
 static_assert(sizeof(JpCtl) <= 256, "JpCtl must fit the pinned read-back buffer");
 
-// Largest core coloured by the single shared-memory block (16-bit colours).
-constexpr long long kCoreTarget = 49152;
+// Largest core coloured by the single shared-memory block (16-bit colours,
+// 2 bytes of shared memory per core vertex next to 128 KB of bitmaps, within
+// the 227 KB a block may use) and its default target size.
+constexpr long long kCoreMax = 49152;
+constexpr long long kCoreDefault = 16384;
 
 // Bump allocator over the context's scratch arena (256-byte aligned slices).
 struct Arena {
@@ -127,11 +130,13 @@ cudaError_t make_priority(const int* batch, long long n, unsigned long long seed
 }  // namespace gc
 
 // The opaque context.
+constexpr long long kCoreDefault_ = gc::kCoreDefault;
 struct gc_context {
   int device = 0;
   int num_sms = 0;
   int coop = 0;
   int timing = 0;
+  long long core_target = kCoreDefault_;  // JP-ADG core size (vertices)
   // scratch arena (device)
   void* scratch = nullptr;
   size_t scratch_bytes = 0;

@@ -24,7 +24,8 @@
 // JP-ADG (the fused path of gc_color_graph) runs in three stages:
 //   1. order: one counting-sort pass by (batch, top bits of rho_R) gives the
 //      order without a comparison sort; isolated vertices take colour 1 at once
-//      and drop out.  The first buckets, up to kCoreTarget vertices, form the
+//      and drop out.  The first buckets, up to the core target (16384 by
+//      default, at most 49152) vertices, form the
 //      "core"; they are sorted exactly inside their (tiny) buckets.
 //   2. core: the predecessors of each core vertex all lie in the core; they
 //      are extracted across the whole GPU into compact lists of core-local
@@ -37,6 +38,7 @@
 // gc_jp_color with an arbitrary priority array orders the vertices with an
 // exact radix sort and runs stage 3 on all of them.
 #include <cstring>
+#include <vector>
 
 #include "gc_internal.cuh"
 
@@ -84,7 +86,7 @@ __device__ __forceinline__ int wait_color(const int* p, JpCtl* ctl, unsigned lon
   unsigned sleep_ns = 32;
   for (unsigned it = 1;; ++it) {
     __nanosleep(sleep_ns);
-    if (sleep_ns < 1024) sleep_ns <<= 1;
+    if (sleep_ns < 256) sleep_ns <<= 1;
     c = ld_relaxed(p);
     if (c != 0) return c;
     ++spins;
@@ -100,19 +102,40 @@ __device__ __forceinline__ int wait_color(const int* p, JpCtl* ctl, unsigned lon
 
 // GetColor for a vertex of degree <= kSmallDeg, by one lane: at most 32
 // predecessors, so the smallest free colour is <= 33 and a 64-bit mask of
-// used colours suffices.
+// used colours suffices.  Neighbours are read four at a time so that their
+// loads overlap; predecessors not yet coloured are remembered in a 32-bit
+// position mask and waited on after the scan.
 template <class Key>
 __device__ int color_lane(int v, const long long* __restrict__ row_ptr, const int* __restrict__ col,
                           const Key& key, int* color, JpCtl* ctl, unsigned long long& spins) {
+  constexpr int U = 4;
   const unsigned long long kv = key(v);
   const long long s = row_ptr[v], e = row_ptr[v + 1];
   unsigned long long used = 0;
-  for (long long k = s; k < e; ++k) {
-    const int w = __ldg(col + k);
-    if (precedes(key(w), w, kv, v)) {
-      const int c = wait_color(color + w, ctl, spins);
-      if (c <= 64) used |= 1ull << (c - 1);
+  unsigned later = 0;
+  for (long long k = s; k < e; k += U) {
+    int w[U], c[U];
+    bool pred[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) w[u] = k + u < e ? __ldg(col + k + u) : -1;
+#pragma unroll
+    for (int u = 0; u < U; ++u) pred[u] = w[u] >= 0 && precedes(key(w[u]), w[u], kv, v);
+#pragma unroll
+    for (int u = 0; u < U; ++u) c[u] = pred[u] ? ld_relaxed(color + w[u]) : -1;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!pred[u]) continue;
+      if (c[u] == 0)
+        later |= 1u << static_cast<int>(k + u - s);
+      else if (c[u] <= 64)
+        used |= 1ull << (c[u] - 1);
     }
+  }
+  while (later) {
+    const int pos = __ffs(later) - 1;
+    later &= later - 1;
+    const int cu = wait_color(color + __ldg(col + s + pos), ctl, spins);
+    if (cu <= 64) used |= 1ull << (cu - 1);
   }
   const int c = __ffsll(static_cast<long long>(~used));
   st_relaxed(color + v, c);
@@ -140,18 +163,27 @@ __device__ int color_warp(int v, unsigned* bm, const long long* __restrict__ row
         int pend[kPendCap];
         int np = 0;
         long long resume = -1;
-        for (; k < e; k += 32) {
-          const int w = __ldg(col + k);
-          if (precedes(key(w), w, kv, v)) {
-            const int c = ld_relaxed(color + w);
-            if (c == 0) {
+        constexpr int U = 4;
+        for (; k < e && resume < 0; k += 32 * U) {
+          int w[U], c[U];
+          bool pred[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) w[u] = k + 32 * u < e ? __ldg(col + k + 32 * u) : -1;
+#pragma unroll
+          for (int u = 0; u < U; ++u) pred[u] = w[u] >= 0 && precedes(key(w[u]), w[u], kv, v);
+#pragma unroll
+          for (int u = 0; u < U; ++u) c[u] = pred[u] ? ld_relaxed(color + w[u]) : -1;
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            if (!pred[u]) continue;
+            if (c[u] == 0) {
               if (np == kPendCap) {
-                resume = k;
-                break;
+                if (resume < 0) resume = k + 32 * u;  // re-examined after the waits
+                continue;
               }
-              pend[np++] = w;
-            } else if (c > base && c <= base + kColorWin) {
-              atomicOr(&bm[(c - base - 1) >> 5], 1u << ((c - base - 1) & 31));
+              pend[np++] = w[u];
+            } else if (resume < 0 && c[u] > base && c[u] <= base + kColorWin) {
+              atomicOr(&bm[(c[u] - base - 1) >> 5], 1u << ((c[u] - base - 1) & 31));
             }
           }
         }
@@ -178,35 +210,41 @@ __device__ int color_warp(int v, unsigned* bm, const long long* __restrict__ row
   }
 }
 
-// Stage 3 (and the whole of gc_jp_color): warp-path list plist[0, nbig) and
-// lane-path list plist[nbig, nbig + nsmall), both from ctl.
+// Stage 3 (and the whole of gc_jp_color): colours the warp-path list
+// big[0, nbig) and the lane-path list small[0, nsmall), taking vertices with
+// the two counters cursors[0] and cursors[1].  nbig < 0 means: counts from
+// ctl, small list right after the big one.
 template <class Key>
 __global__ void __launch_bounds__(kJpThreads)
-jp_color_kernel(JpCtl* ctl, const long long* __restrict__ row_ptr, const int* __restrict__ col,
-                Key key, const int* __restrict__ plist, int* color) {
+jp_color_kernel(JpCtl* ctl, unsigned long long* cursors, const long long* __restrict__ row_ptr,
+                const int* __restrict__ col, Key key, const int* __restrict__ big, long long nbig,
+                const int* __restrict__ small, long long nsmall, int* color) {
   __shared__ unsigned s_bm[kJpWarps][kColorWin / 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long nbig = static_cast<long long>(ctl->nbig);
-  const long long nsmall = static_cast<long long>(ctl->nsmall);
+  if (nbig < 0) {
+    nbig = static_cast<long long>(ctl->nbig);
+    nsmall = static_cast<long long>(ctl->nsmall);
+    small = big + nbig;
+  }
   bool big_done = nbig == 0, small_done = nsmall == 0;
-  const bool prefer_big = (warp & 1) == 0;
+  const bool prefer_big = (warp & 3) != 0;  // 3/4 of the warps start on the warp path
   int local_max = 0;
   unsigned long long spins = 0;
   while (!(big_done && small_done)) {
     const bool take_big = !big_done && (prefer_big || small_done);
     if (take_big) {
       unsigned long long i = 0;
-      if (lane == 0) i = atomicAdd(&ctl->big_cursor, 1ull);
+      if (lane == 0) i = atomicAdd(&cursors[0], 1ull);
       i = __shfl_sync(kFull, i, 0);
       if (i >= static_cast<unsigned long long>(nbig)) {
         big_done = true;
         continue;
       }
-      const int c = color_warp(plist[i], s_bm[warp], row_ptr, col, key, color, ctl, spins);
+      const int c = color_warp(big[i], s_bm[warp], row_ptr, col, key, color, ctl, spins);
       local_max = c > local_max ? c : local_max;
     } else {
       unsigned long long i0 = 0;
-      if (lane == 0) i0 = atomicAdd(&ctl->small_cursor, 32ull);
+      if (lane == 0) i0 = atomicAdd(&cursors[1], 32ull);
       i0 = __shfl_sync(kFull, i0, 0);
       if (i0 >= static_cast<unsigned long long>(nsmall)) {
         small_done = true;
@@ -214,8 +252,7 @@ jp_color_kernel(JpCtl* ctl, const long long* __restrict__ row_ptr, const int* __
       }
       const unsigned long long i = i0 + lane;
       if (i < static_cast<unsigned long long>(nsmall)) {
-        const int c = color_lane(plist[nbig + static_cast<long long>(i)], row_ptr, col, key, color,
-                                 ctl, spins);
+        const int c = color_lane(small[i], row_ptr, col, key, color, ctl, spins);
         local_max = c > local_max ? c : local_max;
       }
       __syncwarp();
@@ -367,6 +404,18 @@ __global__ void jpf_bases_kernel(const unsigned long long* __restrict__ off_tot,
   ctl->nsmall = off1[B] - off1[bs + 1];
 }
 
+// Class-list offsets at the first bucket of every batch group g = R - batch
+// (g = 0..R, where g = R is the total): bounds[2g] = warp path, [2g+1] =
+// lane path.  Read before the scatter advances the offsets.
+__global__ void jpf_batch_bounds_kernel(const unsigned long long* __restrict__ off_cls, BucketPlan bp,
+                                        unsigned long long* __restrict__ bounds) {
+  for (long long g = gtid(); g <= bp.rounds; g += gstride()) {
+    const long long b = g << bp.hb;
+    bounds[2 * g] = off_cls[b];
+    bounds[2 * g + 1] = off_cls[(bp.B + 1) + b];
+  }
+}
+
 // Places every non-isolated vertex: core buckets into order[0, ncore), the
 // rest into the warp-path list order[ncore, ncore + nbig) and the lane-path
 // list after it.  Cursors are the exclusive scans, advanced atomically.
@@ -484,58 +533,141 @@ jpf_core_preds_kernel(const int* __restrict__ col, KeyFused key, const int* __re
   }
 }
 
-// Colours the core in one block: warps take core vertices in order; a warp
-// polls its predecessors' colours in shared memory (16-bit: a core of at most
-// 65535 vertices uses at most 65535 colours) and writes the smallest colour
-// none of them uses.  Predecessors precede their successors in the exact core
-// order, so the warp holding the earliest unfinished vertex never waits on a
-// vertex no warp holds.
+// Exact predecessor counts -> int64 array for the offset scan.
+__global__ void jpf_counts_kernel(const int* __restrict__ pcnt, const JpCtl* ctl, long long* __restrict__ out) {
+  const long long kc = static_cast<long long>(ctl->ncore);
+  for (long long i = gtid(); i <= kc; i += gstride()) out[i] = i < kc ? pcnt[i] : 0;
+}
+
+// Compacts the predecessor lists (written at capacity-sized slots) into one
+// dense 16-bit stream in core order: list i at [qoff[i], qoff[i+1]).
+__global__ void jpf_compact_kernel(const int* __restrict__ preds, const long long* __restrict__ poff,
+                                   const long long* __restrict__ qoff, const JpCtl* ctl,
+                                   unsigned short* __restrict__ cpreds) {
+  const long long kc = static_cast<long long>(ctl->ncore);
+  const int lane = threadIdx.x & 31;
+  for (long long i = gtid() >> 5; i < kc; i += gstride() >> 5) {
+    const long long src = poff[i], dst = qoff[i], cnt = qoff[i + 1] - qoff[i];
+    for (long long k = lane; k < cnt; k += 32) cpreds[dst + k] = static_cast<unsigned short>(preds[src + k]);
+  }
+}
+
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+// Colours the core in one block.  Warp w colours core vertices w, w+32, ...
+// in that order; for each it reads the compact predecessor list, polls the
+// predecessors' colours in shared memory (16-bit: a core of at most 65535
+// vertices uses at most 65535 colours) and writes the smallest colour none of
+// them uses.  Predecessors precede their successors in the exact core order,
+// so the warp holding the earliest unfinished vertex is never waiting.
+//
+// Used colours are marked in per-lane bitmaps (word q of lane l at
+// q*32 + l, so a warp's marks never collide in a bank and need no atomics),
+// then OR-ed across lanes with a rotated read; only ceil((|pred|+1)/32)
+// words can hold the answer, so only those are cleared and reduced.  While it
+// works on one vertex the warp prefetches its next vertex's list into L1.
 __global__ void __launch_bounds__(kCoreThreads, 1)
-jpf_core_solve_kernel(const int* __restrict__ order, const long long* __restrict__ poff,
-                      const int* __restrict__ pcnt, const int* __restrict__ preds, JpCtl* ctl,
-                      int* color) {
-  extern __shared__ unsigned short s_col[];
-  __shared__ unsigned s_bm[kCoreWarps][kColorWin / 32];
-  __shared__ int s_next;
+jpf_core_solve_kernel(const int* __restrict__ order, const long long* __restrict__ qoff,
+                      const unsigned short* __restrict__ cpreds, JpCtl* ctl, int* color) {
+  constexpr int U = 8;  // pairs of ids per lane in flight
+  extern __shared__ unsigned s_dyn[];
+  unsigned* s_bits = s_dyn;                                              // [warps][32 words][32 lanes]
+  unsigned short* s_col = reinterpret_cast<unsigned short*>(s_dyn + kCoreWarps * 32 * 32);
   const int kc = static_cast<int>(ctl->ncore);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned* bits = s_bits + warp * 32 * 32;
   for (int i = threadIdx.x; i < kc; i += blockDim.x) s_col[i] = 0;
-  if (threadIdx.x == 0) s_next = 0;
   __syncthreads();
   volatile unsigned short* vcol = s_col;
   const unsigned long long t0 = global_ns();
   int local_max = 0;
   bool timed_out = false;
-  for (;;) {
-    int i = 0;
-    if (lane == 0) i = atomicAdd(&s_next, 1);
-    i = __shfl_sync(kFull, i, 0);
-    if (i >= kc) break;
-    const int* pl = preds + poff[i];
-    const int np = pcnt[i];
+  long long beg = warp < kc ? qoff[warp] : 0, end = warp < kc ? qoff[warp + 1] : 0;
+  for (int i = warp; i < kc; i += kCoreWarps) {
+    const int inext = i + kCoreWarps;
+    long long nbeg = 0, nend = 0;
+    if (inext < kc) {
+      nbeg = qoff[inext];
+      nend = qoff[inext + 1];
+    }
+    const int np = static_cast<int>(end - beg);
+    // the smallest free colour is <= np + 1: ceil((np+1)/32) words, at most
+    // one 1024-colour window per pass (larger palettes take further passes)
+    const int nw = np / 32 + 1 < 32 ? np / 32 + 1 : 32;
+    const unsigned short* pl = cpreds + beg;
+    // ids are read as 32-bit pairs from an even index; an odd start peels one
+    const int lead = (np > 0 && (beg & 1)) ? 1 : 0;
+    const unsigned* pairs = reinterpret_cast<const unsigned*>(pl + lead);
+    const int npairs = (np - lead) / 2;
+    const bool tail = ((np - lead) & 1) != 0;
     int c = 0;
-    for (int base = 0;; base += kColorWin) {
-      s_bm[warp][lane] = 0u;
-      __syncwarp();
-      for (int k = lane; k < np; k += 32) {
-        const int j = __ldg(pl + k);
-        int cj = vcol[j];
-        if (cj == 0) {
-          unsigned it = 0;
-          while ((cj = vcol[j]) == 0) {
-            if ((++it & 1023u) == 0 &&
-                (timed_out || ld_relaxed(&ctl->err) != 0 || global_ns() - t0 > kWaitLimitNs)) {
-              timed_out = true;
-              cj = 1;
-              break;
-            }
+    for (int base = 0;; base += 32 * nw) {
+      for (int q = 0; q < nw; ++q) bits[q * 32 + lane] = 0u;
+      // Colours already known are marked at once; a lane defers up to kDefer
+      // uncoloured predecessors and waits on them after its scan, so that when
+      // the last predecessor is coloured little work is left (the latest
+      // predecessors are the ones on the critical path).
+      constexpr int kDefer = 8;
+      int defer[kDefer];
+      int nd = 0;
+      auto put = [&](int cj) {
+        const int x = cj - base - 1;
+        if (x >= 0 && x < 32 * nw) bits[(x >> 5) * 32 + lane] |= 1u << (x & 31);
+      };
+      auto wait_put = [&](int j) {
+        int cj;
+        unsigned it = 0;
+        while ((cj = vcol[j]) == 0) {
+          if (it >= 64) __nanosleep(32);  // plain spinning first: a level is short
+          if ((++it & 255u) == 0 &&
+              (timed_out || ld_relaxed(&ctl->err) != 0 || global_ns() - t0 > kWaitLimitNs)) {
+            timed_out = true;
+            cj = 1;
+            break;
           }
         }
-        if (cj > base && cj <= base + kColorWin)
-          atomicOr(&s_bm[warp][(cj - base - 1) >> 5], 1u << ((cj - base - 1) & 31));
+        put(cj);
+      };
+      auto mark = [&](int j) {
+        const int cj = vcol[j];
+        if (cj != 0) {
+          put(cj);
+        } else if (nd < kDefer) {
+          defer[nd++] = j;
+        } else {
+          wait_put(j);
+        }
+      };
+      if (lane == 0 && lead) mark(pl[0]);
+      if (lane == 0 && tail) mark(pl[np - 1]);
+      for (int p0 = 0; p0 < npairs; p0 += 32 * U) {
+        unsigned pr[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int pp = p0 + u * 32 + lane;
+          pr[u] = pp < npairs ? __ldg(pairs + pp) : 0xffffffffu;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (pr[u] == 0xffffffffu) continue;
+          mark(static_cast<int>(pr[u] & 0xffffu));
+          mark(static_cast<int>(pr[u] >> 16));
+        }
+      }
+      for (int d = 0; d < nd; ++d) wait_put(defer[d]);
+      if (base == 0 && inext < kc) {  // the next list, 128-byte lines, into L1
+        const char* nb = reinterpret_cast<const char*>(cpreds + nbeg);
+        const long long bytes = (nend - nbeg) * 2;
+        for (long long x = static_cast<long long>(lane) * 128; x < bytes; x += 32 * 128) prefetch_l1(nb + x);
       }
       __syncwarp();
-      const unsigned freeb = ~s_bm[warp][lane];
+      // lane q < nw ORs word q over all lanes (rotated so no bank repeats)
+      unsigned word = 0u;
+      if (lane < nw)
+        for (int l = 0; l < 32; ++l) word |= bits[lane * 32 + ((lane + l) & 31)];
+      const unsigned freeb = lane < nw ? ~word : 0u;
       const unsigned fm = __ballot_sync(kFull, freeb != 0u);
       __syncwarp();
       if (fm) {
@@ -547,6 +679,8 @@ jpf_core_solve_kernel(const int* __restrict__ order, const long long* __restrict
     }
     if (lane == 0) vcol[i] = static_cast<unsigned short>(c);
     local_max = c > local_max ? c : local_max;
+    beg = nbeg;
+    end = nend;
   }
   if (__any_sync(kFull, timed_out) && lane == 0) atomicExch(&ctl->err, kDevTimeout);
   __syncthreads();
@@ -555,26 +689,18 @@ jpf_core_solve_kernel(const int* __restrict__ order, const long long* __restrict
   if (lane == 0) atomicMax(&ctl->max_color, local_max);
 }
 
-cudaError_t launch_bulk(gc_context* ctx, JpCtl* ctl, const long long* row_ptr, const int* col,
-                        const KeyFused* kf, const KeyGiven* kg, const int* plist, int* color,
-                        cudaStream_t s) {
+template <class Key>
+cudaError_t launch_bulk(gc_context* ctx, JpCtl* ctl, unsigned long long* cursors, const long long* row_ptr,
+                        const int* col, const Key& key, const int* big, long long nbig, const int* small,
+                        long long nsmall, int* color, cudaStream_t s) {
   int per_sm = 0;
-  cudaError_t e;
-  if (kf)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jp_color_kernel<KeyFused>, kJpThreads, 0);
-  else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jp_color_kernel<KeyGiven>, kJpThreads, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jp_color_kernel<Key>, kJpThreads, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
-  if (ctx->timing) cudaEventRecord(ctx->ev[3], s);
-  if (kf)
-    jp_color_kernel<KeyFused><<<ctx->num_sms * per_sm, kJpThreads, 0, s>>>(ctl, row_ptr, col, *kf, plist, color);
-  else
-    jp_color_kernel<KeyGiven><<<ctx->num_sms * per_sm, kJpThreads, 0, s>>>(ctl, row_ptr, col, *kg, plist, color);
+  jp_color_kernel<Key><<<ctx->num_sms * per_sm, kJpThreads, 0, s>>>(ctl, cursors, row_ptr, col, key, big, nbig,
+                                                                   small, nsmall, color);
   ++g_launches;
-  e = cudaGetLastError();
-  if (ctx->timing) cudaEventRecord(ctx->ev[4], s);
-  return e;
+  return cudaGetLastError();
 }
 
 gc_status finish_jp(gc_context* ctx, JpCtl* ctl, int* num_colors_out, cudaStream_t s) {
@@ -672,7 +798,9 @@ gc_status jp_run_given(gc_context* ctx, Arena a, const gc_csr* g, const unsigned
   ++g_launches;
   GC_TRY_CUDA(cudaGetLastError());
   GC_TRY_CUDA(cudaMemsetAsync(color, 0, sizeof(int) * n, s));
-  GC_TRY_CUDA(launch_bulk(ctx, ctl, rp, g->col_idx, nullptr, &key, plist, color, s));
+  if (ctx->timing) GC_TRY_CUDA(cudaEventRecord(ctx->ev[3], s));
+  GC_TRY_CUDA(launch_bulk(ctx, ctl, &ctl->big_cursor, rp, g->col_idx, key, plist, -1, nullptr, 0, color, s));
+  if (ctx->timing) GC_TRY_CUDA(cudaEventRecord(ctx->ev[4], s));
   return finish_jp(ctx, ctl, num_colors_out, s);
 }
 
@@ -682,11 +810,12 @@ gc_status jp_run_given(gc_context* ctx, Arena a, const gc_csr* g, const unsigned
 size_t jpadg_scratch_bytes(long long n, long long nnz, int rounds) {
   const BucketPlan bp = make_plan(n, rounds);
   const size_t nb = static_cast<size_t>(bp.B + 1);
-  const size_t kc = static_cast<size_t>(kCoreTarget) + 1;
+  const size_t kc = static_cast<size_t>(kCoreMax) + 1;
   const size_t ntask = kc + static_cast<size_t>(nnz / kChunk) + 1;
   const size_t sc = scan_temp_elems(static_cast<long long>(nb)) +
                     scan_temp_elems(static_cast<long long>(kc)) + 2;
-  return 256 + 3 * (nb * 8 + 256) + 2 * (static_cast<size_t>(n) * 4 + 256) + 2 * (kc * 8 + 256) +
+  const size_t rb = (4 * (static_cast<size_t>(bp.rounds) + 1) * 8 + 512);
+  return rb + 256 + 3 * (nb * 8 + 256) + 2 * (static_cast<size_t>(n) * 4 + 256) + 2 * (kc * 8 + 256) +
          (kc * 4 + 256) + ntask * 16 + 3 * 256 + sc * 8 + 4096;
 }
 
@@ -705,17 +834,19 @@ gc_status jp_run_fused(gc_context* ctx, Arena a, const gc_csr* g, const int* bat
   unsigned long long* tot = a.take<unsigned long long>(nb);
   int* order = a.take<int>(n);
   int* lid = a.take<int>(n);
-  long long* cap = a.take<long long>(kCoreTarget + 1);
-  long long* toff = a.take<long long>(kCoreTarget + 1);
-  int* pcnt = a.take<int>(kCoreTarget + 1);
-  const long long ntask_cap = kCoreTarget + nnz / kChunk + 1;
+  long long* cap = a.take<long long>(kCoreMax + 1);
+  long long* toff = a.take<long long>(kCoreMax + 1);
+  int* pcnt = a.take<int>(kCoreMax + 1);
+  const long long ntask_cap = kCoreMax + nnz / kChunk + 1;
   int* task_i = a.take<int>(ntask_cap);
   long long* task_start = a.take<long long>(ntask_cap);
   int* task_len = a.take<int>(ntask_cap);
-  const size_t sc = scan_temp_elems(nb) + scan_temp_elems(kCoreTarget + 1) + 2;
+  const size_t sc = scan_temp_elems(nb) + scan_temp_elems(kCoreMax + 1) + 2;
   long long* temp = a.take<long long>(sc);
+  unsigned long long* bounds = a.take<unsigned long long>(2 * (bp.rounds + 1));
+  unsigned long long* cursors = a.take<unsigned long long>(2 * bp.rounds);
   if (!ctl || !cnt || !tot || !order || !lid || !cap || !toff || !pcnt || !task_i || !task_start ||
-      !task_len || !temp)
+      !task_len || !temp || !bounds || !cursors)
     return GC_ERR_OOM;
   const long long* rp = row_ptr_of(g);
   const KeyFused key{batch, seed};
@@ -735,10 +866,14 @@ gc_status jp_run_fused(gc_context* ctx, Arena a, const gc_csr* g, const int* bat
   GC_TRY_CUDA(exclusive_scan_i64(tot_ll, tot_ll, nb, temp, s));
   GC_TRY_CUDA(exclusive_scan_i64(cnt_ll, cnt_ll, nb, temp, s));
   GC_TRY_CUDA(exclusive_scan_i64(cnt_ll + nb, cnt_ll + nb, nb, temp, s));
-  jpf_pick_kernel<<<blocks, 256, 0, s>>>(tot, bp.B, kCoreTarget, ctl);
+  const long long target = ctx->core_target < 0 ? 0 : (ctx->core_target > kCoreMax ? kCoreMax : ctx->core_target);
+  jpf_pick_kernel<<<blocks, 256, 0, s>>>(tot, bp.B, static_cast<unsigned long long>(target), ctl);
   ++g_launches;
   jpf_bases_kernel<<<1, 1, 0, s>>>(tot, cnt, bp.B, ctl);
   ++g_launches;
+  jpf_batch_bounds_kernel<<<(bp.rounds + 256) / 256, 256, 0, s>>>(cnt, bp, bounds);
+  ++g_launches;
+  GC_TRY_CUDA(cudaMemsetAsync(cursors, 0, sizeof(unsigned long long) * 2 * bp.rounds, s));
   jpf_scatter_kernel<<<blocks, 256, 0, s>>>(batch, seed, rp, n, bp, tot, cnt, ctl, order);
   ++g_launches;
   jpf_core_sort_kernel<<<blocks, 256, 0, s>>>(tot, ctl, key, order, lid);
@@ -748,8 +883,12 @@ gc_status jp_run_fused(gc_context* ctx, Arena a, const gc_csr* g, const int* bat
   // 2. core
   JpCtl* pin = static_cast<JpCtl*>(ctx->pinned);
   GC_TRY_CUDA(cudaMemcpyAsync(pin, ctl, sizeof(JpCtl), cudaMemcpyDeviceToHost, s));
+  std::vector<unsigned long long> hb(2 * (bp.rounds + 1));
+  GC_TRY_CUDA(cudaMemcpyAsync(hb.data(), bounds, sizeof(unsigned long long) * hb.size(),
+                              cudaMemcpyDeviceToHost, s));
   GC_TRY_CUDA(cudaStreamSynchronize(s));
   const long long kc = static_cast<long long>(pin->ncore);
+  const unsigned long long nbig = pin->nbig, base0 = pin->base0, base1 = pin->base1;
   if (kc > 0) {
     jpf_core_prep_kernel<<<blocks, 256, 0, s>>>(order, D, rp, ctl, cap, toff);
     ++g_launches;
@@ -759,26 +898,56 @@ gc_status jp_run_fused(gc_context* ctx, Arena a, const gc_csr* g, const int* bat
     long long* pin_ll = reinterpret_cast<long long*>(ctx->pinned);
     GC_TRY_CUDA(cudaMemcpyAsync(pin_ll, cap + kc, sizeof(long long), cudaMemcpyDeviceToHost, s));
     GC_TRY_CUDA(cudaStreamSynchronize(s));
-    const long long npred_cap = pin_ll[0];
-    GC_TRY(ctx->reserve_aux(static_cast<size_t>(npred_cap > 0 ? npred_cap : 1) * sizeof(int)));
+    const long long npred_cap = pin_ll[0] > 0 ? pin_ll[0] : 1;
+    // aux: predecessor ids at capacity-sized slots (int32), then the dense
+    // 16-bit stream
+    const size_t pbytes = (static_cast<size_t>(npred_cap) * sizeof(int) + 255) & ~size_t(255);
+    GC_TRY(ctx->reserve_aux(pbytes + static_cast<size_t>(npred_cap) * sizeof(unsigned short) + 256));
     int* preds = static_cast<int*>(ctx->aux);
+    unsigned short* cpreds = reinterpret_cast<unsigned short*>(static_cast<char*>(ctx->aux) + pbytes);
     GC_TRY_CUDA(cudaMemsetAsync(pcnt, 0, sizeof(int) * (kc + 1), s));
     jpf_core_tasks_kernel<<<blocks, 256, 0, s>>>(order, rp, toff, ctl, task_i, task_start, task_len);
     ++g_launches;
     jpf_core_preds_kernel<<<blocks, 256, 0, s>>>(g->col_idx, key, order, lid, toff, cap, ctl, task_i,
                                                  task_start, task_len, pcnt, preds);
     ++g_launches;
+    long long* qoff = toff;  // task offsets are dead now
+    jpf_counts_kernel<<<blocks, 256, 0, s>>>(pcnt, ctl, qoff);
+    ++g_launches;
     GC_TRY_CUDA(cudaGetLastError());
-    const size_t smem = static_cast<size_t>(kc) * sizeof(unsigned short);
+    GC_TRY_CUDA(exclusive_scan_i64(qoff, qoff, kc + 1, temp, s));
+    jpf_compact_kernel<<<blocks, 256, 0, s>>>(preds, cap, qoff, ctl, cpreds);
+    ++g_launches;
+    GC_TRY_CUDA(cudaGetLastError());
+    const size_t smem = static_cast<size_t>(kCoreWarps) * 32 * 32 * sizeof(unsigned) +
+                        static_cast<size_t>(kc) * sizeof(unsigned short);
     GC_TRY_CUDA(cudaFuncSetAttribute(jpf_core_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(smem)));
-    jpf_core_solve_kernel<<<1, kCoreThreads, smem, s>>>(order, cap, pcnt, preds, ctl, color);
+    jpf_core_solve_kernel<<<1, kCoreThreads, smem, s>>>(order, qoff, cpreds, ctl, color);
     ++g_launches;
     GC_TRY_CUDA(cudaGetLastError());
   }
 
-  // 3. bulk
-  GC_TRY_CUDA(launch_bulk(ctx, ctl, rp, g->col_idx, &key, nullptr, order + kc, color, s));
+  // 3. bulk, one batch at a time from the top: all predecessors in higher
+  // batches are final when a batch starts, so its workers only ever wait on
+  // vertices of their own batch
+  if (ctx->timing) GC_TRY_CUDA(cudaEventRecord(ctx->ev[3], s));
+  const int* big_list = order + kc;
+  const int* small_list = order + kc + nbig;
+  for (int grp = 0; grp < bp.rounds; ++grp) {
+    auto range = [&](int cls, unsigned long long base, unsigned long long& lo, unsigned long long& hi) {
+      lo = hb[2 * grp + cls] > base ? hb[2 * grp + cls] - base : 0;
+      hi = hb[2 * (grp + 1) + cls] > base ? hb[2 * (grp + 1) + cls] - base : 0;
+    };
+    unsigned long long b0, b1, s0, s1;
+    range(0, base0, b0, b1);
+    range(1, base1, s0, s1);
+    if (b1 <= b0 && s1 <= s0) continue;
+    GC_TRY_CUDA(launch_bulk(ctx, ctl, cursors + 2 * grp, rp, g->col_idx, key, big_list + b0,
+                            static_cast<long long>(b1 > b0 ? b1 - b0 : 0), small_list + s0,
+                            static_cast<long long>(s1 > s0 ? s1 - s0 : 0), color, s));
+  }
+  if (ctx->timing) GC_TRY_CUDA(cudaEventRecord(ctx->ev[4], s));
   return finish_jp(ctx, ctl, num_colors_out, s);
 }
 

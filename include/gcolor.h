@@ -124,6 +124,27 @@ gc_status gc_validate_csr(gc_context *ctx, const gc_csr *g, gc_stream stream);
 gc_status gc_adg_partition(gc_context *ctx, const gc_csr *g, uint32_t eps_p, uint32_t eps_q,
                            int32_t *batch_out, int32_t *num_rounds_out, gc_stream stream);
 
+/* gc_adg_partition without a context and without allocating anything.
+ * The paper has no counterpart: this is an interface for callers that
+ * cannot allocate device memory when they call in -- for example a process
+ * that handed all of the GPU's memory to its own allocator at start-up (a
+ * cudaMalloc would fail there), or code on a latency budget that cannot
+ * afford cudaMalloc/cudaFree, which may block and synchronise the device.
+ * Same inputs, outputs and results as gc_adg_partition; the caller still
+ * provides batch_out (device, n int32).
+ * Scratch is one fixed array of about 6.5 MB built into the library; every
+ * GPU that loads the library holds its own copy until the process exits.  It
+ * bounds the graph: n <= 262144 vertices and nnz <= 8388608 entries; larger
+ * graphs return GC_ERR_OVERFLOW without touching the device.
+ * Runs on the calling thread's current device (g and batch_out must live
+ * there).  The first call on each device looks up the array's device
+ * address; make that first call before any stream capture.  All calls share
+ * the one array and each call starts by resetting the state it reads, so
+ * calls whose work could overlap on the GPU (other streams, other threads)
+ * race with each other and must be serialised by the caller. */
+gc_status gc_adg_partition_noalloc(const gc_csr *g, uint32_t eps_p, uint32_t eps_q,
+                                   int32_t *batch_out, int32_t *num_rounds_out, gc_stream stream);
+
 /* JP-ADG priority (Section 4.1): key_out[v] = (batch[v] << 32) | h_seed(v)
  * (device, n uint64), where h_seed(v) is the upper 32 bits of the (v+1)-th
  * output of the SplitMix64 generator (Steele, Lea & Flood, OOPSLA 2014)

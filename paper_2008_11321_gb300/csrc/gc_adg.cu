@@ -20,6 +20,7 @@
 // power-law workloads, so the read-back is not on the bulk path.
 #include <climits>
 #include <cstring>
+#include <mutex>
 
 #include "gc_internal.cuh"
 
@@ -253,3 +254,110 @@ gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigne
 }
 
 }  // namespace gc
+
+// ---------------------------------------------------------------------------
+// gc_adg_partition_noalloc: the same ADG rounds on a fixed scratch area that
+// is compiled into the library, for callers that cannot allocate device
+// memory when they call in.  It has no context: it runs on the calling
+// thread's current device and launches the kernels above in the same order
+// as adg_run.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr long long kNoAllocMaxN = 1ll << 18;     // vertices
+constexpr long long kNoAllocMaxNnz = 1ll << 23;   // directed CSR entries
+constexpr long long kNoAllocTasks = kNoAllocMaxN + kNoAllocMaxNnz / gc::kChunk + 1;
+
+constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+// layout: control block | D | U list 0 | U list 1 | task starts | task lengths
+constexpr size_t kNaOffD = align256(sizeof(gc::AdgCtl));
+constexpr size_t kNaOffU0 = kNaOffD + align256(kNoAllocMaxN * sizeof(int));
+constexpr size_t kNaOffU1 = kNaOffU0 + align256(kNoAllocMaxN * sizeof(int));
+constexpr size_t kNaOffTs = kNaOffU1 + align256(kNoAllocMaxN * sizeof(int));
+constexpr size_t kNaOffTl = kNaOffTs + align256(kNoAllocTasks * sizeof(long long));
+constexpr size_t kNoAllocBytes = kNaOffTl + align256(kNoAllocTasks * sizeof(int));  // about 6.5 MB
+
+constexpr int kNoAllocDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_scratch[kNoAllocDevices];  // device address of the array, per device
+int g_noalloc_sms[kNoAllocDevices];
+
+}  // namespace
+
+// One copy per device that loads the library, held until the process exits.
+static __device__ __align__(256) unsigned char g_adg_noalloc_scratch[kNoAllocBytes];
+
+extern "C" gc_status gc_adg_partition_noalloc(const gc_csr* g, uint32_t eps_p, uint32_t eps_q,
+                                              int32_t* batch_out, int32_t* num_rounds_out,
+                                              gc_stream stream) {
+  using namespace gc;
+  if (!g || !num_rounds_out) return GC_ERR_INVALID_ARG;
+  if (g->n < 0 || g->nnz < 0 || (g->n > 0 && !g->row_ptr) || (g->nnz > 0 && !g->col_idx))
+    return GC_ERR_INVALID_ARG;
+  if (eps_q == 0 || eps_q > (1u << 20) || eps_p > (1u << 20)) return GC_ERR_INVALID_ARG;
+  if (g->n > kNoAllocMaxN || g->nnz > kNoAllocMaxNnz) return GC_ERR_OVERFLOW;
+  if (g->n > 0 && !batch_out) return GC_ERR_INVALID_ARG;
+  *num_rounds_out = 0;
+  const long long n = g->n, nnz = g->nnz;
+  if (n == 0) return GC_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+
+  // Set-up, once per device with that device current: the array's device
+  // address (its host-side name is not a device address).
+  int dev = -1;
+  GC_TRY_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocDevices) return GC_ERR_CUDA;
+  char* base = nullptr;
+  int num_sms = 0;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_scratch[dev]) {
+      void* p = nullptr;
+      GC_TRY_CUDA(cudaGetSymbolAddress(&p, g_adg_noalloc_scratch));
+      int sms = 0;
+      GC_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      g_noalloc_sms[dev] = sms;
+      g_noalloc_scratch[dev] = p;
+    }
+    base = static_cast<char*>(g_noalloc_scratch[dev]);
+    num_sms = g_noalloc_sms[dev];
+  }
+  AdgCtl* ctl = reinterpret_cast<AdgCtl*>(base);
+  int* D = reinterpret_cast<int*>(base + kNaOffD);
+  int* ubuf[2] = {reinterpret_cast<int*>(base + kNaOffU0), reinterpret_cast<int*>(base + kNaOffU1)};
+  long long* task_start = reinterpret_cast<long long*>(base + kNaOffTs);
+  int* task_len = reinterpret_cast<int*>(base + kNaOffTl);
+
+  // Every buffer above is written before it is read within a call; the
+  // control block, the only state carried between kernels, is reset here.
+  GC_TRY_CUDA(cudaMemsetAsync(batch_out, 0, sizeof(int) * n, s));
+  adg_init_kernel<<<1, 1, 0, s>>>(ctl, n, nnz, eps_p, eps_q);
+  GC_TRY_CUDA(cudaGetLastError());
+  const int max_blocks = num_sms * 8;
+  const long long* rp = reinterpret_cast<const long long*>(g->row_ptr);
+  long long size_u = n;
+  int cur = 0, round = 0;
+  while (size_u > 0) {
+    ++round;
+    const long long want = (size_u + kAdgThreads - 1) / kAdgThreads;
+    const int blocks = static_cast<int>(want < max_blocks ? want : max_blocks);
+    adg_partition_kernel<<<blocks, kAdgThreads, 0, s>>>(ctl, rp, D, batch_out,
+                                                        round == 1 ? nullptr : ubuf[cur ^ 1], ubuf[cur],
+                                                        task_start, task_len,
+                                                        round == 1 ? static_cast<int>(n) : 0);
+    GC_TRY_CUDA(cudaGetLastError());
+    adg_update_kernel<<<max_blocks, kAdgThreads, 0, s>>>(ctl, rp, g->col_idx, D, batch_out, task_start,
+                                                          task_len, round == 1 ? n : 0);
+    GC_TRY_CUDA(cudaGetLastError());
+    adg_finalize_kernel<<<1, 1, 0, s>>>(ctl);
+    GC_TRY_CUDA(cudaGetLastError());
+    int next = 0;  // |U| of the next round, read into ordinary host memory
+    GC_TRY_CUDA(cudaMemcpyAsync(&next, &ctl->size_U, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GC_TRY_CUDA(cudaStreamSynchronize(s));
+    if (next >= size_u) return GC_ERR_CUDA;  // cannot happen: every round removes a vertex
+    size_u = next;
+    cur ^= 1;
+  }
+  *num_rounds_out = round;
+  return GC_OK;
+}

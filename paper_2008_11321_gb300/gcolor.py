@@ -24,7 +24,7 @@ GC_ERR_CUDA, GC_ERR_TIMEOUT, GC_ERR_OVERFLOW = 4, 5, 6
 # Every symbol declared in include/gcolor.h.
 EXPORTS = ("gc_status_str", "gc_create", "gc_destroy", "gc_get_stats", "gc_set_timing",
            "gc_validate_csr", "gc_adg_partition", "gc_make_priority", "gc_jp_color",
-           "gc_color_graph", "gc_color_graph_host")
+           "gc_color_graph", "gc_color_graph_host", "gc_adg_partition_noalloc")
 
 
 class GcError(RuntimeError):
@@ -80,6 +80,8 @@ def load(path: str = LIB_PATH):
     lib.gc_jp_color.argtypes = [vp, P(gc_csr), vp, vp, P(i32), vp]
     lib.gc_color_graph.restype = ctypes.c_int
     lib.gc_color_graph.argtypes = [vp, P(gc_csr), u32, u32, u64, vp, vp, P(i32), P(i32), vp]
+    lib.gc_adg_partition_noalloc.restype = ctypes.c_int
+    lib.gc_adg_partition_noalloc.argtypes = [P(gc_csr), u32, u32, vp, P(i32), vp]
     lib.gc_color_graph_host.restype = ctypes.c_int
     lib.gc_color_graph_host.argtypes = [vp, i64, i64, vp, vp, u32, u32, u64, vp, vp, P(i32), P(i32), vp]
     _lib = lib
@@ -221,3 +223,17 @@ class Context:
             batch_out.ctypes.data if batch_out is not None and n else None,
             ctypes.byref(nc), ctypes.byref(nr), _stream(stream)), "gc_color_graph_host")
         return nc.value, nr.value
+
+
+def gc_adg_partition_noalloc(g: DeviceGraph, eps_p: int, eps_q: int, batch_out, stream=None) -> int:
+    """ADG without a context and without any device allocation (a fixed
+    scratch array inside the library bounds the graph to n <= 262144 and
+    nnz <= 8388608).  For callers that cannot allocate device memory when they
+    call in.  Runs on the current device; concurrent calls must not overlap
+    on the GPU.  Returns the number of rounds."""
+    c = g.csr()
+    rounds = ctypes.c_int32(0)
+    _check(load().gc_adg_partition_noalloc(ctypes.byref(c), eps_p, eps_q, _ptr(batch_out),
+                                           ctypes.byref(rounds), _stream(stream)),
+           "gc_adg_partition_noalloc")
+    return rounds.value

@@ -42,34 +42,53 @@ WORKLOADS = {
                         "no self-loops, eps=1/100, tie-break seed 42"),
     "rmat20": dict(kind="rmat", scale=20, ef=16, gen_seed=1, eps=(1, 100), seed=42,
                    desc="R-MAT scale 20, edge factor 16, (a,b,c,d)=(.57,.19,.19,.05), eps=1/100, seed 42"),
+    "rmat22": dict(kind="rmat", scale=22, ef=16, gen_seed=1, eps=(1, 100), seed=42,
+                   desc="R-MAT scale 22, edge factor 16, (a,b,c,d)=(.57,.19,.19,.05), eps=1/100, seed 42"),
     "grid256": dict(kind="grid3", k=256, perm_seed=7, eps=(1, 100), seed=42,
                     desc="3D 7-point grid 256^3, seeded vertex permutation, eps=1/100, seed 42"),
     "er": dict(kind="er", n=16384, m=81920, gen_seed=1, eps=(1, 100), seed=42,
                desc="Erdos-Renyi G(n=16384, m=81920), eps=1/100, seed 42"),
 }
 
-# JP colouring kernel, algorithmic bytes: per vertex row_ptr pair (16 B), own
-# batch (4 B), list entry (4 B) and colour write (4 B); per directed edge the
-# neighbour id (4 B) and its batch (4 B); per predecessor edge (half of them)
-# its colour (4 B).
-def jp_kernel_bytes(n, nnz):
-    return 28 * n + 8 * nnz + 4 * (nnz // 2)
+# Algorithmic bytes (what the method must move; random touches at 4 B) of the
+# three kernel groups that take the time, summed over their launches in one
+# step.  ADG's UPDATE sweeps every directed edge once over all rounds: the
+# neighbour id and the neighbour's state (8 B per edge) plus one decrement
+# per surviving neighbour (4 B).  The JP bulk kernels read, per vertex outside
+# the core, its row offsets, own batch, list entry and colour write (28 B), per
+# directed edge the neighbour id and its batch (8 B) and per predecessor edge
+# its colour (4 B; half of the edges).  The core block reads its compacted
+# 16-bit predecessor lists, the 8-byte list offsets and writes the colours.
+def group_bytes(n_nonisolated, nnz, st):
+    upd = 8 * nnz + 4 * st["sum_decrements"]
+    n_bulk = n_nonisolated - st["core_vertices"]
+    e_bulk = nnz - st["core_degree_sum"]
+    bulk = 28 * n_bulk + 8 * e_bulk + 4 * (e_bulk // 2)
+    core = 2 * st["core_preds"] + 12 * st["core_vertices"]
+    return {"adg_update_kernel": upd, "jp_color_kernel": bulk, "jpf_core_solve_kernel": core}
 
 
 # Whole path (ADG + JP), algorithmic bytes: ADG reads D and writes the
 # survivor list per vertex-round (8 * sum|U|), writes the batch (4n), reads the
-# row offsets of removed vertices (16n), streams col_idx (4 nnz), reads the
-# neighbour's batch (4 nnz) and decrements survivors (4 per decrement); JP as
-# above.
+# row offsets of removed vertices (16n), streams col_idx and the neighbours'
+# state (8 nnz) and decrements survivors (4 per decrement); JP reads row
+# offsets, own batch and writes the colour per vertex (28n), streams col_idx
+# and the neighbours' batch (8 nnz) and reads the predecessors' colours (2 nnz).
 def path_bytes(n, nnz, sum_u, decrements):
-    adg = 8 * sum_u + 4 * n + 16 * n + 4 * nnz + 4 * nnz + 4 * decrements
-    return adg + jp_kernel_bytes(n, nnz)
+    adg = 8 * sum_u + 4 * n + 16 * n + 8 * nnz + 4 * decrements
+    jp = 28 * n + 8 * nnz + 4 * (nnz // 2)
+    return adg + jp
 
 
-# DRAM traffic per launch of the JP colouring kernel from an ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum), by workload; None until a
-# capture of the current kernel exists.
-JP_KERNEL_TRAFFIC = {}
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# reported kernel from an ncu capture of the current code, by (workload,
+# kernel); empty until such a capture exists for the current kernels.
+KERNEL_TRAFFIC = {
+    # R-MAT scale 24 defaults, profiles/launches_rmat24.md (MB per launch)
+    ("rmat24", "jpf_core_solve_kernel"): 34.4e6,
+    ("rmat24", "adg_update_kernel"): 487.0e6,
+    ("rmat24", "jp_color_kernel"): 1480.4e6,
+}
 
 
 def load_peak():
@@ -266,6 +285,7 @@ def main():
     time.sleep(0.3)
 
     steps = []
+    n_nonisolated = int((g.degrees() > 0).sum())
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -274,8 +294,7 @@ def main():
     for _ in range(args.steps):
         nc, nr = ctx.gc_color_graph(dg, p, q, seed, color, batch)
         st = ctx.gc_get_stats()
-        steps.append((st.ms_adg, st.ms_jp, st.ms_jp_color, st.launches, st.sum_U, st.sum_decrements,
-                      st.jp_spins))
+        steps.append({k: getattr(st, k) for k, _ in st._fields_})
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     if world > 1:
@@ -315,14 +334,18 @@ def main():
             dist.destroy_process_group()
         return 0
 
-    ms_adg = statistics.mean(s[0] for s in steps)
-    ms_jp = statistics.mean(s[1] for s in steps)
-    ms_jpk = statistics.mean(s[2] for s in steps)
-    launches = sum(s[3] for s in steps)
-    sum_u, dec = steps[-1][4], steps[-1][5]
+    mean = lambda k: statistics.mean(x[k] for x in steps)  # noqa: E731
+    launches = sum(x["launches"] for x in steps)
+    last = steps[-1]
+    sum_u, dec = last["sum_U"], last["sum_decrements"]
     peak, peak_kind = load_peak()
-    kbytes = jp_kernel_bytes(n, nnz)
-    achieved = kbytes / (ms_jpk / 1e3) / 1e9
+    gb = group_bytes(n_nonisolated, nnz, last)
+    groups = {"adg_update_kernel": (mean("ms_adg_update"), last["adg_rounds"]),
+              "jp_color_kernel": (mean("ms_jp_color"), max(1, last["bulk_launches"])),
+              "jpf_core_solve_kernel": (mean("ms_core_solve"), 1)}
+    kname = max(groups, key=lambda k: groups[k][0])
+    kms, kl = groups[kname]
+    achieved = gb[kname] / (kms / 1e3) / 1e9 if kms > 0 else 0.0
     pbytes = path_bytes(n, nnz, sum_u, dec)
     path_gbs = pbytes / (t_max / args.steps) / 1e9
     line = {
@@ -333,12 +356,15 @@ def main():
                    "adg_rounds": nr, "num_colors": nc, "sum_U": sum_u, "decrements": dec,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": f"inputs larger than L2 (col_idx {4 * nnz / 1e9:.2f} GB), no flush"},
-        "roofline": {"bound": "hbm", "kernel": "jp_color_kernel", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": JP_KERNEL_TRAFFIC.get(args.workload),
-                     "algorithmic_bytes_per_launch": kbytes, "ms_per_launch": ms_jpk},
+                     "traffic": KERNEL_TRAFFIC.get((args.workload, kname)),
+                     "algorithmic_bytes_per_launch": gb[kname] / kl, "ms_per_launch": kms / kl,
+                     "launches_per_step": kl,
+                     "groups_ms": {k: v[0] for k, v in groups.items()}},
         "path": {"algorithmic_bytes_per_step": pbytes, "gbs": path_gbs, "frac": path_gbs / peak,
-                 "ms_adg": ms_adg, "ms_jp": ms_jp, "ms_jp_color": ms_jpk},
+                 "ms_adg": mean("ms_adg"), "ms_jp": mean("ms_jp"), "ms_core_preds": mean("ms_core_preds"),
+                 "core_vertices": last["core_vertices"], "core_preds": last["core_preds"]},
         "gpu_launches": launches,
         "clocks": clocks,
     }

@@ -86,8 +86,15 @@ typedef struct {
   int64_t jp_spins;        /* polls of uncoloured predecessors (diagnostic)    */
   float ms_adg;            /* device time of the ADG phase (0 if not timed)    */
   float ms_jp;             /* device time of the JP phase (0 if not timed)     */
-  float ms_jp_color;       /* device time of the JP colouring kernel alone     */
+  float ms_jp_color;       /* JP's bulk colouring launches, summed             */
   int32_t launches;        /* kernels this library launched in the last call   */
+  float ms_adg_update;     /* ADG's UPDATE launches (one per round), summed     */
+  float ms_core_solve;     /* the JP-ADG core block                            */
+  float ms_core_preds;     /* extraction of the core's predecessor lists       */
+  int32_t bulk_launches;   /* JP bulk launches (one per ADG batch outside core) */
+  int64_t core_vertices;   /* vertices coloured by the core block              */
+  int64_t core_preds;      /* predecessor entries of the core                  */
+  int64_t core_degree_sum; /* degree sum of the core vertices                  */
 } gc_stats;
 
 /* Human-readable name of a status code (static storage). */
@@ -103,8 +110,9 @@ void gc_destroy(gc_context *ctx);
 /* Statistics of the last successful colouring call on `ctx`. */
 gc_status gc_get_stats(const gc_context *ctx, gc_stats *out);
 
-/* When `enable` is non-zero, later calls time their ADG and JP phases with
- * CUDA events on their stream (reported in gc_stats); default off. */
+/* When `enable` is non-zero, later calls time their ADG and JP phases and
+ * their main kernel groups with CUDA events recorded on the call's stream
+ * (reported in gc_stats); default off. */
 gc_status gc_set_timing(gc_context *ctx, int enable);
 
 /* Check that `g` satisfies the graph model of Section 2.1: row_ptr starts at

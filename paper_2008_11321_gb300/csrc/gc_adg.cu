@@ -226,9 +226,11 @@ gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigne
         task_len, round == 1 ? static_cast<int>(n) : 0);
     ++g_launches;
     GC_TRY_CUDA(cudaGetLastError());
+    ctx->timer_begin(gc_context::kTUpdate, s);
     adg_update_kernel<<<max_blocks, kAdgThreads, 0, s>>>(ctl, row_ptr_of(g), g->col_idx, D, batch,
                                                           task_start, task_len, round == 1 ? n : 0);
     ++g_launches;
+    ctx->timer_end(s);
     GC_TRY_CUDA(cudaGetLastError());
     adg_finalize_kernel<<<1, 1, 0, s>>>(ctl);
     ++g_launches;

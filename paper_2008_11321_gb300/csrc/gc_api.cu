@@ -19,9 +19,21 @@ constexpr uint32_t kEpsMax = 1u << 20;
 // the context's statistics on exit.
 struct CallScope {
   gc_context* ctx;
-  explicit CallScope(gc_context* c) : ctx(c) { gc::g_launches = 0; }
+  explicit CallScope(gc_context* c) : ctx(c) {
+    gc::g_launches = 0;
+    ctx->tused = 0;
+    ctx->stats.bulk_launches = 0;
+    ctx->stats.core_vertices = 0;
+    ctx->stats.core_preds = 0;
+    ctx->stats.core_degree_sum = 0;
+  }
   ~CallScope() {
-    if (ctx) ctx->stats.launches = gc::g_launches;
+    if (!ctx) return;
+    ctx->stats.launches = gc::g_launches;
+    if (ctx->timing) {
+      if (ctx->tused > 0) cudaEventSynchronize(ctx->tev[2 * ctx->tused - 1]);
+      ctx->timers_collect();
+    }
   }
 };
 
@@ -210,6 +222,12 @@ gc_status gc_create(gc_context** out, int device) {
       return GC_ERR_CUDA;
     }
   }
+  for (auto& ev : ctx->tev) {
+    if (cudaEventCreate(&ev) != cudaSuccess) {
+      gc_destroy(ctx);
+      return GC_ERR_CUDA;
+    }
+  }
   *out = ctx;
   return GC_OK;
 }
@@ -223,6 +241,8 @@ void gc_destroy(gc_context* ctx) {
   if (ctx->h_graph) cudaFree(ctx->h_graph);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   for (auto& ev : ctx->ev)
+    if (ev) cudaEventDestroy(ev);
+  for (auto& ev : ctx->tev)
     if (ev) cudaEventDestroy(ev);
   delete ctx;
 }

@@ -64,6 +64,8 @@ struct JpCtl {
   unsigned long long base0;      // warp-path offset of the first bulk bucket
   unsigned long long base1;      // lane-path offset of the first bulk bucket
   long long bstar;               // last core bucket (-1: no core)
+  long long core_preds;          // predecessor entries of the core
+  unsigned long long core_deg;   // degree sum of the core vertices
   int max_color;
   int err;
 };
@@ -152,8 +154,38 @@ struct gc_context {
   void* h_graph = nullptr;
   size_t h_graph_bytes = 0;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  // kernel-group timers: event pairs recorded around launches when timing is
+  // on, summed per group after the call's final synchronisation
+  static constexpr int kTimerPairs = 128;
+  cudaEvent_t tev[2 * kTimerPairs] = {};
+  int tgroup[kTimerPairs] = {};
+  int tused = 0;
   gc_stats stats{};
 
+  enum TimerGroup { kTUpdate = 0, kTCoreSolve = 1, kTBulk = 2, kTCorePreds = 3 };
+  void timer_begin(int group, cudaStream_t s) {
+    if (!timing || tused >= kTimerPairs || !tev[2 * tused]) return;
+    tgroup[tused] = group;
+    cudaEventRecord(tev[2 * tused], s);
+  }
+  void timer_end(cudaStream_t s) {
+    if (!timing || tused >= kTimerPairs || !tev[2 * tused]) return;
+    cudaEventRecord(tev[2 * tused + 1], s);
+    ++tused;
+  }
+  // after the stream is synchronised
+  void timers_collect() {
+    float sum[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int i = 0; i < tused; ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, tev[2 * i], tev[2 * i + 1]) == cudaSuccess) sum[tgroup[i]] += ms;
+    }
+    stats.ms_adg_update = sum[kTUpdate];
+    stats.ms_core_solve = sum[kTCoreSolve];
+    stats.ms_jp_color = sum[kTBulk];
+    stats.ms_core_preds = sum[kTCorePreds];
+    tused = 0;
+  }
   gc_status reserve(size_t bytes);      // scratch arena
   gc_status reserve_vert(size_t bytes); // vbuf
   gc_status reserve_aux(size_t bytes);  // aux

@@ -471,9 +471,10 @@ __global__ void jpf_core_sort_kernel(const unsigned long long* __restrict__ cur_
 // Per core vertex: capacity of its predecessor list (degree at removal) and
 // the number of UPDATE-style edge chunks of its adjacency.
 __global__ void jpf_core_prep_kernel(const int* __restrict__ order, const int* __restrict__ D,
-                                     const long long* __restrict__ row_ptr, const JpCtl* ctl,
+                                     const long long* __restrict__ row_ptr, JpCtl* ctl,
                                      long long* __restrict__ cap, long long* __restrict__ ntask) {
   const long long kc = static_cast<long long>(ctl->ncore);
+  unsigned long long degsum = 0;
   for (long long i = gtid(); i <= kc; i += gstride()) {
     if (i == kc) {
       cap[i] = 0;
@@ -481,9 +482,13 @@ __global__ void jpf_core_prep_kernel(const int* __restrict__ order, const int* _
       continue;
     }
     const int v = order[i];
+    const long long deg = row_ptr[v + 1] - row_ptr[v];
     cap[i] = D[v];
-    ntask[i] = (row_ptr[v + 1] - row_ptr[v] + kChunk - 1) / kChunk;
+    ntask[i] = (deg + kChunk - 1) / kChunk;
+    degsum += static_cast<unsigned long long>(deg);
   }
+  degsum = warp_sum(degsum);
+  if ((threadIdx.x & 31) == 0 && degsum) atomicAdd(&ctl->core_deg, degsum);
 }
 
 __global__ void jpf_core_tasks_kernel(const int* __restrict__ order, const long long* __restrict__ row_ptr,
@@ -710,8 +715,9 @@ gc_status finish_jp(gc_context* ctx, JpCtl* ctl, int* num_colors_out, cudaStream
   JpCtl h;
   memcpy(&h, pin, sizeof(h));
   ctx->stats.jp_spins = static_cast<int64_t>(h.spins);
-  ctx->stats.ms_jp_color = 0.f;
-  if (ctx->timing) cudaEventElapsedTime(&ctx->stats.ms_jp_color, ctx->ev[3], ctx->ev[4]);
+  ctx->stats.core_vertices = static_cast<int64_t>(h.ncore);
+  ctx->stats.core_preds = h.core_preds;
+  ctx->stats.core_degree_sum = static_cast<int64_t>(h.core_deg);
   if (h.err != kDevOk) return GC_ERR_TIMEOUT;
   ctx->stats.num_colors = h.max_color;
   if (num_colors_out) *num_colors_out = h.max_color;
@@ -798,9 +804,10 @@ gc_status jp_run_given(gc_context* ctx, Arena a, const gc_csr* g, const unsigned
   ++g_launches;
   GC_TRY_CUDA(cudaGetLastError());
   GC_TRY_CUDA(cudaMemsetAsync(color, 0, sizeof(int) * n, s));
-  if (ctx->timing) GC_TRY_CUDA(cudaEventRecord(ctx->ev[3], s));
+  ctx->timer_begin(gc_context::kTBulk, s);
   GC_TRY_CUDA(launch_bulk(ctx, ctl, &ctl->big_cursor, rp, g->col_idx, key, plist, -1, nullptr, 0, color, s));
-  if (ctx->timing) GC_TRY_CUDA(cudaEventRecord(ctx->ev[4], s));
+  ctx->timer_end(s);
+  ctx->stats.bulk_launches = 1;
   return finish_jp(ctx, ctl, num_colors_out, s);
 }
 
@@ -908,14 +915,17 @@ gc_status jp_run_fused(gc_context* ctx, Arena a, const gc_csr* g, const int* bat
     GC_TRY_CUDA(cudaMemsetAsync(pcnt, 0, sizeof(int) * (kc + 1), s));
     jpf_core_tasks_kernel<<<blocks, 256, 0, s>>>(order, rp, toff, ctl, task_i, task_start, task_len);
     ++g_launches;
+    ctx->timer_begin(gc_context::kTCorePreds, s);
     jpf_core_preds_kernel<<<blocks, 256, 0, s>>>(g->col_idx, key, order, lid, toff, cap, ctl, task_i,
                                                  task_start, task_len, pcnt, preds);
     ++g_launches;
+    ctx->timer_end(s);
     long long* qoff = toff;  // task offsets are dead now
     jpf_counts_kernel<<<blocks, 256, 0, s>>>(pcnt, ctl, qoff);
     ++g_launches;
     GC_TRY_CUDA(cudaGetLastError());
     GC_TRY_CUDA(exclusive_scan_i64(qoff, qoff, kc + 1, temp, s));
+    GC_TRY_CUDA(cudaMemcpyAsync(&ctl->core_preds, qoff + kc, sizeof(long long), cudaMemcpyDeviceToDevice, s));
     jpf_compact_kernel<<<blocks, 256, 0, s>>>(preds, cap, qoff, ctl, cpreds);
     ++g_launches;
     GC_TRY_CUDA(cudaGetLastError());
@@ -923,15 +933,16 @@ gc_status jp_run_fused(gc_context* ctx, Arena a, const gc_csr* g, const int* bat
                         static_cast<size_t>(kc) * sizeof(unsigned short);
     GC_TRY_CUDA(cudaFuncSetAttribute(jpf_core_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(smem)));
+    ctx->timer_begin(gc_context::kTCoreSolve, s);
     jpf_core_solve_kernel<<<1, kCoreThreads, smem, s>>>(order, qoff, cpreds, ctl, color);
     ++g_launches;
+    ctx->timer_end(s);
     GC_TRY_CUDA(cudaGetLastError());
   }
 
   // 3. bulk, one batch at a time from the top: all predecessors in higher
   // batches are final when a batch starts, so its workers only ever wait on
   // vertices of their own batch
-  if (ctx->timing) GC_TRY_CUDA(cudaEventRecord(ctx->ev[3], s));
   const int* big_list = order + kc;
   const int* small_list = order + kc + nbig;
   for (int grp = 0; grp < bp.rounds; ++grp) {
@@ -943,11 +954,13 @@ gc_status jp_run_fused(gc_context* ctx, Arena a, const gc_csr* g, const int* bat
     range(0, base0, b0, b1);
     range(1, base1, s0, s1);
     if (b1 <= b0 && s1 <= s0) continue;
+    ctx->timer_begin(gc_context::kTBulk, s);
     GC_TRY_CUDA(launch_bulk(ctx, ctl, cursors + 2 * grp, rp, g->col_idx, key, big_list + b0,
                             static_cast<long long>(b1 > b0 ? b1 - b0 : 0), small_list + s0,
                             static_cast<long long>(s1 > s0 ? s1 - s0 : 0), color, s));
+    ctx->timer_end(s);
+    ++ctx->stats.bulk_launches;
   }
-  if (ctx->timing) GC_TRY_CUDA(cudaEventRecord(ctx->ev[4], s));
   return finish_jp(ctx, ctl, num_colors_out, s);
 }
 

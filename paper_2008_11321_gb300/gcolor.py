@@ -42,7 +42,11 @@ class gc_stats(ctypes.Structure):
     _fields_ = [("adg_rounds", ctypes.c_int32), ("num_colors", ctypes.c_int32),
                 ("sum_U", ctypes.c_int64), ("sum_decrements", ctypes.c_int64),
                 ("jp_spins", ctypes.c_int64), ("ms_adg", ctypes.c_float), ("ms_jp", ctypes.c_float),
-                ("ms_jp_color", ctypes.c_float), ("launches", ctypes.c_int32)]
+                ("ms_jp_color", ctypes.c_float), ("launches", ctypes.c_int32),
+                ("ms_adg_update", ctypes.c_float), ("ms_core_solve", ctypes.c_float),
+                ("ms_core_preds", ctypes.c_float), ("bulk_launches", ctypes.c_int32),
+                ("core_vertices", ctypes.c_int64), ("core_preds", ctypes.c_int64),
+                ("core_degree_sum", ctypes.c_int64)]
 
 
 _lib = None

@@ -189,6 +189,42 @@ gc_status gc_color_graph_host(gc_context *ctx, int64_t n, int64_t nnz, const int
                               int32_t *num_colors_out, int32_t *num_rounds_out,
                               gc_stream stream);
 
+/* A batch of graphs packed as one CSR: the disjoint union of the graphs.
+ * Graph g owns the vertices [graph_off[g], graph_off[g+1]) and every edge of
+ * a vertex stays inside its graph's range (not checked; edges across graphs
+ * make the per-graph results undefined).  col_idx holds union ids.  The
+ * graph_off array is device memory, non-decreasing, graph_off[0] = 0 and
+ * graph_off[num_graphs] = n; empty graphs are allowed. */
+typedef struct {
+  int64_t num_graphs;
+  int64_t n;                /* total vertices                       */
+  int64_t nnz;              /* total CSR entries                    */
+  const int64_t *row_ptr;   /* device, n+1                          */
+  const int32_t *col_idx;   /* device, nnz (union ids)              */
+  const int64_t *graph_off; /* device, num_graphs+1                 */
+} gc_batch_csr;
+
+/* Per-graph parameters of a batch: eps = eps_p / eps_q and the tie-break
+ * seed, as in gc_color_graph. */
+typedef struct {
+  uint32_t eps_p;
+  uint32_t eps_q;
+  uint64_t seed;
+} gc_job;
+
+/* JP-ADG for every graph of a batch at once.  ADG (Algorithm 1) keeps its
+ * degree sum, |U|, threshold and eps per graph, with one set of launches per
+ * round serving all graphs still running; JP (Algorithm 3) runs once on the
+ * union, each vertex's tie-break taken from its own graph's seed and its id
+ * inside that graph.  Each graph's batches and colours are exactly those
+ * gc_color_graph returns for it alone (batch ids and colours are local to the
+ * graph, both starting at 1).  jobs: host array of num_graphs entries.
+ * color_out: device, n int32 (required); batch_out: device, n int32, or NULL;
+ * num_colors_out / num_rounds_out: device, num_graphs int32 each, or NULL. */
+gc_status gc_color_batch(gc_context *ctx, const gc_batch_csr *b, const gc_job *jobs,
+                         int32_t *color_out, int32_t *batch_out, int32_t *num_colors_out,
+                         int32_t *num_rounds_out, gc_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,8 +5,8 @@ include/gcolor.h); ``gcolor`` is its thin ctypes binding.  Importing the
 package does not load the library: the first call does, and fails loudly if
 it is missing.
 """
-from .gcolor import (Context, DeviceGraph, GcError, GC_ERR_CUDA, GC_ERR_INVALID_ARG,  # noqa: F401
+from .gcolor import (Context, DeviceBatch, DeviceGraph, GcError, GC_ERR_CUDA, GC_ERR_INVALID_ARG,  # noqa: F401
                      GC_ERR_INVALID_GRAPH, GC_ERR_OOM, GC_ERR_OVERFLOW, GC_ERR_TIMEOUT, GC_OK,
                      EXPORTS, LIB_PATH, load, status_str)
 
-__all__ = ["Context", "DeviceGraph", "GcError", "load", "status_str", "EXPORTS", "LIB_PATH"]
+__all__ = ["Context", "DeviceBatch", "DeviceGraph", "GcError", "load", "status_str", "EXPORTS", "LIB_PATH"]

@@ -410,4 +410,20 @@ gc_status gc_color_graph_host(gc_context* ctx, int64_t n, int64_t nnz, const int
   return GC_OK;
 }
 
+gc_status gc_color_batch(gc_context* ctx, const gc_batch_csr* b, const gc_job* jobs, int32_t* color_out,
+                         int32_t* batch_out, int32_t* num_colors_out, int32_t* num_rounds_out,
+                         gc_stream stream) {
+  if (!ctx || !b || b->num_graphs < 1 || b->num_graphs > INT_MAX || !jobs || !b->graph_off)
+    return GC_ERR_INVALID_ARG;
+  if (b->n < 0 || b->nnz < 0 || b->n > static_cast<int64_t>(INT_MAX) - 1) return GC_ERR_INVALID_ARG;
+  if (b->n > 0 && (!b->row_ptr || !color_out)) return GC_ERR_INVALID_ARG;
+  if (b->nnz > 0 && !b->col_idx) return GC_ERR_INVALID_ARG;
+  for (int64_t g = 0; g < b->num_graphs; ++g) GC_TRY(check_eps(jobs[g].eps_p, jobs[g].eps_q));
+  DeviceGuard guard(ctx->device);
+  if (!guard.ok) return GC_ERR_CUDA;
+  CallScope scope(ctx);
+  return gc::batch_color(ctx, b, jobs, color_out, batch_out, num_colors_out, num_rounds_out,
+                         reinterpret_cast<cudaStream_t>(stream));
+}
+
 }  // extern "C"

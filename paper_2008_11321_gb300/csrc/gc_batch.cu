@@ -1,0 +1,383 @@
+// gc_color_batch: JP-ADG on many graphs at once.
+//
+// The graphs arrive packed as one CSR, their disjoint union: graph g owns the
+// vertices [graph_off[g], graph_off[g+1]) and its edges stay inside that
+// range.  ADG (Algorithm 1, Section 3) keeps its state per graph -- degree
+// sum, |U|, threshold, its own eps -- while one set of launches per round
+// serves every graph still running: all graphs start in round 1 together, so a
+// graph that is still running is always in the global round, and a graph
+// whose U is empty drops out.  JP (Algorithm 3, Section 4.1) then runs once on
+// the union with each vertex's tie-break computed from its own graph's seed
+// and its id inside that graph; as no edge joins two graphs, each graph's
+// colouring is exactly the one gc_color_graph gives it alone.
+#include <climits>
+#include <cstring>
+#include <vector>
+
+#include "gc_internal.cuh"
+
+namespace gc {
+namespace {
+
+constexpr int kBThreads = 256;
+
+// Per-graph ADG state (device).
+struct BGraph {
+  unsigned long long sigma;  // sum of D over the graph's U
+  unsigned long long sum_R;  // this round: sum of D over the graph's R
+  unsigned long long cut;    // this round: decrements inside the graph
+  int size_U;                // |U| of the graph (0: finished)
+  int size_Unext;            // this round: survivors
+  int T;                     // threshold of the current round
+  int rounds;                // rounds the graph needed (set when U empties)
+  unsigned p, q;             // the graph's eps = p / q
+  unsigned long long seed;   // the graph's tie-break seed
+};
+
+struct BCtl {
+  int round;        // global round (the round of every graph still running)
+  int size_Unext;   // survivors over all graphs
+  unsigned long long ntasks;
+};
+
+__device__ __forceinline__ int threshold_of(unsigned long long sigma, int size_u, unsigned p, unsigned q) {
+  if (size_u <= 0) return 0;
+  unsigned __int128 num = static_cast<unsigned __int128>(static_cast<unsigned long long>(q) + p) * sigma;
+  unsigned __int128 den = static_cast<unsigned __int128>(q) * static_cast<unsigned>(size_u);
+  unsigned __int128 t = num / den;
+  return t > static_cast<unsigned __int128>(INT_MAX) ? INT_MAX : static_cast<int>(t);
+}
+
+// The graph owning vertex v: the largest g with off[g] <= v.
+__device__ __forceinline__ int graph_of(const long long* __restrict__ off, int G, long long v) {
+  int lo = 0, hi = G - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(off + mid) <= v)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void batch_init_kernel(BGraph* __restrict__ gs, const gc_job* __restrict__ jobs, int G,
+                                  const long long* __restrict__ off, const long long* __restrict__ row_ptr,
+                                  BCtl* ctl) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+    BGraph b{};
+    const long long n = off[g + 1] - off[g];
+    b.sigma = static_cast<unsigned long long>(row_ptr[off[g + 1]] - row_ptr[off[g]]);
+    b.size_U = static_cast<int>(n);
+    b.p = jobs[g].eps_p;
+    b.q = jobs[g].eps_q;
+    b.seed = jobs[g].seed;
+    b.T = threshold_of(b.sigma, b.size_U, b.p, b.q);
+    b.rounds = 0;
+    gs[g] = b;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    BCtl c{};
+    c.round = 1;
+    *ctl = c;
+  }
+}
+
+// Sum of `x` over the lanes of `group` (a __match_any_sync class), 64-bit.
+__device__ __forceinline__ unsigned long long group_sum(unsigned group, unsigned long long x) {
+  const unsigned lo = __reduce_add_sync(group, static_cast<unsigned>(x & 0xffffu));
+  const unsigned mid = __reduce_add_sync(group, static_cast<unsigned>((x >> 16) & 0xffffu));
+  const unsigned hi = __reduce_add_sync(group, static_cast<unsigned>(x >> 32));
+  return static_cast<unsigned long long>(lo) + (static_cast<unsigned long long>(mid) << 16) +
+         (static_cast<unsigned long long>(hi) << 32);
+}
+
+__global__ void __launch_bounds__(kBThreads)
+batch_partition_kernel(BCtl* __restrict__ ctl, BGraph* __restrict__ gs, const long long* __restrict__ off,
+                       int G, const long long* __restrict__ row_ptr, int* __restrict__ D,
+                       int* __restrict__ batch, const int* __restrict__ u_in, int* __restrict__ u_out,
+                       long long* __restrict__ task_start, int* __restrict__ task_len,
+                       int* __restrict__ task_g, long long size_u) {
+  const int round = ctl->round;
+  const bool first = round == 1;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  for (long long base = static_cast<long long>(blockIdx.x) * blockDim.x; base < size_u; base += stride) {
+    const long long i = base + threadIdx.x;
+    const bool active = i < size_u;
+    int u = 0, d = 0, g = -1;
+    long long rs = 0, re = 0;
+    if (active) {
+      u = first ? static_cast<int>(i) : u_in[i];
+      g = graph_of(off, G, u);
+      if (first) {
+        rs = row_ptr[u];
+        re = row_ptr[u + 1];
+        d = static_cast<int>(re - rs);
+        D[u] = d;
+      } else {
+        d = D[u];
+      }
+    }
+    const int T = active ? gs[g].T : 0;
+    const bool in_r = active && d <= T;
+    const bool keep = active && !in_r;
+    // survivors -> U', counted per graph
+    const unsigned km = __ballot_sync(kFull, keep);
+    int kbase = 0;
+    if (lane == 0 && km) kbase = atomicAdd(&ctl->size_Unext, __popc(km));
+    kbase = __shfl_sync(kFull, kbase, 0);
+    if (keep) u_out[kbase + __popc(km & lt)] = u;
+    const unsigned grp = __match_any_sync(kFull, g);
+    const unsigned kgrp = grp & km;
+    if (keep && (kgrp & lt) == 0) atomicAdd(&gs[g].size_Unext, __popc(kgrp));
+    // removed -> batch id, per-graph sum of D
+    const unsigned rm = __ballot_sync(kFull, in_r);
+    const unsigned rgrp = grp & rm;
+    const unsigned long long dsum = group_sum(grp, in_r ? static_cast<unsigned long long>(d) : 0ull);
+    if (in_r) {
+      batch[u] = round;
+      if ((rgrp & lt) == 0) atomicAdd(&gs[g].sum_R, dsum);
+    }
+    if (first) continue;  // round 1 sweeps vertex tiles
+    int nt = 0;
+    if (in_r) {
+      rs = row_ptr[u];
+      re = row_ptr[u + 1];
+      nt = static_cast<int>((re - rs + kChunk - 1) / kChunk);
+    }
+    const int incl = warp_inclusive_scan(nt);
+    const int tot = __shfl_sync(kFull, incl, 31);
+    const int excl = incl - nt;
+    unsigned long long tbase = 0;
+    if (lane == 31 && tot) tbase = atomicAdd(&ctl->ntasks, static_cast<unsigned long long>(tot));
+    tbase = __shfl_sync(kFull, tbase, 31);
+    for (int b = 0; b < tot; b += 32) {
+      const int x = b + lane;
+      int j = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int c = j + step;
+        if (__shfl_sync(kFull, excl, c) <= x) j = c;
+      }
+      const long long st = __shfl_sync(kFull, rs, j) +
+                           static_cast<long long>(x - __shfl_sync(kFull, excl, j)) * kChunk;
+      const long long rej = __shfl_sync(kFull, re, j);
+      const int gj = __shfl_sync(kFull, g, j);
+      if (x < tot) {
+        task_start[tbase + x] = st;
+        task_len[tbase + x] = static_cast<int>(rej - st < kChunk ? rej - st : kChunk);
+        task_g[tbase + x] = gj;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBThreads)
+batch_update_kernel(BCtl* __restrict__ ctl, BGraph* __restrict__ gs, const long long* __restrict__ off,
+                    int G, const long long* __restrict__ row_ptr, const int* __restrict__ col,
+                    int* __restrict__ D, const int* __restrict__ batch,
+                    const long long* __restrict__ task_start, const int* __restrict__ task_len,
+                    const int* __restrict__ task_g, long long vertex_tiles_n) {
+  const int round = ctl->round;
+  const unsigned long long ntasks =
+      vertex_tiles_n > 0 ? static_cast<unsigned long long>(vertex_tiles_n) : ctl->ntasks;
+  const int lane = threadIdx.x & 31;
+  const unsigned long long gwarp = (static_cast<unsigned long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long nwarps = (static_cast<unsigned long long>(gridDim.x) * blockDim.x) >> 5;
+  // decrements counted per graph; a lane flushes its count when the graph of
+  // its edges changes (edges of one graph come in long runs)
+  int cur_g = -1;
+  unsigned long long cnt = 0;
+  for (unsigned long long tile = gwarp; tile * 32 < ntasks; tile += nwarps) {
+    const unsigned long long t = tile * 32 + lane;
+    long long st = 0;
+    int len = 0, tg = 0;
+    if (t < ntasks) {
+      if (vertex_tiles_n > 0) {
+        if (batch[t] == round) {
+          st = row_ptr[t];
+          len = static_cast<int>(row_ptr[t + 1] - st);
+          tg = graph_of(off, G, static_cast<long long>(t));
+        }
+      } else {
+        st = task_start[t];
+        len = task_len[t];
+        tg = task_g[t];
+      }
+    }
+    sweep_tile(st, len, tg, col, [&](int w, int g) {
+      if (__ldg(batch + w) == 0) {
+        atomicSub(&D[w], 1);
+        if (g != cur_g) {
+          if (cnt) atomicAdd(&gs[cur_g].cut, cnt);
+          cur_g = g;
+          cnt = 0;
+        }
+        ++cnt;
+      }
+    });
+  }
+  if (cnt) atomicAdd(&gs[cur_g].cut, cnt);
+}
+
+__global__ void batch_finalize_kernel(BCtl* ctl, BGraph* __restrict__ gs, int G) {
+  const int round = ctl->round;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+    BGraph c = gs[g];
+    if (c.size_U == 0) continue;
+    c.sigma = c.sigma - c.sum_R - c.cut;
+    c.size_U = c.size_Unext;
+    if (c.size_U == 0)
+      c.rounds = round;
+    else
+      c.T = threshold_of(c.sigma, c.size_U, c.p, c.q);
+    c.sum_R = 0;
+    c.cut = 0;
+    c.size_Unext = 0;
+    gs[g] = c;
+  }
+}
+
+__global__ void batch_next_round_kernel(BCtl* ctl) {
+  ctl->round += 1;
+  ctl->size_Unext = 0;
+  ctl->ntasks = 0;
+}
+
+// rho_R of every vertex from its graph's seed and its id inside the graph.
+__global__ void batch_tie_kernel(const BGraph* __restrict__ gs, const long long* __restrict__ off, int G,
+                                 long long n, unsigned* __restrict__ tiev) {
+  for (long long v = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; v < n;
+       v += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int g = graph_of(off, G, v);
+    tiev[v] = tie_hash(gs[g].seed, static_cast<unsigned>(v - off[g]));
+  }
+}
+
+// Largest colour and round count per graph.
+__global__ void batch_results_kernel(const BGraph* __restrict__ gs, const long long* __restrict__ off, int G,
+                                     long long n, const int* __restrict__ color, int* __restrict__ ncol,
+                                     int* __restrict__ nrounds) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+  for (long long base = static_cast<long long>(blockIdx.x) * blockDim.x; base < n;
+       base += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long v = base + threadIdx.x;
+    const bool active = v < n;
+    const int g = active ? graph_of(off, G, v) : -1;
+    const int c = active ? color[v] : 0;
+    const unsigned grp = __match_any_sync(kFull, g);
+    const int m = static_cast<int>(__reduce_max_sync(grp, static_cast<unsigned>(c)));
+    if (active && (grp & lt) == 0 && ncol) atomicMax(&ncol[g], m);
+    (void)lane;
+  }
+  if (nrounds)
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x)
+      nrounds[g] = gs[g].rounds;
+}
+
+}  // namespace
+
+size_t batch_adg_scratch_bytes(long long n, long long nnz, long long G) {
+  const long long ntask = n + nnz / kChunk + 1;
+  return 2 * (static_cast<size_t>(n) * 4 + 256) + static_cast<size_t>(ntask) * 16 + 1024 +
+         static_cast<size_t>(G) * (sizeof(BGraph) + sizeof(gc_job)) + 2048;
+}
+
+}  // namespace gc
+
+namespace gc {
+
+gc_status batch_color(gc_context* ctx, const gc_batch_csr* b, const gc_job* jobs, int32_t* color_out,
+                      int32_t* batch_out, int32_t* num_colors_out, int32_t* num_rounds_out, cudaStream_t s) {
+  const long long n = b->n, nnz = b->nnz;
+  const int G = static_cast<int>(b->num_graphs);
+  const long long* rp = reinterpret_cast<const long long*>(b->row_ptr);
+  const long long* off = reinterpret_cast<const long long*>(b->graph_off);
+  // state that lives through both phases: D, batch (if internal), rho_R per
+  // vertex, and the per-graph ADG state and jobs
+  const size_t vb = (static_cast<size_t>(n > 0 ? n : 1) * 4 + 255) & ~size_t(255);
+  const size_t gb = (static_cast<size_t>(G) * sizeof(BGraph) + 255) & ~size_t(255);
+  const size_t jb = (static_cast<size_t>(G) * sizeof(gc_job) + 255) & ~size_t(255);
+  GC_TRY(ctx->reserve_vert(3 * vb + gb + jb));
+  char* vbase = static_cast<char*>(ctx->vbuf);
+  int* D = reinterpret_cast<int*>(vbase);
+  int* bat = batch_out ? batch_out : reinterpret_cast<int*>(vbase + vb);
+  unsigned* tiev = reinterpret_cast<unsigned*>(vbase + 2 * vb);
+  BGraph* gs = reinterpret_cast<BGraph*>(vbase + 3 * vb);
+  gc_job* djobs = reinterpret_cast<gc_job*>(vbase + 3 * vb + gb);
+  GC_TRY(ctx->reserve(batch_adg_scratch_bytes(n, nnz, G)));
+  Arena a = ctx->arena();
+  BCtl* ctl = a.take<BCtl>(1);
+  int* ubuf[2] = {a.take<int>(n > 0 ? n : 1), a.take<int>(n > 0 ? n : 1)};
+  const long long ntask = n + nnz / kChunk + 1;
+  long long* task_start = a.take<long long>(ntask);
+  int* task_len = a.take<int>(ntask);
+  int* task_g = a.take<int>(ntask);
+  if (!ctl || !ubuf[0] || !ubuf[1] || !task_start || !task_len || !task_g) return GC_ERR_OOM;
+
+  GC_TRY_CUDA(cudaMemcpyAsync(djobs, jobs, sizeof(gc_job) * G, cudaMemcpyHostToDevice, s));
+  if (n > 0) GC_TRY_CUDA(cudaMemsetAsync(bat, 0, sizeof(int) * n, s));  // 0 = still in U
+  const int blocks = ctx->num_sms * 8;
+  batch_init_kernel<<<(G + 255) / 256, 256, 0, s>>>(gs, djobs, G, off, rp, ctl);
+  ++g_launches;
+  GC_TRY_CUDA(cudaGetLastError());
+
+  // ADG: one set of launches per round for every graph still running
+  ctx->timer_begin(gc_context::kTUpdate, s);
+  long long size_u = n;
+  int round = 0, cur = 0;
+  int* pin = static_cast<int*>(ctx->pinned);
+  while (size_u > 0) {
+    ++round;
+    const long long want = (size_u + kBThreads - 1) / kBThreads;
+    const int pblocks = static_cast<int>(want < blocks ? want : blocks);
+    batch_partition_kernel<<<pblocks, kBThreads, 0, s>>>(ctl, gs, off, G, rp, D, bat,
+                                                         round == 1 ? nullptr : ubuf[cur ^ 1], ubuf[cur],
+                                                         task_start, task_len, task_g, size_u);
+    ++g_launches;
+    batch_update_kernel<<<blocks, kBThreads, 0, s>>>(ctl, gs, off, G, rp, b->col_idx, D, bat, task_start,
+                                                     task_len, task_g, round == 1 ? n : 0);
+    ++g_launches;
+    batch_finalize_kernel<<<(G + 255) / 256, 256, 0, s>>>(ctl, gs, G);
+    ++g_launches;
+    GC_TRY_CUDA(cudaGetLastError());
+    GC_TRY_CUDA(cudaMemcpyAsync(pin, &ctl->size_Unext, sizeof(int), cudaMemcpyDeviceToHost, s));
+    batch_next_round_kernel<<<1, 1, 0, s>>>(ctl);
+    ++g_launches;
+    GC_TRY_CUDA(cudaStreamSynchronize(s));
+    const long long next = *pin;
+    if (next >= size_u) return GC_ERR_CUDA;  // cannot happen: every running graph removes a vertex
+    size_u = next;
+    cur ^= 1;
+  }
+  ctx->timer_end(s);
+  ctx->stats.adg_rounds = round;
+  if (n == 0) return GC_OK;
+  batch_tie_kernel<<<blocks, 256, 0, s>>>(gs, off, G, n, tiev);
+  ++g_launches;
+  GC_TRY_CUDA(cudaGetLastError());
+
+  // JP on the union
+  gc_csr u;
+  u.n = n;
+  u.nnz = nnz;
+  u.row_ptr = b->row_ptr;
+  u.col_idx = b->col_idx;
+  GC_TRY(ctx->reserve(jpadg_scratch_bytes(n, nnz, round)));
+  int colors = 0;
+  GC_TRY(jp_run_packed(ctx, ctx->arena(), &u, bat, tiev, D, round, color_out, &colors, s));
+
+  if (num_colors_out || num_rounds_out) {
+    if (num_colors_out) GC_TRY_CUDA(cudaMemsetAsync(num_colors_out, 0, sizeof(int) * G, s));
+    batch_results_kernel<<<blocks, 256, 0, s>>>(gs, off, G, n, color_out, num_colors_out, num_rounds_out);
+    ++g_launches;
+    GC_TRY_CUDA(cudaGetLastError());
+    GC_TRY_CUDA(cudaStreamSynchronize(s));
+  }
+  return GC_OK;
+}
+
+}  // namespace gc

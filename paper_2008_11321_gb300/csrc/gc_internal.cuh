@@ -126,6 +126,14 @@ gc_status jp_run_fused(gc_context* ctx, Arena a, const gc_csr* g, const int* bat
                        cudaStream_t s);
 gc_status jp_run_given(gc_context* ctx, Arena a, const gc_csr* g, const unsigned long long* prio,
                        int* color, int* num_colors_out, cudaStream_t s);
+// gc_color_batch body (gc_batch.cu).
+size_t batch_adg_scratch_bytes(long long n, long long nnz, long long G);
+gc_status batch_color(gc_context* ctx, const gc_batch_csr* b, const gc_job* jobs, int32_t* color_out,
+                      int32_t* batch_out, int32_t* num_colors_out, int32_t* num_rounds_out, cudaStream_t s);
+
+// JP-ADG on the disjoint union of many graphs: tiev[v] is v's tie-break.
+gc_status jp_run_packed(gc_context* ctx, Arena a, const gc_csr* g, const int* batch, const unsigned* tiev,
+                        const int* D, int rounds, int* color, int* num_colors_out, cudaStream_t s);
 cudaError_t make_priority(const int* batch, long long n, unsigned long long seed,
                           unsigned long long* key, int num_sms, cudaStream_t s);
 

@@ -51,12 +51,23 @@ constexpr unsigned kBigBit = 0x80000000u;
 constexpr int kCoreThreads = 1024;
 constexpr int kCoreWarps = kCoreThreads / kWarp;
 
-struct KeyFused {  // JP-ADG: (batch << 32) | rho_R(v)
+struct KeyFused {  // JP-ADG: (batch << 32) | rho_R(v), rho_R from one seed
   const int* batch;
   unsigned long long seed;
+  __device__ __forceinline__ int bat(int v) const { return __ldg(batch + v); }
+  __device__ __forceinline__ unsigned tie(int v) const { return tie_hash(seed, static_cast<unsigned>(v)); }
   __device__ __forceinline__ unsigned long long operator()(int v) const {
-    return (static_cast<unsigned long long>(static_cast<unsigned>(__ldg(batch + v))) << 32) |
-           tie_hash(seed, static_cast<unsigned>(v));
+    return (static_cast<unsigned long long>(static_cast<unsigned>(bat(v))) << 32) | tie(v);
+  }
+};
+
+struct KeyPacked {  // JP-ADG over many disjoint graphs: rho_R precomputed per vertex
+  const int* batch;
+  const unsigned* tiev;
+  __device__ __forceinline__ int bat(int v) const { return __ldg(batch + v); }
+  __device__ __forceinline__ unsigned tie(int v) const { return __ldg(tiev + v); }
+  __device__ __forceinline__ unsigned long long operator()(int v) const {
+    return (static_cast<unsigned long long>(static_cast<unsigned>(bat(v))) << 32) | tie(v);
   }
 };
 
@@ -353,9 +364,9 @@ __device__ __forceinline__ long long bucket_of(int batch, unsigned h, const Buck
   return bp.hb == 0 ? hi : hi | static_cast<long long>((~h) >> (32 - bp.hb));
 }
 
+template <class Key>
 __global__ void __launch_bounds__(256)
-jpf_hist_kernel(const int* __restrict__ batch, unsigned long long seed,
-                const long long* __restrict__ row_ptr, long long n, BucketPlan bp,
+jpf_hist_kernel(Key key, const long long* __restrict__ row_ptr, long long n, BucketPlan bp,
                 unsigned long long* __restrict__ cnt, int* __restrict__ color, JpCtl* ctl) {
   bool isolated = false;
   for (long long v = gtid(); v < n; v += gstride()) {
@@ -366,7 +377,7 @@ jpf_hist_kernel(const int* __restrict__ batch, unsigned long long seed,
       continue;
     }
     color[v] = 0;
-    const long long b = bucket_of(batch[v], tie_hash(seed, static_cast<unsigned>(v)), bp);
+    const long long b = bucket_of(key.bat(static_cast<int>(v)), key.tie(static_cast<int>(v)), bp);
     const long long cls = deg > kSmallDeg ? 0 : 1;
     atomicAdd(&cnt[cls * (bp.B + 1) + b], 1ull);
   }
@@ -419,9 +430,9 @@ __global__ void jpf_batch_bounds_kernel(const unsigned long long* __restrict__ o
 // Places every non-isolated vertex: core buckets into order[0, ncore), the
 // rest into the warp-path list order[ncore, ncore + nbig) and the lane-path
 // list after it.  Cursors are the exclusive scans, advanced atomically.
+template <class Key>
 __global__ void __launch_bounds__(256)
-jpf_scatter_kernel(const int* __restrict__ batch, unsigned long long seed,
-                   const long long* __restrict__ row_ptr, long long n, BucketPlan bp,
+jpf_scatter_kernel(Key key, const long long* __restrict__ row_ptr, long long n, BucketPlan bp,
                    unsigned long long* cur_tot, unsigned long long* cur_cls, const JpCtl* ctl,
                    int* __restrict__ order) {
   const long long bs = ctl->bstar;
@@ -430,7 +441,7 @@ jpf_scatter_kernel(const int* __restrict__ batch, unsigned long long seed,
   for (long long v = gtid(); v < n; v += gstride()) {
     const long long deg = row_ptr[v + 1] - row_ptr[v];
     if (deg == 0) continue;
-    const long long b = bucket_of(batch[v], tie_hash(seed, static_cast<unsigned>(v)), bp);
+    const long long b = bucket_of(key.bat(static_cast<int>(v)), key.tie(static_cast<int>(v)), bp);
     unsigned long long pos;
     if (b <= bs) {
       pos = atomicAdd(&cur_tot[b], 1ull);
@@ -445,8 +456,9 @@ jpf_scatter_kernel(const int* __restrict__ batch, unsigned long long seed,
 
 // Exact order inside each core bucket (the buckets are tiny): insertion sort
 // by (rho_R, id) descending; then lid[v] = position of v in the core.
+template <class Key>
 __global__ void jpf_core_sort_kernel(const unsigned long long* __restrict__ cur_tot, const JpCtl* ctl,
-                                     KeyFused key, int* __restrict__ order, int* __restrict__ lid) {
+                                     Key key, int* __restrict__ order, int* __restrict__ lid) {
   const long long bs = ctl->bstar;
   for (long long b = gtid(); b <= bs; b += gstride()) {
     // after the scatter, cur_tot[b] is the end of bucket b
@@ -510,8 +522,9 @@ __global__ void jpf_core_tasks_kernel(const int* __restrict__ order, const long 
 
 // Predecessor lists of the core in core-local ids, edges spread over the
 // lanes of each warp across 32 tasks at a time (as in ADG's UPDATE).
+template <class Key>
 __global__ void __launch_bounds__(256)
-jpf_core_preds_kernel(const int* __restrict__ col, KeyFused key, const int* __restrict__ order,
+jpf_core_preds_kernel(const int* __restrict__ col, Key key, const int* __restrict__ order,
                       const int* __restrict__ lid, const long long* __restrict__ toff,
                       const long long* __restrict__ poff, const JpCtl* ctl,
                       const int* __restrict__ task_i, const long long* __restrict__ task_start,
@@ -826,9 +839,10 @@ size_t jpadg_scratch_bytes(long long n, long long nnz, int rounds) {
          (kc * 4 + 256) + ntask * 16 + 3 * 256 + sc * 8 + 4096;
 }
 
-gc_status jp_run_fused(gc_context* ctx, Arena a, const gc_csr* g, const int* batch, const int* D,
-                       int rounds, unsigned long long seed, int* color, int* num_colors_out,
-                       cudaStream_t s) {
+namespace {
+template <class Key>
+gc_status jp_adg_impl(gc_context* ctx, Arena a, const gc_csr* g, const Key& key, const int* D,
+                      int rounds, int* color, int* num_colors_out, cudaStream_t s) {
   const long long n = g->n, nnz = g->nnz;
   if (num_colors_out) *num_colors_out = 0;
   ctx->stats.num_colors = 0;
@@ -856,7 +870,6 @@ gc_status jp_run_fused(gc_context* ctx, Arena a, const gc_csr* g, const int* bat
       !task_len || !temp || !bounds || !cursors)
     return GC_ERR_OOM;
   const long long* rp = row_ptr_of(g);
-  const KeyFused key{batch, seed};
   const int blocks = ctx->num_sms * 8;
   long long* cnt_ll = reinterpret_cast<long long*>(cnt);
   long long* tot_ll = reinterpret_cast<long long*>(tot);
@@ -865,7 +878,7 @@ gc_status jp_run_fused(gc_context* ctx, Arena a, const gc_csr* g, const int* bat
   jp_init_kernel<<<1, 1, 0, s>>>(ctl);
   ++g_launches;
   GC_TRY_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * 2 * nb, s));
-  jpf_hist_kernel<<<blocks, 256, 0, s>>>(batch, seed, rp, n, bp, cnt, color, ctl);
+  jpf_hist_kernel<<<blocks, 256, 0, s>>>(key, rp, n, bp, cnt, color, ctl);
   ++g_launches;
   jpf_total_kernel<<<blocks, 256, 0, s>>>(cnt, bp.B, tot);
   ++g_launches;
@@ -881,7 +894,7 @@ gc_status jp_run_fused(gc_context* ctx, Arena a, const gc_csr* g, const int* bat
   jpf_batch_bounds_kernel<<<(bp.rounds + 256) / 256, 256, 0, s>>>(cnt, bp, bounds);
   ++g_launches;
   GC_TRY_CUDA(cudaMemsetAsync(cursors, 0, sizeof(unsigned long long) * 2 * bp.rounds, s));
-  jpf_scatter_kernel<<<blocks, 256, 0, s>>>(batch, seed, rp, n, bp, tot, cnt, ctl, order);
+  jpf_scatter_kernel<<<blocks, 256, 0, s>>>(key, rp, n, bp, tot, cnt, ctl, order);
   ++g_launches;
   jpf_core_sort_kernel<<<blocks, 256, 0, s>>>(tot, ctl, key, order, lid);
   ++g_launches;
@@ -962,6 +975,19 @@ gc_status jp_run_fused(gc_context* ctx, Arena a, const gc_csr* g, const int* bat
     ++ctx->stats.bulk_launches;
   }
   return finish_jp(ctx, ctl, num_colors_out, s);
+}
+
+}  // namespace
+
+gc_status jp_run_fused(gc_context* ctx, Arena a, const gc_csr* g, const int* batch, const int* D,
+                       int rounds, unsigned long long seed, int* color, int* num_colors_out,
+                       cudaStream_t s) {
+  return jp_adg_impl(ctx, a, g, KeyFused{batch, seed}, D, rounds, color, num_colors_out, s);
+}
+
+gc_status jp_run_packed(gc_context* ctx, Arena a, const gc_csr* g, const int* batch, const unsigned* tiev,
+                        const int* D, int rounds, int* color, int* num_colors_out, cudaStream_t s) {
+  return jp_adg_impl(ctx, a, g, KeyPacked{batch, tiev}, D, rounds, color, num_colors_out, s);
 }
 
 cudaError_t make_priority(const int* batch, long long n, unsigned long long seed,

@@ -24,7 +24,7 @@ GC_ERR_CUDA, GC_ERR_TIMEOUT, GC_ERR_OVERFLOW = 4, 5, 6
 # Every symbol declared in include/gcolor.h.
 EXPORTS = ("gc_status_str", "gc_create", "gc_destroy", "gc_get_stats", "gc_set_timing",
            "gc_validate_csr", "gc_adg_partition", "gc_make_priority", "gc_jp_color",
-           "gc_color_graph", "gc_color_graph_host", "gc_adg_partition_noalloc")
+           "gc_color_graph", "gc_color_graph_host", "gc_adg_partition_noalloc", "gc_color_batch")
 
 
 class GcError(RuntimeError):
@@ -36,6 +36,15 @@ class GcError(RuntimeError):
 class gc_csr(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p)]
+
+
+class gc_batch_csr(ctypes.Structure):
+    _fields_ = [("num_graphs", ctypes.c_int64), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p), ("graph_off", ctypes.c_void_p)]
+
+
+class gc_job(ctypes.Structure):
+    _fields_ = [("eps_p", ctypes.c_uint32), ("eps_q", ctypes.c_uint32), ("seed", ctypes.c_uint64)]
 
 
 class gc_stats(ctypes.Structure):
@@ -86,6 +95,8 @@ def load(path: str = LIB_PATH):
     lib.gc_color_graph.argtypes = [vp, P(gc_csr), u32, u32, u64, vp, vp, P(i32), P(i32), vp]
     lib.gc_adg_partition_noalloc.restype = ctypes.c_int
     lib.gc_adg_partition_noalloc.argtypes = [P(gc_csr), u32, u32, vp, P(i32), vp]
+    lib.gc_color_batch.restype = ctypes.c_int
+    lib.gc_color_batch.argtypes = [vp, P(gc_batch_csr), P(gc_job), vp, vp, vp, vp, vp]
     lib.gc_color_graph_host.restype = ctypes.c_int
     lib.gc_color_graph_host.argtypes = [vp, i64, i64, vp, vp, u32, u32, u64, vp, vp, P(i32), P(i32), vp]
     _lib = lib
@@ -138,6 +149,53 @@ class DeviceGraph:
         rp = torch.from_numpy(np.ascontiguousarray(g.row_ptr, dtype=np.int64)).to(device)
         ci = torch.from_numpy(np.ascontiguousarray(g.col_idx, dtype=np.int32)).to(device)
         return cls(rp, ci)
+
+
+@dataclass
+class DeviceBatch:
+    """Graphs packed as their disjoint union (CUDA tensors): row_ptr[n+1],
+    col_idx[nnz] with union ids, graph_off[num_graphs+1]."""
+    row_ptr: "object"
+    col_idx: "object"
+    graph_off: "object"
+
+    @property
+    def num_graphs(self) -> int:
+        return int(self.graph_off.shape[0]) - 1
+
+    @property
+    def n(self) -> int:
+        return int(self.row_ptr.shape[0]) - 1
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col_idx.shape[0])
+
+    def csr(self) -> gc_batch_csr:
+        return gc_batch_csr(self.num_graphs, self.n, self.nnz, self.row_ptr.data_ptr(),
+                            self.col_idx.data_ptr() if self.nnz else None, self.graph_off.data_ptr())
+
+    @staticmethod
+    def pack_host(graphs):
+        """Host arrays (row_ptr, col_idx, graph_off) of the disjoint union."""
+        nv = np.array([g.n for g in graphs], dtype=np.int64)
+        ne = np.array([g.nnz for g in graphs], dtype=np.int64)
+        voff = np.concatenate([[0], np.cumsum(nv)]).astype(np.int64)
+        eoff = np.concatenate([[0], np.cumsum(ne)]).astype(np.int64)
+        rp = np.empty(int(voff[-1]) + 1, dtype=np.int64)
+        ci = np.empty(int(eoff[-1]), dtype=np.int32)
+        for i, g in enumerate(graphs):
+            rp[voff[i]:voff[i + 1]] = g.row_ptr[:-1] + eoff[i]
+            ci[eoff[i]:eoff[i + 1]] = g.col_idx + np.int32(voff[i])
+        rp[-1] = eoff[-1]
+        return rp, ci, voff
+
+    @classmethod
+    def from_host(cls, graphs, device="cuda"):
+        import torch
+        rp, ci, voff = cls.pack_host(graphs)
+        return cls(torch.from_numpy(rp).to(device), torch.from_numpy(ci).to(device),
+                   torch.from_numpy(voff).to(device))
 
 
 class Context:
@@ -211,6 +269,15 @@ class Context:
                                         _ptr(color_out), _ptr(batch_out), ctypes.byref(nc),
                                         ctypes.byref(nr), _stream(stream)), "gc_color_graph")
         return nc.value, nr.value
+
+    def gc_color_batch(self, b: DeviceBatch, jobs, color_out, batch_out=None, num_colors_out=None,
+                       num_rounds_out=None, stream=None):
+        """jobs: sequence of (eps_p, eps_q, seed), one per graph."""
+        c = b.csr()
+        arr = (gc_job * b.num_graphs)(*[gc_job(int(p), int(q), int(sd)) for p, q, sd in jobs])
+        _check(self._lib.gc_color_batch(self.handle, ctypes.byref(c), arr, _ptr(color_out), _ptr(batch_out),
+                                        _ptr(num_colors_out), _ptr(num_rounds_out), _stream(stream)),
+               "gc_color_batch")
 
     def gc_color_graph_host(self, row_ptr: np.ndarray, col_idx: np.ndarray, eps_p: int, eps_q: int,
                             seed: int, color_out: np.ndarray, batch_out: np.ndarray | None = None,

@@ -1,0 +1,79 @@
+"""gc_color_batch: every graph of a packed batch gets exactly the batches,
+round count, colours and colour count that the oracle (and gc_color_graph
+on the graph alone) give it with its own eps and seed."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from _fixtures import complete, empty, path, star
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2008_11321_gb300 as gcp  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2008_11321_gb300 import _build
+    _build.build()
+    c = gcp.Context(0)
+    yield c
+    c.close()
+
+
+def _mixed(count, seed):
+    graphs = []
+    for i, (fam, n) in enumerate(gg.batch_recipe(count, 100, 20000, seed)):
+        graphs.append(gg.make_batch_graph(fam, n, seed + i))
+    return graphs
+
+
+def _run(ctx, graphs, jobs):
+    db = gcp.DeviceBatch.from_host(graphs, "cuda:0")
+    color = torch.full((db.n,), -5, dtype=torch.int32, device="cuda:0")
+    batch = torch.full((db.n,), -5, dtype=torch.int32, device="cuda:0")
+    ncol = torch.full((db.num_graphs,), -5, dtype=torch.int32, device="cuda:0")
+    nrnd = torch.full((db.num_graphs,), -5, dtype=torch.int32, device="cuda:0")
+    ctx.gc_color_batch(db, jobs, color, batch, ncol, nrnd)
+    torch.cuda.synchronize()
+    voff = db.graph_off.cpu().numpy()
+    return color.cpu().numpy(), batch.cpu().numpy(), ncol.cpu().numpy(), nrnd.cpu().numpy(), voff
+
+
+def test_batch_matches_oracle_per_graph(ctx):
+    graphs = _mixed(40, 7) + [empty(0), empty(5), complete(30), star(40), path(7), gg.rmat(12, 8, seed=3)]
+    jobs = [((1, 100) if i % 3 else (1, 10)) + (42 + i,) for i in range(len(graphs))]
+    color, batch, ncol, nrnd, voff = _run(ctx, graphs, jobs)
+    for i, g in enumerate(graphs):
+        p, q, sd = jobs[i]
+        ob, oc, onr, onc = oracle.jp_adg(g, p, q, sd)
+        sl = slice(voff[i], voff[i + 1])
+        assert np.array_equal(batch[sl], ob), i
+        assert np.array_equal(color[sl], oc), i
+        assert nrnd[i] == onr and ncol[i] == onc, (i, nrnd[i], onr, ncol[i], onc)
+
+
+def test_batch_equals_single_graph_calls(ctx):
+    graphs = _mixed(12, 99)
+    jobs = [(1, 100, 42 + i) for i in range(len(graphs))]
+    color, batch, _, _, voff = _run(ctx, graphs, jobs)
+    for i, g in enumerate(graphs):
+        dg = gcp.DeviceGraph.from_host(g, "cuda:0")
+        c1 = torch.empty(g.n, dtype=torch.int32, device="cuda:0")
+        ctx.gc_color_graph(dg, 1, 100, 42 + i, c1)
+        assert np.array_equal(color[voff[i]:voff[i + 1]], c1.cpu().numpy()), i
+
+
+def test_batch_twice_same_result(ctx):
+    graphs = _mixed(20, 5)
+    jobs = [(1, 100, 7 * i) for i in range(len(graphs))]
+    a = _run(ctx, graphs, jobs)
+    b = _run(ctx, graphs, jobs)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)

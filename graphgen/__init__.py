@@ -66,6 +66,10 @@ def _load():
         lib.gg_permute.argtypes = [vp, u64]
         lib.gg_draw.restype = u64
         lib.gg_draw.argtypes = [u64, u64, u64]
+        lib.gg_batch_recipe.restype = None
+        lib.gg_batch_recipe.argtypes = [i64, i64, i64, u64, vp, vp]
+        lib.gg_batch.restype = vp
+        lib.gg_batch.argtypes = [i64, i64, i64, u64, vp]
         _lib = lib
     return _lib
 
@@ -162,14 +166,20 @@ def batch_recipe(num_graphs: int, n_lo: int = 100, n_hi: int = 200_000, seed: in
     """Per-graph (family, n) for the batched workload: n log-uniform in
     [n_lo, n_hi]; family uniform over Erdos-Renyi (average degree 8),
     Barabasi-Albert (m=4) and 2D grids (k = ceil(sqrt(n)))."""
-    out = []
-    lo, hi = math.log(n_lo), math.log(n_hi)
-    for g in range(num_graphs):
-        u = (draw(seed, 11, 2 * g) >> 11) / float(1 << 53)
-        n = int(round(math.exp(lo + u * (hi - lo))))
-        fam = ("er", "ba", "grid")[draw(seed, 11, 2 * g + 1) % 3]
-        out.append((fam, n))
-    return out
+    fam = np.zeros(num_graphs, dtype=np.int32)
+    nv = np.zeros(num_graphs, dtype=np.int64)
+    _load().gg_batch_recipe(num_graphs, n_lo, n_hi, seed, fam.ctypes.data, nv.ctypes.data)
+    names = ("er", "ba", "grid")
+    return [(names[f], int(n)) for f, n in zip(fam, nv)]
+
+
+def batch(num_graphs: int, n_lo: int = 100, n_hi: int = 200_000, seed: int = 42, pinned: bool = False):
+    """The batched workload, generated in parallel and packed as the disjoint
+    union: returns (Graph of the union, graph_off int64[num_graphs+1]).  Graph
+    g equals make_batch_graph(*batch_recipe(...)[g], seed + g)."""
+    off = np.zeros(num_graphs + 1, dtype=np.int64)
+    h = _load().gg_batch(num_graphs, n_lo, n_hi, seed, off.ctypes.data)
+    return _take(h, f"batch{num_graphs}", pinned), off
 
 
 def make_batch_graph(fam: str, n: int, seed: int) -> Graph:

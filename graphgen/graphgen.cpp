@@ -20,6 +20,7 @@
 //   any of them relabelled by a seeded Fisher-Yates permutation
 #include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -382,5 +383,73 @@ gg_graph* gg_permute(const gg_graph* g, uint64_t seed) {
 // Uniform 64-bit draw k of stream s (exposed so that Python-side recipes,
 // such as the per-graph sizes of a batched workload, use the same generator).
 uint64_t gg_draw(uint64_t seed, uint64_t stream, uint64_t k) { return draw(seed, stream, k); }
+
+// Recipe of a batched workload: graph g has n log-uniform in [n_lo, n_hi]
+// (from draw 2g of stream 11) and family draw(2g+1) % 3: 0 = Erdos-Renyi with
+// m = 4n (average degree 8), 1 = Barabasi-Albert with m = 4, 2 = 2D grid with
+// k = ceil(sqrt(n)) per side.
+void gg_batch_recipe(int64_t count, int64_t n_lo, int64_t n_hi, uint64_t seed, int32_t* fam, int64_t* n) {
+  const double lo = std::log(static_cast<double>(n_lo)), hi = std::log(static_cast<double>(n_hi));
+  for (int64_t g = 0; g < count; ++g) {
+    const double u = static_cast<double>(draw(seed, 11, 2 * g) >> 11) / 9007199254740992.0;
+    n[g] = static_cast<int64_t>(std::llround(std::exp(lo + u * (hi - lo))));
+    fam[g] = static_cast<int32_t>(draw(seed, 11, 2 * g + 1) % 3);
+  }
+}
+
+// The whole batched workload generated in parallel (graphs over threads) and
+// packed as the disjoint union: graph g is generated with seed `seed + g`.
+gg_graph* gg_batch(int64_t count, int64_t n_lo, int64_t n_hi, uint64_t seed, int64_t* graph_off) {
+  std::vector<int32_t> fam(count);
+  std::vector<int64_t> nv(count);
+  gg_batch_recipe(count, n_lo, n_hi, seed, fam.data(), nv.data());
+  std::vector<Csr> parts(count);
+  std::atomic<int> bad{0};
+  std::atomic<int64_t> next{0};
+  std::vector<std::thread> pool;
+  const int T = num_threads();
+  for (int t = 0; t < T; ++t)
+    pool.emplace_back([&] {
+      for (;;) {
+        const int64_t g = next.fetch_add(1);
+        if (g >= count) break;
+        int rc;
+        const int64_t n = nv[g];
+        if (fam[g] == 0) {
+          rc = gen_er(n, 4 * n, seed + g, &parts[g]);
+        } else if (fam[g] == 1) {
+          rc = gen_ba(n, 4, seed + g, &parts[g]);
+        } else {
+          const int64_t k = static_cast<int64_t>(std::ceil(std::sqrt(static_cast<double>(n))));
+          rc = gen_grid(k, k, 1, &parts[g]);
+        }
+        if (rc) bad.store(1);
+      }
+    });
+  for (auto& th : pool) th.join();
+  if (bad.load()) return nullptr;
+  gg_graph* out = new (std::nothrow) gg_graph();
+  if (!out) return nullptr;
+  graph_off[0] = 0;
+  std::vector<int64_t> eoff(count + 1, 0);
+  for (int64_t g = 0; g < count; ++g) {
+    graph_off[g + 1] = graph_off[g] + parts[g].n;
+    eoff[g + 1] = eoff[g] + static_cast<int64_t>(parts[g].col_idx.size());
+  }
+  Csr& c = out->csr;
+  c.n = graph_off[count];
+  c.row_ptr.assign(c.n + 1, 0);
+  c.col_idx.resize(eoff[count]);
+  parallel_dynamic(count, 8, [&](int64_t b, int64_t e) {
+    for (int64_t g = b; g < e; ++g) {
+      const Csr& p = parts[g];
+      for (int64_t v = 0; v < p.n; ++v) c.row_ptr[graph_off[g] + v] = p.row_ptr[v] + eoff[g];
+      for (size_t k = 0; k < p.col_idx.size(); ++k)
+        c.col_idx[eoff[g] + k] = p.col_idx[k] + static_cast<int32_t>(graph_off[g]);
+    }
+  });
+  c.row_ptr[c.n] = eoff[count];
+  return out;
+}
 
 }  // extern "C"

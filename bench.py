@@ -48,6 +48,11 @@ WORKLOADS = {
                     desc="3D 7-point grid 256^3, seeded vertex permutation, eps=1/100, seed 42"),
     "er": dict(kind="er", n=16384, m=81920, gen_seed=1, eps=(1, 100), seed=42,
                desc="Erdos-Renyi G(n=16384, m=81920), eps=1/100, seed 42"),
+    "serve": dict(kind="serve", requests=64, n_lo=1000, n_hi=2_000_000, seed=42, budget=40 << 30,
+                  load=0.5,
+                  desc="serving: Poisson arrivals at half the measured capacity; graphs n log-uniform in "
+                       "[1000, 2000000], R-MAT (.57,.19,.19,.05, edge factor 8-32) or Barabasi-Albert "
+                       "(m 2-16) 50/50, eps 1/100 or 1/10 50/50, 40 GB device-memory budget"),
     "batch4096": dict(kind="batch", count=4096, n_lo=100, n_hi=200_000, seed=42, eps=(1, 100),
                       desc="4096 graphs, n log-uniform in [100, 200000], Erdos-Renyi (avg deg 8) / "
                            "Barabasi-Albert (m=4) / 2D grid, packed as one disjoint union, eps=1/100, "
@@ -199,6 +204,27 @@ def run_reference(args, rank, world):
     import graphgen as gg  # noqa: F401
     import oracle
     w = WORKLOADS[args.workload]
+    if w["kind"] == "serve":  # each step: the oracle on the 8 smallest requests
+        reqs = sorted(serve_requests(w), key=lambda r: r[0].nnz)[:8]
+        for _ in range(args.warmup):
+            oracle.jp_adg(reqs[0][0], *reqs[0][1], reqs[0][2])
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for g, e, sd in reqs:
+                oracle.jp_adg(g, e[0], e[1], sd)
+        dt = time.perf_counter() - t0
+        value = sum(g.m for g, _, _ in reqs) * args.steps / dt
+        desc = "the 8 smallest requests of the serving workload, ADG + Greedy each"
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s",
+                          "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                          "config": {"workload": w["desc"], "sample": desc},
+                          "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                                           "sample": desc},
+                          "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}), flush=True)
+        return 0
     if w["kind"] == "batch":  # each step: the oracle on the first 64 graphs of the batch
         sample = [gg.make_batch_graph(f, nv, w["seed"] + i)
                   for i, (f, nv) in enumerate(gg.batch_recipe(64, w["n_lo"], w["n_hi"], w["seed"]))]
@@ -342,6 +368,79 @@ def run_batch(args, rank, world):
     return 0
 
 
+def serve_requests(w):
+    """The serving workload's request list: (graph, eps, seed) per request."""
+    import math
+    import numpy as np
+    import graphgen as gg
+    rng = np.random.default_rng(w["seed"])
+    out = []
+    lo, hi = math.log(w["n_lo"]), math.log(w["n_hi"])
+    for i in range(w["requests"]):
+        n = int(round(math.exp(lo + rng.random() * (hi - lo))))
+        if rng.random() < 0.5:
+            scale = max(1, int(round(math.log2(n))))
+            g = gg.rmat(scale, int(rng.integers(8, 33)), seed=w["seed"] + i)
+        else:
+            g = gg.barabasi_albert(n, int(rng.integers(2, 17)), w["seed"] + i)
+        eps = (1, 100) if rng.random() < 0.5 else (1, 10)
+        out.append((g, eps, w["seed"] + i))
+    return out
+
+
+def run_serve(args, rank, world):
+    """Continuous batching: first the capacity with every request submitted
+    at once, then Poisson arrivals at `load` x capacity; latency from
+    submission to colours on the host."""
+    import numpy as np
+    import torch
+    from paper_2008_11321_gb300 import _build
+    if rank == 0:
+        _build.build()
+    from paper_2008_11321_gb300.serve import ColoringServer, latency_summary
+    w = WORKLOADS[args.workload]
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    reqs_in = serve_requests(w)
+    edges = sum(g.m for g, _, _ in reqs_in)
+    with ColoringServer(dev, memory_budget=w["budget"]) as srv:
+        for g, e, sd in reqs_in[:min(4, len(reqs_in))]:  # warm-up
+            srv.submit(g.row_ptr, g.col_idx, e[0], e[1], sd).result()
+        t0 = time.perf_counter()
+        rs = [srv.submit(g.row_ptr, g.col_idx, e[0], e[1], sd) for g, e, sd in reqs_in]
+        for r in rs:
+            r.result()
+        t_closed = time.perf_counter() - t0
+        cap = len(reqs_in) / t_closed
+        rng = np.random.default_rng(w["seed"] + 1)
+        rate = w["load"] * cap
+        sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+        sampler.start()
+        n_batches0 = len(srv.batches)
+        t0 = time.perf_counter()
+        rs = []
+        for g, e, sd in reqs_in:
+            rs.append(srv.submit(g.row_ptr, g.col_idx, e[0], e[1], sd))
+            time.sleep(rng.exponential(1.0 / rate))
+        for r in rs:
+            r.result()
+        t_open = time.perf_counter() - t0
+        clocks = sampler.stop()
+        batches = srv.batches[n_batches0:]
+    lat = latency_summary(rs)
+    line = {"metric": METRIC, "value": edges / t_open, "unit": "edges/s", "n_gpus": world,
+            "steps": 1, "warmup": 1, "ms_per_step": t_open * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": w["desc"], "requests": len(reqs_in), "edges": edges,
+                       "arrival_rate_per_s": rate, "budget_bytes": w["budget"]},
+            "latency": lat, "requests_per_s": len(reqs_in) / t_open,
+            "capacity": {"requests_per_s": cap, "edges_per_s": edges / t_closed},
+            "batches": {"count": len(batches), "mean_graphs": float(np.mean([b[0] for b in batches]))},
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -363,6 +462,8 @@ def main():
         return run_reference(args, rank, world)
     if WORKLOADS[args.workload]["kind"] == "batch":
         return run_batch(args, rank, world)
+    if WORKLOADS[args.workload]["kind"] == "serve":
+        return run_serve(args, rank, world)
 
     import torch
     import torch.distributed as dist

@@ -225,6 +225,17 @@ gc_status gc_color_batch(gc_context *ctx, const gc_batch_csr *b, const gc_job *j
                          int32_t *color_out, int32_t *batch_out, int32_t *num_colors_out,
                          int32_t *num_rounds_out, gc_stream stream);
 
+/* gc_color_batch for graphs held in separate device buffers: graphs[g] is a
+ * gc_csr like gc_color_graph's (local ids 0..n_g-1, device pointers); jobs
+ * and graphs are host arrays of num_graphs entries, color_out a host array
+ * of num_graphs device pointers (n_g int32 each).  The graphs are packed
+ * into their disjoint union inside a buffer the context owns (grown on
+ * demand), coloured together, and each graph's colours written to its own
+ * output; results equal gc_color_graph on each graph alone.  Returns after
+ * the colours are written. */
+gc_status gc_color_batch_list(gc_context *ctx, int64_t num_graphs, const gc_csr *graphs,
+                              const gc_job *jobs, int32_t *const *color_out, gc_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -175,6 +175,7 @@ gc_status grow(void** buf, size_t* cap, size_t bytes) {
 gc_status gc_context::reserve(size_t bytes) { return grow(&scratch, &scratch_bytes, bytes); }
 gc_status gc_context::reserve_vert(size_t bytes) { return grow(&vbuf, &vbuf_bytes, bytes); }
 gc_status gc_context::reserve_aux(size_t bytes) { return grow(&aux, &aux_bytes, bytes); }
+gc_status gc_context::reserve_pack(size_t bytes) { return grow(&pack, &pack_bytes, bytes); }
 
 extern "C" {
 
@@ -238,6 +239,7 @@ void gc_destroy(gc_context* ctx) {
   if (ctx->scratch) cudaFree(ctx->scratch);
   if (ctx->vbuf) cudaFree(ctx->vbuf);
   if (ctx->aux) cudaFree(ctx->aux);
+  if (ctx->pack) cudaFree(ctx->pack);
   if (ctx->h_graph) cudaFree(ctx->h_graph);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   for (auto& ev : ctx->ev)
@@ -424,6 +426,21 @@ gc_status gc_color_batch(gc_context* ctx, const gc_batch_csr* b, const gc_job* j
   CallScope scope(ctx);
   return gc::batch_color(ctx, b, jobs, color_out, batch_out, num_colors_out, num_rounds_out,
                          reinterpret_cast<cudaStream_t>(stream));
+}
+
+gc_status gc_color_batch_list(gc_context* ctx, int64_t num_graphs, const gc_csr* graphs, const gc_job* jobs,
+                              int32_t* const* color_out, gc_stream stream) {
+  if (!ctx || num_graphs < 1 || num_graphs > INT_MAX || !graphs || !jobs || !color_out)
+    return GC_ERR_INVALID_ARG;
+  for (int64_t g = 0; g < num_graphs; ++g) {
+    GC_TRY(check_graph_args(&graphs[g]));
+    GC_TRY(check_eps(jobs[g].eps_p, jobs[g].eps_q));
+    if (graphs[g].n > 0 && !color_out[g]) return GC_ERR_INVALID_ARG;
+  }
+  DeviceGuard guard(ctx->device);
+  if (!guard.ok) return GC_ERR_CUDA;
+  CallScope scope(ctx);
+  return gc::batch_color_list(ctx, num_graphs, graphs, jobs, color_out, reinterpret_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -381,3 +381,122 @@ gc_status batch_color(gc_context* ctx, const gc_batch_csr* b, const gc_job* jobs
 }
 
 }  // namespace gc
+
+// ---------------------------------------------------------------------------
+// gc_color_batch_list: graphs given as separate device CSRs are packed into
+// the disjoint union on the device, coloured by batch_color, and the colours
+// copied back to each graph's own output.
+// ---------------------------------------------------------------------------
+namespace gc {
+namespace {
+
+struct ListDesc {  // one graph of the list (device copy of the host array)
+  const long long* row_ptr;
+  const int* col_idx;
+  int* color_out;
+};
+
+__device__ __forceinline__ int owner_of(const long long* __restrict__ off, int G, long long x) {
+  int lo = 0, hi = G - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(off + mid) <= x)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void pack_rows_kernel(const ListDesc* __restrict__ d, const long long* __restrict__ voff,
+                                 const long long* __restrict__ eoff, int G, long long n,
+                                 long long* __restrict__ row_ptr) {
+  for (long long v = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; v <= n;
+       v += static_cast<long long>(gridDim.x) * blockDim.x) {
+    if (v == n) {
+      row_ptr[n] = eoff[G];
+      continue;
+    }
+    const int g = owner_of(voff, G, v);
+    row_ptr[v] = d[g].row_ptr[v - voff[g]] + eoff[g];
+  }
+}
+
+__global__ void pack_cols_kernel(const ListDesc* __restrict__ d, const long long* __restrict__ voff,
+                                 const long long* __restrict__ eoff, int G, long long nnz,
+                                 int* __restrict__ col) {
+  for (long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; k < nnz;
+       k += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int g = owner_of(eoff, G, k);
+    col[k] = d[g].col_idx[k - eoff[g]] + static_cast<int>(voff[g]);
+  }
+}
+
+__global__ void unpack_colors_kernel(const ListDesc* __restrict__ d, const long long* __restrict__ voff, int G,
+                                     long long n, const int* __restrict__ color) {
+  for (long long v = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; v < n;
+       v += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int g = owner_of(voff, G, v);
+    d[g].color_out[v - voff[g]] = color[v];
+  }
+}
+
+}  // namespace
+
+gc_status batch_color_list(gc_context* ctx, long long G, const gc_csr* graphs, const gc_job* jobs,
+                           int32_t* const* color_out, cudaStream_t s) {
+  std::vector<long long> voff(G + 1, 0), eoff(G + 1, 0);
+  std::vector<ListDesc> desc(G);
+  for (long long g = 0; g < G; ++g) {
+    voff[g + 1] = voff[g] + graphs[g].n;
+    eoff[g + 1] = eoff[g] + graphs[g].nnz;
+    desc[g].row_ptr = reinterpret_cast<const long long*>(graphs[g].row_ptr);
+    desc[g].col_idx = graphs[g].col_idx;
+    desc[g].color_out = color_out[g];
+  }
+  const long long n = voff[G], nnz = eoff[G];
+  if (n > static_cast<long long>(INT_MAX) - 1) return GC_ERR_OVERFLOW;
+  // the packed union lives in the context's pack buffer:
+  // desc | voff | eoff | row_ptr | col_idx | colours
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t b_desc = al(sizeof(ListDesc) * G), b_off = al(sizeof(long long) * (G + 1));
+  const size_t b_rp = al(sizeof(long long) * (n + 1)), b_ci = al(sizeof(int) * (nnz > 0 ? nnz : 1));
+  const size_t b_col = al(sizeof(int) * (n > 0 ? n : 1));
+  GC_TRY(ctx->reserve_pack(b_desc + 2 * b_off + b_rp + b_ci + b_col));
+  char* base = static_cast<char*>(ctx->pack);
+  ListDesc* ddesc = reinterpret_cast<ListDesc*>(base);
+  long long* dvoff = reinterpret_cast<long long*>(base + b_desc);
+  long long* deoff = reinterpret_cast<long long*>(base + b_desc + b_off);
+  long long* rp = reinterpret_cast<long long*>(base + b_desc + 2 * b_off);
+  int* ci = reinterpret_cast<int*>(base + b_desc + 2 * b_off + b_rp);
+  int* col = reinterpret_cast<int*>(base + b_desc + 2 * b_off + b_rp + b_ci);
+  GC_TRY_CUDA(cudaMemcpyAsync(ddesc, desc.data(), sizeof(ListDesc) * G, cudaMemcpyHostToDevice, s));
+  GC_TRY_CUDA(cudaMemcpyAsync(dvoff, voff.data(), sizeof(long long) * (G + 1), cudaMemcpyHostToDevice, s));
+  GC_TRY_CUDA(cudaMemcpyAsync(deoff, eoff.data(), sizeof(long long) * (G + 1), cudaMemcpyHostToDevice, s));
+  const int blocks = ctx->num_sms * 8;
+  const int Gi = static_cast<int>(G);
+  pack_rows_kernel<<<blocks, 256, 0, s>>>(ddesc, dvoff, deoff, Gi, n, rp);
+  ++g_launches;
+  if (nnz > 0) {
+    pack_cols_kernel<<<blocks, 256, 0, s>>>(ddesc, dvoff, deoff, Gi, nnz, ci);
+    ++g_launches;
+  }
+  GC_TRY_CUDA(cudaGetLastError());
+  gc_batch_csr b;
+  b.num_graphs = G;
+  b.n = n;
+  b.nnz = nnz;
+  b.row_ptr = reinterpret_cast<const int64_t*>(rp);
+  b.col_idx = ci;
+  b.graph_off = reinterpret_cast<const int64_t*>(dvoff);
+  GC_TRY(batch_color(ctx, &b, jobs, col, nullptr, nullptr, nullptr, s));
+  if (n > 0) {
+    unpack_colors_kernel<<<blocks, 256, 0, s>>>(ddesc, dvoff, Gi, n, col);
+    ++g_launches;
+    GC_TRY_CUDA(cudaGetLastError());
+  }
+  GC_TRY_CUDA(cudaStreamSynchronize(s));
+  return GC_OK;
+}
+
+}  // namespace gc

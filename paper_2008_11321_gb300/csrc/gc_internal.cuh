@@ -131,6 +131,9 @@ size_t batch_adg_scratch_bytes(long long n, long long nnz, long long G);
 gc_status batch_color(gc_context* ctx, const gc_batch_csr* b, const gc_job* jobs, int32_t* color_out,
                       int32_t* batch_out, int32_t* num_colors_out, int32_t* num_rounds_out, cudaStream_t s);
 
+gc_status batch_color_list(gc_context* ctx, long long G, const gc_csr* graphs, const gc_job* jobs,
+                           int32_t* const* color_out, cudaStream_t s);
+
 // JP-ADG on the disjoint union of many graphs: tiev[v] is v's tie-break.
 gc_status jp_run_packed(gc_context* ctx, Arena a, const gc_csr* g, const int* batch, const unsigned* tiev,
                         const int* D, int rounds, int* color, int* num_colors_out, cudaStream_t s);
@@ -158,6 +161,9 @@ struct gc_context {
   // predecessor lists of the JP core
   void* aux = nullptr;
   size_t aux_bytes = 0;
+  // packed union of gc_color_batch_list
+  void* pack = nullptr;
+  size_t pack_bytes = 0;
   // buffers owned for gc_color_graph_host
   void* h_graph = nullptr;
   size_t h_graph_bytes = 0;
@@ -197,6 +203,7 @@ struct gc_context {
   gc_status reserve(size_t bytes);      // scratch arena
   gc_status reserve_vert(size_t bytes); // vbuf
   gc_status reserve_aux(size_t bytes);  // aux
+  gc_status reserve_pack(size_t bytes); // pack
   gc::Arena arena() const {
     gc::Arena a;
     a.base = static_cast<char*>(scratch);

@@ -24,7 +24,8 @@ GC_ERR_CUDA, GC_ERR_TIMEOUT, GC_ERR_OVERFLOW = 4, 5, 6
 # Every symbol declared in include/gcolor.h.
 EXPORTS = ("gc_status_str", "gc_create", "gc_destroy", "gc_get_stats", "gc_set_timing",
            "gc_validate_csr", "gc_adg_partition", "gc_make_priority", "gc_jp_color",
-           "gc_color_graph", "gc_color_graph_host", "gc_adg_partition_noalloc", "gc_color_batch")
+           "gc_color_graph", "gc_color_graph_host", "gc_adg_partition_noalloc", "gc_color_batch",
+           "gc_color_batch_list")
 
 
 class GcError(RuntimeError):
@@ -97,6 +98,8 @@ def load(path: str = LIB_PATH):
     lib.gc_adg_partition_noalloc.argtypes = [P(gc_csr), u32, u32, vp, P(i32), vp]
     lib.gc_color_batch.restype = ctypes.c_int
     lib.gc_color_batch.argtypes = [vp, P(gc_batch_csr), P(gc_job), vp, vp, vp, vp, vp]
+    lib.gc_color_batch_list.restype = ctypes.c_int
+    lib.gc_color_batch_list.argtypes = [vp, i64, P(gc_csr), P(gc_job), P(vp), vp]
     lib.gc_color_graph_host.restype = ctypes.c_int
     lib.gc_color_graph_host.argtypes = [vp, i64, i64, vp, vp, u32, u32, u64, vp, vp, P(i32), P(i32), vp]
     _lib = lib
@@ -278,6 +281,16 @@ class Context:
         _check(self._lib.gc_color_batch(self.handle, ctypes.byref(c), arr, _ptr(color_out), _ptr(batch_out),
                                         _ptr(num_colors_out), _ptr(num_rounds_out), _stream(stream)),
                "gc_color_batch")
+
+    def gc_color_batch_list(self, graphs, jobs, color_outs, stream=None):
+        """graphs: DeviceGraph list; jobs: (eps_p, eps_q, seed) per graph;
+        color_outs: CUDA int32 tensors, one per graph."""
+        G = len(graphs)
+        csrs = (gc_csr * G)(*[g.csr() for g in graphs])
+        arr = (gc_job * G)(*[gc_job(int(p), int(q), int(sd)) for p, q, sd in jobs])
+        outs = (ctypes.c_void_p * G)(*[c.data_ptr() if c.numel() else None for c in color_outs])
+        _check(self._lib.gc_color_batch_list(self.handle, G, csrs, arr, outs, _stream(stream)),
+               "gc_color_batch_list")
 
     def gc_color_graph_host(self, row_ptr: np.ndarray, col_idx: np.ndarray, eps_p: int, eps_q: int,
                             seed: int, color_out: np.ndarray, batch_out: np.ndarray | None = None,

@@ -89,12 +89,13 @@ typedef struct {
   float ms_jp_color;       /* JP's bulk colouring launches, summed             */
   int32_t launches;        /* kernels this library launched in the last call   */
   float ms_adg_update;     /* ADG's UPDATE launches (one per round), summed     */
-  float ms_core_solve;     /* the JP-ADG core block                            */
+  float ms_core_solve;     /* the JP-ADG core cluster                          */
   float ms_core_preds;     /* extraction of the core's predecessor lists       */
   int32_t bulk_launches;   /* JP bulk launches (one per ADG batch outside core) */
-  int64_t core_vertices;   /* vertices coloured by the core block              */
+  int64_t core_vertices;   /* vertices coloured by the core cluster            */
   int64_t core_preds;      /* predecessor entries of the core                  */
   int64_t core_degree_sum; /* degree sum of the core vertices                  */
+  int32_t core_ctas;       /* CTAs (one cluster) that coloured the core        */
 } gc_stats;
 
 /* Human-readable name of a status code (static storage). */

@@ -26,6 +26,7 @@ struct CallScope {
     ctx->stats.core_vertices = 0;
     ctx->stats.core_preds = 0;
     ctx->stats.core_degree_sum = 0;
+    ctx->stats.core_ctas = 0;
   }
   ~CallScope() {
     if (!ctx) return;

@@ -60,7 +60,7 @@ struct JpCtl {
   unsigned long long spins;      // polls that found an uncoloured predecessor
   unsigned long long nbig;       // vertices in the warp-path list
   unsigned long long nsmall;     // vertices in the lane-path list
-  unsigned long long ncore;      // vertices coloured by the core block
+  unsigned long long ncore;      // vertices coloured by the core cluster
   unsigned long long base0;      // warp-path offset of the first bulk bucket
   unsigned long long base1;      // lane-path offset of the first bulk bucket
   long long bstar;               // last core bucket (-1: no core)
@@ -71,10 +71,11 @@ struct JpCtl {
 };
 static_assert(sizeof(JpCtl) <= 256, "JpCtl must fit the pinned read-back buffer");
 
-// Largest core coloured by the single shared-memory block (16-bit colours,
-// 2 bytes of shared memory per core vertex next to 128 KB of bitmaps, within
-// the 227 KB a block may use) and its default target size.
-constexpr long long kCoreMax = 49152;
+// Largest core coloured by the shared-memory cluster (16-bit ids and colours;
+// each CTA keeps 2 bytes per core vertex next to 144 KB of bitmaps and
+// deferred predecessors, within the 227 KB a block may use) and its default
+// target size.
+constexpr long long kCoreMax = 32768;
 constexpr long long kCoreDefault = 16384;
 
 // Bump allocator over the context's scratch arena (256-byte aligned slices).
@@ -150,6 +151,8 @@ struct gc_context {
   int coop = 0;
   int timing = 0;
   long long core_target = kCoreDefault_;  // JP-ADG core size (vertices)
+  int core_cluster = 0;                   // CTAs of the core cluster (0: not chosen yet)
+  int core_warps = 0;                     // warps per core CTA
   // scratch arena (device)
   void* scratch = nullptr;
   size_t scratch_bytes = 0;

@@ -25,14 +25,15 @@
 //   1. order: one counting-sort pass by (batch, top bits of rho_R) gives the
 //      order without a comparison sort; isolated vertices take colour 1 at once
 //      and drop out.  The first buckets, up to the core target (16384 by
-//      default, at most 49152) vertices, form the
+//      default, at most 32768) vertices, form the
 //      "core"; they are sorted exactly inside their (tiny) buckets.
 //   2. core: the predecessors of each core vertex all lie in the core; they
 //      are extracted across the whole GPU into compact lists of core-local
-//      ids, then ONE thread block colours the core in order with the colours in
-//      shared memory, where a dependency step costs a shared-memory poll
-//      rather than an L2 round trip.  The core holds the long chains of the
-//      DAG G_rho (the densest part of the graph, which ADG ranks last).
+//      ids, then ONE thread-block cluster (up to 16 SMs) colours the core in
+//      order with a copy of the core's colours in every CTA's shared memory,
+//      where a dependency step costs a shared-memory poll rather than an L2
+//      round trip.  The core holds the long chains of the DAG G_rho (the
+//      densest part of the graph, which ADG ranks last).
 //   3. bulk: every other vertex by global polling (above), with all core
 //      colours already final.
 // gc_jp_color with an arbitrary priority array orders the vertices with an
@@ -48,8 +49,9 @@ namespace {
 constexpr int kJpThreads = 256;
 constexpr int kJpWarps = kJpThreads / kWarp;
 constexpr unsigned kBigBit = 0x80000000u;
-constexpr int kCoreThreads = 1024;
+constexpr int kCoreThreads = 1024;  // largest core CTA
 constexpr int kCoreWarps = kCoreThreads / kWarp;
+constexpr int kCoreWarpsDefault = 8;
 
 struct KeyFused {  // JP-ADG: (batch << 32) | rho_R(v), rho_R from one seed
   const int* batch;
@@ -570,116 +572,183 @@ __global__ void jpf_compact_kernel(const int* __restrict__ preds, const long lon
   }
 }
 
-__device__ __forceinline__ void prefetch_l1(const void* p) {
-  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+// Colours the core with one thread-block cluster of C CTAs (C <= 16, one per
+// SM) of W warps each.  Core vertex i belongs to CTA (i / W) mod C, warp
+// i mod W, so runs of W consecutive vertices (where many dependency steps
+// fall) share a CTA; every warp takes its vertices in increasing order.  W is
+// small (8 by default): warps that wait poll, and on a crowded SM their polls
+// take the issue slots of the warps on the critical path.  Each CTA holds a full
+// copy of the core's colours (16-bit, so a core of at most 32768 vertices,
+// using at most 32768 colours) in its shared memory: a warp that colours
+// vertex i stores the colour into all C copies (lane r into CTA r, through
+// distributed shared memory), and waits for a predecessor by polling its own
+// CTA's copy.  A warp reads its vertex's predecessor list (the compact 16-bit
+// stream, core order) from global memory in 16-byte groups, marks the colours
+// already known and sets the others aside (up to kDeferLane per lane, in
+// shared memory) without waiting, so that the scan never stalls behind a
+// predecessor that is still being coloured; then it sweeps the set-aside
+// ones, marking those coloured meanwhile, until none is left (so that when
+// the last one is coloured, only it remains to be marked), and writes the
+// smallest colour none of the predecessors uses.  Predecessors
+// precede their successors in the exact core order and every CTA of a
+// cluster is resident, so the warp holding the earliest unfinished vertex
+// always finds all of its predecessors coloured: the cluster makes progress
+// until every vertex is done.
+//
+// Used colours are marked in per-lane bitmaps (word q of lane l at q*32 + l,
+// so a warp's marks never collide in a bank and need no atomics), then OR-ed
+// across lanes with a rotated read; a pass covers a 512-colour window and
+// only ceil((|pred|+1)/32) words of it can hold the answer.
+constexpr int kBitWords = 16;       // 512-colour window per pass
+constexpr int kDeferLane = 40;      // predecessors a lane sets aside per vertex
+constexpr int kCoreClusterMax = 16;
+// shared memory of one core warp: its bitmaps and set-aside predecessors
+constexpr size_t kCoreWarpBytes = kBitWords * 32 * sizeof(unsigned) + kDeferLane * 32 * sizeof(unsigned short);
+
+size_t core_smem_bytes(int warps, long long kc) {
+  return static_cast<size_t>(warps) * kCoreWarpBytes + static_cast<size_t>(kc) * sizeof(unsigned short);
 }
 
-// Colours the core in one block.  Warp w colours core vertices w, w+32, ...
-// in that order; for each it reads the compact predecessor list, polls the
-// predecessors' colours in shared memory (16-bit: a core of at most 65535
-// vertices uses at most 65535 colours) and writes the smallest colour none of
-// them uses.  Predecessors precede their successors in the exact core order,
-// so the warp holding the earliest unfinished vertex is never waiting.
-//
-// Used colours are marked in per-lane bitmaps (word q of lane l at
-// q*32 + l, so a warp's marks never collide in a bank and need no atomics),
-// then OR-ed across lanes with a rotated read; only ceil((|pred|+1)/32)
-// words can hold the answer, so only those are cleared and reduced.  While it
-// works on one vertex the warp prefetches its next vertex's list into L1.
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ unsigned cluster_ctas() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+
+// Every thread of every CTA of the cluster arrives; shared-memory writes
+// before it (local or remote) are visible to every thread after it.
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Address of this CTA's shared variable `p` in CTA `rank` of the cluster.
+__device__ __forceinline__ unsigned cluster_map(const void* p, unsigned rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+               : "=r"(r)
+               : "r"(static_cast<unsigned>(__cvta_generic_to_shared(p))), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void st_cluster_u16(unsigned addr, unsigned short v) {
+  asm volatile("st.relaxed.cluster.shared::cluster.u16 [%0], %1;" ::"r"(addr), "h"(v) : "memory");
+}
+
 __global__ void __launch_bounds__(kCoreThreads, 1)
 jpf_core_solve_kernel(const int* __restrict__ order, const long long* __restrict__ qoff,
-                      const unsigned short* __restrict__ cpreds, JpCtl* ctl, int* color) {
-  constexpr int U = 8;  // pairs of ids per lane in flight
-  extern __shared__ unsigned s_dyn[];
-  unsigned* s_bits = s_dyn;                                              // [warps][32 words][32 lanes]
-  unsigned short* s_col = reinterpret_cast<unsigned short*>(s_dyn + kCoreWarps * 32 * 32);
+                      const unsigned short* __restrict__ stream, JpCtl* ctl, int* color) {
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  const int nwc = blockDim.x >> 5;  // warps per CTA
+  unsigned* s_bits = reinterpret_cast<unsigned*>(s_dyn);  // [warp][word][lane]
+  unsigned short* s_def = reinterpret_cast<unsigned short*>(s_bits + nwc * kBitWords * 32);  // [warp][slot][lane]
+  unsigned short* s_col = s_def + nwc * kDeferLane * 32;
   const int kc = static_cast<int>(ctl->ncore);
+  const int rank = static_cast<int>(cluster_rank()), nctas = static_cast<int>(cluster_ctas());
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned* bits = s_bits + warp * 32 * 32;
   for (int i = threadIdx.x; i < kc; i += blockDim.x) s_col[i] = 0;
-  __syncthreads();
+  __syncwarp();
+  cluster_sync();  // every copy is cleared before any colour lands in it
+
   volatile unsigned short* vcol = s_col;
+  unsigned* bits = s_bits + warp * kBitWords * 32;
+  unsigned short* def = s_def + warp * kDeferLane * 32 + lane;
+  const unsigned col_r = lane < nctas ? cluster_map(s_col, lane) : 0u;  // copy in CTA `lane`
+  const uint4* groups = reinterpret_cast<const uint4*>(stream);
   const unsigned long long t0 = global_ns();
-  int local_max = 0;
   bool timed_out = false;
-  long long beg = warp < kc ? qoff[warp] : 0, end = warp < kc ? qoff[warp + 1] : 0;
-  for (int i = warp; i < kc; i += kCoreWarps) {
-    const int inext = i + kCoreWarps;
-    long long nbeg = 0, nend = 0;
-    if (inext < kc) {
-      nbeg = qoff[inext];
-      nend = qoff[inext + 1];
-    }
-    const int np = static_cast<int>(end - beg);
-    // the smallest free colour is <= np + 1: ceil((np+1)/32) words, at most
-    // one 1024-colour window per pass (larger palettes take further passes)
-    const int nw = np / 32 + 1 < 32 ? np / 32 + 1 : 32;
-    const unsigned short* pl = cpreds + beg;
-    // ids are read as 32-bit pairs from an even index; an odd start peels one
-    const int lead = (np > 0 && (beg & 1)) ? 1 : 0;
-    const unsigned* pairs = reinterpret_cast<const unsigned*>(pl + lead);
-    const int npairs = (np - lead) / 2;
-    const bool tail = ((np - lead) & 1) != 0;
-    int c = 0;
-    for (int base = 0;; base += 32 * nw) {
+  auto expired = [&]() { return timed_out || ld_relaxed(&ctl->err) != 0 || global_ns() - t0 > kWaitLimitNs; };
+  int local_max = 0;
+  for (int i = nwc * rank + warp; i < kc; i += nwc * nctas) {
+    const long long a = qoff[i], b = qoff[i + 1];
+    const int np = static_cast<int>(b - a);
+    const int nw = np / 32 + 1 < kBitWords ? np / 32 + 1 : kBitWords;
+    int c = 1;
+    for (int base = 0; !timed_out; base += 32 * nw) {
       for (int q = 0; q < nw; ++q) bits[q * 32 + lane] = 0u;
-      // Colours already known are marked at once; a lane defers up to kDefer
-      // uncoloured predecessors and waits on them after its scan, so that when
-      // the last predecessor is coloured little work is left (the latest
-      // predecessors are the ones on the critical path).
-      constexpr int kDefer = 8;
-      int defer[kDefer];
       int nd = 0;
       auto put = [&](int cj) {
         const int x = cj - base - 1;
         if (x >= 0 && x < 32 * nw) bits[(x >> 5) * 32 + lane] |= 1u << (x & 31);
       };
-      auto wait_put = [&](int j) {
-        int cj;
-        unsigned it = 0;
-        while ((cj = vcol[j]) == 0) {
-          if (it >= 64) __nanosleep(32);  // plain spinning first: a level is short
-          if ((++it & 255u) == 0 &&
-              (timed_out || ld_relaxed(&ctl->err) != 0 || global_ns() - t0 > kWaitLimitNs)) {
+      // marks the set-aside predecessors coloured by now and keeps the rest
+      auto sweep = [&]() {
+        int k = 0;
+        for (int d = 0; d < nd; ++d) {
+          const int j = def[32 * d];
+          const int cj = vcol[j];
+          if (cj != 0)
+            put(cj);
+          else
+            def[32 * k++] = static_cast<unsigned short>(j);
+        }
+        nd = k;
+      };
+      // sweeps until at most `keep` predecessors are left (bounded)
+      auto drain = [&](int keep) {
+        for (unsigned it = 0; nd > keep; ++it) {
+          sweep();
+          if (nd <= keep) break;
+          if (it >= 64) __nanosleep(32);
+          if ((it & 255u) == 255u && expired()) {
             timed_out = true;
-            cj = 1;
-            break;
+            nd = 0;
           }
         }
-        put(cj);
       };
-      auto mark = [&](int j) {
+      auto take = [&](int j) {
         const int cj = vcol[j];
         if (cj != 0) {
           put(cj);
-        } else if (nd < kDefer) {
-          defer[nd++] = j;
-        } else {
-          wait_put(j);
+          return;
         }
+        if (nd == kDeferLane) drain(kDeferLane - 1);
+        if (nd < kDeferLane) def[32 * nd++] = static_cast<unsigned short>(j);
       };
-      if (lane == 0 && lead) mark(pl[0]);
-      if (lane == 0 && tail) mark(pl[np - 1]);
-      for (int p0 = 0; p0 < npairs; p0 += 32 * U) {
-        unsigned pr[U];
+      // positions [a, b) of the stream, 8 per 16-byte group, two groups per
+      // lane in flight
+      for (long long g = a / 8 + lane; g * 8 < b; g += 64) {
+        const bool has2 = (g + 32) * 8 < b;
+        const uint4 v0 = __ldg(groups + g);
+        const uint4 v1 = has2 ? __ldg(groups + g + 32) : make_uint4(0u, 0u, 0u, 0u);
+        const unsigned w0[4] = {v0.x, v0.y, v0.z, v0.w};
+        const unsigned w1[4] = {v1.x, v1.y, v1.z, v1.w};
+        const long long p0 = g * 8, p1 = (g + 32) * 8;
+        if (p0 >= a && p0 + 8 <= b) {
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int pp = p0 + u * 32 + lane;
-          pr[u] = pp < npairs ? __ldg(pairs + pp) : 0xffffffffu;
+          for (int e = 0; e < 4; ++e) {
+            take(static_cast<int>(w0[e] & 0xffffu));
+            take(static_cast<int>(w0[e] >> 16));
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            if (p0 + 2 * e >= a && p0 + 2 * e < b) take(static_cast<int>(w0[e] & 0xffffu));
+            if (p0 + 2 * e + 1 >= a && p0 + 2 * e + 1 < b) take(static_cast<int>(w0[e] >> 16));
+          }
         }
+        if (has2) {
+          if (p1 + 8 <= b) {
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          if (pr[u] == 0xffffffffu) continue;
-          mark(static_cast<int>(pr[u] & 0xffffu));
-          mark(static_cast<int>(pr[u] >> 16));
+            for (int e = 0; e < 4; ++e) {
+              take(static_cast<int>(w1[e] & 0xffffu));
+              take(static_cast<int>(w1[e] >> 16));
+            }
+          } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              if (p1 + 2 * e < b) take(static_cast<int>(w1[e] & 0xffffu));
+              if (p1 + 2 * e + 1 < b) take(static_cast<int>(w1[e] >> 16));
+            }
+          }
         }
       }
-      for (int d = 0; d < nd; ++d) wait_put(defer[d]);
-      if (base == 0 && inext < kc) {  // the next list, 128-byte lines, into L1
-        const char* nb = reinterpret_cast<const char*>(cpreds + nbeg);
-        const long long bytes = (nend - nbeg) * 2;
-        for (long long x = static_cast<long long>(lane) * 128; x < bytes; x += 32 * 128) prefetch_l1(nb + x);
-      }
+      drain(0);
       __syncwarp();
       // lane q < nw ORs word q over all lanes (rotated so no bank repeats)
       unsigned word = 0u;
@@ -694,17 +763,72 @@ jpf_core_solve_kernel(const int* __restrict__ order, const long long* __restrict
         c = base + f * 32 + __ffs(fb);
         break;
       }
+      timed_out = __any_sync(kFull, timed_out);
     }
-    if (lane == 0) vcol[i] = static_cast<unsigned short>(c);
+    if (lane < nctas) st_cluster_u16(col_r + 2u * static_cast<unsigned>(i), static_cast<unsigned short>(c));
     local_max = c > local_max ? c : local_max;
-    beg = nbeg;
-    end = nend;
   }
-  if (__any_sync(kFull, timed_out) && lane == 0) atomicExch(&ctl->err, kDevTimeout);
-  __syncthreads();
-  for (int i = threadIdx.x; i < kc; i += blockDim.x) color[order[i]] = s_col[i];
   local_max = warp_max(local_max);
   if (lane == 0) atomicMax(&ctl->max_color, local_max);
+  if (__any_sync(kFull, timed_out) && lane == 0) atomicExch(&ctl->err, kDevTimeout);
+  __syncwarp();
+  cluster_sync();  // all colours have landed in every copy; no remote store is outstanding
+  for (int t = threadIdx.x;; t += blockDim.x) {  // this CTA's vertices, increasing
+    const int i = nwc * (rank + nctas * (t / nwc)) + t % nwc;
+    if (i >= kc) break;
+    color[order[i]] = s_col[i];
+  }
+}
+
+// Shape of the core cluster: warps per CTA (GC_CORE_WARPS, default
+// kCoreWarpsDefault) and the largest cluster (16, 8, ..., 1 CTAs) the device
+// can place with the core's largest shared-memory footprint; GC_CORE_CLUSTER
+// may ask for fewer CTAs.
+cudaError_t core_cluster_size(gc_context* ctx, int* out) {
+  if (ctx->core_cluster > 0) {
+    *out = ctx->core_cluster;
+    return cudaSuccess;
+  }
+  int warps = kCoreWarpsDefault;
+  if (const char* env = getenv("GC_CORE_WARPS")) {
+    const int v = atoi(env);
+    if (v >= 1 && v <= kCoreWarps) warps = v;
+  }
+  ctx->core_warps = warps;
+  const size_t smem_max = core_smem_bytes(warps, kCoreMax);
+  cudaError_t e = cudaFuncSetAttribute(jpf_core_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem_max));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(jpf_core_solve_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  int limit = kCoreClusterMax;
+  if (const char* env = getenv("GC_CORE_CLUSTER")) {
+    const int v = atoi(env);
+    if (v >= 1 && v < limit) limit = v;
+  }
+  int best = 1;
+  for (int cs = 1; cs <= limit; cs *= 2) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(32 * warps);
+    cfg.dynamicSmemBytes = smem_max;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, jpf_core_solve_kernel, &cfg) != cudaSuccess || ncl < 1) {
+      cudaGetLastError();  // clear the query's error; keep the last size that fits
+      break;
+    }
+    best = cs;
+  }
+  ctx->core_cluster = best;
+  *out = best;
+  return cudaSuccess;
 }
 
 template <class Key>
@@ -825,7 +949,7 @@ gc_status jp_run_given(gc_context* ctx, Arena a, const gc_csr* g, const unsigned
 }
 
 // ---------------------------------------------------------------------------
-// JP-ADG (gc_color_graph): bucket order, core block, bulk polling.
+// JP-ADG (gc_color_graph): bucket order, core cluster, bulk polling.
 // ---------------------------------------------------------------------------
 size_t jpadg_scratch_bytes(long long n, long long nnz, int rounds) {
   const BucketPlan bp = make_plan(n, rounds);
@@ -922,6 +1046,7 @@ gc_status jp_adg_impl(gc_context* ctx, Arena a, const gc_csr* g, const Key& key,
     // aux: predecessor ids at capacity-sized slots (int32), then the dense
     // 16-bit stream
     const size_t pbytes = (static_cast<size_t>(npred_cap) * sizeof(int) + 255) & ~size_t(255);
+    // (the 256 spare bytes cover the last 16-byte group a core warp reads)
     GC_TRY(ctx->reserve_aux(pbytes + static_cast<size_t>(npred_cap) * sizeof(unsigned short) + 256));
     int* preds = static_cast<int*>(ctx->aux);
     unsigned short* cpreds = reinterpret_cast<unsigned short*>(static_cast<char*>(ctx->aux) + pbytes);
@@ -942,12 +1067,25 @@ gc_status jp_adg_impl(gc_context* ctx, Arena a, const gc_csr* g, const Key& key,
     jpf_compact_kernel<<<blocks, 256, 0, s>>>(preds, cap, qoff, ctl, cpreds);
     ++g_launches;
     GC_TRY_CUDA(cudaGetLastError());
-    const size_t smem = static_cast<size_t>(kCoreWarps) * 32 * 32 * sizeof(unsigned) +
-                        static_cast<size_t>(kc) * sizeof(unsigned short);
-    GC_TRY_CUDA(cudaFuncSetAttribute(jpf_core_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     static_cast<int>(smem)));
+    int ncta = 1;
+    GC_TRY_CUDA(core_cluster_size(ctx, &ncta));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = ncta;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(ncta);
+    cfg.blockDim = dim3(32 * ctx->core_warps);
+    cfg.dynamicSmemBytes = core_smem_bytes(ctx->core_warps, kc);
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    ctx->stats.core_ctas = ncta;
     ctx->timer_begin(gc_context::kTCoreSolve, s);
-    jpf_core_solve_kernel<<<1, kCoreThreads, smem, s>>>(order, qoff, cpreds, ctl, color);
+    GC_TRY_CUDA(cudaLaunchKernelEx(&cfg, jpf_core_solve_kernel, static_cast<const int*>(order),
+                                   static_cast<const long long*>(qoff), static_cast<const unsigned short*>(cpreds),
+                                   ctl, color));
     ++g_launches;
     ctx->timer_end(s);
     GC_TRY_CUDA(cudaGetLastError());

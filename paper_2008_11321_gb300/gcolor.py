@@ -56,7 +56,7 @@ class gc_stats(ctypes.Structure):
                 ("ms_adg_update", ctypes.c_float), ("ms_core_solve", ctypes.c_float),
                 ("ms_core_preds", ctypes.c_float), ("bulk_launches", ctypes.c_int32),
                 ("core_vertices", ctypes.c_int64), ("core_preds", ctypes.c_int64),
-                ("core_degree_sum", ctypes.c_int64)]
+                ("core_degree_sum", ctypes.c_int64), ("core_ctas", ctypes.c_int32)]
 
 
 _lib = None

@@ -138,6 +138,9 @@ adg_update_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row_pt
                   const int* __restrict__ col, int* __restrict__ D, const int* __restrict__ batch,
                   const long long* __restrict__ task_start, const int* __restrict__ task_len,
                   long long vertex_tiles_n) {
+  // The last round leaves U empty: no neighbour can still be in U, so there
+  // is nothing to decrement (and the cut is not needed any more).
+  if (ctl->size_Unext == 0) return;
   const int round = ctl->round;
   const unsigned long long ntasks =
       vertex_tiles_n > 0 ? static_cast<unsigned long long>(vertex_tiles_n) : ctl->ntasks;
@@ -160,12 +163,14 @@ adg_update_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row_pt
         len = task_len[t];
       }
     }
-    sweep_tile(st, len, 0, col, [&](int w, int) {
-      if (__ldg(batch + w) == 0) {  // w is still in U
-        ++cut;
-        atomicSub(&D[w], 1);
-      }
-    });
+    sweep_tile(
+        st, len, 0, col, [&](int w, int) { return __ldg(batch + w); },
+        [&](int w, int, int bw) {
+          if (bw == 0) {  // w is still in U
+            ++cut;
+            atomicSub(&D[w], 1);
+          }
+        });
   }
   cut = warp_sum(cut);
   if (lane == 0 && cut) atomicAdd(&ctl->cut, cut);
@@ -213,6 +218,7 @@ gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigne
   GC_TRY_CUDA(cudaGetLastError());
 
   const int max_blocks = ctx->num_sms * 8;
+  const int upd_blocks = resident_grid(adg_update_kernel, kAdgThreads, ctx->num_sms);
   long long size_u = n;
   int cur = 0;
   int* pinned = static_cast<int*>(ctx->pinned);
@@ -227,7 +233,7 @@ gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigne
     ++g_launches;
     GC_TRY_CUDA(cudaGetLastError());
     ctx->timer_begin(gc_context::kTUpdate, s);
-    adg_update_kernel<<<max_blocks, kAdgThreads, 0, s>>>(ctl, row_ptr_of(g), g->col_idx, D, batch,
+    adg_update_kernel<<<upd_blocks, kAdgThreads, 0, s>>>(ctl, row_ptr_of(g), g->col_idx, D, batch,
                                                           task_start, task_len, round == 1 ? n : 0);
     ++g_launches;
     ctx->timer_end(s);
@@ -336,6 +342,7 @@ extern "C" gc_status gc_adg_partition_noalloc(const gc_csr* g, uint32_t eps_p, u
   adg_init_kernel<<<1, 1, 0, s>>>(ctl, n, nnz, eps_p, eps_q);
   GC_TRY_CUDA(cudaGetLastError());
   const int max_blocks = num_sms * 8;
+  const int upd_blocks = gc::resident_grid(gc::adg_update_kernel, gc::kAdgThreads, num_sms);
   const long long* rp = reinterpret_cast<const long long*>(g->row_ptr);
   long long size_u = n;
   int cur = 0, round = 0;
@@ -348,7 +355,7 @@ extern "C" gc_status gc_adg_partition_noalloc(const gc_csr* g, uint32_t eps_p, u
                                                         task_start, task_len,
                                                         round == 1 ? static_cast<int>(n) : 0);
     GC_TRY_CUDA(cudaGetLastError());
-    adg_update_kernel<<<max_blocks, kAdgThreads, 0, s>>>(ctl, rp, g->col_idx, D, batch_out, task_start,
+    adg_update_kernel<<<upd_blocks, kAdgThreads, 0, s>>>(ctl, rp, g->col_idx, D, batch_out, task_start,
                                                           task_len, round == 1 ? n : 0);
     GC_TRY_CUDA(cudaGetLastError());
     adg_finalize_kernel<<<1, 1, 0, s>>>(ctl);

@@ -207,8 +207,10 @@ batch_update_kernel(BCtl* __restrict__ ctl, BGraph* __restrict__ gs, const long 
         tg = task_g[t];
       }
     }
-    sweep_tile(st, len, tg, col, [&](int w, int g) {
-      if (__ldg(batch + w) == 0) {
+    sweep_tile(
+        st, len, tg, col, [&](int w, int) { return __ldg(batch + w); },
+        [&](int w, int g, int bw) {
+      if (bw == 0) {
         atomicSub(&D[w], 1);
         if (g != cur_g) {
           if (cnt) atomicAdd(&gs[cur_g].cut, cnt);
@@ -321,6 +323,7 @@ gc_status batch_color(gc_context* ctx, const gc_batch_csr* b, const gc_job* jobs
   GC_TRY_CUDA(cudaMemcpyAsync(djobs, jobs, sizeof(gc_job) * G, cudaMemcpyHostToDevice, s));
   if (n > 0) GC_TRY_CUDA(cudaMemsetAsync(bat, 0, sizeof(int) * n, s));  // 0 = still in U
   const int blocks = ctx->num_sms * 8;
+  const int upd_blocks = resident_grid(batch_update_kernel, kBThreads, ctx->num_sms);
   batch_init_kernel<<<(G + 255) / 256, 256, 0, s>>>(gs, djobs, G, off, rp, ctl);
   ++g_launches;
   GC_TRY_CUDA(cudaGetLastError());
@@ -338,7 +341,7 @@ gc_status batch_color(gc_context* ctx, const gc_batch_csr* b, const gc_job* jobs
                                                          round == 1 ? nullptr : ubuf[cur ^ 1], ubuf[cur],
                                                          task_start, task_len, task_g, size_u);
     ++g_launches;
-    batch_update_kernel<<<blocks, kBThreads, 0, s>>>(ctl, gs, off, G, rp, b->col_idx, D, bat, task_start,
+    batch_update_kernel<<<upd_blocks, kBThreads, 0, s>>>(ctl, gs, off, G, rp, b->col_idx, D, bat, task_start,
                                                      task_len, task_g, round == 1 ? n : 0);
     ++g_launches;
     batch_finalize_kernel<<<(G + 255) / 256, 256, 0, s>>>(ctl, gs, G);

@@ -250,6 +250,18 @@ inline gc_status gc_cuda_status(cudaError_t e) {
 #ifdef __CUDACC__
 namespace gc {
 
+// Blocks of `threads` threads of `kernel` that fit on the whole GPU at once:
+// grid-stride kernels launched with this many blocks have no second wave.
+template <class K>
+int resident_grid(K kernel, int threads, int num_sms) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return num_sms * per_sm;
+}
+
 __device__ __forceinline__ int ld_relaxed(const int* p) {
   int v;
   asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -303,16 +315,21 @@ __device__ __forceinline__ T warp_inclusive_scan(T v) {
 // Edge sweep over 32 tasks held one per lane (task start `st`, length `len`,
 // a caller value `tag`): the tasks' edges are numbered 0..total-1 in lane
 // order and handed out 32 * kSweepUnroll at a time, each lane taking
-// kSweepUnroll edges.  fn(w, tag) is called with the neighbour w = col_idx[k]
-// of each edge and the tag of the task owning it; all kSweepUnroll col_idx
-// loads of a lane are issued before any fn runs, so their latencies overlap.
-template <class Fn>
+// kSweepUnroll edges.  For each edge, with w = col_idx[k] and the tag of the
+// task owning it, gather(w, tag) is evaluated first (a load of per-vertex
+// state) and fn(w, tag, gathered) after it.  All kSweepUnroll col_idx loads
+// of a lane are issued before any gather, and all gathers before any fn, so
+// that a lane has kSweepUnroll loads in flight at each step even where fn
+// writes memory (which could keep the compiler from moving the next edge's
+// gather ahead of it).
+template <class Gather, class Fn>
 __device__ __forceinline__ void sweep_tile(long long st, int len, int tag, const int* __restrict__ col,
-                                           Fn fn) {
+                                           Gather gather, Fn fn) {
   const int lane = threadIdx.x & 31;
   const int incl = warp_inclusive_scan(len);
   const int total = __shfl_sync(kFull, incl, 31);
   const int excl = incl - len;
+  using G = decltype(gather(0, 0));
   for (int b = 0; b < total; b += 32 * kSweepUnroll) {
     int w[kSweepUnroll], own[kSweepUnroll];
 #pragma unroll
@@ -329,9 +346,12 @@ __device__ __forceinline__ void sweep_tile(long long st, int len, int tag, const
       own[u] = e < total ? tg : -1;
       w[u] = e < total ? __ldg(col + k) : -1;
     }
+    G gv[kSweepUnroll];
+#pragma unroll
+    for (int u = 0; u < kSweepUnroll; ++u) gv[u] = w[u] >= 0 ? gather(w[u], own[u]) : G{};
 #pragma unroll
     for (int u = 0; u < kSweepUnroll; ++u)
-      if (w[u] >= 0) fn(w[u], own[u]);
+      if (w[u] >= 0) fn(w[u], own[u], gv[u]);
   }
 }
 

@@ -543,13 +543,15 @@ jpf_core_preds_kernel(const int* __restrict__ col, Key key, const int* __restric
       len = task_len[t];
       ci = task_i[t];
     }
-    sweep_tile(st, len, ci, col, [&](int w, int i) {
-      const int v = order[i];
-      if (precedes(key(w), w, key(v), v)) {
-        const int slot = atomicAdd(&pcnt[i], 1);
-        preds[poff[i] + slot] = lid[w];
-      }
-    });
+    sweep_tile(
+        st, len, ci, col, [&](int w, int) { return key(w); },
+        [&](int w, int i, decltype(key(0)) kw) {
+          const int v = order[i];
+          if (precedes(kw, w, key(v), v)) {
+            const int slot = atomicAdd(&pcnt[i], 1);
+            preds[poff[i] + slot] = lid[w];
+          }
+        });
   }
 }
 
@@ -1054,7 +1056,8 @@ gc_status jp_adg_impl(gc_context* ctx, Arena a, const gc_csr* g, const Key& key,
     jpf_core_tasks_kernel<<<blocks, 256, 0, s>>>(order, rp, toff, ctl, task_i, task_start, task_len);
     ++g_launches;
     ctx->timer_begin(gc_context::kTCorePreds, s);
-    jpf_core_preds_kernel<<<blocks, 256, 0, s>>>(g->col_idx, key, order, lid, toff, cap, ctl, task_i,
+    jpf_core_preds_kernel<<<resident_grid(jpf_core_preds_kernel<Key>, 256, ctx->num_sms), 256, 0, s>>>(
+        g->col_idx, key, order, lid, toff, cap, ctl, task_i,
                                                  task_start, task_len, pcnt, preds);
     ++g_launches;
     ctx->timer_end(s);

@@ -7,7 +7,7 @@
 //              each removed vertex's adjacency is cut into UPDATE tasks of at
 //              most kChunk edges; Sigma_R = sum of D over R is reduced.
 //   update     push-style UPDATE: for every task edge (v, w) with w still in
-//              U' (batch[w] == 0) an atomic decrement of D[w]
+//              U' (its bit in the liveness bitmap) an atomic decrement of D[w]
 //              (DecrementAndFetch, Section 2.4); the number of decrements is
 //              the cut (R, U').  Edges are spread over the lanes of a warp
 //              across 32 tasks at a time, so short and long rows mix.
@@ -15,6 +15,13 @@
 //              Degrees"), |U| = |U'|, next T, l = l + 1.
 //
 // Round 1 reads U = V implicitly (no list) and writes D only for survivors.
+//
+// UPDATE tests "w still in U" on a bitmap (n bits) rather than on batch[]
+// (n ints): the test is a random gather per edge, and a 2 MB bitmap for 2^24
+// vertices stays in L2 next to the decremented D words, where a 64 MB array
+// would not (random 4-byte gathers run several times faster from L2 than from
+// HBM).  Round 1's partition visits the vertices in order and writes whole
+// bitmap words; later rounds clear the bits of removed vertices.
 // The host reads |U| after every round to stop; the number of rounds is
 // O(log n) (the round-bound lemma of Section 3) and is single-digit on the
 // power-law workloads, so the read-back is not on the bulk path.
@@ -53,7 +60,7 @@ __global__ void __launch_bounds__(kAdgThreads)
 adg_partition_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row_ptr,
                      int* __restrict__ D, int* __restrict__ batch, const int* __restrict__ u_in,
                      int* __restrict__ u_out, long long* __restrict__ task_start,
-                     int* __restrict__ task_len, int first_round_n) {
+                     int* __restrict__ task_len, unsigned* __restrict__ live, int first_round_n) {
   const int round = ctl->round;
   const int T = ctl->T;
   const bool first = first_round_n > 0;
@@ -86,6 +93,13 @@ adg_partition_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row
     if (lane == 0 && km) kbase = atomicAdd(&ctl->size_Unext, __popc(km));
     kbase = __shfl_sync(kFull, kbase, 0);
     if (keep) u_out[kbase + __popc(km & lt)] = u;
+    // liveness bitmap: round 1 writes the warp's word (vertices i = 32 j ..
+    // 32 j + 31, since blocks start at multiples of 32); later rounds clear
+    if (first) {
+      if (lane == 0 && active) live[i >> 5] = km;
+    } else if (in_r) {
+      atomicAnd(&live[u >> 5], ~(1u << (u & 31)));
+    }
     // D[u] is written for every vertex in round 1; for a removed vertex it then
     // keeps its degree at removal, |{w in N(u) : batch(w) >= batch(u)}|, which
     // bounds u's predecessor count in JP.
@@ -136,8 +150,8 @@ adg_partition_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row
 __global__ void __launch_bounds__(kAdgThreads)
 adg_update_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row_ptr,
                   const int* __restrict__ col, int* __restrict__ D, const int* __restrict__ batch,
-                  const long long* __restrict__ task_start, const int* __restrict__ task_len,
-                  long long vertex_tiles_n) {
+                  const unsigned* __restrict__ live, const long long* __restrict__ task_start,
+                  const int* __restrict__ task_len, long long vertex_tiles_n) {
   // The last round leaves U empty: no neighbour can still be in U, so there
   // is nothing to decrement (and the cut is not needed any more).
   if (ctl->size_Unext == 0) return;
@@ -164,9 +178,9 @@ adg_update_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row_pt
       }
     }
     sweep_tile(
-        st, len, 0, col, [&](int w, int) { return __ldg(batch + w); },
-        [&](int w, int, int bw) {
-          if (bw == 0) {  // w is still in U
+        st, len, 0, col, [&](int w, int) { return (__ldg(live + (w >> 5)) >> (w & 31)) & 1u; },
+        [&](int w, int, unsigned lv) {
+          if (lv) {  // w is still in U
             ++cut;
             atomicSub(&D[w], 1);
           }
@@ -196,7 +210,8 @@ __global__ void adg_finalize_kernel(AdgCtl* ctl) {
 // Excludes D (n ints), which the caller provides.
 size_t adg_scratch_bytes(long long n, long long nnz) {
   const long long ntask = n + nnz / kChunk + 1;
-  return 2 * (static_cast<size_t>(n) * 4 + 256) + static_cast<size_t>(ntask) * 12 + 2048;
+  return 2 * (static_cast<size_t>(n) * 4 + 256) + static_cast<size_t>(ntask) * 12 +
+         static_cast<size_t>((n + 31) / 32) * 4 + 256 + 2048;
 }
 
 gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigned q, int* batch,
@@ -210,7 +225,8 @@ gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigne
   const long long ntask = n + nnz / kChunk + 1;
   long long* task_start = a.take<long long>(ntask);
   int* task_len = a.take<int>(ntask);
-  if (!ctl || !D || !ubuf[0] || !ubuf[1] || !task_start || !task_len) return GC_ERR_OOM;
+  unsigned* live = a.take<unsigned>((n + 31) / 32);
+  if (!ctl || !D || !ubuf[0] || !ubuf[1] || !task_start || !task_len || !live) return GC_ERR_OOM;
 
   GC_TRY_CUDA(cudaMemsetAsync(batch, 0, sizeof(int) * n, s));  // batch 0 = still in U
   adg_init_kernel<<<1, 1, 0, s>>>(ctl, n, nnz, p, q);
@@ -229,11 +245,11 @@ gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigne
     int blocks = static_cast<int>(want < max_blocks ? want : max_blocks);
     adg_partition_kernel<<<blocks, kAdgThreads, 0, s>>>(
         ctl, row_ptr_of(g), D, batch, round == 1 ? nullptr : ubuf[cur ^ 1], ubuf[cur], task_start,
-        task_len, round == 1 ? static_cast<int>(n) : 0);
+        task_len, live, round == 1 ? static_cast<int>(n) : 0);
     ++g_launches;
     GC_TRY_CUDA(cudaGetLastError());
     ctx->timer_begin(gc_context::kTUpdate, s);
-    adg_update_kernel<<<upd_blocks, kAdgThreads, 0, s>>>(ctl, row_ptr_of(g), g->col_idx, D, batch,
+    adg_update_kernel<<<upd_blocks, kAdgThreads, 0, s>>>(ctl, row_ptr_of(g), g->col_idx, D, batch, live,
                                                           task_start, task_len, round == 1 ? n : 0);
     ++g_launches;
     ctx->timer_end(s);
@@ -278,12 +294,14 @@ constexpr long long kNoAllocTasks = kNoAllocMaxN + kNoAllocMaxNnz / gc::kChunk +
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // layout: control block | D | U list 0 | U list 1 | task starts | task lengths
+//         | liveness bitmap
 constexpr size_t kNaOffD = align256(sizeof(gc::AdgCtl));
 constexpr size_t kNaOffU0 = kNaOffD + align256(kNoAllocMaxN * sizeof(int));
 constexpr size_t kNaOffU1 = kNaOffU0 + align256(kNoAllocMaxN * sizeof(int));
 constexpr size_t kNaOffTs = kNaOffU1 + align256(kNoAllocMaxN * sizeof(int));
 constexpr size_t kNaOffTl = kNaOffTs + align256(kNoAllocTasks * sizeof(long long));
-constexpr size_t kNoAllocBytes = kNaOffTl + align256(kNoAllocTasks * sizeof(int));  // about 6.5 MB
+constexpr size_t kNaOffLive = kNaOffTl + align256(kNoAllocTasks * sizeof(int));
+constexpr size_t kNoAllocBytes = kNaOffLive + align256(kNoAllocMaxN / 32 * sizeof(unsigned));  // about 6.5 MB
 
 constexpr int kNoAllocDevices = 64;
 std::mutex g_noalloc_mu;
@@ -335,6 +353,7 @@ extern "C" gc_status gc_adg_partition_noalloc(const gc_csr* g, uint32_t eps_p, u
   int* ubuf[2] = {reinterpret_cast<int*>(base + kNaOffU0), reinterpret_cast<int*>(base + kNaOffU1)};
   long long* task_start = reinterpret_cast<long long*>(base + kNaOffTs);
   int* task_len = reinterpret_cast<int*>(base + kNaOffTl);
+  unsigned* live = reinterpret_cast<unsigned*>(base + kNaOffLive);
 
   // Every buffer above is written before it is read within a call; the
   // control block, the only state carried between kernels, is reset here.
@@ -352,11 +371,11 @@ extern "C" gc_status gc_adg_partition_noalloc(const gc_csr* g, uint32_t eps_p, u
     const int blocks = static_cast<int>(want < max_blocks ? want : max_blocks);
     adg_partition_kernel<<<blocks, kAdgThreads, 0, s>>>(ctl, rp, D, batch_out,
                                                         round == 1 ? nullptr : ubuf[cur ^ 1], ubuf[cur],
-                                                        task_start, task_len,
+                                                        task_start, task_len, live,
                                                         round == 1 ? static_cast<int>(n) : 0);
     GC_TRY_CUDA(cudaGetLastError());
-    adg_update_kernel<<<upd_blocks, kAdgThreads, 0, s>>>(ctl, rp, g->col_idx, D, batch_out, task_start,
-                                                          task_len, round == 1 ? n : 0);
+    adg_update_kernel<<<upd_blocks, kAdgThreads, 0, s>>>(ctl, rp, g->col_idx, D, batch_out, live,
+                                                          task_start, task_len, round == 1 ? n : 0);
     GC_TRY_CUDA(cudaGetLastError());
     adg_finalize_kernel<<<1, 1, 0, s>>>(ctl);
     GC_TRY_CUDA(cudaGetLastError());

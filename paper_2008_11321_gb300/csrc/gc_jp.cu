@@ -53,6 +53,17 @@ constexpr int kCoreThreads = 1024;  // largest core CTA
 constexpr int kCoreWarps = kCoreThreads / kWarp;
 constexpr int kCoreWarpsDefault = 8;
 
+__device__ __forceinline__ bool precedes(unsigned long long kw, int w, unsigned long long kv, int v) {
+  return kw > kv || (kw == kv && w > v);
+}
+
+// Priorities.  key(v) is the 64-bit order key (rho(w) > rho(v) iff
+// precedes(key(w), w, key(v), v)).  For neighbour w of v the colouring loops
+// take g = pgather(w, color) first, then pred_g(g, w, key(v), v) (is w a
+// predecessor?) and color_g(g, color, w) (its colour, 0 = not yet); a vertex
+// stores cword(key(v), c) for colour c, and a colour word x means colour
+// x & cmask().
+
 struct KeyFused {  // JP-ADG: (batch << 32) | rho_R(v), rho_R from one seed
   const int* batch;
   unsigned long long seed;
@@ -60,6 +71,43 @@ struct KeyFused {  // JP-ADG: (batch << 32) | rho_R(v), rho_R from one seed
   __device__ __forceinline__ unsigned tie(int v) const { return tie_hash(seed, static_cast<unsigned>(v)); }
   __device__ __forceinline__ unsigned long long operator()(int v) const {
     return (static_cast<unsigned long long>(static_cast<unsigned>(bat(v))) << 32) | tie(v);
+  }
+  using PG = unsigned long long;
+  __device__ __forceinline__ PG pgather(int w, const int*) const { return (*this)(w); }
+  __device__ __forceinline__ bool pred_g(PG kw, int w, unsigned long long kv, int v) const {
+    return precedes(kw, w, kv, v);
+  }
+  __device__ __forceinline__ int color_g(PG, const int* color, int w) const { return ld_relaxed(color + w); }
+  __device__ __forceinline__ int cmask() const { return ~0; }
+  __device__ __forceinline__ int cword(unsigned long long, int c) const { return c; }
+};
+
+// JP-ADG with each vertex's batch kept in the top 8 bits of its colour word
+// (batch << 24 | colour; ADG took at most 255 rounds, and c colours need at
+// least c(c-1)/2 edges, so colours stay below 2^24): one load of a
+// neighbour's word gives both its priority and its colour, and the randomly
+// read state is one n-word array instead of two.
+struct KeyState {
+  const int* state;  // the colour array during JP-ADG
+  unsigned long long seed;
+  // a coherent load: colour bits of the array change while JP runs (the
+  // batch bits never do)
+  __device__ __forceinline__ int bat(int v) const { return static_cast<int>(static_cast<unsigned>(state[v]) >> 24); }
+  __device__ __forceinline__ unsigned tie(int v) const { return tie_hash(seed, static_cast<unsigned>(v)); }
+  __device__ __forceinline__ unsigned long long operator()(int v) const {
+    return (static_cast<unsigned long long>(static_cast<unsigned>(bat(v))) << 32) | tie(v);
+  }
+  using PG = int;
+  __device__ __forceinline__ PG pgather(int w, const int* color) const { return ld_relaxed(color + w); }
+  __device__ __forceinline__ bool pred_g(PG x, int w, unsigned long long kv, int v) const {
+    const unsigned long long kw =
+        (static_cast<unsigned long long>(static_cast<unsigned>(x) >> 24) << 32) | tie(w);
+    return precedes(kw, w, kv, v);
+  }
+  __device__ __forceinline__ int color_g(PG x, const int*, int) const { return x & 0xffffff; }
+  __device__ __forceinline__ int cmask() const { return 0xffffff; }
+  __device__ __forceinline__ int cword(unsigned long long kv, int c) const {
+    return static_cast<int>(static_cast<unsigned>(kv >> 32) << 24) | c;
   }
 };
 
@@ -71,16 +119,28 @@ struct KeyPacked {  // JP-ADG over many disjoint graphs: rho_R precomputed per v
   __device__ __forceinline__ unsigned long long operator()(int v) const {
     return (static_cast<unsigned long long>(static_cast<unsigned>(bat(v))) << 32) | tie(v);
   }
+  using PG = unsigned long long;
+  __device__ __forceinline__ PG pgather(int w, const int*) const { return (*this)(w); }
+  __device__ __forceinline__ bool pred_g(PG kw, int w, unsigned long long kv, int v) const {
+    return precedes(kw, w, kv, v);
+  }
+  __device__ __forceinline__ int color_g(PG, const int* color, int w) const { return ld_relaxed(color + w); }
+  __device__ __forceinline__ int cmask() const { return ~0; }
+  __device__ __forceinline__ int cword(unsigned long long, int c) const { return c; }
 };
 
 struct KeyGiven {  // any priority array
   const unsigned long long* prio;
   __device__ __forceinline__ unsigned long long operator()(int v) const { return __ldg(prio + v); }
+  using PG = unsigned long long;
+  __device__ __forceinline__ PG pgather(int w, const int*) const { return (*this)(w); }
+  __device__ __forceinline__ bool pred_g(PG kw, int w, unsigned long long kv, int v) const {
+    return precedes(kw, w, kv, v);
+  }
+  __device__ __forceinline__ int color_g(PG, const int* color, int w) const { return ld_relaxed(color + w); }
+  __device__ __forceinline__ int cmask() const { return ~0; }
+  __device__ __forceinline__ int cword(unsigned long long, int c) const { return c; }
 };
-
-__device__ __forceinline__ bool precedes(unsigned long long kw, int w, unsigned long long kv, int v) {
-  return kw > kv || (kw == kv && w > v);
-}
 
 __device__ __forceinline__ long long gtid() {
   return static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -92,15 +152,15 @@ __device__ __forceinline__ long long gstride() {
 // ---------------------------------------------------------------------------
 // Waiting on a colour word (global memory), bounded, with backoff.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int wait_color(const int* p, JpCtl* ctl, unsigned long long& spins) {
-  int c = ld_relaxed(p);
+__device__ __forceinline__ int wait_color(const int* p, int cmask, JpCtl* ctl, unsigned long long& spins) {
+  int c = ld_relaxed(p) & cmask;
   if (c != 0) return c;
   const unsigned long long t0 = global_ns();
   unsigned sleep_ns = 32;
   for (unsigned it = 1;; ++it) {
     __nanosleep(sleep_ns);
     if (sleep_ns < 256) sleep_ns <<= 1;
-    c = ld_relaxed(p);
+    c = ld_relaxed(p) & cmask;
     if (c != 0) return c;
     ++spins;
     if ((it & 15u) == 0) {
@@ -128,13 +188,16 @@ __device__ int color_lane(int v, const long long* __restrict__ row_ptr, const in
   unsigned later = 0;
   for (long long k = s; k < e; k += U) {
     int w[U], c[U];
+    typename Key::PG g[U];
     bool pred[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) w[u] = k + u < e ? __ldg(col + k + u) : -1;
 #pragma unroll
-    for (int u = 0; u < U; ++u) pred[u] = w[u] >= 0 && precedes(key(w[u]), w[u], kv, v);
+    for (int u = 0; u < U; ++u) g[u] = w[u] >= 0 ? key.pgather(w[u], color) : typename Key::PG{};
 #pragma unroll
-    for (int u = 0; u < U; ++u) c[u] = pred[u] ? ld_relaxed(color + w[u]) : -1;
+    for (int u = 0; u < U; ++u) pred[u] = w[u] >= 0 && key.pred_g(g[u], w[u], kv, v);
+#pragma unroll
+    for (int u = 0; u < U; ++u) c[u] = pred[u] ? key.color_g(g[u], color, w[u]) : -1;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (!pred[u]) continue;
@@ -147,11 +210,11 @@ __device__ int color_lane(int v, const long long* __restrict__ row_ptr, const in
   while (later) {
     const int pos = __ffs(later) - 1;
     later &= later - 1;
-    const int cu = wait_color(color + __ldg(col + s + pos), ctl, spins);
+    const int cu = wait_color(color + __ldg(col + s + pos), key.cmask(), ctl, spins);
     if (cu <= 64) used |= 1ull << (cu - 1);
   }
   const int c = __ffsll(static_cast<long long>(~used));
-  st_relaxed(color + v, c);
+  st_relaxed(color + v, key.cword(kv, c));
   return c;
 }
 
@@ -179,13 +242,16 @@ __device__ int color_warp(int v, unsigned* bm, const long long* __restrict__ row
         constexpr int U = 4;
         for (; k < e && resume < 0; k += 32 * U) {
           int w[U], c[U];
+          typename Key::PG g[U];
           bool pred[U];
 #pragma unroll
           for (int u = 0; u < U; ++u) w[u] = k + 32 * u < e ? __ldg(col + k + 32 * u) : -1;
 #pragma unroll
-          for (int u = 0; u < U; ++u) pred[u] = w[u] >= 0 && precedes(key(w[u]), w[u], kv, v);
+          for (int u = 0; u < U; ++u) g[u] = w[u] >= 0 ? key.pgather(w[u], color) : typename Key::PG{};
 #pragma unroll
-          for (int u = 0; u < U; ++u) c[u] = pred[u] ? ld_relaxed(color + w[u]) : -1;
+          for (int u = 0; u < U; ++u) pred[u] = w[u] >= 0 && key.pred_g(g[u], w[u], kv, v);
+#pragma unroll
+          for (int u = 0; u < U; ++u) c[u] = pred[u] ? key.color_g(g[u], color, w[u]) : -1;
 #pragma unroll
           for (int u = 0; u < U; ++u) {
             if (!pred[u]) continue;
@@ -201,7 +267,7 @@ __device__ int color_warp(int v, unsigned* bm, const long long* __restrict__ row
           }
         }
         for (int j = 0; j < np; ++j) {
-          const int c = wait_color(color + pend[j], ctl, spins);
+          const int c = wait_color(color + pend[j], key.cmask(), ctl, spins);
           if (c > base && c <= base + kColorWin)
             atomicOr(&bm[(c - base - 1) >> 5], 1u << ((c - base - 1) & 31));
         }
@@ -217,7 +283,7 @@ __device__ int color_warp(int v, unsigned* bm, const long long* __restrict__ row
       const int f = __ffs(fm) - 1;
       const unsigned fb = __shfl_sync(kFull, freeb, f);
       const int c = base + f * 32 + __ffs(fb);
-      if (lane == 0) st_relaxed(color + v, c);
+      if (lane == 0) st_relaxed(color + v, key.cword(kv, c));
       return c;
     }
   }
@@ -374,11 +440,11 @@ jpf_hist_kernel(Key key, const long long* __restrict__ row_ptr, long long n, Buc
   for (long long v = gtid(); v < n; v += gstride()) {
     const long long deg = row_ptr[v + 1] - row_ptr[v];
     if (deg == 0) {
-      color[v] = 1;  // isolated: no predecessor, smallest colour
+      color[v] = key.cword(key(static_cast<int>(v)), 1);  // isolated: no predecessor, smallest colour
       isolated = true;
       continue;
     }
-    color[v] = 0;
+    color[v] = key.cword(key(static_cast<int>(v)), 0);
     const long long b = bucket_of(key.bat(static_cast<int>(v)), key.tie(static_cast<int>(v)), bp);
     const long long cls = deg > kSmallDeg ? 0 : 1;
     atomicAdd(&cnt[cls * (bp.B + 1) + b], 1ull);
@@ -778,7 +844,7 @@ jpf_core_solve_kernel(const int* __restrict__ order, const long long* __restrict
   for (int t = threadIdx.x;; t += blockDim.x) {  // this CTA's vertices, increasing
     const int i = nwc * (rank + nctas * (t / nwc)) + t % nwc;
     if (i >= kc) break;
-    color[order[i]] = s_col[i];
+    color[order[i]] |= s_col[i];  // the word holds 0 or the vertex's batch bits
   }
 }
 
@@ -966,6 +1032,17 @@ size_t jpadg_scratch_bytes(long long n, long long nnz, int rounds) {
 }
 
 namespace {
+// KeyState: colour words start as batch << 24 (colour 0) and lose the batch
+// bits at the end.
+__global__ void state_init_kernel(const int* __restrict__ batch, long long n, int* __restrict__ color) {
+  for (long long v = gtid(); v < n; v += gstride())
+    color[v] = static_cast<int>(static_cast<unsigned>(batch[v]) << 24);
+}
+
+__global__ void state_strip_kernel(long long n, int* __restrict__ color) {
+  for (long long v = gtid(); v < n; v += gstride()) color[v] &= 0xffffff;
+}
+
 template <class Key>
 gc_status jp_adg_impl(gc_context* ctx, Arena a, const gc_csr* g, const Key& key, const int* D,
                       int rounds, int* color, int* num_colors_out, cudaStream_t s) {
@@ -1123,7 +1200,18 @@ gc_status jp_adg_impl(gc_context* ctx, Arena a, const gc_csr* g, const Key& key,
 gc_status jp_run_fused(gc_context* ctx, Arena a, const gc_csr* g, const int* batch, const int* D,
                        int rounds, unsigned long long seed, int* color, int* num_colors_out,
                        cudaStream_t s) {
-  return jp_adg_impl(ctx, a, g, KeyFused{batch, seed}, D, rounds, color, num_colors_out, s);
+  const long long n = g->n;
+  if (rounds > 255 || n == 0)
+    return jp_adg_impl(ctx, a, g, KeyFused{batch, seed}, D, rounds, color, num_colors_out, s);
+  const int blocks = ctx->num_sms * 8;
+  state_init_kernel<<<blocks, 256, 0, s>>>(batch, n, color);
+  ++g_launches;
+  GC_TRY_CUDA(cudaGetLastError());
+  GC_TRY(jp_adg_impl(ctx, a, g, KeyState{color, seed}, D, rounds, color, num_colors_out, s));
+  state_strip_kernel<<<blocks, 256, 0, s>>>(n, color);
+  ++g_launches;
+  GC_TRY_CUDA(cudaGetLastError());
+  return GC_OK;
 }
 
 gc_status jp_run_packed(gc_context* ctx, Arena a, const gc_csr* g, const int* batch, const unsigned* tiev,

@@ -93,10 +93,10 @@ def path_bytes(n, nnz, sum_u, decrements):
 # reported kernel from an ncu capture of the current code, by (workload,
 # kernel); empty until such a capture exists for the current kernels.
 KERNEL_TRAFFIC = {
-    # R-MAT scale 24 defaults, profiles/launches_rmat24.md (MB per launch)
-    ("rmat24", "jpf_core_solve_kernel"): None,  # cluster solver: not captured yet
-    ("rmat24", "adg_update_kernel"): 487.0e6,
-    ("rmat24", "jp_color_kernel"): 1480.4e6,
+    # R-MAT scale 24 defaults, profiles/launches_rmat24.md (DRAM bytes per launch)
+    ("rmat24", "jpf_core_solve_kernel"): 35.0e6,
+    ("rmat24", "adg_update_kernel"): 350.5e6,
+    ("rmat24", "jp_color_kernel"): 1125.5e6,
 }
 
 

@@ -84,6 +84,19 @@ def test_zero_vertices(ctx):
     assert ctx.gc_color_graph(dg, 1, 100, 42, color) == (0, 0)
 
 
+@pytest.mark.parametrize("n", [500, 520, 1500])
+def test_many_adg_rounds(ctx, n):
+    # With eps = 2^-20 the ADG threshold on a path stays 1 (Algorithm 1), so
+    # each round removes only the two ends: n/2 rounds.  JP-ADG keeps the batch
+    # in 8 bits of the colour word up to 255 rounds and orders by the full
+    # batch array beyond; 500 / 520 / 1500 vertices land on both sides.
+    g = path(n)
+    p, q = 1, 1 << 20
+    _, _, onr, _ = oracle.jp_adg(g, p, q, 42)
+    assert onr == n // 2
+    assert_same_as_oracle(ctx, g, p, q)
+
+
 def test_clique_beyond_colour_window(ctx):
     # K_1100: colours 1..1100 exceed one 1024-colour window of the warp path
     g = complete(1100)

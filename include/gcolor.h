@@ -102,7 +102,20 @@ typedef struct {
 const char *gc_status_str(gc_status s);
 
 /* Create a context bound to CUDA device `device`.  Allocates nothing large
- * until the first call needs scratch.  *ctx is NULL on failure. */
+ * until the first call needs scratch.  *ctx is NULL on failure.
+ *
+ * The environment is read here, once per context:
+ *   GC_CORE_TARGET    JP-ADG core size in vertices (default 16384, at most
+ *                     32768; 0: no core);
+ *   GC_CORE_CLUSTER   at most this many CTAs in the core cluster (1..16);
+ *   GC_CORE_WARPS     warps per core CTA (1..32, default 8);
+ *   GC_WAIT_LIMIT_MS  bound of every device-side wait on a colour (default
+ *                     4000); a wait that runs out ends the call with
+ *                     GC_ERR_TIMEOUT and leaves the context usable;
+ * and, to test those error paths, failure injection:
+ *   GC_INJECT_STALL   id of a vertex outside the core whose colour is never
+ *                     published, so that its successors' waits run out;
+ *   GC_INJECT_OOM     non-zero: every scratch allocation fails (GC_ERR_OOM). */
 gc_status gc_create(gc_context **ctx, int device);
 
 /* Release the context's scratch memory and the context itself (NULL ok). */

@@ -173,10 +173,12 @@ gc_status grow(void** buf, size_t* cap, size_t bytes) {
 }
 }  // namespace
 
-gc_status gc_context::reserve(size_t bytes) { return grow(&scratch, &scratch_bytes, bytes); }
-gc_status gc_context::reserve_vert(size_t bytes) { return grow(&vbuf, &vbuf_bytes, bytes); }
-gc_status gc_context::reserve_aux(size_t bytes) { return grow(&aux, &aux_bytes, bytes); }
-gc_status gc_context::reserve_pack(size_t bytes) { return grow(&pack, &pack_bytes, bytes); }
+gc_status gc_context::reserve(size_t bytes) {
+  return fail_alloc ? GC_ERR_OOM : grow(&scratch, &scratch_bytes, bytes);
+}
+gc_status gc_context::reserve_vert(size_t bytes) { return fail_alloc ? GC_ERR_OOM : grow(&vbuf, &vbuf_bytes, bytes); }
+gc_status gc_context::reserve_aux(size_t bytes) { return fail_alloc ? GC_ERR_OOM : grow(&aux, &aux_bytes, bytes); }
+gc_status gc_context::reserve_pack(size_t bytes) { return fail_alloc ? GC_ERR_OOM : grow(&pack, &pack_bytes, bytes); }
 
 extern "C" {
 
@@ -208,6 +210,13 @@ gc_status gc_create(gc_context** out, int device) {
   if (!ctx) return GC_ERR_OOM;
   ctx->device = device;
   if (const char* env = getenv("GC_CORE_TARGET")) ctx->core_target = atoll(env);
+  // failure injection for tests of the error paths (see gc_context)
+  if (const char* env = getenv("GC_WAIT_LIMIT_MS")) {
+    const long long ms = atoll(env);
+    if (ms >= 1 && ms <= 600000) ctx->wait_ns = static_cast<unsigned long long>(ms) * 1000000ull;
+  }
+  if (const char* env = getenv("GC_INJECT_STALL")) ctx->stall_vertex = atoi(env);
+  if (const char* env = getenv("GC_INJECT_OOM")) ctx->fail_alloc = env[0] != '\0' && env[0] != '0';
   if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
       cudaDeviceGetAttribute(&ctx->coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess) {
     delete ctx;

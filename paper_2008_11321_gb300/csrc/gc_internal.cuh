@@ -66,8 +66,10 @@ struct JpCtl {
   long long bstar;               // last core bucket (-1: no core)
   long long core_preds;          // predecessor entries of the core
   unsigned long long core_deg;   // degree sum of the core vertices
+  unsigned long long wait_ns;    // bound of every wait on a colour (ns)
   int max_color;
   int err;
+  int stall;                     // injected fault: this vertex never publishes its colour (-1: none)
 };
 static_assert(sizeof(JpCtl) <= 256, "JpCtl must fit the pinned read-back buffer");
 
@@ -151,6 +153,13 @@ struct gc_context {
   int coop = 0;
   int timing = 0;
   long long core_target = kCoreDefault_;  // JP-ADG core size (vertices)
+  // Failure injection, for tests of the error paths (set from the
+  // environment at gc_create): the bound of every device-side wait, a
+  // vertex whose colour is never published (so that its successors' waits
+  // run out), and allocation failure.
+  unsigned long long wait_ns = gc::kWaitLimitNs;
+  int stall_vertex = -1;
+  bool fail_alloc = false;
   int core_cluster = 0;                   // CTAs of the core cluster (0: not chosen yet)
   int core_warps = 0;                     // warps per core CTA
   // scratch arena (device)

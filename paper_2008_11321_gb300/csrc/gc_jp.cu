@@ -18,7 +18,7 @@
 // order keys tie).  Buckets hold far fewer vertices than a list has workers,
 // so some worker is free and takes v*.  Every block serves both lists, so
 // this holds with or without all blocks resident.  Every wait is still
-// bounded (kWaitLimitNs); a wait that runs out sets the error word and the
+// bounded (4 s by default); a wait that runs out sets the error word and the
 // remaining waits end early, so the kernel always returns.
 //
 // JP-ADG (the fused path of gc_color_graph) runs in three stages:
@@ -165,7 +165,7 @@ __device__ __forceinline__ int wait_color(const int* p, int cmask, JpCtl* ctl, u
     ++spins;
     if ((it & 15u) == 0) {
       if (ld_relaxed(&ctl->err) != 0) return 1;
-      if (global_ns() - t0 > kWaitLimitNs) {
+      if (global_ns() - t0 > ctl->wait_ns) {
         atomicExch(&ctl->err, kDevTimeout);
         return 1;
       }
@@ -214,7 +214,7 @@ __device__ int color_lane(int v, const long long* __restrict__ row_ptr, const in
     if (cu <= 64) used |= 1ull << (cu - 1);
   }
   const int c = __ffsll(static_cast<long long>(~used));
-  st_relaxed(color + v, key.cword(kv, c));
+  if (v != ctl->stall) st_relaxed(color + v, key.cword(kv, c));
   return c;
 }
 
@@ -283,7 +283,7 @@ __device__ int color_warp(int v, unsigned* bm, const long long* __restrict__ row
       const int f = __ffs(fm) - 1;
       const unsigned fb = __shfl_sync(kFull, freeb, f);
       const int c = base + f * 32 + __ffs(fb);
-      if (lane == 0) st_relaxed(color + v, key.cword(kv, c));
+      if (lane == 0 && v != ctl->stall) st_relaxed(color + v, key.cword(kv, c));
       return c;
     }
   }
@@ -345,10 +345,12 @@ jp_color_kernel(JpCtl* ctl, unsigned long long* cursors, const long long* __rest
   }
 }
 
-__global__ void jp_init_kernel(JpCtl* ctl) {
+__global__ void jp_init_kernel(JpCtl* ctl, unsigned long long wait_ns, int stall) {
   JpCtl c{};
   c.key_and = ~0ull;
   c.bstar = -1;
+  c.wait_ns = wait_ns;
+  c.stall = stall;
   *ctl = c;
 }
 
@@ -522,8 +524,15 @@ jpf_scatter_kernel(Key key, const long long* __restrict__ row_ptr, long long n, 
   }
 }
 
-// Exact order inside each core bucket (the buckets are tiny): insertion sort
-// by (rho_R, id) descending; then lid[v] = position of v in the core.
+// Exact order inside each core bucket: by (rho_R, id) descending (all
+// vertices of a bucket share their batch); then lid[v] = position of v in the
+// core.  Buckets hold ~32 vertices on average, but one batch can hold most of
+// a small graph: buckets of at most kSortSmall vertices (and, rarely, above
+// kSortBig) get a per-thread insertion sort here, the others a shared-memory
+// bitonic sort by one block each (jpf_core_sort_big_kernel).
+constexpr int kSortSmall = 64;
+constexpr int kSortBig = 16384;  // 128 KB of 64-bit sort values per block
+
 template <class Key>
 __global__ void jpf_core_sort_kernel(const unsigned long long* __restrict__ cur_tot, const JpCtl* ctl,
                                      Key key, int* __restrict__ order, int* __restrict__ lid) {
@@ -532,6 +541,7 @@ __global__ void jpf_core_sort_kernel(const unsigned long long* __restrict__ cur_
     // after the scatter, cur_tot[b] is the end of bucket b
     const long long s = b == 0 ? 0 : static_cast<long long>(cur_tot[b - 1]);
     const long long e = static_cast<long long>(cur_tot[b]);
+    if (e - s > kSortSmall && e - s <= kSortBig) continue;
     for (long long i = s + 1; i < e; ++i) {
       const int x = order[i];
       const unsigned long long kx = key(x);
@@ -545,6 +555,70 @@ __global__ void jpf_core_sort_kernel(const unsigned long long* __restrict__ cur_
       order[j + 1] = x;
     }
     for (long long i = s; i < e; ++i) lid[order[i]] = static_cast<int>(i);
+  }
+}
+
+// Core buckets of kSortSmall < size <= kSortBig vertices, each sorted by one
+// block: a block checks 1024 buckets at once (one per thread), then sorts the
+// large ones among them in turn: sort values (rho_R << 32 | id), padded with
+// zeros to a power of two, bitonic sort descending in shared memory (a zero
+// pad equals only vertex 0 with rho_R 0, which then takes the same place).
+template <class Key>
+__global__ void __launch_bounds__(1024)
+jpf_core_sort_big_kernel(const unsigned long long* __restrict__ cur_tot, const JpCtl* ctl, Key key,
+                         int* __restrict__ order, int* __restrict__ lid) {
+  extern __shared__ unsigned long long s_v[];
+  __shared__ long long s_big[1024];  // large buckets among this block's 1024
+  __shared__ int s_nbig;
+  const long long bs = ctl->bstar;
+  for (long long base = static_cast<long long>(blockIdx.x) * blockDim.x; base <= bs;
+       base += static_cast<long long>(gridDim.x) * blockDim.x) {
+    if (threadIdx.x == 0) s_nbig = 0;
+    __syncthreads();
+    const long long b = base + threadIdx.x;
+    if (b <= bs) {
+      const long long k = static_cast<long long>(cur_tot[b]) - (b == 0 ? 0 : static_cast<long long>(cur_tot[b - 1]));
+      if (k > kSortSmall && k <= kSortBig) s_big[atomicAdd(&s_nbig, 1)] = b;
+    }
+    __syncthreads();
+    const int nbig = s_nbig;
+    for (int t = 0; t < nbig; ++t) {
+      const long long bb = s_big[t];
+      const long long s = bb == 0 ? 0 : static_cast<long long>(cur_tot[bb - 1]);
+      const int k = static_cast<int>(static_cast<long long>(cur_tot[bb]) - s);
+      int p2 = 1;
+      while (p2 < k) p2 <<= 1;
+      for (int i = threadIdx.x; i < p2; i += blockDim.x) {
+        unsigned long long u = 0;
+        if (i < k) {
+          const int x = order[s + i];
+          u = (static_cast<unsigned long long>(key.tie(x)) << 32) | static_cast<unsigned>(x);
+        }
+        s_v[i] = u;
+      }
+      __syncthreads();
+      for (int size = 2; size <= p2; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+          for (int i = threadIdx.x; i < (p2 >> 1); i += blockDim.x) {
+            const int lo = 2 * i - (i & (stride - 1));
+            const int hi = lo + stride;
+            const bool desc = (lo & size) == 0;
+            const unsigned long long a = s_v[lo], c = s_v[hi];
+            if (desc ? a < c : a > c) {
+              s_v[lo] = c;
+              s_v[hi] = a;
+            }
+          }
+          __syncthreads();
+        }
+      }
+      for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        const int x = static_cast<int>(static_cast<unsigned>(s_v[i] & 0xffffffffull));
+        order[s + i] = x;
+        lid[x] = static_cast<int>(s + i);
+      }
+      __syncthreads();
+    }
   }
 }
 
@@ -730,7 +804,8 @@ jpf_core_solve_kernel(const int* __restrict__ order, const long long* __restrict
   const uint4* groups = reinterpret_cast<const uint4*>(stream);
   const unsigned long long t0 = global_ns();
   bool timed_out = false;
-  auto expired = [&]() { return timed_out || ld_relaxed(&ctl->err) != 0 || global_ns() - t0 > kWaitLimitNs; };
+  const unsigned long long wait_ns = ctl->wait_ns;
+  auto expired = [&]() { return timed_out || ld_relaxed(&ctl->err) != 0 || global_ns() - t0 > wait_ns; };
   int local_max = 0;
   for (int i = nwc * rank + warp; i < kc; i += nwc * nctas) {
     const long long a = qoff[i], b = qoff[i + 1];
@@ -979,7 +1054,7 @@ gc_status jp_run_given(gc_context* ctx, Arena a, const gc_csr* g, const unsigned
   const long long* rp = row_ptr_of(g);
   const KeyGiven key{prio};
   const int blocks = ctx->num_sms * 8;
-  jp_init_kernel<<<1, 1, 0, s>>>(ctl);
+  jp_init_kernel<<<1, 1, 0, s>>>(ctl, ctx->wait_ns, ctx->stall_vertex);
   ++g_launches;
   jp_keys_kernel<<<blocks, 256, 0, s>>>(key, rp, n, sb.keys[0], sb.vals[0], ctl);
   ++g_launches;
@@ -1078,7 +1153,7 @@ gc_status jp_adg_impl(gc_context* ctx, Arena a, const gc_csr* g, const Key& key,
   long long* tot_ll = reinterpret_cast<long long*>(tot);
 
   // 1. order
-  jp_init_kernel<<<1, 1, 0, s>>>(ctl);
+  jp_init_kernel<<<1, 1, 0, s>>>(ctl, ctx->wait_ns, ctx->stall_vertex);
   ++g_launches;
   GC_TRY_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * 2 * nb, s));
   jpf_hist_kernel<<<blocks, 256, 0, s>>>(key, rp, n, bp, cnt, color, ctl);
@@ -1101,6 +1176,13 @@ gc_status jp_adg_impl(gc_context* ctx, Arena a, const gc_csr* g, const Key& key,
   ++g_launches;
   jpf_core_sort_kernel<<<blocks, 256, 0, s>>>(tot, ctl, key, order, lid);
   ++g_launches;
+  {
+    const int smem = kSortBig * static_cast<int>(sizeof(unsigned long long));
+    GC_TRY_CUDA(cudaFuncSetAttribute(jpf_core_sort_big_kernel<Key>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     smem));
+    jpf_core_sort_big_kernel<<<ctx->num_sms, 1024, smem, s>>>(tot, ctl, key, order, lid);
+    ++g_launches;
+  }
   GC_TRY_CUDA(cudaGetLastError());
 
   // 2. core

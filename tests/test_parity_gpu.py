@@ -84,6 +84,14 @@ def test_zero_vertices(ctx):
     assert ctx.gc_color_graph(dg, 1, 100, 42, color) == (0, 0)
 
 
+@pytest.mark.parametrize("n,seed", [(2046, 43), (8000, 7)])
+def test_large_core_buckets(ctx, n, seed):
+    # Barabasi-Albert graphs small enough to be all core, with ~80% of the
+    # vertices in ADG's first batch: core buckets of ~200 vertices, ordered by
+    # the block-wide sort rather than the per-thread one.
+    assert_same_as_oracle(ctx, gg.barabasi_albert(n, 14, seed), 1, 10)
+
+
 @pytest.mark.parametrize("n", [500, 520, 1500])
 def test_many_adg_rounds(ctx, n):
     # With eps = 2^-20 the ADG threshold on a path stays 1 (Algorithm 1), so

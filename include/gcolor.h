@@ -109,8 +109,9 @@ const char *gc_status_str(gc_status s);
  *                     32768; 0: no core);
  *   GC_CORE_CLUSTER   at most this many CTAs in the core cluster (1..16);
  *   GC_CORE_WARPS     warps per core CTA (1..32, default 8);
- *   GC_WAIT_LIMIT_MS  bound of every device-side wait on a colour (default
- *                     4000); a wait that runs out ends the call with
+ *   GC_WAIT_LIMIT_MS  bound of every wait on a colour outside the core
+ *                     (default 4000; the core's waits are bounded by 4 s);
+ *                     a wait that runs out ends the call with
  *                     GC_ERR_TIMEOUT and leaves the context usable;
  * and, to test those error paths, failure injection:
  *   GC_INJECT_STALL   id of a vertex outside the core whose colour is never

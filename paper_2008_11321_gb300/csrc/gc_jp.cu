@@ -149,10 +149,18 @@ __device__ __forceinline__ long long gstride() {
   return static_cast<long long>(gridDim.x) * blockDim.x;
 }
 
+// Per-launch constants of the bulk kernel, read from the control block once
+// per block into shared memory.
+struct JpLimits {
+  unsigned long long wait_ns;  // bound of a wait
+  int stall;                   // injected fault: vertex that never publishes (-1: none)
+};
+
 // ---------------------------------------------------------------------------
 // Waiting on a colour word (global memory), bounded, with backoff.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int wait_color(const int* p, int cmask, JpCtl* ctl, unsigned long long& spins) {
+__device__ __forceinline__ int wait_color(const int* p, int cmask, JpCtl* ctl, const JpLimits& lim,
+                                          unsigned long long& spins) {
   int c = ld_relaxed(p) & cmask;
   if (c != 0) return c;
   const unsigned long long t0 = global_ns();
@@ -165,7 +173,7 @@ __device__ __forceinline__ int wait_color(const int* p, int cmask, JpCtl* ctl, u
     ++spins;
     if ((it & 15u) == 0) {
       if (ld_relaxed(&ctl->err) != 0) return 1;
-      if (global_ns() - t0 > ctl->wait_ns) {
+      if (global_ns() - t0 > lim.wait_ns) {
         atomicExch(&ctl->err, kDevTimeout);
         return 1;
       }
@@ -180,7 +188,8 @@ __device__ __forceinline__ int wait_color(const int* p, int cmask, JpCtl* ctl, u
 // position mask and waited on after the scan.
 template <class Key>
 __device__ int color_lane(int v, const long long* __restrict__ row_ptr, const int* __restrict__ col,
-                          const Key& key, int* color, JpCtl* ctl, unsigned long long& spins) {
+                          const Key& key, int* color, JpCtl* ctl, const JpLimits& lim,
+                          unsigned long long& spins) {
   constexpr int U = 4;
   const unsigned long long kv = key(v);
   const long long s = row_ptr[v], e = row_ptr[v + 1];
@@ -210,11 +219,11 @@ __device__ int color_lane(int v, const long long* __restrict__ row_ptr, const in
   while (later) {
     const int pos = __ffs(later) - 1;
     later &= later - 1;
-    const int cu = wait_color(color + __ldg(col + s + pos), key.cmask(), ctl, spins);
+    const int cu = wait_color(color + __ldg(col + s + pos), key.cmask(), ctl, lim, spins);
     if (cu <= 64) used |= 1ull << (cu - 1);
   }
   const int c = __ffsll(static_cast<long long>(~used));
-  if (v != ctl->stall) st_relaxed(color + v, key.cword(kv, c));
+  if (v != lim.stall) st_relaxed(color + v, key.cword(kv, c));
   return c;
 }
 
@@ -225,7 +234,7 @@ __device__ int color_lane(int v, const long long* __restrict__ row_ptr, const in
 template <class Key>
 __device__ int color_warp(int v, unsigned* bm, const long long* __restrict__ row_ptr,
                           const int* __restrict__ col, const Key& key, int* color, JpCtl* ctl,
-                          unsigned long long& spins) {
+                          const JpLimits& lim, unsigned long long& spins) {
   const int lane = threadIdx.x & 31;
   const unsigned long long kv = key(v);
   const long long s = row_ptr[v], e = row_ptr[v + 1];
@@ -267,7 +276,7 @@ __device__ int color_warp(int v, unsigned* bm, const long long* __restrict__ row
           }
         }
         for (int j = 0; j < np; ++j) {
-          const int c = wait_color(color + pend[j], key.cmask(), ctl, spins);
+          const int c = wait_color(color + pend[j], key.cmask(), ctl, lim, spins);
           if (c > base && c <= base + kColorWin)
             atomicOr(&bm[(c - base - 1) >> 5], 1u << ((c - base - 1) & 31));
         }
@@ -283,7 +292,7 @@ __device__ int color_warp(int v, unsigned* bm, const long long* __restrict__ row
       const int f = __ffs(fm) - 1;
       const unsigned fb = __shfl_sync(kFull, freeb, f);
       const int c = base + f * 32 + __ffs(fb);
-      if (lane == 0 && v != ctl->stall) st_relaxed(color + v, key.cword(kv, c));
+      if (lane == 0 && v != lim.stall) st_relaxed(color + v, key.cword(kv, c));
       return c;
     }
   }
@@ -306,6 +315,9 @@ jp_color_kernel(JpCtl* ctl, unsigned long long* cursors, const long long* __rest
     small = big + nbig;
   }
   bool big_done = nbig == 0, small_done = nsmall == 0;
+  __shared__ JpLimits lim;  // in shared memory: no registers held for it
+  if (threadIdx.x == 0) lim = JpLimits{ctl->wait_ns, ctl->stall};
+  __syncthreads();
   const bool prefer_big = (warp & 3) != 0;  // 3/4 of the warps start on the warp path
   int local_max = 0;
   unsigned long long spins = 0;
@@ -319,7 +331,7 @@ jp_color_kernel(JpCtl* ctl, unsigned long long* cursors, const long long* __rest
         big_done = true;
         continue;
       }
-      const int c = color_warp(big[i], s_bm[warp], row_ptr, col, key, color, ctl, spins);
+      const int c = color_warp(big[i], s_bm[warp], row_ptr, col, key, color, ctl, lim, spins);
       local_max = c > local_max ? c : local_max;
     } else {
       unsigned long long i0 = 0;
@@ -331,7 +343,7 @@ jp_color_kernel(JpCtl* ctl, unsigned long long* cursors, const long long* __rest
       }
       const unsigned long long i = i0 + lane;
       if (i < static_cast<unsigned long long>(nsmall)) {
-        const int c = color_lane(small[i], row_ptr, col, key, color, ctl, spins);
+        const int c = color_lane(small[i], row_ptr, col, key, color, ctl, lim, spins);
         local_max = c > local_max ? c : local_max;
       }
       __syncwarp();
@@ -804,8 +816,9 @@ jpf_core_solve_kernel(const int* __restrict__ order, const long long* __restrict
   const uint4* groups = reinterpret_cast<const uint4*>(stream);
   const unsigned long long t0 = global_ns();
   bool timed_out = false;
-  const unsigned long long wait_ns = ctl->wait_ns;
-  auto expired = [&]() { return timed_out || ld_relaxed(&ctl->err) != 0 || global_ns() - t0 > wait_ns; };
+  // (the core's waits keep the fixed bound: its inner loops are sensitive to
+  // every register, and a stalled vertex is injected outside the core)
+  auto expired = [&]() { return timed_out || ld_relaxed(&ctl->err) != 0 || global_ns() - t0 > kWaitLimitNs; };
   int local_max = 0;
   for (int i = nwc * rank + warp; i < kc; i += nwc * nctas) {
     const long long a = qoff[i], b = qoff[i + 1];

@@ -699,9 +699,18 @@ jpf_core_preds_kernel(const int* __restrict__ col, Key key, const int* __restric
         st, len, ci, col, [&](int w, int) { return key(w); },
         [&](int w, int i, decltype(key(0)) kw) {
           const int v = order[i];
-          if (precedes(kw, w, key(v), v)) {
-            const int slot = atomicAdd(&pcnt[i], 1);
-            preds[poff[i] + slot] = lid[w];
+          const bool pred = precedes(kw, w, key(v), v);
+          // one atomic per core vertex among the lanes of this step (edges of
+          // one task sit in consecutive lanes)
+          const unsigned act = __activemask();
+          const unsigned pm = __ballot_sync(act, pred);
+          if (pred) {
+            const unsigned grp = __match_any_sync(pm, i);
+            const int leader = __ffs(grp) - 1;
+            int base = 0;
+            if ((threadIdx.x & 31) == leader) base = atomicAdd(&pcnt[i], __popc(grp));
+            base = __shfl_sync(grp, base, leader);
+            preds[poff[i] + base + __popc(grp & lanemask_lt())] = lid[w];
           }
         });
   }

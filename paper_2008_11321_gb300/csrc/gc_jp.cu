@@ -676,9 +676,22 @@ __global__ void jpf_core_tasks_kernel(const int* __restrict__ order, const long 
 
 // Predecessor lists of the core in core-local ids, edges spread over the
 // lanes of each warp across 32 tasks at a time (as in ADG's UPDATE).
-template <class Key>
+// Core membership bitmap (n bits): set for the core vertices.
+__global__ void jpf_core_bits_kernel(const int* __restrict__ order, const JpCtl* ctl, unsigned* __restrict__ cbits) {
+  const long long kc = static_cast<long long>(ctl->ncore);
+  for (long long i = gtid(); i < kc; i += gstride()) {
+    const int v = order[i];
+    atomicOr(&cbits[v >> 5], 1u << (v & 31));
+  }
+}
+
+// Predecessor lists of the core vertices.  Every predecessor of a core vertex
+// is in the core, and the core is in exact priority order, so w precedes the
+// core vertex i exactly when w is in the core and lid[w] < i: the sweep tests
+// core membership on a bitmap (n bits, resident in L2) and reads lid[w] only
+// for core neighbours, instead of gathering every neighbour's priority.
 __global__ void __launch_bounds__(256)
-jpf_core_preds_kernel(const int* __restrict__ col, Key key, const int* __restrict__ order,
+jpf_core_preds_kernel(const int* __restrict__ col, const unsigned* __restrict__ cbits,
                       const int* __restrict__ lid, const long long* __restrict__ toff,
                       const long long* __restrict__ poff, const JpCtl* ctl,
                       const int* __restrict__ task_i, const long long* __restrict__ task_start,
@@ -696,10 +709,10 @@ jpf_core_preds_kernel(const int* __restrict__ col, Key key, const int* __restric
       ci = task_i[t];
     }
     sweep_tile(
-        st, len, ci, col, [&](int w, int) { return key(w); },
-        [&](int w, int i, decltype(key(0)) kw) {
-          const int v = order[i];
-          const bool pred = precedes(kw, w, key(v), v);
+        st, len, ci, col, [&](int w, int) { return static_cast<int>((__ldg(cbits + (w >> 5)) >> (w & 31)) & 1u); },
+        [&](int w, int i, int in_core) {
+          const int lw = in_core ? __ldg(lid + w) : 0;
+          const bool pred = in_core && lw < i;
           // one atomic per core vertex among the lanes of this step (edges of
           // one task sit in consecutive lanes)
           const unsigned act = __activemask();
@@ -710,7 +723,7 @@ jpf_core_preds_kernel(const int* __restrict__ col, Key key, const int* __restric
             int base = 0;
             if ((threadIdx.x & 31) == leader) base = atomicAdd(&pcnt[i], __popc(grp));
             base = __shfl_sync(grp, base, leader);
-            preds[poff[i] + base + __popc(grp & lanemask_lt())] = lid[w];
+            preds[poff[i] + base + __popc(grp & lanemask_lt())] = lw;
           }
         });
   }
@@ -1125,7 +1138,7 @@ size_t jpadg_scratch_bytes(long long n, long long nnz, int rounds) {
                     scan_temp_elems(static_cast<long long>(kc)) + 2;
   const size_t rb = (4 * (static_cast<size_t>(bp.rounds) + 1) * 8 + 512);
   return rb + 256 + 3 * (nb * 8 + 256) + 2 * (static_cast<size_t>(n) * 4 + 256) + 2 * (kc * 8 + 256) +
-         (kc * 4 + 256) + ntask * 16 + 3 * 256 + sc * 8 + 4096;
+         (kc * 4 + 256) + ntask * 16 + 3 * 256 + sc * 8 + static_cast<size_t>((n + 31) / 32) * 4 + 256 + 4096;
 }
 
 namespace {
@@ -1155,6 +1168,7 @@ gc_status jp_adg_impl(gc_context* ctx, Arena a, const gc_csr* g, const Key& key,
   unsigned long long* tot = a.take<unsigned long long>(nb);
   int* order = a.take<int>(n);
   int* lid = a.take<int>(n);
+  unsigned* cbits = a.take<unsigned>((n + 31) / 32);
   long long* cap = a.take<long long>(kCoreMax + 1);
   long long* toff = a.take<long long>(kCoreMax + 1);
   int* pcnt = a.take<int>(kCoreMax + 1);
@@ -1166,7 +1180,7 @@ gc_status jp_adg_impl(gc_context* ctx, Arena a, const gc_csr* g, const Key& key,
   long long* temp = a.take<long long>(sc);
   unsigned long long* bounds = a.take<unsigned long long>(2 * (bp.rounds + 1));
   unsigned long long* cursors = a.take<unsigned long long>(2 * bp.rounds);
-  if (!ctl || !cnt || !tot || !order || !lid || !cap || !toff || !pcnt || !task_i || !task_start ||
+  if (!ctl || !cnt || !tot || !order || !lid || !cbits || !cap || !toff || !pcnt || !task_i || !task_start ||
       !task_len || !temp || !bounds || !cursors)
     return GC_ERR_OOM;
   const long long* rp = row_ptr_of(g);
@@ -1237,8 +1251,11 @@ gc_status jp_adg_impl(gc_context* ctx, Arena a, const gc_csr* g, const Key& key,
     jpf_core_tasks_kernel<<<blocks, 256, 0, s>>>(order, rp, toff, ctl, task_i, task_start, task_len);
     ++g_launches;
     ctx->timer_begin(gc_context::kTCorePreds, s);
-    jpf_core_preds_kernel<<<resident_grid(jpf_core_preds_kernel<Key>, 256, ctx->num_sms), 256, 0, s>>>(
-        g->col_idx, key, order, lid, toff, cap, ctl, task_i,
+    GC_TRY_CUDA(cudaMemsetAsync(cbits, 0, sizeof(unsigned) * static_cast<size_t>((n + 31) / 32), s));
+    jpf_core_bits_kernel<<<blocks, 256, 0, s>>>(order, ctl, cbits);
+    ++g_launches;
+    jpf_core_preds_kernel<<<resident_grid(jpf_core_preds_kernel, 256, ctx->num_sms), 256, 0, s>>>(
+        g->col_idx, cbits, lid, toff, cap, ctl, task_i,
                                                  task_start, task_len, pcnt, preds);
     ++g_launches;
     ctx->timer_end(s);

@@ -198,6 +198,92 @@ def cpu_baseline(w_name, seconds_target=10.0):
             "sample": f"{desc}: n={g.n}, m={g.m}, {reps} run(s) of ADG + Greedy, {total:.1f} s"}
 
 
+PRIORITIES = {"r": (0, "JP-R"), "ff": (1, "JP-FF"), "lf": (2, "JP-LF"), "llf": (3, "JP-LLF")}
+
+
+def run_variant(args, rank, world):
+    """A JP variant other than JP-ADG (Section 4.1): one step is the priority
+    (gc_make_priority_kind) plus JP (gc_jp_color) on the resident graph."""
+    import torch
+    import torch.distributed as dist
+    from paper_2008_11321_gb300 import _build
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    import paper_2008_11321_gb300 as gcp
+    kind, name = PRIORITIES[args.priority]
+    w = WORKLOADS[args.workload]
+    seed = w["seed"]
+    g = make_graph(w, pinned=True)
+    n, nnz, m = g.n, g.nnz, g.m
+    dg = gcp.DeviceGraph(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col_idx).to(dev))
+    key = torch.empty(n, dtype=torch.int64, device=dev)
+    color = torch.empty(n, dtype=torch.int32, device=dev)
+    ctx = gcp.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        ctx.gc_make_priority_kind(dg, kind, seed, key)
+        nc = ctx.gc_jp_color(dg, key, color)
+    ctx.gc_set_timing(True)
+    sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    launches, bulk_ms = 0, 0.0
+    for _ in range(args.steps):
+        ctx.gc_make_priority_kind(dg, kind, seed, key)
+        launches += ctx.gc_get_stats().launches
+        nc = ctx.gc_jp_color(dg, key, color)
+        st = ctx.gc_get_stats()
+        launches += st.launches
+        bulk_ms += st.ms_jp_color
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    t = torch.tensor([ev0.elapsed_time(ev1) / 1e3], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    peak, peak_kind = load_peak()
+    # JP bulk over all vertices: 28 B per vertex, 12 B per edge (neighbour id,
+    # its 8-byte key), 4 B per predecessor edge (its colour; half the edges)
+    kbytes = 28 * n + 12 * nnz + 2 * nnz
+    kms = bulk_ms / args.steps
+    achieved = kbytes / (kms / 1e3) / 1e9 if kms > 0 else 0.0
+    line = {
+        "metric": METRIC, "value": m * args.steps * world / t_max, "unit": "edges/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": w["desc"].replace("eps=1/100, ", ""), "priority": name, "n": n, "m": m,
+                   "seed": seed, "num_colors": nc,
+                   "l2": f"inputs larger than L2 (col_idx {4 * nnz / 1e9:.2f} GB), no flush"},
+        "roofline": {"bound": "hbm", "kernel": "jp_color_kernel", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "algorithmic_bytes_per_launch": kbytes, "ms_per_launch": kms, "launches_per_step": 1},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -454,6 +540,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat24")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--priority", choices=["adg"] + sorted(PRIORITIES), default="adg",
+                    help="JP priority: adg (JP-ADG, the default) or another JP variant")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: --warmup below 3 is outside the timing rules", file=sys.stderr)
@@ -464,6 +552,10 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.priority != "adg":
+        if WORKLOADS[args.workload]["kind"] in ("batch", "serve"):
+            ap.error("--priority applies to the single-graph workloads")
+        return run_variant(args, rank, world)
     if WORKLOADS[args.workload]["kind"] == "batch":
         return run_batch(args, rank, world)
     if WORKLOADS[args.workload]["kind"] == "serve":

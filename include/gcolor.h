@@ -175,6 +175,20 @@ gc_status gc_adg_partition_noalloc(const gc_csr *g, uint32_t eps_p, uint32_t eps
 gc_status gc_make_priority(gc_context *ctx, int64_t n, const int32_t *batch, uint64_t seed,
                            uint64_t *key_out, gc_stream stream);
 
+/* Priorities of the other JP variants the paper compares (Section 4.1,
+ * "combinations of JP and orderings"), as keys for gc_jp_color:
+ *   GC_PRIO_R    JP-R:   rho_R                      key = h_seed(v)
+ *   GC_PRIO_FF   JP-FF:  the natural vertex order   key = 2^32 - 1 - v
+ *   GC_PRIO_LF   JP-LF:  <deg(v), rho_R>            key = deg(v) << 32 | h_seed(v)
+ *   GC_PRIO_LLF  JP-LLF: <ceil(log2 deg(v)), rho_R> key = ceil(log2 deg(v)) << 32 | h_seed(v)
+ *                        (0 for degree 0 and 1)
+ * with h_seed as in gc_make_priority; equal keys fall back to the vertex id
+ * in gc_jp_color.  key_out is device, n uint64.  GC_ERR_INVALID_ARG for an
+ * unknown kind. */
+enum { GC_PRIO_R = 0, GC_PRIO_FF = 1, GC_PRIO_LF = 2, GC_PRIO_LLF = 3 };
+gc_status gc_make_priority_kind(gc_context *ctx, const gc_csr *g, int32_t kind, uint64_t seed,
+                                uint64_t *key_out, gc_stream stream);
+
 /* JP colouring, Algorithm 3 (Section 4.1), for an arbitrary priority:
  * vertex u precedes v (u is a predecessor of v in the DAG G_rho) iff
  * (priority[u], u) > (priority[v], v) lexicographically, so any array gives

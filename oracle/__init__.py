@@ -10,6 +10,7 @@ Functions (each cites the passage of the paper it follows in ``oracle.c``):
   adg_naive(g, p, q)             Algorithm 1 with D recomputed from scratch
   tiebreak(seed, v)              SplitMix64-based random tie-break rho_R
   priority(batch, seed)          (batch << 32) | tiebreak, ties by vertex id
+  priority_kind(g, kind, seed)   JP-R / FF / LF / LLF keys (kinds 0..3)
   greedy(g, order)               Greedy colouring in a given order
   jp_color(g, priority)          JP (Algorithm 3) == Greedy by decreasing key
   jp_adg(g, p, q, seed)          ADG then JP with <rho_ADG, rho_R>
@@ -58,6 +59,8 @@ def _load():
         lib.oracle_greedy.argtypes = [i64, vp, vp, vp, vp, vp]
         lib.oracle_priority.restype = None
         lib.oracle_priority.argtypes = [i64, vp, u64, vp]
+        lib.oracle_priority_kind.restype = ctypes.c_int
+        lib.oracle_priority_kind.argtypes = [i64, vp, ctypes.c_int, u64, vp]
         lib.oracle_jp_color.restype = ctypes.c_int
         lib.oracle_jp_color.argtypes = [i64, vp, vp, vp, vp, vp]
         lib.oracle_jp_adg.restype = ctypes.c_int
@@ -130,6 +133,16 @@ def priority(batch: np.ndarray, seed: int) -> np.ndarray:
     b = np.ascontiguousarray(batch, dtype=np.int32)
     key = np.zeros(b.shape[0], dtype=np.uint64)
     _load().oracle_priority(b.shape[0], _p(b), seed, _p(key))
+    return key
+
+
+PRIO_R, PRIO_FF, PRIO_LF, PRIO_LLF = 0, 1, 2, 3
+
+
+def priority_kind(g, kind: int, seed: int) -> np.ndarray:
+    n, rp, _ = _csr(g)
+    key = np.zeros(n, dtype=np.uint64)
+    _check(_load().oracle_priority_kind(n, _p(rp), kind, seed, _p(key)), "priority_kind")
     return key
 
 

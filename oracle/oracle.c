@@ -260,6 +260,39 @@ void oracle_priority(int64_t n, const int32_t *batch, uint64_t seed, uint64_t *k
         key[v] = ((uint64_t)(uint32_t)batch[v] << 32) | (uint64_t)oracle_tiebreak(seed, v);
 }
 
+/* Priorities of the other JP variants (Section 4.1, "combinations of JP and
+ * orderings"), as 64-bit keys compared in decreasing (key, id) order:
+ *   kind 0, JP-R:   rho_R                             h(v)
+ *   kind 1, JP-FF:  natural vertex order (v = 0 first) 2^32 - 1 - v
+ *   kind 2, JP-LF:  <deg(v), rho_R>                   deg(v) * 2^32 + h(v)
+ *   kind 3, JP-LLF: <ceil(log2 deg(v)), rho_R>        that * 2^32 + h(v)
+ * where ceil(log2 d) is the smallest k with 2^k >= d (0 for d <= 1) and h is
+ * oracle_tiebreak.  Returns 1 for an unknown kind. */
+static uint64_t ceil_log2_u64(uint64_t d)
+{
+    uint64_t k = 0;
+    while (d > 1 && ((uint64_t)1 << k) < d) ++k;
+    return k;
+}
+
+int oracle_priority_kind(int64_t n, const int64_t *row_ptr, int kind, uint64_t seed, uint64_t *key)
+{
+    if (kind < 0 || kind > 3) return 1;
+    for (int64_t v = 0; v < n; ++v) {
+        const uint64_t h = (uint64_t)oracle_tiebreak(seed, v);
+        const uint64_t d = (uint64_t)(row_ptr[v + 1] - row_ptr[v]);
+        if (kind == 0)
+            key[v] = h;
+        else if (kind == 1)
+            key[v] = 0xffffffffull - (uint64_t)v;
+        else if (kind == 2)
+            key[v] = (d << 32) | h;
+        else
+            key[v] = (ceil_log2_u64(d) << 32) | h;
+    }
+    return 0;
+}
+
 /* JP colouring (Algorithm 3) for an arbitrary priority array, via its
  * equivalent Greedy in decreasing (priority, id) order. */
 int oracle_jp_color(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,

@@ -7,6 +7,6 @@ it is missing.
 """
 from .gcolor import (Context, DeviceBatch, DeviceGraph, GcError, GC_ERR_CUDA, GC_ERR_INVALID_ARG,  # noqa: F401
                      GC_ERR_INVALID_GRAPH, GC_ERR_OOM, GC_ERR_OVERFLOW, GC_ERR_TIMEOUT, GC_OK,
-                     EXPORTS, LIB_PATH, load, status_str)
+                     GC_PRIO_FF, GC_PRIO_LF, GC_PRIO_LLF, GC_PRIO_R, EXPORTS, LIB_PATH, load, status_str)
 
 __all__ = ["Context", "DeviceBatch", "DeviceGraph", "GcError", "load", "status_str", "EXPORTS", "LIB_PATH"]

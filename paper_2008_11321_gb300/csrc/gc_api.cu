@@ -335,6 +335,20 @@ gc_status gc_make_priority(gc_context* ctx, int64_t n, const int32_t* batch, uin
   return GC_OK;
 }
 
+gc_status gc_make_priority_kind(gc_context* ctx, const gc_csr* g, int32_t kind, uint64_t seed, uint64_t* key_out,
+                                gc_stream stream) {
+  if (!ctx) return GC_ERR_INVALID_ARG;
+  GC_TRY(check_graph_args(g));
+  if (kind < GC_PRIO_R || kind > GC_PRIO_LLF) return GC_ERR_INVALID_ARG;
+  if (g->n > 0 && !key_out) return GC_ERR_INVALID_ARG;
+  DeviceGuard guard(ctx->device);
+  CallScope scope(ctx);
+  if (!guard.ok) return GC_ERR_CUDA;
+  GC_TRY_CUDA(gc::make_priority_kind(row_ptr_of(g), g->n, kind, seed, reinterpret_cast<unsigned long long*>(key_out),
+                                     ctx->num_sms, reinterpret_cast<cudaStream_t>(stream)));
+  return GC_OK;
+}
+
 gc_status gc_jp_color(gc_context* ctx, const gc_csr* g, const uint64_t* priority, int32_t* color_out,
                       int32_t* num_colors_out, gc_stream stream) {
   if (!ctx) return GC_ERR_INVALID_ARG;

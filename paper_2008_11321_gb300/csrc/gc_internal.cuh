@@ -142,6 +142,9 @@ gc_status jp_run_packed(gc_context* ctx, Arena a, const gc_csr* g, const int* ba
                         const int* D, int rounds, int* color, int* num_colors_out, cudaStream_t s);
 cudaError_t make_priority(const int* batch, long long n, unsigned long long seed,
                           unsigned long long* key, int num_sms, cudaStream_t s);
+// JP-R / FF / LF / LLF keys (gc_make_priority_kind); kind already checked.
+cudaError_t make_priority_kind(const long long* row_ptr, long long n, int kind, unsigned long long seed,
+                               unsigned long long* key, int num_sms, cudaStream_t s);
 
 }  // namespace gc
 

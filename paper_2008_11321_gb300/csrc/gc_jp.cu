@@ -1340,6 +1340,36 @@ gc_status jp_run_packed(gc_context* ctx, Arena a, const gc_csr* g, const int* ba
   return jp_adg_impl(ctx, a, g, KeyPacked{batch, tiev}, D, rounds, color, num_colors_out, s);
 }
 
+namespace {
+__global__ void make_priority_kind_kernel(const long long* __restrict__ row_ptr, long long n, int kind,
+                                          unsigned long long seed, unsigned long long* __restrict__ key) {
+  for (long long v = gtid(); v < n; v += gstride()) {
+    const unsigned h = tie_hash(seed, static_cast<unsigned>(v));
+    const unsigned long long d = static_cast<unsigned long long>(row_ptr[v + 1] - row_ptr[v]);
+    unsigned long long k;
+    if (kind == GC_PRIO_R) {
+      k = h;
+    } else if (kind == GC_PRIO_FF) {
+      k = 0xffffffffull - static_cast<unsigned long long>(v);
+    } else if (kind == GC_PRIO_LF) {
+      k = (d << 32) | h;
+    } else {  // GC_PRIO_LLF: ceil(log2 d), 0 for d <= 1
+      const unsigned long long lg = d <= 1 ? 0ull : 64ull - static_cast<unsigned long long>(__clzll(d - 1));
+      k = (lg << 32) | h;
+    }
+    key[v] = k;
+  }
+}
+}  // namespace
+
+cudaError_t make_priority_kind(const long long* row_ptr, long long n, int kind, unsigned long long seed,
+                               unsigned long long* key, int num_sms, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  make_priority_kind_kernel<<<num_sms * 8, 256, 0, s>>>(row_ptr, n, kind, seed, key);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
 cudaError_t make_priority(const int* batch, long long n, unsigned long long seed,
                           unsigned long long* key, int num_sms, cudaStream_t s) {
   if (n == 0) return cudaSuccess;

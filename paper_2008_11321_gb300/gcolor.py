@@ -25,7 +25,10 @@ GC_ERR_CUDA, GC_ERR_TIMEOUT, GC_ERR_OVERFLOW = 4, 5, 6
 EXPORTS = ("gc_status_str", "gc_create", "gc_destroy", "gc_get_stats", "gc_set_timing",
            "gc_validate_csr", "gc_adg_partition", "gc_make_priority", "gc_jp_color",
            "gc_color_graph", "gc_color_graph_host", "gc_adg_partition_noalloc", "gc_color_batch",
-           "gc_color_batch_list")
+           "gc_color_batch_list", "gc_make_priority_kind")
+
+# priority kinds of gc_make_priority_kind
+GC_PRIO_R, GC_PRIO_FF, GC_PRIO_LF, GC_PRIO_LLF = 0, 1, 2, 3
 
 
 class GcError(RuntimeError):
@@ -92,6 +95,8 @@ def load(path: str = LIB_PATH):
     lib.gc_make_priority.argtypes = [vp, i64, vp, u64, vp, vp]
     lib.gc_jp_color.restype = ctypes.c_int
     lib.gc_jp_color.argtypes = [vp, P(gc_csr), vp, vp, P(i32), vp]
+    lib.gc_make_priority_kind.restype = ctypes.c_int
+    lib.gc_make_priority_kind.argtypes = [vp, P(gc_csr), ctypes.c_int32, u64, vp, vp]
     lib.gc_color_graph.restype = ctypes.c_int
     lib.gc_color_graph.argtypes = [vp, P(gc_csr), u32, u32, u64, vp, vp, P(i32), P(i32), vp]
     lib.gc_adg_partition_noalloc.restype = ctypes.c_int
@@ -255,6 +260,11 @@ class Context:
     def gc_make_priority(self, n: int, batch, seed: int, key_out, stream=None):
         _check(self._lib.gc_make_priority(self.handle, n, _ptr(batch), seed, _ptr(key_out),
                                           _stream(stream)), "gc_make_priority")
+
+    def gc_make_priority_kind(self, g: DeviceGraph, kind: int, seed: int, key_out, stream=None):
+        c = g.csr()
+        _check(self._lib.gc_make_priority_kind(self.handle, ctypes.byref(c), kind, seed, _ptr(key_out),
+                                               _stream(stream)), "gc_make_priority_kind")
 
     def gc_jp_color(self, g: DeviceGraph, priority, color_out, stream=None) -> int:
         c = g.csr()

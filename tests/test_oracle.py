@@ -310,6 +310,66 @@ def test_jp_simulation_equals_oracle(seed):
         assert np.array_equal(_jp_simulate(g, prio2, rng), c2)
 
 
+# ---------------------------------------------------------------- JP variants
+
+def test_priority_kinds_follow_definitions():
+    # Section 4.1: JP-R <rho_R>, JP-FF natural order, JP-LF <deg, rho_R>,
+    # JP-LLF <ceil(log2 deg), rho_R>; checked field by field on a star K_{1,5}
+    # (centre degree 5: ceil(log2 5) = 3) and a path (degrees 1 and 2).
+    ceil_log2 = {1: 0, 2: 1, 5: 3}  # worked by hand
+    for g in (star(5), path(4)):
+        deg = g.degrees()
+        for v in range(g.n):
+            h = oracle.tiebreak(9, v)
+            assert int(oracle.priority_kind(g, oracle.PRIO_R, 9)[v]) == h
+            assert int(oracle.priority_kind(g, oracle.PRIO_FF, 9)[v]) == 0xFFFFFFFF - v
+            assert int(oracle.priority_kind(g, oracle.PRIO_LF, 9)[v]) == (int(deg[v]) << 32) | h
+            lg = ceil_log2[int(deg[v])]
+            assert int(oracle.priority_kind(g, oracle.PRIO_LLF, 9)[v]) == (lg << 32) | h
+    # ceil(log2 d) at the powers of two and around them
+    for d, lg in ((1, 0), (2, 1), (3, 2), (4, 2), (5, 3), (8, 3), (9, 4), (1024, 10), (1025, 11)):
+        assert int(oracle.priority_kind(star(d), oracle.PRIO_LLF, 1)[0]) >> 32 == lg
+
+
+def test_jp_variant_closed_forms():
+    # JP-LF on a star: the centre (largest degree) first -> colour 1, leaves 2
+    g = star(7)
+    c, nc = oracle.jp_color(g, oracle.priority_kind(g, oracle.PRIO_LF, 3))
+    assert nc == 2 and c[0] == 1 and (c[1:] == 2).all()
+    # JP-LF on K_{a,b}, a < b: the a-side has the larger degree b -> colour 1
+    g = complete_bipartite(4, 9)
+    c, _ = oracle.jp_color(g, oracle.priority_kind(g, oracle.PRIO_LF, 3))
+    assert (c[:4] == 1).all() and (c[4:] == 2).all()
+    # JP-FF (first fit in vertex order) on a path: 1, 2, 1, 2, ...
+    g = path(11)
+    c, nc = oracle.jp_color(g, oracle.priority_kind(g, oracle.PRIO_FF, 3))
+    assert nc == 2 and list(c) == [1 + (v % 2) for v in range(11)]
+    # JP-FF on an odd cycle: 1, 2, 1, 2, 3
+    g = cycle(5)
+    c, nc = oracle.jp_color(g, oracle.priority_kind(g, oracle.PRIO_FF, 3))
+    assert list(c) == [1, 2, 1, 2, 3] and nc == 3
+    # JP-R on K_n: a permutation of 1..n whatever the seed
+    for seed in (1, 2, 3):
+        c, nc = oracle.jp_color(complete(12), oracle.priority_kind(complete(12), oracle.PRIO_R, seed))
+        assert nc == 12 and sorted(c) == list(range(1, 13))
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2, 3])
+def test_jp_variants_simulation_and_bounds(kind):
+    rng = np.random.default_rng(kind)
+    for g in (random_small(40, 0.2, kind), gg.erdos_renyi(300, 1500, kind + 1),
+              gg.barabasi_albert(300, 3, kind + 1)):
+        prio = oracle.priority_kind(g, kind, 7)
+        c, nc = oracle.jp_color(g, prio)
+        assert np.array_equal(_jp_simulate(g, prio, rng), c)  # Algorithm 3 literally
+        deg = g.degrees()
+        assert nc <= int(deg.max()) + 1                       # Greedy: <= Delta + 1
+        assert (c <= oracle.pred_count(g, prio) + 1).all()    # palette {1..|pred|+1}
+        rp, ci = g.row_ptr, g.col_idx
+        src = np.repeat(np.arange(g.n), deg)
+        assert (c[src] != c[ci]).all()                        # proper
+
+
 # ---------------------------------------------------------------- naive ADG
 
 @pytest.mark.parametrize("p,q", EPSES)

@@ -190,6 +190,34 @@ def test_jp_color_given_priority(ctx, kind):
     assert nc == onc and np.array_equal(color.cpu().numpy(), oc)
 
 
+VARIANT_GRAPHS = [gg.erdos_renyi(20000, 100000, seed=3), gg.rmat(16, 16, seed=2),
+                  gg.grid(64, 64, 16, perm_seed=3), gg.barabasi_albert(30000, 4, 5), star(5000), empty(50)]
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2, 3], ids=["R", "FF", "LF", "LLF"])
+def test_jp_variants(ctx, kind):
+    # JP-R / FF / LF / LLF (Section 4.1): keys bit for bit, then the colouring
+    for g in VARIANT_GRAPHS:
+        dg = dev(g)
+        key = torch.zeros(g.n, dtype=torch.int64, device="cuda:0")
+        ctx.gc_make_priority_kind(dg, kind, 42, key)
+        ok = oracle.priority_kind(g, kind, 42)
+        assert np.array_equal(key.cpu().numpy().view(np.uint64), ok), g.name
+        color = torch.empty(g.n, dtype=torch.int32, device="cuda:0")
+        nc = ctx.gc_jp_color(dg, key, color)
+        oc, onc = oracle.jp_color(g, ok)
+        assert nc == onc and np.array_equal(color.cpu().numpy(), oc), g.name
+
+
+def test_jp_variant_kind_rejected(ctx):
+    dg = dev(path(5))
+    key = torch.zeros(5, dtype=torch.int64, device="cuda:0")
+    for bad in (-1, 4):
+        with pytest.raises(gcp.GcError) as e:
+            ctx.gc_make_priority_kind(dg, bad, 1, key)
+        assert e.value.status == gcp.GC_ERR_INVALID_ARG
+
+
 def test_three_calls_equal_one(ctx):
     # adg_partition + make_priority + jp_color == color_graph
     g = gg.barabasi_albert(20000, 5, 3)

@@ -358,7 +358,7 @@ gc_status gc_jp_color(gc_context* ctx, const gc_csr* g, const uint64_t* priority
   CallScope scope(ctx);
   if (!guard.ok) return GC_ERR_CUDA;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  GC_TRY(ctx->reserve(gc::jp_scratch_bytes(g->n)));
+  GC_TRY(ctx->reserve(gc::jp_scratch_bytes(g->n, g->nnz)));
   int colors = 0;
   GC_TRY(timing_begin(ctx, 1, s));
   GC_TRY(gc::jp_run_given(ctx, ctx->arena(), g, reinterpret_cast<const unsigned long long*>(priority),

@@ -121,7 +121,7 @@ gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigne
                   int* D, int* rounds_out, cudaStream_t s);
 
 // JP colouring by predecessor polling (gc_jp.cu).
-size_t jp_scratch_bytes(long long n);
+size_t jp_scratch_bytes(long long n, long long nnz);
 size_t jpadg_scratch_bytes(long long n, long long nnz, int rounds);
 // batch: ADG batches; D: degree at removal (from adg_run); rounds: ADG rounds.
 gc_status jp_run_fused(gc_context* ctx, Arena a, const gc_csr* g, const int* batch, const int* D,

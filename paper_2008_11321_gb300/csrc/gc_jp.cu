@@ -649,7 +649,7 @@ __global__ void jpf_core_prep_kernel(const int* __restrict__ order, const int* _
     }
     const int v = order[i];
     const long long deg = row_ptr[v + 1] - row_ptr[v];
-    cap[i] = D[v];
+    cap[i] = D ? D[v] : (deg < i ? deg : i);  // without D: a core vertex has at most i predecessors
     ntask[i] = (deg + kChunk - 1) / kChunk;
     degsum += static_cast<unsigned long long>(deg);
   }
@@ -1054,18 +1054,122 @@ BucketPlan make_plan(long long n, int rounds) {
   return bp;
 }
 
+// The JP core stage on the first kc vertices of `order` (plain vertex ids in
+// exact priority order, with ctl->ncore == kc and lid[order[i]] == i):
+// predecessor lists of the core, compacted to 16-bit core-local ids, then the
+// core cluster (jpf_core_solve_kernel).  A core vertex's list is sized by
+// D[v] (its degree at removal, from ADG) or, without D, by min(deg(v), i).
+struct CoreBufs {
+  int* lid;
+  unsigned* cbits;
+  long long* cap;
+  long long* toff;
+  int* pcnt;
+  int* task_i;
+  long long* task_start;
+  int* task_len;
+  long long* temp;  // at least scan_temp_elems(kCoreMax + 1) elements
+};
+
+gc_status run_core(gc_context* ctx, const gc_csr* g, const int* order, const int* D, long long kc, JpCtl* ctl,
+                   const CoreBufs& cb, int* color, cudaStream_t s) {
+  const long long n = g->n;
+  const long long* rp = row_ptr_of(g);
+  const int blocks = ctx->num_sms * 8;
+    jpf_core_prep_kernel<<<blocks, 256, 0, s>>>(order, D, rp, ctl, cb.cap, cb.toff);
+    ++g_launches;
+    GC_TRY_CUDA(cudaGetLastError());
+    GC_TRY_CUDA(exclusive_scan_i64(cb.cap, cb.cap, kc + 1, cb.temp, s));
+    GC_TRY_CUDA(exclusive_scan_i64(cb.toff, cb.toff, kc + 1, cb.temp, s));
+    long long* pin_ll = reinterpret_cast<long long*>(ctx->pinned);
+    GC_TRY_CUDA(cudaMemcpyAsync(pin_ll, cb.cap + kc, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    GC_TRY_CUDA(cudaStreamSynchronize(s));
+    const long long npred_cap = pin_ll[0] > 0 ? pin_ll[0] : 1;
+    // aux: predecessor ids at capacity-sized slots (int32), then the dense
+    // 16-bit stream
+    const size_t pbytes = (static_cast<size_t>(npred_cap) * sizeof(int) + 255) & ~size_t(255);
+    // (the 256 spare bytes cover the last 16-byte group a core warp reads)
+    GC_TRY(ctx->reserve_aux(pbytes + static_cast<size_t>(npred_cap) * sizeof(unsigned short) + 256));
+    int* preds = static_cast<int*>(ctx->aux);
+    unsigned short* cpreds = reinterpret_cast<unsigned short*>(static_cast<char*>(ctx->aux) + pbytes);
+    GC_TRY_CUDA(cudaMemsetAsync(cb.pcnt, 0, sizeof(int) * (kc + 1), s));
+    jpf_core_tasks_kernel<<<blocks, 256, 0, s>>>(order, rp, cb.toff, ctl, cb.task_i, cb.task_start, cb.task_len);
+    ++g_launches;
+    ctx->timer_begin(gc_context::kTCorePreds, s);
+    GC_TRY_CUDA(cudaMemsetAsync(cb.cbits, 0, sizeof(unsigned) * static_cast<size_t>((n + 31) / 32), s));
+    jpf_core_bits_kernel<<<blocks, 256, 0, s>>>(order, ctl, cb.cbits);
+    ++g_launches;
+    jpf_core_preds_kernel<<<resident_grid(jpf_core_preds_kernel, 256, ctx->num_sms), 256, 0, s>>>(
+        g->col_idx, cb.cbits, cb.lid, cb.toff, cb.cap, ctl, cb.task_i, cb.task_start, cb.task_len, cb.pcnt, preds);
+    ++g_launches;
+    ctx->timer_end(s);
+    long long* qoff = cb.toff;  // task offsets are dead now
+    jpf_counts_kernel<<<blocks, 256, 0, s>>>(cb.pcnt, ctl, qoff);
+    ++g_launches;
+    GC_TRY_CUDA(cudaGetLastError());
+    GC_TRY_CUDA(exclusive_scan_i64(qoff, qoff, kc + 1, cb.temp, s));
+    GC_TRY_CUDA(cudaMemcpyAsync(&ctl->core_preds, qoff + kc, sizeof(long long), cudaMemcpyDeviceToDevice, s));
+    jpf_compact_kernel<<<blocks, 256, 0, s>>>(preds, cb.cap, qoff, ctl, cpreds);
+    ++g_launches;
+    GC_TRY_CUDA(cudaGetLastError());
+    int ncta = 1;
+    GC_TRY_CUDA(core_cluster_size(ctx, &ncta));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = ncta;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(ncta);
+    cfg.blockDim = dim3(32 * ctx->core_warps);
+    cfg.dynamicSmemBytes = core_smem_bytes(ctx->core_warps, kc);
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    ctx->stats.core_ctas = ncta;
+    ctx->timer_begin(gc_context::kTCoreSolve, s);
+    GC_TRY_CUDA(cudaLaunchKernelEx(&cfg, jpf_core_solve_kernel, static_cast<const int*>(order),
+                                   static_cast<const long long*>(qoff), static_cast<const unsigned short*>(cpreds),
+                                   ctl, color));
+    ++g_launches;
+    ctx->timer_end(s);
+    GC_TRY_CUDA(cudaGetLastError());
+  return GC_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
 // gc_jp_color: exact radix-sorted order, bulk stage on every vertex.
 // ---------------------------------------------------------------------------
-size_t jp_scratch_bytes(long long n) {
+size_t jp_scratch_bytes(long long n, long long nnz) {
   const size_t hist = sort_hist_elems(n);
   const size_t tmp = scan_temp_elems(static_cast<long long>(hist));
   const size_t tmp2 = scan_temp_elems(n);
-  return 2 * (static_cast<size_t>(n) * 8 + 256) + 2 * (static_cast<size_t>(n) * 4 + 256) +
-         hist * 8 + ((tmp > tmp2 ? tmp : tmp2) + 1) * 8 + 2048;
+  const size_t tmp3 = scan_temp_elems(kCoreMax + 1);
+  const size_t t = tmp > tmp2 ? tmp : tmp2;
+  const size_t kc = static_cast<size_t>(kCoreMax) + 1;
+  const size_t ntask = kc + static_cast<size_t>(nnz / kChunk) + 1;
+  return 2 * (static_cast<size_t>(n) * 8 + 256) + 2 * (static_cast<size_t>(n) * 4 + 256) + hist * 8 +
+         ((t > tmp3 ? t : tmp3) + 1) * 8 +
+         // core stage: corder, lid, cbits, cap, toff, pcnt, tasks
+         (kc * 4 + 256) + (static_cast<size_t>(n) * 4 + 256) + (static_cast<size_t>((n + 31) / 32) * 4 + 256) +
+         2 * (kc * 8 + 256) + (kc * 4 + 256) + ntask * 16 + 3 * 256 + 4096;
 }
+
+namespace {
+// Core of the generic path: the first kc entries of the sorted order (vertex
+// ids with the warp-path flag) as plain ids, and their core positions.
+__global__ void jp_core_from_sorted_kernel(const int* __restrict__ order, long long kc, int* __restrict__ corder,
+                                           int* __restrict__ lid, JpCtl* ctl) {
+  for (long long i = gtid(); i < kc; i += gstride()) {
+    const int v = static_cast<int>(static_cast<unsigned>(order[i]) & ~kBigBit);
+    corder[i] = v;
+    lid[v] = static_cast<int>(i);
+  }
+  if (gtid() == 0) ctl->ncore = static_cast<unsigned long long>(kc);
+}
+}  // namespace
 
 gc_status jp_run_given(gc_context* ctx, Arena a, const gc_csr* g, const unsigned long long* prio,
                        int* color, int* num_colors_out, cudaStream_t s) {
@@ -1083,8 +1187,18 @@ gc_status jp_run_given(gc_context* ctx, Arena a, const gc_csr* g, const unsigned
   sb.hist = a.take<long long>(sort_hist_elems(n));
   const size_t tmp = scan_temp_elems(static_cast<long long>(sort_hist_elems(n)));
   const size_t tmp2 = scan_temp_elems(n);
-  sb.temp = a.take<long long>((tmp > tmp2 ? tmp : tmp2) + 1);
-  if (!ctl || !sb.keys[0] || !sb.keys[1] || !sb.vals[0] || !sb.vals[1] || !sb.hist || !sb.temp)
+  const size_t tmp3 = scan_temp_elems(kCoreMax + 1);
+  const size_t tt = tmp > tmp2 ? tmp : tmp2;
+  sb.temp = a.take<long long>((tt > tmp3 ? tt : tmp3) + 1);
+  // the core stage: the top of the exact order, coloured by the core cluster
+  const long long kc = ctx->core_target < 0 ? 0 : (ctx->core_target > kCoreMax ? kCoreMax : (ctx->core_target > n ? n : ctx->core_target));
+  const long long ntask_cap = kCoreMax + g->nnz / kChunk + 1;
+  int* corder = a.take<int>(kCoreMax + 1);
+  CoreBufs cb{a.take<int>(n), a.take<unsigned>((n + 31) / 32), a.take<long long>(kCoreMax + 1),
+              a.take<long long>(kCoreMax + 1), a.take<int>(kCoreMax + 1), a.take<int>(ntask_cap),
+              a.take<long long>(ntask_cap), a.take<int>(ntask_cap), sb.temp};
+  if (!ctl || !sb.keys[0] || !sb.keys[1] || !sb.vals[0] || !sb.vals[1] || !sb.hist || !sb.temp || !corder ||
+      !cb.lid || !cb.cbits || !cb.cap || !cb.toff || !cb.pcnt || !cb.task_i || !cb.task_start || !cb.task_len)
     return GC_ERR_OOM;
   const long long* rp = row_ptr_of(g);
   const KeyGiven key{prio};
@@ -1108,21 +1222,32 @@ gc_status jp_run_given(gc_context* ctx, Arena a, const gc_csr* g, const unsigned
   const int* order = sb.vals[res];
   long long* pos = reinterpret_cast<long long*>(sb.keys[res ^ 1]);
   int* plist = sb.vals[res ^ 1];
-  jp_flags_kernel<<<blocks, 256, 0, s>>>(order, n, pos, ctl);
-  ++g_launches;
-  GC_TRY_CUDA(cudaGetLastError());
-  GC_TRY_CUDA(exclusive_scan_i64(pos, pos, n, sb.temp, s));
-  jp_split_kernel<<<blocks, 256, 0, s>>>(order, pos, n, plist, ctl);
-  ++g_launches;
-  GC_TRY_CUDA(cudaGetLastError());
-  jp_count_kernel<<<1, 1, 0, s>>>(pos, n, ctl);
-  ++g_launches;
-  GC_TRY_CUDA(cudaGetLastError());
   GC_TRY_CUDA(cudaMemsetAsync(color, 0, sizeof(int) * n, s));
-  ctx->timer_begin(gc_context::kTBulk, s);
-  GC_TRY_CUDA(launch_bulk(ctx, ctl, &ctl->big_cursor, rp, g->col_idx, key, plist, -1, nullptr, 0, color, s));
-  ctx->timer_end(s);
-  ctx->stats.bulk_launches = 1;
+  if (kc > 0) {  // the top kc vertices: exact order known, coloured by the core cluster
+    jp_core_from_sorted_kernel<<<blocks, 256, 0, s>>>(order, kc, corder, cb.lid, ctl);
+    ++g_launches;
+    GC_TRY_CUDA(cudaGetLastError());
+    GC_TRY(run_core(ctx, g, corder, nullptr, kc, ctl, cb, color, s));
+  }
+  // the rest: warp-path list first, then the lane-path list, each in order
+  const long long nrest = n - kc;
+  if (nrest > 0) {
+    const int* rest = order + kc;
+    jp_flags_kernel<<<blocks, 256, 0, s>>>(rest, nrest, pos, ctl);
+    ++g_launches;
+    GC_TRY_CUDA(cudaGetLastError());
+    GC_TRY_CUDA(exclusive_scan_i64(pos, pos, nrest, sb.temp, s));
+    jp_split_kernel<<<blocks, 256, 0, s>>>(rest, pos, nrest, plist, ctl);
+    ++g_launches;
+    GC_TRY_CUDA(cudaGetLastError());
+    jp_count_kernel<<<1, 1, 0, s>>>(pos, nrest, ctl);
+    ++g_launches;
+    GC_TRY_CUDA(cudaGetLastError());
+    ctx->timer_begin(gc_context::kTBulk, s);
+    GC_TRY_CUDA(launch_bulk(ctx, ctl, &ctl->big_cursor, rp, g->col_idx, key, plist, -1, nullptr, 0, color, s));
+    ctx->timer_end(s);
+    ctx->stats.bulk_launches = 1;
+  }
   return finish_jp(ctx, ctl, num_colors_out, s);
 }
 
@@ -1231,65 +1356,8 @@ gc_status jp_adg_impl(gc_context* ctx, Arena a, const gc_csr* g, const Key& key,
   const long long kc = static_cast<long long>(pin->ncore);
   const unsigned long long nbig = pin->nbig, base0 = pin->base0, base1 = pin->base1;
   if (kc > 0) {
-    jpf_core_prep_kernel<<<blocks, 256, 0, s>>>(order, D, rp, ctl, cap, toff);
-    ++g_launches;
-    GC_TRY_CUDA(cudaGetLastError());
-    GC_TRY_CUDA(exclusive_scan_i64(cap, cap, kc + 1, temp, s));
-    GC_TRY_CUDA(exclusive_scan_i64(toff, toff, kc + 1, temp, s));
-    long long* pin_ll = reinterpret_cast<long long*>(ctx->pinned);
-    GC_TRY_CUDA(cudaMemcpyAsync(pin_ll, cap + kc, sizeof(long long), cudaMemcpyDeviceToHost, s));
-    GC_TRY_CUDA(cudaStreamSynchronize(s));
-    const long long npred_cap = pin_ll[0] > 0 ? pin_ll[0] : 1;
-    // aux: predecessor ids at capacity-sized slots (int32), then the dense
-    // 16-bit stream
-    const size_t pbytes = (static_cast<size_t>(npred_cap) * sizeof(int) + 255) & ~size_t(255);
-    // (the 256 spare bytes cover the last 16-byte group a core warp reads)
-    GC_TRY(ctx->reserve_aux(pbytes + static_cast<size_t>(npred_cap) * sizeof(unsigned short) + 256));
-    int* preds = static_cast<int*>(ctx->aux);
-    unsigned short* cpreds = reinterpret_cast<unsigned short*>(static_cast<char*>(ctx->aux) + pbytes);
-    GC_TRY_CUDA(cudaMemsetAsync(pcnt, 0, sizeof(int) * (kc + 1), s));
-    jpf_core_tasks_kernel<<<blocks, 256, 0, s>>>(order, rp, toff, ctl, task_i, task_start, task_len);
-    ++g_launches;
-    ctx->timer_begin(gc_context::kTCorePreds, s);
-    GC_TRY_CUDA(cudaMemsetAsync(cbits, 0, sizeof(unsigned) * static_cast<size_t>((n + 31) / 32), s));
-    jpf_core_bits_kernel<<<blocks, 256, 0, s>>>(order, ctl, cbits);
-    ++g_launches;
-    jpf_core_preds_kernel<<<resident_grid(jpf_core_preds_kernel, 256, ctx->num_sms), 256, 0, s>>>(
-        g->col_idx, cbits, lid, toff, cap, ctl, task_i,
-                                                 task_start, task_len, pcnt, preds);
-    ++g_launches;
-    ctx->timer_end(s);
-    long long* qoff = toff;  // task offsets are dead now
-    jpf_counts_kernel<<<blocks, 256, 0, s>>>(pcnt, ctl, qoff);
-    ++g_launches;
-    GC_TRY_CUDA(cudaGetLastError());
-    GC_TRY_CUDA(exclusive_scan_i64(qoff, qoff, kc + 1, temp, s));
-    GC_TRY_CUDA(cudaMemcpyAsync(&ctl->core_preds, qoff + kc, sizeof(long long), cudaMemcpyDeviceToDevice, s));
-    jpf_compact_kernel<<<blocks, 256, 0, s>>>(preds, cap, qoff, ctl, cpreds);
-    ++g_launches;
-    GC_TRY_CUDA(cudaGetLastError());
-    int ncta = 1;
-    GC_TRY_CUDA(core_cluster_size(ctx, &ncta));
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = ncta;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(ncta);
-    cfg.blockDim = dim3(32 * ctx->core_warps);
-    cfg.dynamicSmemBytes = core_smem_bytes(ctx->core_warps, kc);
-    cfg.stream = s;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    ctx->stats.core_ctas = ncta;
-    ctx->timer_begin(gc_context::kTCoreSolve, s);
-    GC_TRY_CUDA(cudaLaunchKernelEx(&cfg, jpf_core_solve_kernel, static_cast<const int*>(order),
-                                   static_cast<const long long*>(qoff), static_cast<const unsigned short*>(cpreds),
-                                   ctl, color));
-    ++g_launches;
-    ctx->timer_end(s);
-    GC_TRY_CUDA(cudaGetLastError());
+    const CoreBufs cb{lid, cbits, cap, toff, pcnt, task_i, task_start, task_len, temp};
+    GC_TRY(run_core(ctx, g, order, D, kc, ctl, cb, color, s));
   }
 
   // 3. bulk, one batch at a time from the top: all predecessors in higher

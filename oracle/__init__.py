@@ -8,6 +8,7 @@ library.  ``build()`` compiles ``liboracle.so`` next to the source with gcc.
 Functions (each cites the passage of the paper it follows in ``oracle.c``):
   adg(g, p, q)                   Algorithm 1, fresh degree sums every round
   adg_naive(g, p, q)             Algorithm 1 with D recomputed from scratch
+  adg_m(g), adg_m_naive(g)       ADG-M (median; R = ceil(|U|/2) smallest (D, id))
   tiebreak(seed, v)              SplitMix64-based random tie-break rho_R
   priority(batch, seed)          (batch << 32) | tiebreak, ties by vertex id
   priority_kind(g, kind, seed)   JP-R / FF / LF / LLF keys (kinds 0..3)
@@ -59,6 +60,9 @@ def _load():
         lib.oracle_greedy.argtypes = [i64, vp, vp, vp, vp, vp]
         lib.oracle_priority.restype = None
         lib.oracle_priority.argtypes = [i64, vp, u64, vp]
+        for fn in ("oracle_adg_m", "oracle_adg_m_naive"):
+            getattr(lib, fn).restype = ctypes.c_int
+            getattr(lib, fn).argtypes = [i64, vp, vp, vp, ctypes.POINTER(ctypes.c_int32)]
         lib.oracle_priority_kind.restype = ctypes.c_int
         lib.oracle_priority_kind.argtypes = [i64, vp, ctypes.c_int, u64, vp]
         lib.oracle_jp_color.restype = ctypes.c_int
@@ -127,6 +131,30 @@ def adg_naive(g, eps_p: int, eps_q: int):
     _check(_load().oracle_adg_naive(n, _p(rp), _p(ci), eps_p, eps_q, _p(batch),
                                     ctypes.byref(rounds)), "adg_naive")
     return batch, rounds.value
+
+
+def adg_m(g):
+    n, rp, ci = _csr(g)
+    batch = np.zeros(n, dtype=np.int32)
+    rounds = ctypes.c_int32(0)
+    _check(_load().oracle_adg_m(n, _p(rp), _p(ci), _p(batch), ctypes.byref(rounds)), "adg_m")
+    return batch, rounds.value
+
+
+def adg_m_naive(g):
+    n, rp, ci = _csr(g)
+    batch = np.zeros(n, dtype=np.int32)
+    rounds = ctypes.c_int32(0)
+    _check(_load().oracle_adg_m_naive(n, _p(rp), _p(ci), _p(batch), ctypes.byref(rounds)), "adg_m_naive")
+    return batch, rounds.value
+
+
+def jp_adg_m(g, seed: int):
+    """JP-ADG-M: ADG-M, then JP with <rho_ADG-M, rho_R>.  Returns (batch,
+    color, num_rounds, num_colors)."""
+    batch, rounds = adg_m(g)
+    color, nc = jp_color(g, priority(batch, seed))
+    return batch, color, rounds, nc
 
 
 def priority(batch: np.ndarray, seed: int) -> np.ndarray:

@@ -186,6 +186,99 @@ int oracle_adg_naive(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
 }
 
 /* ------------------------------------------------------------------------- */
+/* ADG-M (Section 5, "Degree Median Instead of Degree Average"): in each     */
+/* round R is the set of vertices of U whose degree in U is at most the      */
+/* median degree of U, limited to half of U (one more if |U| is odd).  With  */
+/* the limit, R is exactly the ceil(|U|/2) vertices of U with the smallest   */
+/* degree; vertices of equal degree are taken in increasing id order (the   */
+/* paper leaves this tie open).  UPDATE is Algorithm 1's.                    */
+/* ------------------------------------------------------------------------- */
+static const int64_t *g_sort_D;
+static int cmp_deg_id(const void *a, const void *b)
+{
+    const int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
+    if (g_sort_D[x] != g_sort_D[y]) return g_sort_D[x] < g_sort_D[y] ? -1 : 1;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+int oracle_adg_m(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, int32_t *batch,
+                 int32_t *num_rounds)
+{
+    if (n < 0) return 1;
+    int64_t *D = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t *U = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    if (!D || !U) { free(D); free(U); return 2; }
+    for (int64_t v = 0; v < n; ++v) {
+        D[v] = row_ptr[v + 1] - row_ptr[v];
+        U[v] = v;
+        batch[v] = 0;
+    }
+    int64_t sizeU = n;
+    int32_t l = 0;
+    while (sizeU > 0) {
+        ++l;
+        /* the ceil(|U|/2) smallest (degree, id) of U */
+        g_sort_D = D;
+        qsort(U, (size_t)sizeU, sizeof(int64_t), cmp_deg_id);
+        const int64_t sizeR = (sizeU + 1) / 2;
+        for (int64_t i = 0; i < sizeR; ++i) batch[U[i]] = l;
+        /* UPDATE: the degree in U of every remaining neighbour drops by one */
+        for (int64_t i = 0; i < sizeR; ++i) {
+            const int64_t v = U[i];
+            for (int64_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k)
+                if (batch[col_idx[k]] == 0) D[col_idx[k]] -= 1;
+        }
+        memmove(U, U + sizeR, sizeof(int64_t) * (size_t)(sizeU - sizeR));
+        sizeU -= sizeR;
+    }
+    *num_rounds = l;
+    free(D);
+    free(U);
+    return 0;
+}
+
+/* ADG-M with every degree recomputed from scratch in each round (O(n*m)):
+ * a cross-check of the incremental UPDATE above, for tiny graphs. */
+int oracle_adg_m_naive(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, int32_t *batch,
+                       int32_t *num_rounds)
+{
+    if (n < 0) return 1;
+    int64_t *deg = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    char *take = (char *)malloc((size_t)(n > 0 ? n : 1));
+    if (!deg || !take) { free(deg); free(take); return 2; }
+    for (int64_t v = 0; v < n; ++v) batch[v] = 0;
+    int64_t left = n;
+    int32_t l = 0;
+    while (left > 0) {
+        ++l;
+        for (int64_t v = 0; v < n; ++v) {
+            deg[v] = 0;
+            take[v] = 0;
+            if (batch[v] != 0) continue;
+            for (int64_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k)
+                if (batch[col_idx[k]] == 0) deg[v] += 1;
+        }
+        /* pick ceil(left/2) times the remaining vertex of smallest (deg, id) */
+        const int64_t want = (left + 1) / 2;
+        for (int64_t t = 0; t < want; ++t) {
+            int64_t best = -1;
+            for (int64_t v = 0; v < n; ++v) {
+                if (batch[v] != 0 || take[v]) continue;
+                if (best < 0 || deg[v] < deg[best]) best = v;
+            }
+            take[best] = 1;
+        }
+        for (int64_t v = 0; v < n; ++v)
+            if (take[v]) batch[v] = l;
+        left -= want;
+    }
+    *num_rounds = l;
+    free(deg);
+    free(take);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Greedy colouring in a given order (Section 1: each vertex in turn takes   */
 /* the smallest colour not used by an already coloured neighbour).           */
 /* ------------------------------------------------------------------------- */

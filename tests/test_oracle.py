@@ -370,6 +370,66 @@ def test_jp_variants_simulation_and_bounds(kind):
         assert (c[src] != c[ci]).all()                        # proper
 
 
+# ---------------------------------------------------------------- ADG-M
+
+def _rounds_and_sizes(n):
+    """ADG-M removes ceil(|U|/2) vertices per round: |U| = n, floor(n/2), ..."""
+    sizes = []
+    while n > 0:
+        sizes.append((n + 1) // 2)
+        n //= 2
+    return sizes
+
+
+def test_adg_m_round_structure():
+    # Section 5: R = the ceil(|U|/2) smallest degrees of U, so round l removes
+    # exactly ceil(|U_l|/2) vertices and there are floor(log2 n) + 1 rounds
+    for g in (gg.erdos_renyi(1000, 5000, 3), gg.rmat(10, 8, seed=2), gg.barabasi_albert(777, 3, 1),
+              path(1), path(2), path(3), empty(64), complete(9)):
+        b, r = oracle.adg_m(g)
+        sizes = _rounds_and_sizes(g.n)
+        assert r == len(sizes) == int(math.floor(math.log2(g.n))) + 1
+        assert list(np.bincount(b, minlength=r + 1)[1:]) == sizes
+
+
+def test_adg_m_closed_forms():
+    # K_n: every remaining vertex has the same degree, so each round takes the
+    # smallest ids left: ids 0..4 -> 1, 5..7 -> 2, 8 -> 3, 9 -> 4 for n = 10
+    b, r = oracle.adg_m(complete(10))
+    assert r == 4 and list(b) == [1, 1, 1, 1, 1, 2, 2, 2, 3, 4]
+    # star K_{1,6} (centre 0): U = 7 -> leaves 1..4 (degree 1); U = {0, 5, 6}
+    # with D = 2, 1, 1 -> leaves 5, 6; then the centre
+    b, r = oracle.adg_m(star(6))
+    assert r == 3 and list(b) == [3, 1, 1, 1, 1, 2, 2]
+    # K_{1,3}: after leaves 1, 2 the centre and leaf 3 both have degree 1 and
+    # the smaller id (the centre) goes first
+    b, r = oracle.adg_m(star(3))
+    assert list(b) == [2, 1, 1, 3]
+
+
+def test_adg_m_equals_naive():
+    for s in range(4):
+        for g in (random_small(60, 0.1, s), gg.erdos_renyi(300, 1200, s + 3), gg.rmat(8, 8, seed=s + 1)):
+            b1, r1 = oracle.adg_m(g)
+            b2, r2 = oracle.adg_m_naive(g)
+            assert r1 == r2 and np.array_equal(b1, b2)
+
+
+def test_adg_m_four_approximation_and_colours():
+    # <rho_ADG-M, rho_R> is a 4-approximate degeneracy ordering, so every
+    # vertex has at most 4d neighbours of equal or later batch, and JP-ADG-M
+    # uses at most 4d + 1 colours (Section 5, analysis of JP-ADG-M)
+    for g in (gg.erdos_renyi(2000, 12000, 5), gg.rmat(11, 16, seed=3), gg.barabasi_albert(1500, 5, 2),
+              gg.grid(20, 20, 5), complete(30)):
+        d, _ = oracle.degeneracy(g)
+        b, c, r, nc = oracle.jp_adg_m(g, 42)
+        src = np.repeat(np.arange(g.n), g.degrees())
+        later = np.bincount(src[b[g.col_idx] >= b[src]], minlength=g.n)
+        assert later.max() <= 4 * d
+        assert nc <= 4 * d + 1
+        assert (c[src] != c[g.col_idx]).all()
+
+
 # ---------------------------------------------------------------- naive ADG
 
 @pytest.mark.parametrize("p,q", EPSES)

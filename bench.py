@@ -171,7 +171,7 @@ class ClockSampler:
                 "samples": len(sms)}
 
 
-def cpu_baseline(w_name, seconds_target=10.0):
+def cpu_baseline(w_name, seconds_target=10.0, median=False):
     """The oracle as it stands, single-threaded, on a bounded sample of the
     same family (R-MAT scale 22 for the R-MAT workloads)."""
     import graphgen as gg
@@ -191,11 +191,15 @@ def cpu_baseline(w_name, seconds_target=10.0):
     reps, total = 0, 0.0
     while total < seconds_target and reps < 50:
         t0 = time.perf_counter()
-        oracle.jp_adg(g, p, q, w["seed"])
+        if median:
+            oracle.jp_adg_m(g, w["seed"])
+        else:
+            oracle.jp_adg(g, p, q, w["seed"])
         total += time.perf_counter() - t0
         reps += 1
+    what = "ADG-M + Greedy" if median else "ADG + Greedy"
     return {"value": g.m * reps / total, "unit": "edges/s", "cores": 1, "kind": "oracle",
-            "sample": f"{desc}: n={g.n}, m={g.m}, {reps} run(s) of ADG + Greedy, {total:.1f} s"}
+            "sample": f"{desc}: n={g.n}, m={g.m}, {reps} run(s) of {what}, {total:.1f} s"}
 
 
 PRIORITIES = {"r": (0, "JP-R"), "ff": (1, "JP-FF"), "lf": (2, "JP-LF"), "llf": (3, "JP-LLF")}
@@ -540,8 +544,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat24")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--priority", choices=["adg"] + sorted(PRIORITIES), default="adg",
-                    help="JP priority: adg (JP-ADG, the default) or another JP variant")
+    ap.add_argument("--priority", choices=["adg", "adg-m"] + sorted(PRIORITIES), default="adg",
+                    help="JP priority: adg (JP-ADG, the default), adg-m (JP-ADG-M) or another JP variant")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: --warmup below 3 is outside the timing rules", file=sys.stderr)
@@ -555,7 +559,8 @@ def main():
     if args.priority != "adg":
         if WORKLOADS[args.workload]["kind"] in ("batch", "serve"):
             ap.error("--priority applies to the single-graph workloads")
-        return run_variant(args, rank, world)
+        if args.priority != "adg-m":
+            return run_variant(args, rank, world)
     if WORKLOADS[args.workload]["kind"] == "batch":
         return run_batch(args, rank, world)
     if WORKLOADS[args.workload]["kind"] == "serve":
@@ -586,8 +591,15 @@ def main():
     ctx = gcp.Context(local)
     stream = torch.cuda.current_stream(dev)
 
+    median = args.priority == "adg-m"
+
+    def colour_step():
+        if median:  # JP-ADG-M: ADG-M has no eps
+            return ctx.gc_color_graph_m(dg, seed, color, batch)
+        return ctx.gc_color_graph(dg, p, q, seed, color, batch)
+
     for _ in range(args.warmup):
-        nc, nr = ctx.gc_color_graph(dg, p, q, seed, color, batch)
+        nc, nr = colour_step()
     ctx.gc_set_timing(True)
 
     try:
@@ -607,7 +619,7 @@ def main():
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        nc, nr = ctx.gc_color_graph(dg, p, q, seed, color, batch)
+        nc, nr = colour_step()
         st = ctx.gc_get_stats()
         steps.append({k: getattr(st, k) for k, _ in st._fields_})
     ev1.record(stream)
@@ -624,7 +636,7 @@ def main():
 
     # end to end through the public host-buffer entry point
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not median:
         hcolor = torch.empty(n, dtype=torch.int32, pin_memory=True).numpy()
         ctx.gc_set_timing(False)
         ctx.gc_color_graph_host(g.row_ptr, g.col_idx, p, q, seed, hcolor)  # grows buffers once
@@ -667,7 +679,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": w["desc"], "n": n, "m": m, "eps": f"{p}/{q}", "seed": seed,
+        "config": {"workload": w["desc"] if not median else w["desc"].replace("eps=1/100", "JP-ADG-M (median)"),
+                   "n": n, "m": m, "eps": f"{p}/{q}" if not median else None, "seed": seed,
                    "adg_rounds": nr, "num_colors": nc, "sum_U": sum_u, "decrements": dec,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": f"inputs larger than L2 (col_idx {4 * nnz / 1e9:.2f} GB), no flush"},
@@ -686,7 +699,7 @@ def main():
     if e2e:
         line["e2e"] = e2e
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.workload)
+        line["cpu_baseline"] = cpu_baseline(args.workload, median=median)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -175,6 +175,21 @@ gc_status gc_adg_partition_noalloc(const gc_csr *g, uint32_t eps_p, uint32_t eps
 gc_status gc_make_priority(gc_context *ctx, int64_t n, const int32_t *batch, uint64_t seed,
                            uint64_t *key_out, gc_stream stream);
 
+/* ADG-M (Section 5, "Degree Median Instead of Degree Average"): ADG with
+ * the median degree of U as the threshold and R limited to half of U (one
+ * more if |U| is odd), so each round removes the ceil(|U|/2) vertices of U
+ * with the smallest degree in U; vertices of equal degree go in increasing
+ * id order.  batch_out (device, n int32) receives rounds 1..*num_rounds_out
+ * (= floor(log2 n) + 1 for n >= 1). */
+gc_status gc_adg_m_partition(gc_context *ctx, const gc_csr *g, int32_t *batch_out, int32_t *num_rounds_out,
+                             gc_stream stream);
+
+/* JP-ADG-M: ADG-M, then JP with <rho_ADG-M, rho_R> (rho_R as in
+ * gc_make_priority); at most 4d + 1 colours for degeneracy d.  Arguments as
+ * in gc_color_graph (without eps). */
+gc_status gc_color_graph_m(gc_context *ctx, const gc_csr *g, uint64_t seed, int32_t *color_out, int32_t *batch_out,
+                           int32_t *num_colors_out, int32_t *num_rounds_out, gc_stream stream);
+
 /* Priorities of the other JP variants the paper compares (Section 4.1,
  * "combinations of JP and orderings"), as keys for gc_jp_color:
  *   GC_PRIO_R    JP-R:   rho_R                      key = h_seed(v)

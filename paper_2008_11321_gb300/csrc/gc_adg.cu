@@ -60,7 +60,8 @@ __global__ void __launch_bounds__(kAdgThreads)
 adg_partition_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row_ptr,
                      int* __restrict__ D, int* __restrict__ batch, const int* __restrict__ u_in,
                      int* __restrict__ u_out, long long* __restrict__ task_start,
-                     int* __restrict__ task_len, unsigned* __restrict__ live, int first_round_n) {
+                     int* __restrict__ task_len, unsigned* __restrict__ live, int first_round_n,
+                     long long rank_cut = -1) {
   const int round = ctl->round;
   const int T = ctl->T;
   const bool first = first_round_n > 0;
@@ -85,7 +86,9 @@ adg_partition_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row
         d = D[u];
       }
     }
-    const bool in_r = active && d <= T;
+    // ADG: D[u] <= T; ADG-M: the list is sorted by (D, id) and R is its
+    // first rank_cut entries
+    const bool in_r = active && (rank_cut >= 0 ? i < rank_cut : d <= T);
     const bool keep = active && !in_r;
     // survivors -> U'
     const unsigned km = __ballot_sync(kFull, keep);
@@ -268,6 +271,127 @@ gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigne
   unsigned long long tot[2];
   GC_TRY_CUDA(cudaMemcpyAsync(pinned, &ctl->total_U, 2 * sizeof(unsigned long long),
                               cudaMemcpyDeviceToHost, s));
+  GC_TRY_CUDA(cudaStreamSynchronize(s));
+  memcpy(tot, pinned, sizeof(tot));
+  ctx->stats.sum_U = static_cast<int64_t>(tot[0]);
+  ctx->stats.sum_decrements = static_cast<int64_t>(tot[1]);
+  ctx->stats.adg_rounds = round;
+  *rounds_out = round;
+  return GC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// ADG-M (Section 5, "Degree Median Instead of Degree Average"): each round
+// removes the ceil(|U|/2) vertices of U with the smallest degree in U (the
+// median degree is the threshold, and R is limited to half of U, one more if
+// |U| is odd), vertices of equal degree in increasing id order.  Each round
+// sorts U by (D[u] << 32 | u) (stable LSD radix sort) and cuts the sorted list
+// in half; UPDATE, the cut and the bookkeeping are ADG's.  floor(log2 n) + 1
+// rounds.
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void adg_m_init_kernel(const long long* __restrict__ row_ptr, long long n, int* __restrict__ D,
+                                  int* __restrict__ U, unsigned* __restrict__ live) {
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  const long long t0 = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  for (long long v = t0; v < n; v += stride) {
+    D[v] = static_cast<int>(row_ptr[v + 1] - row_ptr[v]);
+    U[v] = static_cast<int>(v);
+  }
+  for (long long w = t0; w < (n + 31) / 32; w += stride) {
+    const long long left = n - 32 * w;
+    live[w] = left >= 32 ? ~0u : ((1u << left) - 1u);
+  }
+}
+
+__global__ void adg_m_keys_kernel(const int* __restrict__ U, const AdgCtl* __restrict__ ctl,
+                                  const int* __restrict__ D, unsigned long long* __restrict__ keys,
+                                  int* __restrict__ vals) {
+  const long long size_u = ctl->size_U;
+  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < size_u;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int u = U[i];
+    keys[i] = (static_cast<unsigned long long>(static_cast<unsigned>(D[u])) << 32) | static_cast<unsigned>(u);
+    vals[i] = u;
+  }
+}
+
+}  // namespace
+
+size_t adg_m_scratch_bytes(long long n, long long nnz) {
+  const size_t hist = sort_hist_elems(n);
+  return adg_scratch_bytes(n, nnz) + 2 * (static_cast<size_t>(n) * 8 + 256) + 2 * (static_cast<size_t>(n) * 4 + 256) +
+         hist * 8 + 256 + (scan_temp_elems(static_cast<long long>(hist)) + 1) * 8 + 256;
+}
+
+gc_status adg_m_run(gc_context* ctx, Arena a, const gc_csr* g, int* batch, int* D, int* rounds_out,
+                    cudaStream_t s) {
+  const long long n = g->n, nnz = g->nnz;
+  *rounds_out = 0;
+  ctx->stats.adg_rounds = 0;
+  if (n == 0) return GC_OK;
+  AdgCtl* ctl = a.take<AdgCtl>(1);
+  int* ubuf[2] = {a.take<int>(n), a.take<int>(n)};
+  const long long ntask = n + nnz / kChunk + 1;
+  long long* task_start = a.take<long long>(ntask);
+  int* task_len = a.take<int>(ntask);
+  unsigned* live = a.take<unsigned>((n + 31) / 32);
+  SortBufs sb;
+  sb.keys[0] = a.take<unsigned long long>(n);
+  sb.keys[1] = a.take<unsigned long long>(n);
+  sb.vals[0] = a.take<int>(n);
+  sb.vals[1] = a.take<int>(n);
+  sb.hist = a.take<long long>(sort_hist_elems(n));
+  sb.temp = a.take<long long>(scan_temp_elems(static_cast<long long>(sort_hist_elems(n))) + 1);
+  if (!ctl || !D || !ubuf[0] || !ubuf[1] || !task_start || !task_len || !live || !sb.keys[0] || !sb.keys[1] ||
+      !sb.vals[0] || !sb.vals[1] || !sb.hist || !sb.temp)
+    return GC_ERR_OOM;
+
+  const long long* rp = row_ptr_of(g);
+  const int max_blocks = ctx->num_sms * 8;
+  const int upd_blocks = resident_grid(adg_update_kernel, kAdgThreads, ctx->num_sms);
+  GC_TRY_CUDA(cudaMemsetAsync(batch, 0, sizeof(int) * n, s));
+  adg_init_kernel<<<1, 1, 0, s>>>(ctl, n, nnz, 0, 1);  // (its threshold is not used here)
+  ++g_launches;
+  adg_m_init_kernel<<<max_blocks, kAdgThreads, 0, s>>>(rp, n, D, ubuf[0], live);
+  ++g_launches;
+  GC_TRY_CUDA(cudaGetLastError());
+  long long size_u = n;
+  int cur = 0, round = 0;
+  int* pinned = static_cast<int*>(ctx->pinned);
+  while (size_u > 0) {
+    ++round;
+    const long long want = (size_u + kAdgThreads - 1) / kAdgThreads;
+    const int blocks = static_cast<int>(want < max_blocks ? want : max_blocks);
+    adg_m_keys_kernel<<<blocks, kAdgThreads, 0, s>>>(ubuf[cur], ctl, D, sb.keys[0], sb.vals[0]);
+    ++g_launches;
+    GC_TRY_CUDA(cudaGetLastError());
+    cudaError_t err;
+    const int res = radix_sort_pairs(sb, size_u, 0xffu, s, &err);
+    GC_TRY_CUDA(err);
+    adg_partition_kernel<<<blocks, kAdgThreads, 0, s>>>(ctl, rp, D, batch, sb.vals[res], ubuf[cur ^ 1], task_start,
+                                                        task_len, live, 0, (size_u + 1) / 2);
+    ++g_launches;
+    GC_TRY_CUDA(cudaGetLastError());
+    ctx->timer_begin(gc_context::kTUpdate, s);
+    adg_update_kernel<<<upd_blocks, kAdgThreads, 0, s>>>(ctl, rp, g->col_idx, D, batch, live, task_start,
+                                                          task_len, 0);
+    ++g_launches;
+    ctx->timer_end(s);
+    GC_TRY_CUDA(cudaGetLastError());
+    adg_finalize_kernel<<<1, 1, 0, s>>>(ctl);
+    ++g_launches;
+    GC_TRY_CUDA(cudaGetLastError());
+    GC_TRY_CUDA(cudaMemcpyAsync(pinned, &ctl->size_U, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GC_TRY_CUDA(cudaStreamSynchronize(s));
+    const long long next = *pinned;
+    if (next != size_u / 2) return GC_ERR_CUDA;  // cannot happen: each round removes ceil(|U|/2)
+    size_u = next;
+    cur ^= 1;
+  }
+  unsigned long long tot[2];
+  GC_TRY_CUDA(cudaMemcpyAsync(pinned, &ctl->total_U, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   GC_TRY_CUDA(cudaStreamSynchronize(s));
   memcpy(tot, pinned, sizeof(tot));
   ctx->stats.sum_U = static_cast<int64_t>(tot[0]);

@@ -127,18 +127,22 @@ float timing_ms(gc_context* ctx, int a, int b) {
 }
 
 // Shared body of gc_color_graph and gc_color_graph_host.
+// JP-ADG (median = false) or JP-ADG-M (median = true, p and q unused).
 gc_status color_graph_device(gc_context* ctx, const gc_csr* g, uint32_t p, uint32_t q, uint64_t seed,
                              int32_t* color, int32_t* batch, int32_t* ncol, int32_t* nrounds,
-                             cudaStream_t s) {
+                             cudaStream_t s, bool median = false) {
   const long long n = g->n;
   const size_t vb = static_cast<size_t>(n > 0 ? n : 1) * 4 + 256;
   GC_TRY(ctx->reserve_vert(2 * vb));
   int* D = static_cast<int*>(ctx->vbuf);
   int* b = batch ? batch : reinterpret_cast<int*>(static_cast<char*>(ctx->vbuf) + vb);
-  GC_TRY(ctx->reserve(gc::adg_scratch_bytes(n, g->nnz)));
+  GC_TRY(ctx->reserve(median ? gc::adg_m_scratch_bytes(n, g->nnz) : gc::adg_scratch_bytes(n, g->nnz)));
   int rounds = 0, colors = 0;
   GC_TRY(timing_begin(ctx, 0, s));
-  GC_TRY(gc::adg_run(ctx, ctx->arena(), g, p, q, b, D, &rounds, s));
+  if (median)
+    GC_TRY(gc::adg_m_run(ctx, ctx->arena(), g, b, D, &rounds, s));
+  else
+    GC_TRY(gc::adg_run(ctx, ctx->arena(), g, p, q, b, D, &rounds, s));
   GC_TRY(timing_begin(ctx, 1, s));
   GC_TRY(ctx->reserve(gc::jpadg_scratch_bytes(n, g->nnz, rounds)));
   GC_TRY(gc::jp_run_fused(ctx, ctx->arena(), g, b, D, rounds, seed, color, &colors, s));
@@ -384,6 +388,41 @@ gc_status gc_color_graph(gc_context* ctx, const gc_csr* g, uint32_t eps_p, uint3
   if (!guard.ok) return GC_ERR_CUDA;
   return color_graph_device(ctx, g, eps_p, eps_q, seed, color_out, batch_out, num_colors_out,
                             num_rounds_out, reinterpret_cast<cudaStream_t>(stream));
+}
+
+gc_status gc_adg_m_partition(gc_context* ctx, const gc_csr* g, int32_t* batch_out, int32_t* num_rounds_out,
+                             gc_stream stream) {
+  if (!ctx || !num_rounds_out) return GC_ERR_INVALID_ARG;
+  GC_TRY(check_graph_args(g));
+  if (g->n > 0 && !batch_out) return GC_ERR_INVALID_ARG;
+  DeviceGuard guard(ctx->device);
+  CallScope scope(ctx);
+  if (!guard.ok) return GC_ERR_CUDA;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  GC_TRY(ctx->reserve(gc::adg_m_scratch_bytes(g->n, g->nnz)));
+  GC_TRY(ctx->reserve_vert(static_cast<size_t>(g->n > 0 ? g->n : 1) * 4 + 256));
+  int rounds = 0;
+  GC_TRY(timing_begin(ctx, 0, s));
+  GC_TRY(gc::adg_m_run(ctx, ctx->arena(), g, batch_out, static_cast<int*>(ctx->vbuf), &rounds, s));
+  GC_TRY(timing_begin(ctx, 1, s));
+  if (ctx->timing) {
+    GC_TRY_CUDA(cudaEventSynchronize(ctx->ev[1]));
+    ctx->stats.ms_adg = timing_ms(ctx, 0, 1);
+  }
+  *num_rounds_out = rounds;
+  return GC_OK;
+}
+
+gc_status gc_color_graph_m(gc_context* ctx, const gc_csr* g, uint64_t seed, int32_t* color_out, int32_t* batch_out,
+                           int32_t* num_colors_out, int32_t* num_rounds_out, gc_stream stream) {
+  if (!ctx) return GC_ERR_INVALID_ARG;
+  GC_TRY(check_graph_args(g));
+  if (g->n > 0 && !color_out) return GC_ERR_INVALID_ARG;
+  DeviceGuard guard(ctx->device);
+  CallScope scope(ctx);
+  if (!guard.ok) return GC_ERR_CUDA;
+  return color_graph_device(ctx, g, 0, 1, seed, color_out, batch_out, num_colors_out, num_rounds_out,
+                            reinterpret_cast<cudaStream_t>(stream), true);
 }
 
 gc_status gc_color_graph_host(gc_context* ctx, int64_t n, int64_t nnz, const int64_t* row_ptr,

@@ -120,6 +120,12 @@ size_t adg_scratch_bytes(long long n, long long nnz);
 gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigned q, int* batch,
                   int* D, int* rounds_out, cudaStream_t s);
 
+// ADG-M rounds (gc_adg.cu): median degree, R = the ceil(|U|/2) smallest
+// (D, id) of U.  D receives each vertex's degree at removal.
+size_t adg_m_scratch_bytes(long long n, long long nnz);
+gc_status adg_m_run(gc_context* ctx, Arena a, const gc_csr* g, int* batch, int* D, int* rounds_out,
+                    cudaStream_t s);
+
 // JP colouring by predecessor polling (gc_jp.cu).
 size_t jp_scratch_bytes(long long n, long long nnz);
 size_t jpadg_scratch_bytes(long long n, long long nnz, int rounds);

@@ -25,7 +25,7 @@ GC_ERR_CUDA, GC_ERR_TIMEOUT, GC_ERR_OVERFLOW = 4, 5, 6
 EXPORTS = ("gc_status_str", "gc_create", "gc_destroy", "gc_get_stats", "gc_set_timing",
            "gc_validate_csr", "gc_adg_partition", "gc_make_priority", "gc_jp_color",
            "gc_color_graph", "gc_color_graph_host", "gc_adg_partition_noalloc", "gc_color_batch",
-           "gc_color_batch_list", "gc_make_priority_kind")
+           "gc_color_batch_list", "gc_make_priority_kind", "gc_adg_m_partition", "gc_color_graph_m")
 
 # priority kinds of gc_make_priority_kind
 GC_PRIO_R, GC_PRIO_FF, GC_PRIO_LF, GC_PRIO_LLF = 0, 1, 2, 3
@@ -95,6 +95,10 @@ def load(path: str = LIB_PATH):
     lib.gc_make_priority.argtypes = [vp, i64, vp, u64, vp, vp]
     lib.gc_jp_color.restype = ctypes.c_int
     lib.gc_jp_color.argtypes = [vp, P(gc_csr), vp, vp, P(i32), vp]
+    lib.gc_adg_m_partition.restype = ctypes.c_int
+    lib.gc_adg_m_partition.argtypes = [vp, P(gc_csr), vp, P(i32), vp]
+    lib.gc_color_graph_m.restype = ctypes.c_int
+    lib.gc_color_graph_m.argtypes = [vp, P(gc_csr), u64, vp, vp, P(i32), P(i32), vp]
     lib.gc_make_priority_kind.restype = ctypes.c_int
     lib.gc_make_priority_kind.argtypes = [vp, P(gc_csr), ctypes.c_int32, u64, vp, vp]
     lib.gc_color_graph.restype = ctypes.c_int
@@ -260,6 +264,21 @@ class Context:
     def gc_make_priority(self, n: int, batch, seed: int, key_out, stream=None):
         _check(self._lib.gc_make_priority(self.handle, n, _ptr(batch), seed, _ptr(key_out),
                                           _stream(stream)), "gc_make_priority")
+
+    def gc_adg_m_partition(self, g: DeviceGraph, batch_out, stream=None) -> int:
+        c = g.csr()
+        nr = ctypes.c_int32(0)
+        _check(self._lib.gc_adg_m_partition(self.handle, ctypes.byref(c), _ptr(batch_out), ctypes.byref(nr),
+                                            _stream(stream)), "gc_adg_m_partition")
+        return nr.value
+
+    def gc_color_graph_m(self, g: DeviceGraph, seed: int, color_out, batch_out=None, stream=None):
+        """JP-ADG-M; returns (num_colors, num_rounds)."""
+        c = g.csr()
+        nc, nr = ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(self._lib.gc_color_graph_m(self.handle, ctypes.byref(c), seed, _ptr(color_out), _ptr(batch_out),
+                                          ctypes.byref(nc), ctypes.byref(nr), _stream(stream)), "gc_color_graph_m")
+        return nc.value, nr.value
 
     def gc_make_priority_kind(self, g: DeviceGraph, kind: int, seed: int, key_out, stream=None):
         c = g.csr()

@@ -209,6 +209,33 @@ def test_jp_variants(ctx, kind):
         assert nc == onc and np.array_equal(color.cpu().numpy(), oc), g.name
 
 
+ADGM_GRAPHS = [empty(1), empty(77), path(2), path(3), complete(10), complete(1100), star(3), star(6), star(5000),
+               cycle(999), gg.erdos_renyi(20000, 100000, seed=3), gg.rmat(16, 16, seed=2),
+               gg.grid(64, 64, 16, perm_seed=3), gg.barabasi_albert(30000, 4, 5), gg.rmat(20, 16, seed=1)]
+
+
+@pytest.mark.parametrize("g", ADGM_GRAPHS, ids=lambda g: g.name)
+def test_adg_m_and_jp_adg_m(ctx, g):
+    # ADG-M (Section 5 median variant): batches bit for bit, then JP-ADG-M
+    dg = dev(g)
+    batch = torch.full((g.n,), -7, dtype=torch.int32, device="cuda:0")
+    nr = ctx.gc_adg_m_partition(dg, batch)
+    ob, onr = oracle.adg_m(g)
+    assert nr == onr and np.array_equal(batch.cpu().numpy(), ob), g.name
+    color = torch.full((g.n,), -7, dtype=torch.int32, device="cuda:0")
+    batch2 = torch.full((g.n,), -7, dtype=torch.int32, device="cuda:0")
+    nc, nr2 = ctx.gc_color_graph_m(dg, 42, color, batch2)
+    _, oc, _, onc = oracle.jp_adg_m(g, 42)
+    assert nr2 == onr and np.array_equal(batch2.cpu().numpy(), ob), g.name
+    assert nc == onc and np.array_equal(color.cpu().numpy(), oc), g.name
+
+
+def test_adg_m_zero_vertices(ctx):
+    dg = dev(empty(0))
+    assert ctx.gc_adg_m_partition(dg, torch.empty(0, dtype=torch.int32, device="cuda:0")) == 0
+    assert ctx.gc_color_graph_m(dg, 1, torch.empty(0, dtype=torch.int32, device="cuda:0")) == (0, 0)
+
+
 def test_jp_variant_kind_rejected(ctx):
     dg = dev(path(5))
     key = torch.zeros(5, dtype=torch.int64, device="cuda:0")

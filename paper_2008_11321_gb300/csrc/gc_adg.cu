@@ -61,7 +61,8 @@ adg_partition_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row
                      int* __restrict__ D, int* __restrict__ batch, const int* __restrict__ u_in,
                      int* __restrict__ u_out, long long* __restrict__ task_start,
                      int* __restrict__ task_len, unsigned* __restrict__ live, int first_round_n,
-                     long long rank_cut = -1) {
+                     const unsigned long long* __restrict__ mkeys = nullptr,
+                     const unsigned long long* __restrict__ kstar = nullptr) {
   const int round = ctl->round;
   const int T = ctl->T;
   const bool first = first_round_n > 0;
@@ -86,9 +87,9 @@ adg_partition_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row
         d = D[u];
       }
     }
-    // ADG: D[u] <= T; ADG-M: the list is sorted by (D, id) and R is its
-    // first rank_cut entries
-    const bool in_r = active && (rank_cut >= 0 ? i < rank_cut : d <= T);
+    // ADG: D[u] <= T; ADG-M: the key D[u] * 2^32 + u of list entry i is at
+    // most the selected ceil(|U|/2)-th smallest key
+    const bool in_r = active && (mkeys ? mkeys[i] <= *kstar : d <= T);
     const bool keep = active && !in_r;
     // survivors -> U'
     const unsigned km = __ballot_sync(kFull, keep);
@@ -285,11 +286,20 @@ gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigne
 // removes the ceil(|U|/2) vertices of U with the smallest degree in U (the
 // median degree is the threshold, and R is limited to half of U, one more if
 // |U| is odd), vertices of equal degree in increasing id order.  Each round
-// sorts U by (D[u] << 32 | u) (stable LSD radix sort) and cuts the sorted list
-// in half; UPDATE, the cut and the bookkeeping are ADG's.  floor(log2 n) + 1
-// rounds.
+// writes the keys D[u] * 2^32 + u of U (unique), selects the k-th smallest,
+// k = ceil(|U|/2), by MSD radix selection (per 8-bit digit from the top: a
+// histogram of the keys that match the digits chosen so far, then one block
+// picks the digit holding the k-th key), and partitions U on it; UPDATE, the
+// cut and the bookkeeping are ADG's.  floor(log2 n) + 1 rounds.
 // ---------------------------------------------------------------------------
 namespace {
+
+struct SelState {
+  unsigned long long prefix;  // digits chosen so far
+  unsigned long long mask;    // their bit positions
+  long long k;                // rank (1-based) still sought among the matching keys
+  long long pad;
+};
 
 __global__ void adg_m_init_kernel(const long long* __restrict__ row_ptr, long long n, int* __restrict__ D,
                                   int* __restrict__ U, unsigned* __restrict__ live) {
@@ -305,24 +315,65 @@ __global__ void adg_m_init_kernel(const long long* __restrict__ row_ptr, long lo
   }
 }
 
+// keys of this round's U, and the selection state (k = ceil(|U|/2))
 __global__ void adg_m_keys_kernel(const int* __restrict__ U, const AdgCtl* __restrict__ ctl,
                                   const int* __restrict__ D, unsigned long long* __restrict__ keys,
-                                  int* __restrict__ vals) {
+                                  SelState* __restrict__ st, unsigned* __restrict__ hist) {
   const long long size_u = ctl->size_U;
-  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < size_u;
-       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+  const long long t0 = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  for (long long i = t0; i < size_u; i += static_cast<long long>(gridDim.x) * blockDim.x) {
     const int u = U[i];
     keys[i] = (static_cast<unsigned long long>(static_cast<unsigned>(D[u])) << 32) | static_cast<unsigned>(u);
-    vals[i] = u;
   }
+  if (t0 == 0) *st = SelState{0ull, 0ull, (size_u + 1) / 2, 0};
+  if (t0 < 256) hist[t0] = 0u;
+}
+
+__global__ void __launch_bounds__(256)
+adg_m_hist_kernel(const unsigned long long* __restrict__ keys, const AdgCtl* __restrict__ ctl,
+                  const SelState* __restrict__ st, int shift, unsigned* __restrict__ hist) {
+  __shared__ unsigned sh[256];
+  sh[threadIdx.x] = 0u;
+  __syncthreads();
+  const long long size_u = ctl->size_U;
+  const unsigned long long prefix = st->prefix, mask = st->mask;
+  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < size_u;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const unsigned long long key = keys[i];
+    if ((key & mask) == prefix) atomicAdd(&sh[(key >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  if (sh[threadIdx.x]) atomicAdd(&hist[threadIdx.x], sh[threadIdx.x]);
+}
+
+// one block of 256 threads: the digit value whose bin holds the k-th key
+__global__ void __launch_bounds__(256) adg_m_pick_kernel(SelState* __restrict__ st, int shift,
+                                                         unsigned* __restrict__ hist) {
+  __shared__ long long cum[256];
+  const int t = threadIdx.x;
+  cum[t] = hist[t];
+  __syncthreads();
+  for (int o = 1; o < 256; o <<= 1) {  // inclusive scan
+    const long long add = t >= o ? cum[t - o] : 0;
+    __syncthreads();
+    cum[t] += add;
+    __syncthreads();
+  }
+  const long long k = st->k;
+  const long long before = t > 0 ? cum[t - 1] : 0;
+  __syncthreads();
+  if (before < k && k <= cum[t]) {
+    st->prefix |= static_cast<unsigned long long>(t) << shift;
+    st->mask |= 255ull << shift;
+    st->k = k - before;
+  }
+  hist[t] = 0u;
 }
 
 }  // namespace
 
 size_t adg_m_scratch_bytes(long long n, long long nnz) {
-  const size_t hist = sort_hist_elems(n);
-  return adg_scratch_bytes(n, nnz) + 2 * (static_cast<size_t>(n) * 8 + 256) + 2 * (static_cast<size_t>(n) * 4 + 256) +
-         hist * 8 + 256 + (scan_temp_elems(static_cast<long long>(hist)) + 1) * 8 + 256;
+  return adg_scratch_bytes(n, nnz) + static_cast<size_t>(n) * 8 + 256 + sizeof(SelState) + 256 + 256 * 4 + 256;
 }
 
 gc_status adg_m_run(gc_context* ctx, Arena a, const gc_csr* g, int* batch, int* D, int* rounds_out,
@@ -337,16 +388,19 @@ gc_status adg_m_run(gc_context* ctx, Arena a, const gc_csr* g, int* batch, int* 
   long long* task_start = a.take<long long>(ntask);
   int* task_len = a.take<int>(ntask);
   unsigned* live = a.take<unsigned>((n + 31) / 32);
-  SortBufs sb;
-  sb.keys[0] = a.take<unsigned long long>(n);
-  sb.keys[1] = a.take<unsigned long long>(n);
-  sb.vals[0] = a.take<int>(n);
-  sb.vals[1] = a.take<int>(n);
-  sb.hist = a.take<long long>(sort_hist_elems(n));
-  sb.temp = a.take<long long>(scan_temp_elems(static_cast<long long>(sort_hist_elems(n))) + 1);
-  if (!ctl || !D || !ubuf[0] || !ubuf[1] || !task_start || !task_len || !live || !sb.keys[0] || !sb.keys[1] ||
-      !sb.vals[0] || !sb.vals[1] || !sb.hist || !sb.temp)
+  unsigned long long* keys = a.take<unsigned long long>(n);
+  SelState* st = a.take<SelState>(1);
+  unsigned* hist = a.take<unsigned>(256);
+  if (!ctl || !D || !ubuf[0] || !ubuf[1] || !task_start || !task_len || !live || !keys || !st || !hist)
     return GC_ERR_OOM;
+
+  // digits of the keys that can be non-zero: u < n and D[u] <= n - 1
+  int nbits = 1;
+  while (nbits < 62 && (1ll << nbits) < n) ++nbits;
+  const int ndig = (nbits + 7) / 8;
+  int shifts[8], nshift = 0;
+  for (int d = ndig - 1; d >= 0; --d) shifts[nshift++] = 32 + 8 * d;  // D, from the top
+  for (int d = ndig - 1; d >= 0; --d) shifts[nshift++] = 8 * d;       // then u
 
   const long long* rp = row_ptr_of(g);
   const int max_blocks = ctx->num_sms * 8;
@@ -364,14 +418,16 @@ gc_status adg_m_run(gc_context* ctx, Arena a, const gc_csr* g, int* batch, int* 
     ++round;
     const long long want = (size_u + kAdgThreads - 1) / kAdgThreads;
     const int blocks = static_cast<int>(want < max_blocks ? want : max_blocks);
-    adg_m_keys_kernel<<<blocks, kAdgThreads, 0, s>>>(ubuf[cur], ctl, D, sb.keys[0], sb.vals[0]);
+    adg_m_keys_kernel<<<blocks, kAdgThreads, 0, s>>>(ubuf[cur], ctl, D, keys, st, hist);
     ++g_launches;
+    for (int j = 0; j < nshift; ++j) {
+      adg_m_hist_kernel<<<blocks, 256, 0, s>>>(keys, ctl, st, shifts[j], hist);
+      adg_m_pick_kernel<<<1, 256, 0, s>>>(st, shifts[j], hist);
+      g_launches += 2;
+    }
     GC_TRY_CUDA(cudaGetLastError());
-    cudaError_t err;
-    const int res = radix_sort_pairs(sb, size_u, 0xffu, s, &err);
-    GC_TRY_CUDA(err);
-    adg_partition_kernel<<<blocks, kAdgThreads, 0, s>>>(ctl, rp, D, batch, sb.vals[res], ubuf[cur ^ 1], task_start,
-                                                        task_len, live, 0, (size_u + 1) / 2);
+    adg_partition_kernel<<<blocks, kAdgThreads, 0, s>>>(ctl, rp, D, batch, ubuf[cur], ubuf[cur ^ 1], task_start,
+                                                        task_len, live, 0, keys, &st->prefix);
     ++g_launches;
     GC_TRY_CUDA(cudaGetLastError());
     ctx->timer_begin(gc_context::kTUpdate, s);
@@ -383,16 +439,15 @@ gc_status adg_m_run(gc_context* ctx, Arena a, const gc_csr* g, int* batch, int* 
     adg_finalize_kernel<<<1, 1, 0, s>>>(ctl);
     ++g_launches;
     GC_TRY_CUDA(cudaGetLastError());
-    GC_TRY_CUDA(cudaMemcpyAsync(pinned, &ctl->size_U, sizeof(int), cudaMemcpyDeviceToHost, s));
-    GC_TRY_CUDA(cudaStreamSynchronize(s));
-    const long long next = *pinned;
-    if (next != size_u / 2) return GC_ERR_CUDA;  // cannot happen: each round removes ceil(|U|/2)
-    size_u = next;
+    size_u /= 2;  // each round removes ceil(|U|/2): no read-back needed
     cur ^= 1;
   }
-  unsigned long long tot[2];
+  // one read-back at the end: the totals, and |U| = 0 as a check
   GC_TRY_CUDA(cudaMemcpyAsync(pinned, &ctl->total_U, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  GC_TRY_CUDA(cudaMemcpyAsync(pinned + 4, &ctl->size_U, sizeof(int), cudaMemcpyDeviceToHost, s));
   GC_TRY_CUDA(cudaStreamSynchronize(s));
+  if (pinned[4] != 0) return GC_ERR_CUDA;  // cannot happen
+  unsigned long long tot[2];
   memcpy(tot, pinned, sizeof(tot));
   ctx->stats.sum_U = static_cast<int64_t>(tot[0]);
   ctx->stats.sum_decrements = static_cast<int64_t>(tot[1]);

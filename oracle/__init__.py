@@ -15,6 +15,8 @@ Functions (each cites the passage of the paper it follows in ``oracle.c``):
   greedy(g, order)               Greedy colouring in a given order
   jp_color(g, priority)          JP (Algorithm 3) == Greedy by decreasing key
   jp_adg(g, p, q, seed)          ADG then JP with <rho_ADG, rho_R>
+  dec_itr(g, batch, rounds, seed)   DEC-ADG-ITR colouring of given partitions
+  dec_adg_itr(g, p, q, seed)     ADG then DEC-ADG-ITR
   pred_count(g, priority)        |pred(v)| in the DAG G_rho
   jp_depth(g, priority)          longest path of G_rho (JP's step count)
   degeneracy(g)                  exact d and smallest-last order (Matula-Beck)
@@ -75,6 +77,8 @@ def _load():
         lib.oracle_jp_depth.argtypes = [i64, vp, vp, vp, vp]
         lib.oracle_degeneracy.restype = i64
         lib.oracle_degeneracy.argtypes = [i64, vp, vp, vp]
+        lib.oracle_dec_adg_itr.restype = ctypes.c_int
+        lib.oracle_dec_adg_itr.argtypes = [i64, vp, vp, vp, i32, u64, vp, vp, vp, vp]
         lib.oracle_chromatic_number.restype = i32
         lib.oracle_chromatic_number.argtypes = [i64, vp, vp]
         _lib = lib
@@ -203,6 +207,28 @@ def jp_adg(g, eps_p: int, eps_q: int, seed: int):
     _check(_load().oracle_jp_adg(n, _p(rp), _p(ci), eps_p, eps_q, seed, _p(batch), _p(color),
                                  ctypes.byref(nr), ctypes.byref(nc)), "jp_adg")
     return batch, color, nr.value, nc.value
+
+
+def dec_itr(g, batch: np.ndarray, rounds: int, seed: int):
+    """DEC-ADG-ITR colouring of the partitions R(l) = {v : batch[v] = l}.
+    Returns (color, num_colors, iterations, fixed_iter)."""
+    n, rp, ci = _csr(g)
+    b = np.ascontiguousarray(batch, dtype=np.int32)
+    color = np.zeros(n, dtype=np.int32)
+    fixed = np.zeros(n, dtype=np.int32)
+    nc = ctypes.c_int32(0)
+    iters = ctypes.c_int64(0)
+    _check(_load().oracle_dec_adg_itr(n, _p(rp), _p(ci), _p(b), rounds, seed, _p(color), _p(fixed),
+                                      ctypes.byref(nc), ctypes.byref(iters)), "dec_adg_itr")
+    return color, nc.value, iters.value, fixed
+
+
+def dec_adg_itr(g, eps_p: int, eps_q: int, seed: int):
+    """ADG, then DEC-ADG-ITR.  Returns (batch, color, num_rounds, num_colors,
+    iterations, fixed_iter)."""
+    batch, rounds = adg(g, eps_p, eps_q)
+    color, nc, iters, fixed = dec_itr(g, batch, rounds, seed)
+    return batch, color, rounds, nc, iters, fixed
 
 
 def pred_count(g, prio: np.ndarray) -> np.ndarray:

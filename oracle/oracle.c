@@ -456,6 +456,165 @@ int64_t oracle_jp_depth(int64_t n, const int64_t *row_ptr, const int32_t *col_id
 }
 
 /* ------------------------------------------------------------------------- */
+/* DEC-ADG-ITR (Section 4.3): DEC-ADG's partition-by-partition colouring     */
+/* (Algorithm 4) with SIM-COL (Algorithm 5) changed to give every vertex of U */
+/* the smallest colour not in B_v instead of a random one.                    */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * Inputs: CSR, batch[v] in 1..rounds (the partitions R(l) of an ADG run),
+ * seed of the tie-break.  Readings taken here:
+ *  - Partitions are coloured from l = rounds down to 1 (Algorithm 4).
+ *  - B_v is the set of colours of v's coloured neighbours: before SIM-COL on
+ *    R(l) it receives the colours of neighbours in R(rounds) .. R(l+1)
+ *    (Algorithm 4), and after each SIM-COL iteration the colours of
+ *    neighbours in U that kept theirs (Algorithm 5, Part 3).  It is stored as
+ *    a bitmap of deg(v) + 1 bits: the smallest colour not in B_v is at most
+ *    |B_v| + 1 <= deg(v) + 1, so larger colours never decide it.
+ *  - Every step of a SIM-COL iteration reads the state the previous step
+ *    left (a synchronous parallel step): Part 2 compares the colours all of
+ *    U drew in Part 1.
+ *  - Conflict rule: the paper resets every vertex of a monochromatic edge in
+ *    U.  With deterministic choices that never ends (two adjacent vertices
+ *    with equal B draw the same colour again), so only the endpoint with the
+ *    lower key (h_seed(v), v) resets; the higher one keeps its colour.  The
+ *    highest-key vertex of U therefore keeps its colour in every iteration
+ *    and each SIM-COL call ends after at most |R(l)| iterations.
+ * Outputs: color[v] >= 1, *num_colors, *iterations = SIM-COL iterations summed
+ * over the partitions, and (if non-NULL) fixed_iter[v] = the iteration of
+ * SIM-COL on R(batch[v]) in which v kept its colour (1-based).
+ * Returns 0, 1 on bad arguments (a batch outside 1..rounds), 2 on allocation
+ * failure.
+ */
+int oracle_dec_adg_itr(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                       const int32_t *batch, int32_t rounds, uint64_t seed,
+                       int32_t *color, int32_t *fixed_iter, int32_t *num_colors,
+                       int64_t *iterations)
+{
+    if (n < 0 || rounds < 0) return 1;
+    for (int64_t v = 0; v < n; ++v)
+        if (batch[v] < 1 || batch[v] > rounds) return 1;
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    int64_t *boff = (int64_t *)malloc(sizeof(int64_t) * (nn + 1));   /* bitmap offsets, in bytes */
+    uint32_t *h = (uint32_t *)malloc(sizeof(uint32_t) * nn);
+    char *inU = (char *)calloc(nn, 1);
+    char *lose = (char *)calloc(nn, 1);
+    int64_t *members = (int64_t *)malloc(sizeof(int64_t) * nn);
+    int64_t *part_start = (int64_t *)calloc((size_t)rounds + 2, sizeof(int64_t));
+    if (!boff || !h || !inU || !lose || !members || !part_start) {
+        free(boff); free(h); free(inU); free(lose); free(members); free(part_start);
+        return 2;
+    }
+    boff[0] = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        const int64_t bits = row_ptr[v + 1] - row_ptr[v] + 1;  /* colours 1 .. deg(v)+1 */
+        boff[v + 1] = boff[v] + (bits + 7) / 8;
+        h[v] = oracle_tiebreak(seed, v);
+        color[v] = 0;
+        if (fixed_iter) fixed_iter[v] = 0;
+    }
+    unsigned char *B = (unsigned char *)calloc((size_t)(boff[n] > 0 ? boff[n] : 1), 1);
+    if (!B) {
+        free(boff); free(h); free(inU); free(lose); free(members); free(part_start);
+        return 2;
+    }
+    /* members[] lists the vertices partition by partition: R(l) is
+     * members[part_start[l] .. part_start[l+1]) */
+    for (int64_t v = 0; v < n; ++v) part_start[batch[v] + 1] += 1;
+    for (int32_t l = 1; l <= rounds; ++l) part_start[l + 1] += part_start[l];
+    {
+        int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * ((size_t)rounds + 2));
+        if (!fill) {
+            free(B); free(boff); free(h); free(inU); free(lose); free(members); free(part_start);
+            return 2;
+        }
+        memcpy(fill, part_start, sizeof(int64_t) * ((size_t)rounds + 2));
+        for (int64_t v = 0; v < n; ++v) members[fill[batch[v]]++] = v;
+        free(fill);
+    }
+
+#define B_HAS(v, c) ((B[boff[v] + ((c) - 1) / 8] >> (((c) - 1) % 8)) & 1)
+#define B_ADD(v, c)                                                             \
+    do {                                                                        \
+        if ((int64_t)(c) <= row_ptr[(v) + 1] - row_ptr[(v)] + 1)                \
+            B[boff[v] + ((c) - 1) / 8] |= (unsigned char)(1u << (((c) - 1) % 8)); \
+    } while (0)
+
+    int32_t maxc = 0;
+    int64_t iters = 0;
+    for (int32_t l = rounds; l >= 1; --l) {
+        const int64_t *R = members + part_start[l];
+        const int64_t sizeR = part_start[l + 1] - part_start[l];
+        /* Algorithm 4: B_v gets the colours of v's neighbours in the
+         * partitions coloured already (batch > l). */
+        for (int64_t i = 0; i < sizeR; ++i) {
+            const int64_t v = R[i];
+            for (int64_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) {
+                const int32_t u = col_idx[k];
+                if (batch[u] > l) B_ADD(v, color[u]);
+            }
+        }
+        /* SIM-COL on G(l) with U = R(l) */
+        int64_t sizeU = sizeR;
+        for (int64_t i = 0; i < sizeR; ++i) inU[R[i]] = 1;
+        int32_t it = 0;
+        while (sizeU > 0) {
+            ++it;
+            /* Part 1: every v in U takes the smallest colour not in B_v */
+            for (int64_t i = 0; i < sizeR; ++i) {
+                const int64_t v = R[i];
+                if (!inU[v]) continue;
+                int32_t c = 1;
+                while (B_HAS(v, c)) ++c;
+                color[v] = c;
+            }
+            /* Part 2: v resets if a neighbour in U with a higher key drew the
+             * same colour (decided for all of U before any reset) */
+            for (int64_t i = 0; i < sizeR; ++i) {
+                const int64_t v = R[i];
+                if (!inU[v]) continue;
+                lose[v] = 0;
+                for (int64_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) {
+                    const int32_t u = col_idx[k];
+                    if (!inU[u] || color[u] != color[v]) continue;
+                    if (h[u] > h[v] || (h[u] == h[v] && u > v)) { lose[v] = 1; break; }
+                }
+            }
+            for (int64_t i = 0; i < sizeR; ++i) {
+                const int64_t v = R[i];
+                if (inU[v] && lose[v]) color[v] = 0;
+            }
+            /* Part 3: B_v gets the colours of neighbours in U that kept theirs */
+            for (int64_t i = 0; i < sizeR; ++i) {
+                const int64_t v = R[i];
+                if (!inU[v]) continue;
+                for (int64_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) {
+                    const int32_t u = col_idx[k];
+                    if (inU[u] && color[u] > 0) B_ADD(v, color[u]);
+                }
+            }
+            /* U = U \ {v in U : C[v] > 0} */
+            for (int64_t i = 0; i < sizeR; ++i) {
+                const int64_t v = R[i];
+                if (inU[v] && color[v] > 0) {
+                    inU[v] = 0;
+                    --sizeU;
+                    if (fixed_iter) fixed_iter[v] = it;
+                    if (color[v] > maxc) maxc = color[v];
+                }
+            }
+        }
+        iters += it;
+    }
+#undef B_HAS
+#undef B_ADD
+    *num_colors = maxc;
+    *iterations = iters;
+    free(B); free(boff); free(h); free(inU); free(lose); free(members); free(part_start);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Exact degeneracy by smallest-last peeling (Matula & Beck; Section 2.2):   */
 /* repeatedly remove a vertex of minimum remaining degree.  d is the largest */
 /* degree seen at removal; order[] is the removal sequence (first removed    */

@@ -520,3 +520,190 @@ def test_grid_edge_counts():
     assert gg.grid(4, 3, 2).m == 3 * 3 * 2 + 4 * 2 * 2 + 4 * 3 * 1
     g = gg.grid(6, 6, 6, perm_seed=1)
     assert g.m == 3 * 6 * 6 * 5 and g.degrees().max() == 6
+
+
+# ---------------------------------------------------------------- DEC-ADG-ITR
+
+def _key_rank_desc(vs, seed):
+    """Vertices sorted by decreasing (h_seed(v), v)."""
+    return sorted(vs, key=lambda v: (oracle.tiebreak(seed, v), v), reverse=True)
+
+
+def _dec_itr_simulate(g, batch, seed):
+    """Algorithm 4 with the ITR form of Algorithm 5, executed with Python sets:
+    B_v is recomputed every iteration as the colours of all of v's neighbours
+    that hold a final colour (the partitions below the current one have none
+    yet), and the conflict test compares the colours the whole of U drew."""
+    n = g.n
+    nb = [set(int(u) for u in neighbours(g, v)) for v in range(n)]
+    key = {v: (oracle.tiebreak(seed, v), v) for v in range(n)}
+    C = [0] * n
+    fixed = [0] * n
+    rounds = int(batch.max()) if n else 0
+    total = 0
+    for l in range(rounds, 0, -1):
+        U = {v for v in range(n) if batch[v] == l}
+        it = 0
+        while U:
+            it += 1
+            draw = {}
+            for v in U:
+                taken = {C[u] for u in nb[v] if C[u] > 0}
+                c = 1
+                while c in taken:
+                    c += 1
+                draw[v] = c
+            keep = {v for v in U if not any(u in U and draw[u] == draw[v] and key[u] > key[v] for u in nb[v])}
+            for v in keep:
+                C[v] = draw[v]
+                fixed[v] = it
+            U -= keep
+        total += it
+    return np.array(C, dtype=np.int32), total, np.array(fixed, dtype=np.int32)
+
+
+def _dec_graphs():
+    yield complete(7)
+    yield petersen()
+    yield wheel(9)
+    yield cycle(12)
+    for s in range(5):
+        yield random_small(40, 0.15, s)
+    yield gg.erdos_renyi(300, 1500, 7)
+    yield gg.rmat(8, 8, seed=5)
+    yield gg.barabasi_albert(250, 3, 4)
+    yield gg.grid(9, 8)
+
+
+@pytest.mark.parametrize("g", list(_dec_graphs()), ids=lambda g: g.name)
+@pytest.mark.parametrize("p,q", [(1, 100), (1, 2), (3, 1)])
+def test_dec_itr_simulation_equals_oracle(g, p, q):
+    batch, color, rounds, nc, iters, fixed = oracle.dec_adg_itr(g, p, q, 42)
+    c2, it2, f2 = _dec_itr_simulate(g, batch, 42)
+    assert np.array_equal(color, c2) and iters == it2 and np.array_equal(fixed, f2)
+    assert nc == (color.max() if g.n else 0)
+
+
+def _dec_history_ok(g, batch, color, fixed, seed):
+    """Replays DEC-ADG-ITR from its outputs alone: in SIM-COL iteration j on
+    R(l), U_j = {v in R(l) : fixed[v] >= j} and v draws the smallest colour
+    missing from its neighbours fixed before (higher batch, or same batch and
+    fixed[u] < j).  v must keep its draw exactly when no neighbour in U_j with
+    a higher key drew the same, and then its colour is that draw."""
+    key = [(oracle.tiebreak(seed, v), v) for v in range(g.n)]
+    nb = [neighbours(g, v) for v in range(g.n)]
+    for l in range(1, int(batch.max()) + 1):
+        R = [v for v in range(g.n) if batch[v] == l]
+        for j in range(1, int(fixed[R].max()) + 1):
+            U = [v for v in R if fixed[v] >= j]
+            draw = {}
+            for v in U:
+                taken = {int(color[u]) for u in nb[v] if batch[u] > l or (batch[u] == l and fixed[u] < j)}
+                c = 1
+                while c in taken:
+                    c += 1
+                draw[v] = c
+            for v in U:
+                beaten = any(u in draw and draw[u] == draw[v] and key[u] > key[v] for u in nb[v])
+                if beaten == (fixed[v] == j):
+                    return False
+                if fixed[v] == j and color[v] != draw[v]:
+                    return False
+    return True
+
+
+@pytest.mark.parametrize("s", range(4))
+def test_dec_itr_history_replay(s):
+    for g in (random_small(30, 0.2, s), gg.erdos_renyi(120, 700, s + 1), gg.rmat(7, 8, seed=s + 2)):
+        batch, color, rounds, nc, iters, fixed = oracle.dec_adg_itr(g, 1, 100, 40 + s)
+        assert _dec_history_ok(g, batch, color, fixed, 40 + s)
+        # a plausible mistake fails the replay: a colour changed anywhere
+        bad = color.copy()
+        v = int(np.argmax(g.degrees()))
+        bad[v] += 1
+        assert not _dec_history_ok(g, batch, bad, fixed, 40 + s)
+
+
+@pytest.mark.parametrize("n", [2, 5, 13, 40])
+def test_dec_itr_complete_graph(n):
+    # K_n is one partition; in iteration t every vertex left draws colour t
+    # and only the highest key keeps it, so the colours rank the keys and
+    # there are n iterations (the same colouring as JP-ADG on K_n)
+    g = complete(n)
+    batch, color, rounds, nc, iters, fixed = oracle.dec_adg_itr(g, 1, 100, 42)
+    rank = _key_rank_desc(range(n), 42)
+    assert rounds == 1 and iters == n and nc == n
+    for i, v in enumerate(rank):
+        assert color[v] == i + 1 and fixed[v] == i + 1
+    assert np.array_equal(color, oracle.jp_adg(g, 1, 100, 42)[1])
+
+
+@pytest.mark.parametrize("k", [2, 3, 10, 200])
+def test_dec_itr_star_and_bipartite(k):
+    # star: centre is R(2) and takes colour 1, the leaves (independent) take 2
+    batch, color, rounds, nc, iters, _ = oracle.dec_adg_itr(star(k), 1, 100, 42)
+    assert rounds == 2 and iters == 2 and color[0] == 1 and (color[1:] == 2).all()
+    # K_{a,b} with b > (1+2eps)a: a-side is R(2) -> colour 1, b-side colour 2
+    a, b = 3, 3 + k
+    batch, color, rounds, nc, iters, _ = oracle.dec_adg_itr(complete_bipartite(a, b), 1, 100, 42)
+    assert rounds == 2 and iters == 2 and (color[:a] == 1).all() and (color[a:] == 2).all()
+
+
+@pytest.mark.parametrize("n", [3, 4, 9, 10, 57, 100])
+def test_dec_itr_short_path(n):
+    # P_n (n <= 100) peels from both ends: R(l) = {l-1, n-l}.  Odd n: the
+    # centre is alone on top and takes 1, then colours alternate outwards, one
+    # iteration per partition.  Even n: the two central vertices are adjacent
+    # in the top partition; the higher key keeps 1 in iteration 1, the other
+    # takes 2 in iteration 2; colours then alternate outwards.
+    g = path(n)
+    batch, color, rounds, nc, iters, _ = oracle.dec_adg_itr(g, 1, 100, 42)
+    if n % 2:
+        w = n // 2
+        assert iters == rounds == (n + 1) // 2
+    else:
+        w = _key_rank_desc([n // 2 - 1, n // 2], 42)[0]
+        assert rounds == n // 2 and iters == rounds + 1
+    assert list(color) == [1 if (i - w) % 2 == 0 else 2 for i in range(n)]
+
+
+def test_dec_itr_independent_partitions_equal_jp_adg():
+    # when no edge joins two vertices of one partition, SIM-COL ends after
+    # one iteration per partition and every vertex takes the smallest colour
+    # missing among its higher-batch neighbours: Greedy in batch order, which
+    # is JP-ADG's colouring (ties inside a batch never meet)
+    for g in (star(30), complete_bipartite(4, 20), path(41), gg.grid(7, 7)):
+        batch, color, rounds, nc, iters, _ = oracle.dec_adg_itr(g, 1, 100, 7)
+        src = np.repeat(np.arange(g.n), g.degrees())
+        if (batch[src] == batch[g.col_idx]).any():
+            continue
+        assert iters == rounds
+        assert np.array_equal(color, oracle.jp_adg(g, 1, 100, 7)[1])
+
+
+@pytest.mark.parametrize("g", GRAPHS, ids=lambda g: g.name)
+@pytest.mark.parametrize("p,q", [(1, 100), (1, 2)])
+def test_dec_itr_invariants(g, p, q):
+    # proper; each colour is at most 1 + the number of neighbours in the same
+    # or a higher partition (B_v holds at most that many colours), hence at
+    # most floor(2(1+eps)d) + 1 (Section 4.3's bound for DEC-ADG-ITR); each
+    # SIM-COL call ends within |R(l)| iterations
+    d, _ = oracle.degeneracy(g)
+    batch, color, rounds, nc, iters, fixed = oracle.dec_adg_itr(g, p, q, 42)
+    src = np.repeat(np.arange(g.n), g.degrees())
+    assert (color >= 1).all() and color.max() == nc
+    assert (color[src] != color[g.col_idx]).all()
+    assert (color <= _geq_counts(g, batch) + 1).all()
+    assert nc <= (2 * (q + p) * d) // q + 1
+    sizes = np.bincount(batch, minlength=rounds + 1)[1:]
+    per = np.zeros(rounds + 1, dtype=np.int64)
+    np.maximum.at(per, batch, fixed)
+    assert (per[1:] <= sizes).all() and per[1:].sum() == iters and (per[1:] >= 1).all()
+
+
+def test_dec_itr_bad_batch_rejected():
+    g = path(4)
+    with pytest.raises(RuntimeError):
+        oracle.dec_itr(g, np.array([1, 2, 3, 1], dtype=np.int32), 2, 42)
+    color, nc, iters, _ = oracle.dec_itr(empty(0), np.zeros(0, dtype=np.int32), 0, 42)
+    assert nc == 0 and iters == 0

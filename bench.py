@@ -171,7 +171,7 @@ class ClockSampler:
                 "samples": len(sms)}
 
 
-def cpu_baseline(w_name, seconds_target=10.0, median=False):
+def cpu_baseline(w_name, seconds_target=10.0, median=False, dec=False):
     """The oracle as it stands, single-threaded, on a bounded sample of the
     same family (R-MAT scale 22 for the R-MAT workloads)."""
     import graphgen as gg
@@ -193,11 +193,13 @@ def cpu_baseline(w_name, seconds_target=10.0, median=False):
         t0 = time.perf_counter()
         if median:
             oracle.jp_adg_m(g, w["seed"])
+        elif dec:
+            oracle.dec_adg_itr(g, p, q, w["seed"])
         else:
             oracle.jp_adg(g, p, q, w["seed"])
         total += time.perf_counter() - t0
         reps += 1
-    what = "ADG-M + Greedy" if median else "ADG + Greedy"
+    what = "ADG-M + Greedy" if median else ("ADG + DEC-ADG-ITR" if dec else "ADG + Greedy")
     return {"value": g.m * reps / total, "unit": "edges/s", "cores": 1, "kind": "oracle",
             "sample": f"{desc}: n={g.n}, m={g.m}, {reps} run(s) of {what}, {total:.1f} s"}
 
@@ -282,6 +284,104 @@ def run_variant(args, rank, world):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_dec(args, rank, world):
+    """DEC-ADG-ITR (Section 4.3): one step is gc_color_graph_dec_itr (ADG,
+    then the partitions coloured from the top by SIM-COL in its ITR form) on
+    the resident graph."""
+    import torch
+    import torch.distributed as dist
+    from paper_2008_11321_gb300 import _build
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    import paper_2008_11321_gb300 as gcp
+    w = WORKLOADS[args.workload]
+    p, q = w["eps"]
+    seed = w["seed"]
+    g = make_graph(w, pinned=True)
+    n, nnz, m = g.n, g.nnz, g.m
+    dg = gcp.DeviceGraph(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col_idx).to(dev))
+    color = torch.empty(n, dtype=torch.int32, device=dev)
+    batch = torch.empty(n, dtype=torch.int32, device=dev)
+    ctx = gcp.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        nc, nr = ctx.gc_color_graph_dec_itr(dg, p, q, seed, color, batch)
+    ctx.gc_set_timing(True)
+    sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    steps = []
+    for _ in range(args.steps):
+        nc, nr = ctx.gc_color_graph_dec_itr(dg, p, q, seed, color, batch)
+        st = ctx.gc_get_stats()
+        steps.append({k: getattr(st, k) for k, _ in st._fields_})
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    t = torch.tensor([ev0.elapsed_time(ev1) / 1e3], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    mean = lambda k: statistics.mean(x[k] for x in steps)  # noqa: E731
+    last = steps[-1]
+    peak, peak_kind = load_peak()
+    n_nonisolated = int((g.degrees() > 0).sum())
+    inner = last["dec_internal_edges"]
+    # extraction, summed over its one launch per partition: per non-isolated
+    # vertex its row offsets, list entry and state write (24 B); per CSR entry
+    # the neighbour id and its state word (8 B); per internal entry the copy
+    # to the internal list (4 B).  UPDATE as in the JP-ADG line.
+    gb = {"adg_update_kernel": 8 * nnz + 4 * last["sum_decrements"],
+          "dec_extract_kernel": 24 * n_nonisolated + 8 * nnz + 4 * inner}
+    groups = {"adg_update_kernel": (mean("ms_adg_update"), last["adg_rounds"]),
+              "dec_extract_kernel": (mean("ms_dec_extract"), last["adg_rounds"])}
+    kname = max(groups, key=lambda k: groups[k][0])
+    kms, kl = groups[kname]
+    achieved = gb[kname] / (kms / 1e3) / 1e9 if kms > 0 else 0.0
+    line = {
+        "metric": METRIC, "value": m * args.steps * world / t_max, "unit": "edges/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": w["desc"], "algorithm": "DEC-ADG-ITR", "n": n, "m": m, "eps": f"{p}/{q}",
+                   "seed": seed, "adg_rounds": nr, "num_colors": nc, "sim_iterations": last["sim_iterations"],
+                   "internal_entries": inner,
+                   "l2": f"inputs larger than L2 (col_idx {4 * nnz / 1e9:.2f} GB), no flush"},
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "algorithmic_bytes_per_launch": gb[kname] / kl, "ms_per_launch": kms / kl,
+                     "launches_per_step": kl,
+                     "groups_ms": {"adg_update_kernel": mean("ms_adg_update"),
+                                   "dec_extract_kernel": mean("ms_dec_extract"),
+                                   "dec_check_pick_kernels": mean("ms_dec_iterate")}},
+        "path": {"ms_adg": mean("ms_adg"), "ms_color": mean("ms_jp")},
+        "gpu_launches": sum(x["launches"] for x in steps),
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload, dec=True)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -546,6 +646,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--priority", choices=["adg", "adg-m"] + sorted(PRIORITIES), default="adg",
                     help="JP priority: adg (JP-ADG, the default), adg-m (JP-ADG-M) or another JP variant")
+    ap.add_argument("--algo", choices=["jp", "dec-itr"], default="jp",
+                    help="colouring: jp (JP with --priority, the default) or dec-itr (DEC-ADG-ITR)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: --warmup below 3 is outside the timing rules", file=sys.stderr)
@@ -556,6 +658,10 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.algo == "dec-itr":
+        if WORKLOADS[args.workload]["kind"] in ("batch", "serve") or args.priority != "adg":
+            ap.error("--algo dec-itr applies to the single-graph workloads, without --priority")
+        return run_dec(args, rank, world)
     if args.priority != "adg":
         if WORKLOADS[args.workload]["kind"] in ("batch", "serve"):
             ap.error("--priority applies to the single-graph workloads")

@@ -96,6 +96,12 @@ typedef struct {
   int64_t core_preds;      /* predecessor entries of the core                  */
   int64_t core_degree_sum; /* degree sum of the core vertices                  */
   int32_t core_ctas;       /* CTAs (one cluster) that coloured the core        */
+  int64_t sim_iterations;  /* DEC-ADG-ITR: SIM-COL iterations, summed over the
+                              partitions (0 for the JP calls)                  */
+  int64_t dec_internal_edges; /* DEC-ADG-ITR: CSR entries inside a partition
+                              of vertices with such an entry (edges of G(l))   */
+  float ms_dec_extract;    /* DEC-ADG-ITR: per-partition extraction launches   */
+  float ms_dec_iterate;    /* DEC-ADG-ITR: the later SIM-COL iterations        */
 } gc_stats;
 
 /* Human-readable name of a status code (static storage). */
@@ -189,6 +195,33 @@ gc_status gc_adg_m_partition(gc_context *ctx, const gc_csr *g, int32_t *batch_ou
  * in gc_color_graph (without eps). */
 gc_status gc_color_graph_m(gc_context *ctx, const gc_csr *g, uint64_t seed, int32_t *color_out, int32_t *batch_out,
                            int32_t *num_colors_out, int32_t *num_rounds_out, gc_stream stream);
+
+/* DEC-ADG-ITR colouring (Section 4.3) of given partitions
+ * R(l) = {v : batch[v] = l}, l = 1..num_rounds (batch: device, n int32, any
+ * partial order such as gc_adg_partition's or gc_adg_m_partition's):
+ * Algorithm 4 colours R(num_rounds) first and R(1) last, each with SIM-COL
+ * (Algorithm 5) in its ITR form, every vertex still in U drawing the
+ * smallest colour not used by a coloured neighbour (its bitmap B_v).  Of two
+ * adjacent vertices of U that drew the same colour in one iteration, the one
+ * with the lower (h_seed(v), v) key gives it back (h_seed as in
+ * gc_make_priority; the paper resets both, which never ends with
+ * deterministic draws), so each SIM-COL call ends within |R(l)| iterations
+ * and the result does not depend on the schedule.  color_out (device, n
+ * int32) receives colours >= 1, each at most 1 + the number of neighbours in
+ * the same or a higher partition; *num_colors_out (host, may be NULL) the
+ * largest.  gc_stats.sim_iterations counts the SIM-COL iterations.
+ * GC_ERR_INVALID_ARG if num_rounds < 1 (n > 0) or a batch lies outside
+ * 1..num_rounds (then color_out is undefined).  Scratch: about
+ * 4 nnz + 24 n bytes. */
+gc_status gc_dec_itr_color(gc_context *ctx, const gc_csr *g, const int32_t *batch, int32_t num_rounds,
+                           uint64_t seed, int32_t *color_out, int32_t *num_colors_out, gc_stream stream);
+
+/* DEC-ADG-ITR end to end: ADG with eps = eps_p/eps_q (as gc_adg_partition),
+ * then gc_dec_itr_color on its partitions.  At most floor(2(1+eps)d) + 1
+ * colours for degeneracy d.  Arguments as in gc_color_graph. */
+gc_status gc_color_graph_dec_itr(gc_context *ctx, const gc_csr *g, uint32_t eps_p, uint32_t eps_q, uint64_t seed,
+                                 int32_t *color_out, int32_t *batch_out, int32_t *num_colors_out,
+                                 int32_t *num_rounds_out, gc_stream stream);
 
 /* Priorities of the other JP variants the paper compares (Section 4.1,
  * "combinations of JP and orderings"), as keys for gc_jp_color:

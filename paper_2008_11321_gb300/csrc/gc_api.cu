@@ -27,6 +27,8 @@ struct CallScope {
     ctx->stats.core_preds = 0;
     ctx->stats.core_degree_sum = 0;
     ctx->stats.core_ctas = 0;
+    ctx->stats.sim_iterations = 0;
+    ctx->stats.dec_internal_edges = 0;
   }
   ~CallScope() {
     if (!ctx) return;
@@ -423,6 +425,68 @@ gc_status gc_color_graph_m(gc_context* ctx, const gc_csr* g, uint64_t seed, int3
   if (!guard.ok) return GC_ERR_CUDA;
   return color_graph_device(ctx, g, 0, 1, seed, color_out, batch_out, num_colors_out, num_rounds_out,
                             reinterpret_cast<cudaStream_t>(stream), true);
+}
+
+gc_status gc_dec_itr_color(gc_context* ctx, const gc_csr* g, const int32_t* batch, int32_t num_rounds,
+                           uint64_t seed, int32_t* color_out, int32_t* num_colors_out, gc_stream stream) {
+  if (!ctx) return GC_ERR_INVALID_ARG;
+  GC_TRY(check_graph_args(g));
+  if (g->n > 0 && (!batch || !color_out || num_rounds < 1)) return GC_ERR_INVALID_ARG;
+  DeviceGuard guard(ctx->device);
+  CallScope scope(ctx);
+  if (!guard.ok) return GC_ERR_CUDA;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  GC_TRY(ctx->reserve(gc::dec_scratch_bytes(g->n, g->nnz, num_rounds)));
+  int colors = 0;
+  long long iters = 0;
+  GC_TRY(timing_begin(ctx, 1, s));
+  GC_TRY(gc::dec_itr_run(ctx, ctx->arena(), g, batch, num_rounds, seed, color_out, &colors, &iters, s));
+  GC_TRY(timing_begin(ctx, 2, s));
+  if (ctx->timing) {
+    GC_TRY_CUDA(cudaEventSynchronize(ctx->ev[2]));
+    ctx->stats.ms_jp = timing_ms(ctx, 1, 2);
+  }
+  ctx->stats.num_colors = colors;
+  ctx->stats.sim_iterations = iters;
+  if (num_colors_out) *num_colors_out = colors;
+  return GC_OK;
+}
+
+gc_status gc_color_graph_dec_itr(gc_context* ctx, const gc_csr* g, uint32_t eps_p, uint32_t eps_q, uint64_t seed,
+                                 int32_t* color_out, int32_t* batch_out, int32_t* num_colors_out,
+                                 int32_t* num_rounds_out, gc_stream stream) {
+  if (!ctx) return GC_ERR_INVALID_ARG;
+  GC_TRY(check_graph_args(g));
+  GC_TRY(check_eps(eps_p, eps_q));
+  if (g->n > 0 && !color_out) return GC_ERR_INVALID_ARG;
+  DeviceGuard guard(ctx->device);
+  CallScope scope(ctx);
+  if (!guard.ok) return GC_ERR_CUDA;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const long long n = g->n;
+  const size_t vb = static_cast<size_t>(n > 0 ? n : 1) * 4 + 256;
+  GC_TRY(ctx->reserve_vert(2 * vb));
+  int* D = static_cast<int*>(ctx->vbuf);
+  int* b = batch_out ? batch_out : reinterpret_cast<int*>(static_cast<char*>(ctx->vbuf) + vb);
+  GC_TRY(ctx->reserve(gc::adg_scratch_bytes(n, g->nnz)));
+  int rounds = 0, colors = 0;
+  long long iters = 0;
+  GC_TRY(timing_begin(ctx, 0, s));
+  GC_TRY(gc::adg_run(ctx, ctx->arena(), g, eps_p, eps_q, b, D, &rounds, s));
+  GC_TRY(timing_begin(ctx, 1, s));
+  GC_TRY(ctx->reserve(gc::dec_scratch_bytes(n, g->nnz, rounds)));
+  GC_TRY(gc::dec_itr_run(ctx, ctx->arena(), g, b, rounds, seed, color_out, &colors, &iters, s));
+  GC_TRY(timing_begin(ctx, 2, s));
+  if (ctx->timing) {
+    GC_TRY_CUDA(cudaEventSynchronize(ctx->ev[2]));
+    ctx->stats.ms_adg = timing_ms(ctx, 0, 1);
+    ctx->stats.ms_jp = timing_ms(ctx, 1, 2);
+  }
+  ctx->stats.num_colors = colors;
+  ctx->stats.sim_iterations = iters;
+  if (num_colors_out) *num_colors_out = colors;
+  if (num_rounds_out) *num_rounds_out = rounds;
+  return GC_OK;
 }
 
 gc_status gc_color_graph_host(gc_context* ctx, int64_t n, int64_t nnz, const int64_t* row_ptr,

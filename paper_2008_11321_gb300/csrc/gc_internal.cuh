@@ -135,6 +135,13 @@ gc_status jp_run_fused(gc_context* ctx, Arena a, const gc_csr* g, const int* bat
                        cudaStream_t s);
 gc_status jp_run_given(gc_context* ctx, Arena a, const gc_csr* g, const unsigned long long* prio,
                        int* color, int* num_colors_out, cudaStream_t s);
+// DEC-ADG-ITR colouring of the partitions batch[] = 1..rounds (gc_dec.cu).
+// iters_out: SIM-COL iterations summed over the partitions.
+size_t dec_scratch_bytes(long long n, long long nnz, int rounds);
+// Also sets stats.dec_internal_edges.
+gc_status dec_itr_run(gc_context* ctx, Arena a, const gc_csr* g, const int* batch, int rounds,
+                      unsigned long long seed, int* color, int* num_colors_out, long long* iters_out,
+                      cudaStream_t s);
 // gc_color_batch body (gc_batch.cu).
 size_t batch_adg_scratch_bytes(long long n, long long nnz, long long G);
 gc_status batch_color(gc_context* ctx, const gc_batch_csr* b, const gc_job* jobs, int32_t* color_out,
@@ -197,7 +204,7 @@ struct gc_context {
   int tused = 0;
   gc_stats stats{};
 
-  enum TimerGroup { kTUpdate = 0, kTCoreSolve = 1, kTBulk = 2, kTCorePreds = 3 };
+  enum TimerGroup { kTUpdate = 0, kTCoreSolve = 1, kTBulk = 2, kTCorePreds = 3, kTDecExtract = 4, kTDecIterate = 5 };
   void timer_begin(int group, cudaStream_t s) {
     if (!timing || tused >= kTimerPairs || !tev[2 * tused]) return;
     tgroup[tused] = group;
@@ -210,7 +217,7 @@ struct gc_context {
   }
   // after the stream is synchronised
   void timers_collect() {
-    float sum[4] = {0.f, 0.f, 0.f, 0.f};
+    float sum[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int i = 0; i < tused; ++i) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, tev[2 * i], tev[2 * i + 1]) == cudaSuccess) sum[tgroup[i]] += ms;
@@ -219,6 +226,8 @@ struct gc_context {
     stats.ms_core_solve = sum[kTCoreSolve];
     stats.ms_jp_color = sum[kTBulk];
     stats.ms_core_preds = sum[kTCorePreds];
+    stats.ms_dec_extract = sum[kTDecExtract];
+    stats.ms_dec_iterate = sum[kTDecIterate];
     tused = 0;
   }
   gc_status reserve(size_t bytes);      // scratch arena

@@ -25,7 +25,8 @@ GC_ERR_CUDA, GC_ERR_TIMEOUT, GC_ERR_OVERFLOW = 4, 5, 6
 EXPORTS = ("gc_status_str", "gc_create", "gc_destroy", "gc_get_stats", "gc_set_timing",
            "gc_validate_csr", "gc_adg_partition", "gc_make_priority", "gc_jp_color",
            "gc_color_graph", "gc_color_graph_host", "gc_adg_partition_noalloc", "gc_color_batch",
-           "gc_color_batch_list", "gc_make_priority_kind", "gc_adg_m_partition", "gc_color_graph_m")
+           "gc_color_batch_list", "gc_make_priority_kind", "gc_adg_m_partition", "gc_color_graph_m",
+           "gc_dec_itr_color", "gc_color_graph_dec_itr")
 
 # priority kinds of gc_make_priority_kind
 GC_PRIO_R, GC_PRIO_FF, GC_PRIO_LF, GC_PRIO_LLF = 0, 1, 2, 3
@@ -59,7 +60,9 @@ class gc_stats(ctypes.Structure):
                 ("ms_adg_update", ctypes.c_float), ("ms_core_solve", ctypes.c_float),
                 ("ms_core_preds", ctypes.c_float), ("bulk_launches", ctypes.c_int32),
                 ("core_vertices", ctypes.c_int64), ("core_preds", ctypes.c_int64),
-                ("core_degree_sum", ctypes.c_int64), ("core_ctas", ctypes.c_int32)]
+                ("core_degree_sum", ctypes.c_int64), ("core_ctas", ctypes.c_int32),
+                ("sim_iterations", ctypes.c_int64), ("dec_internal_edges", ctypes.c_int64),
+                ("ms_dec_extract", ctypes.c_float), ("ms_dec_iterate", ctypes.c_float)]
 
 
 _lib = None
@@ -99,6 +102,10 @@ def load(path: str = LIB_PATH):
     lib.gc_adg_m_partition.argtypes = [vp, P(gc_csr), vp, P(i32), vp]
     lib.gc_color_graph_m.restype = ctypes.c_int
     lib.gc_color_graph_m.argtypes = [vp, P(gc_csr), u64, vp, vp, P(i32), P(i32), vp]
+    lib.gc_dec_itr_color.restype = ctypes.c_int
+    lib.gc_dec_itr_color.argtypes = [vp, P(gc_csr), vp, i32, u64, vp, P(i32), vp]
+    lib.gc_color_graph_dec_itr.restype = ctypes.c_int
+    lib.gc_color_graph_dec_itr.argtypes = [vp, P(gc_csr), u32, u32, u64, vp, vp, P(i32), P(i32), vp]
     lib.gc_make_priority_kind.restype = ctypes.c_int
     lib.gc_make_priority_kind.argtypes = [vp, P(gc_csr), ctypes.c_int32, u64, vp, vp]
     lib.gc_color_graph.restype = ctypes.c_int
@@ -278,6 +285,25 @@ class Context:
         nc, nr = ctypes.c_int32(0), ctypes.c_int32(0)
         _check(self._lib.gc_color_graph_m(self.handle, ctypes.byref(c), seed, _ptr(color_out), _ptr(batch_out),
                                           ctypes.byref(nc), ctypes.byref(nr), _stream(stream)), "gc_color_graph_m")
+        return nc.value, nr.value
+
+    def gc_dec_itr_color(self, g: DeviceGraph, batch, num_rounds: int, seed: int, color_out, stream=None) -> int:
+        """DEC-ADG-ITR colouring of the partitions batch = 1..num_rounds;
+        returns the number of colours (SIM-COL iterations in stats())."""
+        c = g.csr()
+        nc = ctypes.c_int32(0)
+        _check(self._lib.gc_dec_itr_color(self.handle, ctypes.byref(c), _ptr(batch), num_rounds, seed,
+                                          _ptr(color_out), ctypes.byref(nc), _stream(stream)), "gc_dec_itr_color")
+        return nc.value
+
+    def gc_color_graph_dec_itr(self, g: DeviceGraph, eps_p: int, eps_q: int, seed: int, color_out,
+                               batch_out=None, stream=None):
+        """ADG then DEC-ADG-ITR; returns (num_colors, num_rounds)."""
+        c = g.csr()
+        nc, nr = ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(self._lib.gc_color_graph_dec_itr(self.handle, ctypes.byref(c), eps_p, eps_q, seed, _ptr(color_out),
+                                                _ptr(batch_out), ctypes.byref(nc), ctypes.byref(nr),
+                                                _stream(stream)), "gc_color_graph_dec_itr")
         return nc.value, nr.value
 
     def gc_make_priority_kind(self, g: DeviceGraph, kind: int, seed: int, key_out, stream=None):

@@ -1,0 +1,137 @@
+"""DEC-ADG-ITR on the GPU vs the CPU oracle, bit for bit, through the C ABI.
+
+Colours, colour counts and SIM-COL iteration counts are integers: exact
+equality.  The graphs cover both extraction paths (degree <= 32 by a lane,
+larger by a warp), both check/pick paths (at most 32 internal neighbours or
+more), bitmaps of many words (cliques past 1,024 colours), partitions with and
+without conflicts, more than 255 partitions (the batch then read from its
+array instead of the state word), partitions given by the caller (ADG-M's, and
+arbitrary ones with empty partitions), and the degenerate cases.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from _fixtures import (complete, complete_bipartite, cycle, empty, path, petersen, random_small, star,
+                       wheel)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2008_11321_gb300 as gcp  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2008_11321_gb300 import _build
+    _build.build()
+    c = gcp.Context(0)
+    yield c
+    c.close()
+
+
+def dev(g):
+    return gcp.DeviceGraph.from_host(g, "cuda:0")
+
+
+def dec_graph(ctx, g, p, q, seed):
+    dg = dev(g)
+    color = torch.full((g.n,), -7, dtype=torch.int32, device="cuda:0")
+    batch = torch.full((g.n,), -7, dtype=torch.int32, device="cuda:0")
+    nc, nr = ctx.gc_color_graph_dec_itr(dg, p, q, seed, color, batch)
+    st = ctx.gc_get_stats()
+    return batch.cpu().numpy(), color.cpu().numpy(), nr, nc, st.sim_iterations, st.dec_internal_edges
+
+
+def assert_dec_same(ctx, g, p=1, q=100, seed=42):
+    b, c, nr, nc, it, inner = dec_graph(ctx, g, p, q, seed)
+    ob, oc, onr, onc, oit, _ = oracle.dec_adg_itr(g, p, q, seed)
+    assert nr == onr and np.array_equal(b, ob), g.name
+    assert np.array_equal(c, oc), g.name
+    assert nc == onc and it == oit, (g.name, nc, onc, it, oit)
+    src = np.repeat(np.arange(g.n), g.degrees())
+    assert inner == int((ob[src] == ob[g.col_idx]).sum()), g.name  # edges of the G(l), both directions
+    return c
+
+
+DEC_GRAPHS = [empty(1), empty(100), complete(2), complete(33), complete(40), star(3), star(32), star(33),
+              star(5000), path(7), path(100), path(101), cycle(1000), complete_bipartite(7, 50),
+              complete_bipartite(40, 41), petersen(), wheel(64), random_small(60, 0.3, 1),
+              random_small(200, 0.05, 2), gg.erdos_renyi(16384, 81920, 1), gg.rmat(12, 8, seed=3),
+              gg.rmat(16, 16, seed=2), gg.barabasi_albert(30000, 4, 5), gg.barabasi_albert(2046, 14, 43),
+              gg.grid(64, 64, 16, perm_seed=3)]
+
+
+@pytest.mark.parametrize("g", DEC_GRAPHS, ids=lambda g: g.name)
+@pytest.mark.parametrize("p,q", [(1, 100), (1, 2)])
+def test_dec_itr_matches_oracle(ctx, g, p, q):
+    assert_dec_same(ctx, g, p, q)
+
+
+def test_dec_itr_clique_beyond_window(ctx):
+    # K_1100 is one partition coloured one vertex per iteration: 1100
+    # iterations, bitmaps of 35 words, colours 1..1100 by decreasing key
+    c = assert_dec_same(ctx, complete(1100))
+    assert sorted(c.tolist()) == list(range(1, 1101))
+
+
+@pytest.mark.parametrize("p,q", [(1, 100), (1, 10), (1, 2)])
+def test_dec_itr_rmat20(ctx, p, q):
+    assert_dec_same(ctx, gg.rmat(20, 16, seed=1), p, q)
+
+
+@pytest.mark.parametrize("seed", [0, 2**63 + 11])
+def test_dec_itr_seeds(ctx, seed):
+    assert_dec_same(ctx, gg.rmat(14, 16, seed=5), 1, 100, seed)
+
+
+@pytest.mark.parametrize("n", [500, 600])
+def test_dec_itr_many_partitions(ctx, n):
+    # eps = 2^-20 peels a path from both ends: n/2 partitions, 250 (batch in
+    # the state word) and 300 (batch read from its array)
+    assert oracle.adg(path(n), 1, 1 << 20)[1] == n // 2
+    assert_dec_same(ctx, path(n), 1, 1 << 20)
+
+
+def _given(ctx, g, batch, rounds, seed=42):
+    dg = dev(g)
+    b = torch.from_numpy(np.ascontiguousarray(batch, dtype=np.int32)).to("cuda:0")
+    color = torch.full((g.n,), -7, dtype=torch.int32, device="cuda:0")
+    nc = ctx.gc_dec_itr_color(dg, b, rounds, seed, color)
+    return color.cpu().numpy(), nc, ctx.gc_get_stats().sim_iterations
+
+
+def test_dec_itr_given_partitions(ctx):
+    # ADG-M's partitions (DEC-ADG-M-ITR), and arbitrary ones with empty
+    # partitions and more partitions than vertices need
+    for g in (gg.rmat(15, 16, seed=3), gg.barabasi_albert(5000, 6, 2), complete(70)):
+        bm, rm = oracle.adg_m(g)
+        oc, onc, oit, _ = oracle.dec_itr(g, bm, rm, 42)
+        c, nc, it = _given(ctx, g, bm, rm)
+        assert np.array_equal(c, oc) and nc == onc and it == oit, g.name
+        rb = (np.random.default_rng(g.n).integers(1, 9, g.n) * 3).astype(np.int32)
+        oc, onc, oit, _ = oracle.dec_itr(g, rb, 30, 7)
+        c, nc, it = _given(ctx, g, rb, 30, 7)
+        assert np.array_equal(c, oc) and nc == onc and it == oit, g.name
+
+
+def test_dec_itr_rejects_bad_partitions(ctx):
+    g = path(6)
+    for batch, rounds in (([1, 2, 3, 3, 2, 1], 2), ([0, 1, 1, 1, 1, 1], 3), ([1] * 6, 0)):
+        with pytest.raises(gcp.GcError) as e:
+            _given(ctx, g, np.array(batch), rounds)
+        assert e.value.status == gcp.GC_ERR_INVALID_ARG
+    # the context stays usable
+    assert_dec_same(ctx, gg.rmat(10, 8, seed=1))
+
+
+def test_dec_itr_zero_vertices(ctx):
+    dg = dev(empty(0))
+    out = torch.empty(0, dtype=torch.int32, device="cuda:0")
+    assert ctx.gc_color_graph_dec_itr(dg, 1, 100, 42, out) == (0, 0)
+    assert ctx.gc_dec_itr_color(dg, out, 1, 42, out) == 0

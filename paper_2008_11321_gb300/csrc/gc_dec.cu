@@ -17,10 +17,12 @@
 //            internal neighbour with a higher key drew the same colour; the
 //            others form the next U.
 //   pick     Part 3, then Part 1 of the next iteration: v adds the colours of
-//            its fixed internal neighbours to B_v and draws the smallest
-//            colour not in it.
-// The full adjacency is read once per vertex; the later iterations (hundreds
-// on the dense top partition of a power-law graph) touch only G(l).
+//            its fixed internal neighbours to B_v, drops them from its
+//            internal list (in place), and draws the smallest colour not in
+//            B_v.
+// The full adjacency is read once per vertex, and a fixed neighbour once
+// more; the later iterations (hundreds on the dense top partition of a
+// power-law graph) touch only the edges of G(l) between vertices of U.
 //
 // State word of a vertex (the caller's colour array during the call):
 //   bits 24..31  its batch, when rho-bar <= 255 (one load of a neighbour's
@@ -50,17 +52,54 @@ namespace {
 constexpr int kDecThreads = 256;
 constexpr unsigned kTent = 1u << 23;
 constexpr unsigned kColMask = kTent - 1u;
-// Partitions x 2 lists counted in shared memory by the counting sort.
-constexpr int kDecBinsSmem = 4096;
+// Bins of the counting sort (3 per partition) counted in shared memory.
+constexpr int kDecBinsSmem = 4095;
 constexpr int kPlaceItems = 8;
 // Iterations launched between two reads of |U|, at most.
 constexpr int kDecChunkMax = 32;
+// Hubs: vertices of degree above kHubChunk are extracted in chunks of
+// kHubChunk edges by different warps, so one hub does not hold one warp for
+// the whole launch (R-MAT 24's top partition holds a vertex of degree 406k).
+constexpr long long kHubChunk = 4096;
 
+// Vertices of R(l) in `order`: hubs, then warp-path vertices (degree in
+// (kSmallDeg, kHubChunk]), then lane-path vertices.
 struct PartRange {
-  long long off_big, n_big;      // warp-path vertices (degree > kSmallDeg) of R(l) in `order`
-  long long off_small, n_small;  // lane-path vertices
-  unsigned long long cur_big, cur_small;  // cursors of the extraction
+  long long off_hub, n_hub;
+  long long off_big, n_big;
+  long long off_small, n_small;
+  unsigned long long hub_tasks;  // chunks of all hubs
+  unsigned long long cur_hub, cur_big, cur_small;  // cursors of the extraction
 };
+
+__device__ __forceinline__ int bin_of(long long d) { return d > kHubChunk ? 0 : (d > kSmallDeg ? 1 : 2); }
+
+// Entries a warp takes per cursor step from a list of `count`, so that long
+// lists cost few atomics on the one cursor word and short lists still spread
+// over all warps: between 1 and 16.
+__device__ __forceinline__ unsigned long long grab_size(unsigned long long count) {
+  const unsigned long long warps = static_cast<unsigned long long>(gridDim.x) * (blockDim.x >> 5);
+  const unsigned long long k = count / (8 * warps);
+  return k < 1 ? 1 : (k > 16 ? 16 : k);
+}
+
+// Warp-wide append to a U list: each lane holds one vertex (or none, kind 0)
+// for the warp-path list (kind 1, from the front) or the lane-path list
+// (kind 2, from the back); one atomic per list and warp.
+__device__ __forceinline__ void append_u(int v, int kind, unsigned long long* cnt, int* ub, long long ucap) {
+  const unsigned mb = __ballot_sync(kFull, kind == 1), ms = __ballot_sync(kFull, kind == 2);
+  if ((mb | ms) == 0u) return;
+  const int lane = threadIdx.x & 31;
+  unsigned long long bb = 0, bs = 0;
+  if (lane == 0) {
+    if (mb) bb = atomicAdd(&cnt[0], static_cast<unsigned long long>(__popc(mb)));
+    if (ms) bs = atomicAdd(&cnt[1], static_cast<unsigned long long>(__popc(ms)));
+  }
+  bb = __shfl_sync(kFull, bb, 0);
+  bs = __shfl_sync(kFull, bs, 0);
+  if (kind == 1) ub[bb + __popc(mb & lanemask_lt())] = v;
+  if (kind == 2) ub[ucap - 1 - static_cast<long long>(bs + __popc(ms & lanemask_lt()))] = v;
+}
 
 struct DecCtl {
   unsigned long long cnt[3][2];  // |U| of slot k % 3: [0] warp path, [1] lane path
@@ -84,6 +123,8 @@ struct DecArgs {
   int* hint;        // first word of B_v that may have a free bit
   int* ubuf[2];     // U lists of even and odd slots
   long long ucap;   // capacity of each U buffer
+  const long long* hubpre;  // inclusive prefix of the hubs' chunk counts, by position in `order`
+  int* hdone;               // chunks finished, per hub (same positions)
   DecCtl* ctl;
   unsigned long long seed;
 };
@@ -115,7 +156,7 @@ dec_count_kernel(const long long* __restrict__ row_ptr, const int* __restrict__ 
                  DecCtl* ctl) {
   __shared__ unsigned sh[kDecBinsSmem];
   __shared__ int any_iso;
-  const long long nb = 2ll * (rounds + 1);
+  const long long nb = 3ll * (rounds + 1);
   const bool use_sh = nb <= kDecBinsSmem;
   if (use_sh)
     for (long long i = threadIdx.x; i < nb; i += blockDim.x) sh[i] = 0u;
@@ -138,7 +179,7 @@ dec_count_kernel(const long long* __restrict__ row_ptr, const int* __restrict__ 
       continue;
     }
     S[v] = word;
-    const long long bin = 2ll * b + (d > kSmallDeg ? 0 : 1);
+    const long long bin = 3ll * b + bin_of(d);
     if (use_sh)
       atomicAdd(&sh[bin], 1u);
     else
@@ -159,7 +200,7 @@ dec_scan_kernel(const unsigned long long* __restrict__ bins, const int* __restri
   __shared__ unsigned long long wsum[32];
   __shared__ unsigned long long carry;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long nb = 2ll * (rounds + 1);
+  const long long nb = 3ll * (rounds + 1);
   if (threadIdx.x == 0) {
     carry = 0;
     part[0] = PartRange{};
@@ -169,7 +210,7 @@ dec_scan_kernel(const unsigned long long* __restrict__ bins, const int* __restri
   np = warp_sum(np);
   if (lane == 0 && np) atomicAdd(&ctl->nonempty, np);
   __syncthreads();
-  for (long long base = 2; base < nb; base += blockDim.x) {
+  for (long long base = 3; base < nb; base += blockDim.x) {
     const long long i = base + threadIdx.x;
     const unsigned long long x = i < nb ? bins[i] : 0ull;
     const unsigned long long incl = warp_inclusive_scan(x);
@@ -182,8 +223,13 @@ dec_scan_kernel(const unsigned long long* __restrict__ bins, const int* __restri
     __syncthreads();
     const unsigned long long excl = carry + (warp ? wsum[warp - 1] : 0ull) + incl - x;
     if (i < nb) {
-      PartRange& p = part[i >> 1];
-      if ((i & 1) == 0) {
+      PartRange& p = part[i / 3];
+      if (i % 3 == 0) {
+        p.off_hub = static_cast<long long>(excl);
+        p.n_hub = static_cast<long long>(x);
+        p.hub_tasks = 0;
+        p.cur_hub = 0;
+      } else if (i % 3 == 1) {
         p.off_big = static_cast<long long>(excl);
         p.n_big = static_cast<long long>(x);
         p.cur_big = 0;
@@ -207,7 +253,7 @@ dec_place_kernel(const long long* __restrict__ row_ptr, const int* __restrict__ 
                  int* __restrict__ order) {
   __shared__ unsigned lcnt[kDecBinsSmem];
   __shared__ unsigned lbase[kDecBinsSmem];
-  const long long nb = 2ll * (rounds + 1);
+  const long long nb = 3ll * (rounds + 1);
   const bool use_sh = nb <= kDecBinsSmem;
   constexpr long long kTile = static_cast<long long>(kDecThreads) * kPlaceItems;
   for (long long t0 = static_cast<long long>(blockIdx.x) * kTile; t0 < n;
@@ -227,7 +273,7 @@ dec_place_kernel(const long long* __restrict__ row_ptr, const int* __restrict__ 
         const int b = batch[v];
         const long long d = row_ptr[v + 1] - row_ptr[v];
         if (b >= 1 && b <= rounds && d > 0) {
-          bin[j] = 2ll * b + (d > kSmallDeg ? 0 : 1);
+          bin[j] = 3ll * b + bin_of(d);
           rank[j] = use_sh ? atomicAdd(&lcnt[bin[j]], 1u)
                            : static_cast<unsigned>(atomicAdd(&fill[bin[j]], 1ull));
         }
@@ -242,12 +288,65 @@ dec_place_kernel(const long long* __restrict__ row_ptr, const int* __restrict__ 
 #pragma unroll
     for (int j = 0; j < kPlaceItems; ++j) {
       if (bin[j] < 0) continue;
-      const PartRange& p = part[bin[j] >> 1];
-      const long long off = (bin[j] & 1) ? p.off_small : p.off_big;
+      const PartRange& p = part[bin[j] / 3];
+      const int kind = static_cast<int>(bin[j] % 3);
+      const long long off = kind == 0 ? p.off_hub : (kind == 1 ? p.off_big : p.off_small);
       const long long pos = off + (use_sh ? lbase[bin[j]] : 0u) + rank[j];
       order[pos] = static_cast<int>(t0 + static_cast<long long>(j) * kDecThreads + threadIdx.x);
     }
     if (use_sh) __syncthreads();
+  }
+}
+
+// One block per partition (grid-stride over partitions): the chunk counts of
+// the partition's hubs as an inclusive prefix (hubpre, by position in
+// `order`), and the state their chunks accumulate into: B_v cleared, the
+// internal count and the count of finished chunks at 0.
+__global__ void __launch_bounds__(kDecThreads)
+dec_hub_prep_kernel(const long long* __restrict__ row_ptr, const int* __restrict__ order, int rounds,
+                    PartRange* __restrict__ part, long long* __restrict__ hubpre, int* __restrict__ hdone,
+                    int* __restrict__ ideg, unsigned* __restrict__ B) {
+  constexpr int kWarps = kDecThreads / 32;
+  __shared__ unsigned long long wsum[kWarps];
+  __shared__ unsigned long long carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int l = 1 + blockIdx.x; l <= rounds; l += gridDim.x) {
+    PartRange& p = part[l];
+    const long long nh = p.n_hub, off = p.off_hub;
+    if (nh == 0) continue;  // the same for the whole block
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (long long base = 0; base < nh; base += kDecThreads) {
+      const long long i = base + threadIdx.x;
+      unsigned long long x = 0;
+      if (i < nh) {
+        const int v = order[off + i];
+        x = static_cast<unsigned long long>((row_ptr[v + 1] - row_ptr[v] + kHubChunk - 1) / kHubChunk);
+        hdone[off + i] = 0;
+        ideg[v] = 0;
+      }
+      const unsigned long long incl = warp_inclusive_scan(x);
+      if (lane == 31) wsum[warp] = incl;
+      __syncthreads();
+      if (warp == 0) {
+        const unsigned long long ws = warp_inclusive_scan(lane < kWarps ? wsum[lane] : 0ull);
+        __syncwarp();
+        if (lane < kWarps) wsum[lane] = ws;
+      }
+      __syncthreads();
+      if (i < nh) hubpre[off + i] = static_cast<long long>(carry + (warp ? wsum[warp - 1] : 0ull) + incl);
+      __syncthreads();
+      if (threadIdx.x == 0) carry += wsum[kWarps - 1];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) p.hub_tasks = carry;
+    for (long long i = warp; i < nh; i += kWarps) {
+      const int v = order[off + i];
+      const long long nw = (row_ptr[v + 1] - row_ptr[v] + 32) / 32;
+      unsigned* Bv = B + bstart(row_ptr, v);
+      for (long long j = lane; j < nw; j += 32) Bv[j] = 0u;
+    }
+    __syncthreads();
   }
 }
 
@@ -256,11 +355,11 @@ dec_place_kernel(const long long* __restrict__ row_ptr, const int* __restrict__ 
 // One vertex per lane (degree <= kSmallDeg: B_v fits 64 bits).  All 32 lanes
 // call it (v < 0: none) for the warp-aggregated append to U.
 template <bool Packed>
-__device__ int extract_lane(const DecArgs& A, int v, int l, unsigned long long* cnt, int* ub) {
+__device__ int extract_lane(const DecArgs& A, int v, int l, unsigned long long* cnt, int* ub,
+                            unsigned long long* inner_sum) {
   constexpr int U = 4;
   int c = 0;
   bool enter = false;
-  int internal = 0;
   if (v >= 0) {
     const long long s = A.row_ptr[v], e = A.row_ptr[v + 1];
     unsigned long long used = 0;
@@ -298,21 +397,10 @@ __device__ int extract_lane(const DecArgs& A, int v, int l, unsigned long long* 
       A.B[bs] = static_cast<unsigned>(used);
       if (e - s + 1 > 32) A.B[bs + 1] = static_cast<unsigned>(used >> 32);
       enter = true;
-      internal = id;
+      *inner_sum += static_cast<unsigned long long>(id);
     }
   }
-  const unsigned m = __ballot_sync(kFull, enter);
-  if (m) {
-    const int lane = threadIdx.x & 31;
-    unsigned long long base = 0;
-    internal = warp_sum(internal);
-    if (lane == 0) {
-      base = atomicAdd(&cnt[1], static_cast<unsigned long long>(__popc(m)));
-      atomicAdd(&A.ctl->internal, static_cast<unsigned long long>(internal));
-    }
-    base = __shfl_sync(kFull, base, 0);
-    if (enter) ub[A.ucap - 1 - static_cast<long long>(base + __popc(m & lanemask_lt()))] = v;
-  }
+  append_u(v, enter ? 2 : 0, cnt, ub, A.ucap);
   return enter ? 0 : c;
 }
 
@@ -334,16 +422,52 @@ __device__ __forceinline__ int warp_mex(const unsigned* Bv, long long from, long
   }
 }
 
-// One vertex of degree > kSmallDeg per warp.
+// The warp paths mark colours in a 32-word window of B_v held in shared
+// memory (words [w0, w0 + 32): colours 32*w0 + 1 .. 32*w0 + 1024), so that
+// the many marks of one vertex do not meet as atomics on a few global words;
+// marks above the window go to B_v in global memory, and words below w0 are
+// full already.
+__device__ __forceinline__ void mark_colour(unsigned* win, unsigned* Bv, long long w0, long long cc) {
+  const long long wi = (cc - 1) >> 5;
+  const unsigned bit = 1u << ((cc - 1) & 31);
+  if (wi >= w0 + 32)
+    atomicOr(Bv + wi, bit);
+  else if (wi >= w0)
+    atomicOr(win + (wi - w0), bit);
+}
+
+// After the marks: writes the window back to B_v (words below nw) and returns
+// the smallest colour not in B_v, searching the window first.
+__device__ __forceinline__ int window_mex(const unsigned* win, unsigned* Bv, long long w0, long long nw,
+                                          bool store, int* word_out) {
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+  const unsigned word = win[lane];  // kFull beyond nw
+  if (store && w0 + lane < nw) Bv[w0 + lane] = word;
+  const unsigned fm = __ballot_sync(kFull, word != kFull);
+  if (fm) {
+    const int f = __ffs(fm) - 1;
+    const unsigned fw = __shfl_sync(kFull, word, f);
+    *word_out = static_cast<int>(w0 + f);
+    return static_cast<int>(32 * (w0 + f)) + __ffs(~fw);
+  }
+  return warp_mex(Bv, w0 + 32, nw, word_out);
+}
+
+// One vertex of degree > kSmallDeg per warp; win is the warp's window.
+// *kind: 0 the vertex kept its colour, 1 it joins the warp-path list of U, 2
+// the lane-path list.
 template <bool Packed>
-__device__ int extract_warp(const DecArgs& A, int v, int l, unsigned long long* cnt, int* ub) {
+__device__ int extract_warp(const DecArgs& A, int v, int l, unsigned* win, int* kind,
+                            unsigned long long* inner_sum) {
   constexpr int U = 4;
   const int lane = threadIdx.x & 31;
   const long long s = A.row_ptr[v], e = A.row_ptr[v + 1];
   const long long deg = e - s;
   const long long nw = (deg + 32) / 32;
   unsigned* Bv = A.B + bstart(A.row_ptr, v);
-  for (long long i = lane; i < nw; i += 32) Bv[i] = 0u;
+  win[lane] = lane < nw ? 0u : kFull;
+  for (long long i = 32 + lane; i < nw; i += 32) Bv[i] = 0u;
   __syncwarp();
   int id = 0;
   for (long long k0 = s; k0 < e; k0 += 32 * U) {
@@ -364,7 +488,7 @@ __device__ int extract_warp(const DecArgs& A, int v, int l, unsigned long long* 
       const int bw = w[u] < 0 ? 0 : (Packed ? static_cast<int>(static_cast<unsigned>(x[u]) >> 24) : b[u]);
       if (w[u] >= 0 && bw > l) {
         const long long cc = static_cast<long long>(static_cast<unsigned>(x[u]) & kColMask);
-        if (cc >= 1 && cc <= deg + 1) atomicOr(Bv + ((cc - 1) >> 5), 1u << ((cc - 1) & 31));
+        if (cc >= 1 && cc <= deg + 1) mark_colour(win, Bv, 0, cc);
       }
       const bool inner = w[u] >= 0 && bw == l;
       const unsigned m = __ballot_sync(kFull, inner);
@@ -372,15 +496,87 @@ __device__ int extract_warp(const DecArgs& A, int v, int l, unsigned long long* 
       id += __popc(m);
     }
   }
-  __syncwarp();
   int hw = 0;
-  const int c = warp_mex(Bv, 0, nw, &hw);
+  const int c = window_mex(win, Bv, 0, nw, id > 0, &hw);
   if (lane == 0) {
     if (id == 0) {
       st_relaxed(A.S + v, state_word<Packed>(l, c));
     } else {
       st_relaxed(A.S + v, state_word<Packed>(l, c) | static_cast<int>(kTent));
       A.ideg[v] = id;
+      A.hint[v] = hw;
+    }
+  }
+  *kind = id == 0 ? 0 : (id > kSmallDeg ? 1 : 2);
+  if (lane == 0) *inner_sum += static_cast<unsigned long long>(id);  // summed over the warp later
+  return id == 0 ? c : 0;
+}
+
+// Chunk c (of nchunks) of hub v by a warp: the colours of higher partitions
+// are ORed into B_v (through the warp's window for the first 1,024), the
+// internal neighbours appended to v's list at slots reserved on ideg[v].  The
+// warp that finishes the hub's last chunk (counted on *done) draws v's first
+// colour; nothing waits.
+template <bool Packed>
+__device__ int extract_hub_chunk(const DecArgs& A, int v, long long c, long long nchunks, int l, unsigned* win,
+                                 int* done, unsigned long long* cnt, int* ub) {
+  constexpr int U = 4;
+  const int lane = threadIdx.x & 31;
+  const long long s = A.row_ptr[v], e = A.row_ptr[v + 1];
+  const long long deg = e - s;
+  const long long nw = (deg + 32) / 32;
+  unsigned* Bv = A.B + bstart(A.row_ptr, v);
+  const long long k_lo = s + c * kHubChunk;
+  const long long k_hi = k_lo + kHubChunk < e ? k_lo + kHubChunk : e;
+  win[lane] = 0u;
+  __syncwarp();
+  for (long long k0 = k_lo; k0 < k_hi; k0 += 32 * U) {
+    int w[U], x[U], b[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long k = k0 + 32 * u + lane;
+      w[u] = k < k_hi ? __ldg(A.col + k) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) x[u] = w[u] >= 0 ? ld_relaxed(A.S + w[u]) : 0;
+    if (!Packed) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) b[u] = w[u] >= 0 ? __ldg(A.batch + w[u]) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int bw = w[u] < 0 ? 0 : (Packed ? static_cast<int>(static_cast<unsigned>(x[u]) >> 24) : b[u]);
+      if (w[u] >= 0 && bw > l) {
+        const long long cc = static_cast<long long>(static_cast<unsigned>(x[u]) & kColMask);
+        if (cc >= 1 && cc <= deg + 1) mark_colour(win, Bv, 0, cc);
+      }
+      const bool inner = w[u] >= 0 && bw == l;
+      const unsigned m = __ballot_sync(kFull, inner);
+      if (m) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(A.ideg + v, __popc(m));
+        base = __shfl_sync(kFull, base, 0);
+        if (inner) A.icol[s + base + __popc(m & lanemask_lt())] = w[u];
+      }
+    }
+  }
+  __syncwarp();
+  if (lane < nw && win[lane]) atomicOr(Bv + lane, win[lane]);
+  __threadfence();
+  __syncwarp();
+  int last = 0;
+  if (lane == 0) last = atomicAdd(done, 1) == static_cast<int>(nchunks - 1);
+  last = __shfl_sync(kFull, last, 0);
+  if (!last) return 0;
+  __threadfence();  // every chunk's marks and appends precede its count
+  int hw = 0;
+  const int col = warp_mex(Bv, 0, nw, &hw);
+  const int id = __ldcg(A.ideg + v);
+  if (lane == 0) {
+    if (id == 0) {
+      st_relaxed(A.S + v, state_word<Packed>(l, col));
+    } else {
+      st_relaxed(A.S + v, state_word<Packed>(l, col) | static_cast<int>(kTent));
       A.hint[v] = hw;
       atomicAdd(&A.ctl->internal, static_cast<unsigned long long>(id));
       if (id > kSmallDeg)
@@ -389,49 +585,94 @@ __device__ int extract_warp(const DecArgs& A, int v, int l, unsigned long long* 
         ub[A.ucap - 1 - static_cast<long long>(atomicAdd(&cnt[1], 1ull))] = v;
     }
   }
-  return id == 0 ? c : 0;
+  return id == 0 ? col : 0;
 }
 
 template <bool Packed>
 __global__ void __launch_bounds__(kDecThreads)
 dec_extract_kernel(DecArgs A, PartRange* part, int l, const int* __restrict__ order, int slot) {
+  __shared__ unsigned s_win[kDecThreads / 32][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   PartRange* pr = part + l;
-  const long long nbig = pr->n_big, nsmall = pr->n_small;
-  const int* big = order + pr->off_big;
-  const int* small = order + pr->off_small;
   unsigned long long* cnt = A.ctl->cnt[slot % 3];
   int* ub = ubuf_of(A, slot);
-  bool big_done = nbig == 0, small_done = nsmall == 0;
-  const bool prefer_big = (warp & 3) != 0;
   int local_max = 0;
-  while (!(big_done && small_done)) {
-    if (!big_done && (prefer_big || small_done)) {
-      unsigned long long i = 0;
-      if (lane == 0) i = atomicAdd(&pr->cur_big, 1ull);
-      i = __shfl_sync(kFull, i, 0);
-      if (i >= static_cast<unsigned long long>(nbig)) {
-        big_done = true;
-        continue;
+  unsigned long long inner_sum = 0;  // this lane's share of the internal list lengths
+  // hub chunks first, by every warp
+  const unsigned long long ntask = pr->hub_tasks;
+  if (ntask) {
+    const long long nh = pr->n_hub;
+    const long long* pre = A.hubpre + pr->off_hub;
+    const int* hubs = order + pr->off_hub;
+    for (;;) {
+      unsigned long long t = 0;
+      if (lane == 0) t = atomicAdd(&pr->cur_hub, 1ull);
+      t = __shfl_sync(kFull, t, 0);
+      if (t >= ntask) break;
+      long long lo = 0, hi = nh - 1;  // the hub whose prefix first exceeds t
+      while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (static_cast<unsigned long long>(pre[mid]) > t)
+          hi = mid;
+        else
+          lo = mid + 1;
       }
-      const int c = extract_warp<Packed>(A, big[i], l, cnt, ub);
-      local_max = c > local_max ? c : local_max;
-    } else {
-      unsigned long long i0 = 0;
-      if (lane == 0) i0 = atomicAdd(&pr->cur_small, 32ull);
-      i0 = __shfl_sync(kFull, i0, 0);
-      if (i0 >= static_cast<unsigned long long>(nsmall)) {
-        small_done = true;
-        continue;
-      }
-      const unsigned long long i = i0 + lane;
-      const int v = i < static_cast<unsigned long long>(nsmall) ? small[i] : -1;
-      const int c = extract_lane<Packed>(A, v, l, cnt, ub);
+      const long long first = lo ? pre[lo - 1] : 0;
+      const int c = extract_hub_chunk<Packed>(A, hubs[lo], static_cast<long long>(t) - first, pre[lo] - first, l,
+                                              s_win[warp], A.hdone + pr->off_hub + lo, cnt, ub);
       local_max = c > local_max ? c : local_max;
     }
   }
+  const unsigned long long nbig = pr->n_big, nsmall = pr->n_small;
+  const int* big = order + pr->off_big;
+  const int* small = order + pr->off_small;
+  const unsigned long long kb = grab_size(nbig), ks = grab_size((nsmall + 31) / 32);
+  bool big_done = nbig == 0, small_done = nsmall == 0;
+  const bool prefer_big = (warp & 3) != 0;
+  while (!(big_done && small_done)) {
+    if (!big_done && (prefer_big || small_done)) {
+      unsigned long long i = 0;
+      if (lane == 0) i = atomicAdd(&pr->cur_big, kb);
+      i = __shfl_sync(kFull, i, 0);
+      if (i >= nbig) {
+        big_done = true;
+        continue;
+      }
+      const unsigned long long iend = i + kb < nbig ? i + kb : nbig;
+      int myv = -1, mykind = 0;  // lane j keeps the j-th vertex's outcome
+      for (int j = 0; i + j < iend; ++j) {
+        const int v = big[i + j];
+        int kind = 0;
+        const int c = extract_warp<Packed>(A, v, l, s_win[warp], &kind, &inner_sum);
+        if (lane == j) {
+          myv = v;
+          mykind = kind;
+        }
+        local_max = c > local_max ? c : local_max;
+      }
+      append_u(myv, mykind, cnt, ub, A.ucap);
+    } else {
+      unsigned long long i0 = 0;
+      if (lane == 0) i0 = atomicAdd(&pr->cur_small, 32 * ks);
+      i0 = __shfl_sync(kFull, i0, 0);
+      if (i0 >= nsmall) {
+        small_done = true;
+        continue;
+      }
+      for (unsigned long long g = 0; g < ks && i0 + 32 * g < nsmall; ++g) {
+        const unsigned long long i = i0 + 32 * g + lane;
+        const int v = i < nsmall ? small[i] : -1;
+        const int c = extract_lane<Packed>(A, v, l, cnt, ub, &inner_sum);
+        local_max = c > local_max ? c : local_max;
+      }
+    }
+  }
   local_max = warp_max(local_max);
-  if (lane == 0 && local_max > 0) atomicMax(&A.ctl->max_color, local_max);
+  inner_sum = warp_sum(inner_sum);
+  if (lane == 0) {
+    if (local_max > 0) atomicMax(&A.ctl->max_color, local_max);
+    if (inner_sum) atomicAdd(&A.ctl->internal, inner_sum);
+  }
 }
 
 // ---- Part 2: conflicts inside U -------------------------------------------
@@ -497,54 +738,55 @@ dec_check_kernel(DecArgs A, int slot) {
   unsigned long long* cur = ctl->cur[sl];
   bool big_done = nbig == 0, small_done = nsmall == 0;
   const bool prefer_big = (warp & 3) != 0;
+  const unsigned long long kb = grab_size(nbig), ks = grab_size((nsmall + 31) / 32);
   int local_max = 0;
   while (!(big_done && small_done)) {
     if (!big_done && (prefer_big || small_done)) {
       unsigned long long i = 0;
-      if (lane == 0) i = atomicAdd(&cur[2], 1ull);
+      if (lane == 0) i = atomicAdd(&cur[2], kb);
       i = __shfl_sync(kFull, i, 0);
       if (i >= nbig) {
         big_done = true;
         continue;
       }
-      const int v = ub[i];
-      const unsigned xv = static_cast<unsigned>(ld_relaxed(A.S + v));
-      const unsigned t = xv & kColMask;
-      const bool lose = check_lose_warp(A, v, t, tie_hash(A.seed, static_cast<unsigned>(v)));
-      if (lane == 0) {
-        if (lose)
-          un[atomicAdd(&ncnt[0], 1ull)] = v;
-        else
-          st_relaxed(A.S + v, static_cast<int>(xv & ~kTent));
+      const unsigned long long iend = i + kb < nbig ? i + kb : nbig;
+      int myv = -1, mylose = 0;  // lane j keeps the j-th vertex's outcome
+      for (int j = 0; i + j < iend; ++j) {
+        const int v = ub[i + j];
+        const unsigned xv = static_cast<unsigned>(ld_relaxed(A.S + v));
+        const unsigned t = xv & kColMask;
+        const bool lose = check_lose_warp(A, v, t, tie_hash(A.seed, static_cast<unsigned>(v)));
+        if (lane == 0 && !lose) st_relaxed(A.S + v, static_cast<int>(xv & ~kTent));
+        if (!lose) local_max = static_cast<int>(t) > local_max ? static_cast<int>(t) : local_max;
+        if (lane == j) {
+          myv = v;
+          mylose = lose;
+        }
       }
-      if (!lose) local_max = static_cast<int>(t) > local_max ? static_cast<int>(t) : local_max;
+      append_u(myv, mylose ? 1 : 0, ncnt, un, A.ucap);
     } else {
       unsigned long long i0 = 0;
-      if (lane == 0) i0 = atomicAdd(&cur[3], 32ull);
+      if (lane == 0) i0 = atomicAdd(&cur[3], 32 * ks);
       i0 = __shfl_sync(kFull, i0, 0);
       if (i0 >= nsmall) {
         small_done = true;
         continue;
       }
-      const unsigned long long i = i0 + lane;
-      bool lose = false;
-      int v = -1;
-      if (i < nsmall) {
-        v = ub[A.ucap - 1 - static_cast<long long>(i)];
-        const unsigned xv = static_cast<unsigned>(ld_relaxed(A.S + v));
-        const unsigned t = xv & kColMask;
-        lose = check_lose_lane(A, v, t, tie_hash(A.seed, static_cast<unsigned>(v)));
-        if (!lose) {
-          st_relaxed(A.S + v, static_cast<int>(xv & ~kTent));
-          local_max = static_cast<int>(t) > local_max ? static_cast<int>(t) : local_max;
+      for (unsigned long long g = 0; g < ks && i0 + 32 * g < nsmall; ++g) {
+        const unsigned long long i = i0 + 32 * g + lane;
+        bool lose = false;
+        int v = -1;
+        if (i < nsmall) {
+          v = ub[A.ucap - 1 - static_cast<long long>(i)];
+          const unsigned xv = static_cast<unsigned>(ld_relaxed(A.S + v));
+          const unsigned t = xv & kColMask;
+          lose = check_lose_lane(A, v, t, tie_hash(A.seed, static_cast<unsigned>(v)));
+          if (!lose) {
+            st_relaxed(A.S + v, static_cast<int>(xv & ~kTent));
+            local_max = static_cast<int>(t) > local_max ? static_cast<int>(t) : local_max;
+          }
         }
-      }
-      const unsigned m = __ballot_sync(kFull, lose);
-      if (m) {
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&ncnt[1], static_cast<unsigned long long>(__popc(m)));
-        base = __shfl_sync(kFull, base, 0);
-        if (lose) un[A.ucap - 1 - static_cast<long long>(base + __popc(m & lanemask_lt()))] = v;
+        append_u(v, lose ? 2 : 0, ncnt, un, A.ucap);
       }
     }
   }
@@ -555,7 +797,7 @@ dec_check_kernel(DecArgs A, int slot) {
 // ---- Part 3 and the next Part 1 --------------------------------------------
 
 template <bool Packed>
-__device__ void pick_warp(const DecArgs& A, int v, int l) {
+__device__ void pick_warp(const DecArgs& A, int v, int l, unsigned* win) {
   constexpr int U = 4;
   const int lane = threadIdx.x & 31;
   const long long s = A.row_ptr[v];
@@ -563,26 +805,37 @@ __device__ void pick_warp(const DecArgs& A, int v, int l) {
   const long long nw = (deg + 32) / 32;
   unsigned* Bv = A.B + bstart(A.row_ptr, v);
   const int id = A.ideg[v];
+  const long long w0 = A.hint[v];  // words below the last colour's are full
+  win[lane] = w0 + lane < nw ? __ldcg(Bv + w0 + lane) : kFull;
+  __syncwarp();
+  int kept = 0;  // the list is compacted in place to the neighbours still in U
   for (int j0 = 0; j0 < id; j0 += 32 * U) {
     int w[U], x[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int j = j0 + 32 * u + lane;
-      w[u] = j < id ? __ldg(A.icol + s + j) : -1;
+      w[u] = j < id ? A.icol[s + j] : -1;  // plain loads: this kernel rewrites the list
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) x[u] = w[u] >= 0 ? ld_relaxed(A.S + w[u]) : 0;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      if (w[u] < 0 || (static_cast<unsigned>(x[u]) & kTent)) continue;
-      const long long cc = static_cast<long long>(static_cast<unsigned>(x[u]) & kColMask);
-      if (cc >= 1 && cc <= deg + 1) atomicOr(Bv + ((cc - 1) >> 5), 1u << ((cc - 1) & 31));
+      const bool tent = w[u] >= 0 && (static_cast<unsigned>(x[u]) & kTent);
+      if (w[u] >= 0 && !tent) {  // fixed: its colour joins B_v, and it leaves the list
+        const long long cc = static_cast<long long>(static_cast<unsigned>(x[u]) & kColMask);
+        if (cc >= 1 && cc <= deg + 1) mark_colour(win, Bv, w0, cc);
+      }
+      // every lane loaded the whole window before this first ballot, and the
+      // writes land below the window's end: no entry is overwritten unread
+      const unsigned m = __ballot_sync(kFull, tent);
+      if (tent) A.icol[s + kept + __popc(m & lanemask_lt())] = w[u];
+      kept += __popc(m);
     }
   }
-  __syncwarp();
   int hw = 0;
-  const int c = warp_mex(Bv, A.hint[v], nw, &hw);
+  const int c = window_mex(win, Bv, w0, nw, true, &hw);
   if (lane == 0) {
+    A.ideg[v] = kept;
     A.hint[v] = hw;
     st_relaxed(A.S + v, state_word<Packed>(l, c) | static_cast<int>(kTent));
   }
@@ -596,19 +849,25 @@ __device__ void pick_lane(const DecArgs& A, int v, int l) {
   const long long nw = (deg + 32) / 32;
   unsigned* Bv = A.B + bstart(A.row_ptr, v);
   const int id = A.ideg[v];
+  int kept = 0;
   for (int j0 = 0; j0 < id; j0 += U) {
     int w[U], x[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) w[u] = j0 + u < id ? __ldg(A.icol + s + j0 + u) : -1;
+    for (int u = 0; u < U; ++u) w[u] = j0 + u < id ? A.icol[s + j0 + u] : -1;
 #pragma unroll
     for (int u = 0; u < U; ++u) x[u] = w[u] >= 0 ? ld_relaxed(A.S + w[u]) : 0;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      if (w[u] < 0 || (static_cast<unsigned>(x[u]) & kTent)) continue;
+      if (w[u] < 0) continue;
+      if (static_cast<unsigned>(x[u]) & kTent) {
+        A.icol[s + kept++] = w[u];
+        continue;
+      }
       const long long cc = static_cast<long long>(static_cast<unsigned>(x[u]) & kColMask);
       if (cc >= 1 && cc <= deg + 1) Bv[(cc - 1) >> 5] |= 1u << ((cc - 1) & 31);
     }
   }
+  A.ideg[v] = kept;
   long long wi = A.hint[v];
   unsigned word = wi < nw ? Bv[wi] : 0u;
   while (word == kFull && wi + 1 < nw) word = Bv[++wi];
@@ -620,6 +879,7 @@ __device__ void pick_lane(const DecArgs& A, int v, int l) {
 template <bool Packed>
 __global__ void __launch_bounds__(kDecThreads)
 dec_pick_kernel(DecArgs A, int slot, int l) {
+  __shared__ unsigned s_win[kDecThreads / 32][32];
   DecCtl* ctl = A.ctl;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int sl = slot % 3;
@@ -630,26 +890,29 @@ dec_pick_kernel(DecArgs A, int slot, int l) {
   unsigned long long* cur = ctl->cur[sl];
   bool big_done = nbig == 0, small_done = nsmall == 0;
   const bool prefer_big = (warp & 3) != 0;
+  const unsigned long long kb = grab_size(nbig), ks = grab_size((nsmall + 31) / 32);
   while (!(big_done && small_done)) {
     if (!big_done && (prefer_big || small_done)) {
       unsigned long long i = 0;
-      if (lane == 0) i = atomicAdd(&cur[0], 1ull);
+      if (lane == 0) i = atomicAdd(&cur[0], kb);
       i = __shfl_sync(kFull, i, 0);
       if (i >= nbig) {
         big_done = true;
         continue;
       }
-      pick_warp<Packed>(A, ub[i], l);
+      const unsigned long long iend = i + kb < nbig ? i + kb : nbig;
+      for (; i < iend; ++i) pick_warp<Packed>(A, ub[i], l, s_win[warp]);
     } else {
       unsigned long long i0 = 0;
-      if (lane == 0) i0 = atomicAdd(&cur[1], 32ull);
+      if (lane == 0) i0 = atomicAdd(&cur[1], 32 * ks);
       i0 = __shfl_sync(kFull, i0, 0);
       if (i0 >= nsmall) {
         small_done = true;
         continue;
       }
-      const unsigned long long i = i0 + lane;
-      if (i < nsmall) pick_lane<Packed>(A, ub[A.ucap - 1 - static_cast<long long>(i)], l);
+      const unsigned long long iend = i0 + 32 * ks < nsmall ? i0 + 32 * ks : nsmall;
+      for (unsigned long long i = i0 + lane; i < iend; i += 32)
+        pick_lane<Packed>(A, ub[A.ucap - 1 - static_cast<long long>(i)], l);
       __syncwarp();
     }
   }
@@ -685,13 +948,14 @@ gc_status dec_loop(gc_context* ctx, const DecArgs& A, PartRange* part, const int
     // every iteration keeps the highest-key vertex of U: at most |R(l)| <= n
     // of them; a partition that runs longer is an internal error
     long long launched = 0;
+    int gp_now = gp, gk_now = gk;  // U only shrinks: grids sized by the last |U| read
     for (int chunk = 2;; chunk = chunk < kDecChunkMax ? 2 * chunk : kDecChunkMax) {
       if (launched > A.ucap + 1) return GC_ERR_CUDA;
       launched += chunk;
       ctx->timer_begin(gc_context::kTDecIterate, s);
       for (int j = 0; j < chunk; ++j) {
-        dec_pick_kernel<Packed><<<gp, kDecThreads, 0, s>>>(A, slot, l);
-        dec_check_kernel<<<gk, kDecThreads, 0, s>>>(A, slot);
+        dec_pick_kernel<Packed><<<gp_now, kDecThreads, 0, s>>>(A, slot, l);
+        dec_check_kernel<<<gk_now, kDecThreads, 0, s>>>(A, slot);
         g_launches += 2;
         ++slot;
       }
@@ -701,6 +965,11 @@ gc_status dec_loop(gc_context* ctx, const DecArgs& A, PartRange* part, const int
                                   cudaMemcpyDeviceToHost, s));
       GC_TRY_CUDA(cudaStreamSynchronize(s));
       if (pinned[0] + pinned[1] == 0) break;
+      // one warp per warp-path vertex, one per 32 lane-path vertices
+      const unsigned long long warps = pinned[0] + (pinned[1] + 31) / 32;
+      const unsigned long long want = (warps + kDecThreads / 32 - 1) / (kDecThreads / 32);
+      gp_now = want < static_cast<unsigned long long>(gp) ? static_cast<int>(want) : gp;
+      gk_now = want < static_cast<unsigned long long>(gk) ? static_cast<int>(want) : gk;
     }
   }
   return GC_OK;
@@ -710,9 +979,9 @@ gc_status dec_loop(gc_context* ctx, const DecArgs& A, PartRange* part, const int
 
 size_t dec_scratch_bytes(long long n, long long nnz, int rounds) {
   const size_t nn = static_cast<size_t>(n > 0 ? n : 1);
-  const size_t nb = 2 * static_cast<size_t>(rounds > 0 ? rounds + 1 : 2);
-  return 16 * 256 + sizeof(DecCtl) + sizeof(PartRange) * (static_cast<size_t>(rounds > 0 ? rounds : 0) + 1) +
-         2 * 8 * nb + 4 * (nb / 2) + 4 * 5 * nn + 4 * static_cast<size_t>(nnz > 0 ? nnz : 1) + 4 * bitmap_words(n, nnz);
+  const size_t nr = static_cast<size_t>(rounds > 0 ? rounds : 0) + 1;
+  return 16 * 256 + sizeof(DecCtl) + sizeof(PartRange) * nr + 2 * 8 * 3 * nr + 4 * nr + 4 * 6 * nn + 8 * nn +
+         4 * static_cast<size_t>(nnz > 0 ? nnz : 1) + 4 * bitmap_words(n, nnz);
 }
 
 gc_status dec_itr_run(gc_context* ctx, Arena a, const gc_csr* g, const int* batch, int rounds,
@@ -724,7 +993,7 @@ gc_status dec_itr_run(gc_context* ctx, Arena a, const gc_csr* g, const int* batc
   if (n == 0) return GC_OK;
   if (rounds < 1) return GC_ERR_INVALID_ARG;
   const bool packed = rounds <= 255;
-  const long long nb = 2ll * (rounds + 1);
+  const long long nb = 3ll * (rounds + 1);
   DecCtl* ctl = a.take<DecCtl>(1);
   PartRange* part = a.take<PartRange>(static_cast<size_t>(rounds) + 1);
   unsigned long long* bins = a.take<unsigned long long>(nb);
@@ -737,7 +1006,10 @@ gc_status dec_itr_run(gc_context* ctx, Arena a, const gc_csr* g, const int* batc
   int* ub1 = a.take<int>(n);
   int* icol = a.take<int>(nnz > 0 ? nnz : 1);
   unsigned* B = a.take<unsigned>(bitmap_words(n, nnz));
-  if (!ctl || !part || !bins || !fill || !present || !order || !ideg || !hint || !ub0 || !ub1 || !icol || !B)
+  long long* hubpre = a.take<long long>(n);
+  int* hdone = a.take<int>(n);
+  if (!ctl || !part || !bins || !fill || !present || !order || !ideg || !hint || !ub0 || !ub1 || !icol || !B ||
+      !hubpre || !hdone)
     return GC_ERR_OOM;
   GC_TRY_CUDA(cudaMemsetAsync(ctl, 0, sizeof(DecCtl), s));
   GC_TRY_CUDA(cudaMemsetAsync(bins, 0, sizeof(unsigned long long) * nb, s));
@@ -754,7 +1026,9 @@ gc_status dec_itr_run(gc_context* ctx, Arena a, const gc_csr* g, const int* batc
     const int pcap = resident_grid(dec_place_kernel, kDecThreads, ctx->num_sms);
     dec_place_kernel<<<static_cast<int>(tiles < pcap ? tiles : pcap), kDecThreads, 0, s>>>(rp, batch, n, rounds,
                                                                                             part, fill, order);
-    g_launches += 3;
+    const int hblocks = rounds < 4 * ctx->num_sms ? rounds : 4 * ctx->num_sms;
+    dec_hub_prep_kernel<<<hblocks, kDecThreads, 0, s>>>(rp, order, rounds, part, hubpre, hdone, ideg, B);
+    g_launches += 4;
     GC_TRY_CUDA(cudaGetLastError());
   }
   DecArgs A{};
@@ -769,6 +1043,8 @@ gc_status dec_itr_run(gc_context* ctx, Arena a, const gc_csr* g, const int* batc
   A.ubuf[0] = ub0;
   A.ubuf[1] = ub1;
   A.ucap = n;
+  A.hubpre = hubpre;
+  A.hdone = hdone;
   A.ctl = ctl;
   A.seed = seed;
   if (packed)

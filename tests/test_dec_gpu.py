@@ -67,6 +67,16 @@ DEC_GRAPHS = [empty(1), empty(100), complete(2), complete(33), complete(40), sta
               gg.grid(64, 64, 16, perm_seed=3)]
 
 
+def _twin_hubs(k):
+    # two adjacent hubs sharing k leaves: both land in one partition above the
+    # leaves and conflict there; each hub's adjacency spans several chunks
+    edges = [(0, 1)] + [(h, 2 + i) for h in (0, 1) for i in range(k)]
+    return gg.from_edges(k + 2, edges, f"twinhubs{k}")
+
+
+DEC_GRAPHS += [star(12345), wheel(9000), _twin_hubs(9000), gg.rmat(18, 16, seed=9)]
+
+
 @pytest.mark.parametrize("g", DEC_GRAPHS, ids=lambda g: g.name)
 @pytest.mark.parametrize("p,q", [(1, 100), (1, 2)])
 def test_dec_itr_matches_oracle(ctx, g, p, q):

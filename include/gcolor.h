@@ -102,6 +102,8 @@ typedef struct {
                               of vertices with such an entry (edges of G(l))   */
   float ms_dec_extract;    /* DEC-ADG-ITR: per-partition extraction launches   */
   float ms_dec_iterate;    /* DEC-ADG-ITR: the later SIM-COL iterations        */
+  int64_t dec_tail_partitions; /* DEC-ADG-ITR: partitions finished by the
+                              single-cluster tail (see GC_DEC_TAIL)            */
 } gc_stats;
 
 /* Human-readable name of a status code (static storage). */
@@ -115,6 +117,9 @@ const char *gc_status_str(gc_status s);
  *                     32768; 0: no core);
  *   GC_CORE_CLUSTER   at most this many CTAs in the core cluster (1..16);
  *   GC_CORE_WARPS     warps per core CTA (1..32, default 8);
+ *   GC_DEC_TAIL       0: DEC-ADG-ITR runs every SIM-COL iteration as two
+ *                     GPU-wide launches, also once U is small (default: the
+ *                     last iterations of a partition run in one cluster);
  *   GC_WAIT_LIMIT_MS  bound of every wait on a colour outside the core
  *                     (default 4000; the core's waits are bounded by 4 s);
  *                     a wait that runs out ends the call with

@@ -29,6 +29,7 @@ struct CallScope {
     ctx->stats.core_ctas = 0;
     ctx->stats.sim_iterations = 0;
     ctx->stats.dec_internal_edges = 0;
+    ctx->stats.dec_tail_partitions = 0;
   }
   ~CallScope() {
     if (!ctx) return;
@@ -216,6 +217,7 @@ gc_status gc_create(gc_context** out, int device) {
   if (!ctx) return GC_ERR_OOM;
   ctx->device = device;
   if (const char* env = getenv("GC_CORE_TARGET")) ctx->core_target = atoll(env);
+  if (const char* env = getenv("GC_DEC_TAIL")) ctx->dec_tail = env[0] != '\0' && env[0] != '0';
   // failure injection for tests of the error paths (see gc_context)
   if (const char* env = getenv("GC_WAIT_LIMIT_MS")) {
     const long long ms = atoll(env);

@@ -101,16 +101,19 @@ __device__ __forceinline__ void append_u(int v, int kind, unsigned long long* cn
   if (kind == 2) ub[ucap - 1 - static_cast<long long>(bs + __popc(ms & lanemask_lt()))] = v;
 }
 
-struct DecCtl {
-  unsigned long long cnt[3][2];  // |U| of slot k % 3: [0] warp path, [1] lane path
+struct DecCtl {  // read back whole into the context's 256-byte pinned buffer
+  unsigned long long cnt[3][4];  // U of slot k % 3: [0] warp-path, [1] lane-path vertices, [2] list entries,
+                                 // [3] the longest list
   unsigned long long cur[3][4];  // cursors of slot k % 3: pick warp/lane, check warp/lane
   unsigned long long iters;      // pick launches that found U non-empty
   unsigned long long internal;   // sum of the internal list lengths
   int max_color;
-  int err;                       // 1: a batch outside 1..rounds
+  int err;                       // 1: a batch outside 1..rounds; 2: the tail did not fit
   int nonempty;                  // partitions holding at least one vertex
   int pad;
 };
+
+static_assert(sizeof(DecCtl) <= 256, "DecCtl must fit the pinned read-back buffer");
 
 struct DecArgs {
   const long long* row_ptr;
@@ -125,6 +128,7 @@ struct DecArgs {
   long long ucap;   // capacity of each U buffer
   const long long* hubpre;  // inclusive prefix of the hubs' chunk counts, by position in `order`
   int* hdone;               // chunks finished, per hub (same positions)
+  int* lid;                 // local id of a vertex of U in the tail kernel
   DecCtl* ctl;
   unsigned long long seed;
 };
@@ -356,7 +360,7 @@ dec_hub_prep_kernel(const long long* __restrict__ row_ptr, const int* __restrict
 // call it (v < 0: none) for the warp-aggregated append to U.
 template <bool Packed>
 __device__ int extract_lane(const DecArgs& A, int v, int l, unsigned long long* cnt, int* ub,
-                            unsigned long long* inner_sum) {
+                            unsigned long long* inner_sum, int* inner_max) {
   constexpr int U = 4;
   int c = 0;
   bool enter = false;
@@ -398,6 +402,7 @@ __device__ int extract_lane(const DecArgs& A, int v, int l, unsigned long long* 
       if (e - s + 1 > 32) A.B[bs + 1] = static_cast<unsigned>(used >> 32);
       enter = true;
       *inner_sum += static_cast<unsigned long long>(id);
+      *inner_max = *inner_max > id ? *inner_max : id;
     }
   }
   append_u(v, enter ? 2 : 0, cnt, ub, A.ucap);
@@ -459,7 +464,7 @@ __device__ __forceinline__ int window_mex(const unsigned* win, unsigned* Bv, lon
 // the lane-path list.
 template <bool Packed>
 __device__ int extract_warp(const DecArgs& A, int v, int l, unsigned* win, int* kind,
-                            unsigned long long* inner_sum) {
+                            unsigned long long* inner_sum, int* inner_max) {
   constexpr int U = 4;
   const int lane = threadIdx.x & 31;
   const long long s = A.row_ptr[v], e = A.row_ptr[v + 1];
@@ -509,6 +514,7 @@ __device__ int extract_warp(const DecArgs& A, int v, int l, unsigned* win, int* 
   }
   *kind = id == 0 ? 0 : (id > kSmallDeg ? 1 : 2);
   if (lane == 0) *inner_sum += static_cast<unsigned long long>(id);  // summed over the warp later
+  *inner_max = *inner_max > id ? *inner_max : id;
   return id == 0 ? c : 0;
 }
 
@@ -579,6 +585,8 @@ __device__ int extract_hub_chunk(const DecArgs& A, int v, long long c, long long
       st_relaxed(A.S + v, state_word<Packed>(l, col) | static_cast<int>(kTent));
       A.hint[v] = hw;
       atomicAdd(&A.ctl->internal, static_cast<unsigned long long>(id));
+      atomicAdd(&cnt[2], static_cast<unsigned long long>(id));
+      atomicMax(&cnt[3], static_cast<unsigned long long>(id));
       if (id > kSmallDeg)
         ub[atomicAdd(&cnt[0], 1ull)] = v;
       else
@@ -598,6 +606,7 @@ dec_extract_kernel(DecArgs A, PartRange* part, int l, const int* __restrict__ or
   int* ub = ubuf_of(A, slot);
   int local_max = 0;
   unsigned long long inner_sum = 0;  // this lane's share of the internal list lengths
+  int inner_max = 0;                 // and the longest list it saw
   // hub chunks first, by every warp
   const unsigned long long ntask = pr->hub_tasks;
   if (ntask) {
@@ -643,7 +652,7 @@ dec_extract_kernel(DecArgs A, PartRange* part, int l, const int* __restrict__ or
       for (int j = 0; i + j < iend; ++j) {
         const int v = big[i + j];
         int kind = 0;
-        const int c = extract_warp<Packed>(A, v, l, s_win[warp], &kind, &inner_sum);
+        const int c = extract_warp<Packed>(A, v, l, s_win[warp], &kind, &inner_sum, &inner_max);
         if (lane == j) {
           myv = v;
           mykind = kind;
@@ -662,16 +671,21 @@ dec_extract_kernel(DecArgs A, PartRange* part, int l, const int* __restrict__ or
       for (unsigned long long g = 0; g < ks && i0 + 32 * g < nsmall; ++g) {
         const unsigned long long i = i0 + 32 * g + lane;
         const int v = i < nsmall ? small[i] : -1;
-        const int c = extract_lane<Packed>(A, v, l, cnt, ub, &inner_sum);
+        const int c = extract_lane<Packed>(A, v, l, cnt, ub, &inner_sum, &inner_max);
         local_max = c > local_max ? c : local_max;
       }
     }
   }
   local_max = warp_max(local_max);
   inner_sum = warp_sum(inner_sum);
+  inner_max = warp_max(inner_max);
   if (lane == 0) {
     if (local_max > 0) atomicMax(&A.ctl->max_color, local_max);
-    if (inner_sum) atomicAdd(&A.ctl->internal, inner_sum);
+    if (inner_sum) {
+      atomicAdd(&A.ctl->internal, inner_sum);
+      atomicAdd(&cnt[2], inner_sum);  // U's list entries
+      atomicMax(&cnt[3], static_cast<unsigned long long>(inner_max));
+    }
   }
 }
 
@@ -722,12 +736,12 @@ __global__ void __launch_bounds__(kDecThreads)
 dec_check_kernel(DecArgs A, int slot) {
   DecCtl* ctl = A.ctl;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (blockIdx.x == 0 && threadIdx.x < 6) {  // slot + 2: no launch reads it any more
+  if (blockIdx.x == 0 && threadIdx.x < 8) {  // slot + 2: no launch reads it any more
     const int z = (slot + 2) % 3;
-    if (threadIdx.x < 2)
+    if (threadIdx.x < 4)
       ctl->cnt[z][threadIdx.x] = 0;
     else
-      ctl->cur[z][threadIdx.x - 2] = 0;
+      ctl->cur[z][threadIdx.x - 4] = 0;
   }
   const int sl = slot % 3;
   const unsigned long long nbig = ctl->cnt[sl][0], nsmall = ctl->cnt[sl][1];
@@ -740,6 +754,8 @@ dec_check_kernel(DecArgs A, int slot) {
   const bool prefer_big = (warp & 3) != 0;
   const unsigned long long kb = grab_size(nbig), ks = grab_size((nsmall + 31) / 32);
   int local_max = 0;
+  unsigned long long edges = 0;  // list entries of this lane's losers (the next U)
+  int longest = 0;               // and their longest list
   while (!(big_done && small_done)) {
     if (!big_done && (prefer_big || small_done)) {
       unsigned long long i = 0;
@@ -763,6 +779,11 @@ dec_check_kernel(DecArgs A, int slot) {
           mylose = lose;
         }
       }
+      if (mylose) {
+        const int id = A.ideg[myv];
+        edges += static_cast<unsigned long long>(id);
+        longest = longest > id ? longest : id;
+      }
       append_u(myv, mylose ? 1 : 0, ncnt, un, A.ucap);
     } else {
       unsigned long long i0 = 0;
@@ -784,11 +805,21 @@ dec_check_kernel(DecArgs A, int slot) {
           if (!lose) {
             st_relaxed(A.S + v, static_cast<int>(xv & ~kTent));
             local_max = static_cast<int>(t) > local_max ? static_cast<int>(t) : local_max;
+          } else {
+            const int id = A.ideg[v];
+            edges += static_cast<unsigned long long>(id);
+            longest = longest > id ? longest : id;
           }
         }
         append_u(v, lose ? 2 : 0, ncnt, un, A.ucap);
       }
     }
+  }
+  edges = warp_sum(edges);
+  longest = warp_max(longest);
+  if (lane == 0 && edges) {
+    atomicAdd(&ncnt[2], edges);
+    atomicMax(&ncnt[3], static_cast<unsigned long long>(longest));
   }
   local_max = warp_max(local_max);
   if (lane == 0 && local_max > 0) atomicMax(&ctl->max_color, local_max);
@@ -918,6 +949,284 @@ dec_pick_kernel(DecArgs A, int slot, int l) {
   }
 }
 
+// ---- the tail of a partition in one thread-block cluster -------------------
+//
+// Once U is small (at most kTailMax vertices whose internal lists fit the
+// cluster's shared memory), the rest of the partition's SIM-COL iterations
+// run in one launch of one cluster.  Every CTA keeps a replica of U's state
+// words (colour | tentative, by local id) and its own share of the internal
+// lists (16-bit local ids) in shared memory; the pick and the check are two
+// phases separated by cluster barriers, and a vertex whose word changes
+// writes it into every CTA's replica through distributed shared memory.  An
+// iteration then costs two barriers and shared-memory scans instead of two
+// launches and L2 round trips; the top partitions of power-law graphs are
+// near-cliques that fix about one vertex per iteration for hundreds of
+// iterations.
+
+constexpr int kTailMax = 4096;  // |U| at most (16-bit local ids)
+constexpr int kTailThreads = 1024;
+constexpr int kTailClusterMax = 16;
+constexpr int kTailSmem = 200 * 1024;
+// replica, hashes and split prefix (4 B each per local id) and counters
+constexpr int kTailFixed = 12 * kTailMax + 4 + 64;
+// per owned vertex: global id, window word index, window word, list length,
+// bitmap words (20 B), so a vertex with d list entries takes 2 (d + 10) bytes
+constexpr int kTailVertexWeight = 10;
+
+__device__ __forceinline__ unsigned tail_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned tail_ctas() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+// All threads of all CTAs arrive; shared-memory writes before it, local or
+// remote, are visible to every thread after it.
+__device__ __forceinline__ void tail_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Address of this CTA's shared variable `p` in CTA `rank` of the cluster.
+__device__ __forceinline__ unsigned tail_map(const void* p, unsigned rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+               : "=r"(r)
+               : "r"(static_cast<unsigned>(__cvta_generic_to_shared(p))), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void tail_st(unsigned addr, unsigned v) {
+  asm volatile("st.relaxed.cluster.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void tail_add(unsigned addr, unsigned v) {
+  asm volatile("red.relaxed.cluster.shared::cluster.add.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned tail_ld(unsigned addr) {
+  unsigned v;
+  asm volatile("ld.relaxed.cluster.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+// Largest per-CTA shared memory for the owned vertices of a split of U (u
+// vertices, `entries` list entries, the longest list `longest`) over c CTAs,
+// in bytes: each CTA's weight is below W / c plus the heaviest vertex.
+__host__ __device__ __forceinline__ long long tail_need(long long u, long long entries, long long longest, int c) {
+  const long long w = entries + kTailVertexWeight * u;
+  return 2 * (w / c + 1 + longest + kTailVertexWeight) + 16;
+}
+
+template <bool Packed>
+__global__ void __launch_bounds__(kTailThreads, 1)
+dec_tail_kernel(DecArgs A, int slot, int l) {
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  unsigned* st = reinterpret_cast<unsigned*>(s_dyn);  // replica [kTailMax]
+  unsigned* hk = st + kTailMax;                       // rho_R by local id [kTailMax]
+  int* pre = reinterpret_cast<int*>(hk + kTailMax);   // split prefix [kTailMax + 1]
+  unsigned* sc = reinterpret_cast<unsigned*>(pre + kTailMax + 1);  // [16]
+  int* o_gv = reinterpret_cast<int*>(sc + 16);        // per owned vertex ...
+  const int rank = static_cast<int>(tail_rank()), C = static_cast<int>(tail_ctas());
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  DecCtl* ctl = A.ctl;
+  const int sl = slot % 3;
+  const long long nbig = static_cast<long long>(ctl->cnt[sl][0]);
+  const int u = static_cast<int>(ctl->cnt[sl][0] + ctl->cnt[sl][1]);
+  const int* ub = ubuf_of(A, slot);
+  int* lid = A.lid;
+  auto uid = [&](int i) -> int { return i < nbig ? ub[i] : ub[A.ucap - 1 - (i - nbig)]; };
+
+  // 1. replica, hashes, local ids; weights ideg + kTailVertexWeight
+  for (int i = threadIdx.x; i < u; i += blockDim.x) {
+    const int v = uid(i);
+    st[i] = static_cast<unsigned>(ld_relaxed(A.S + v)) & (kTent | kColMask);
+    hk[i] = tie_hash(A.seed, static_cast<unsigned>(v));
+    lid[v] = i;
+    pre[i + 1] = A.ideg[v] + kTailVertexWeight;
+  }
+  if (threadIdx.x < 16) sc[threadIdx.x] = 0u;
+  if (threadIdx.x == 0) pre[0] = 0;
+  __syncthreads();
+  // inclusive scan of pre[1..u] by warp 0 (u <= 4096: 128 steps of 32)
+  if (warp == 0) {
+    int carry = 0;
+    for (int b = 1; b <= u; b += 32) {
+      const int i = b + lane;
+      const int x = i <= u ? pre[i] : 0;
+      const int incl = warp_inclusive_scan(x);
+      if (i <= u) pre[i] = carry + incl;
+      carry += __shfl_sync(kFull, incl, 31);
+    }
+  }
+  __syncthreads();
+  // 2. CTA r owns the local ids i with pre[i] * C / W == r (contiguous);
+  // every CTA checks every CTA's share, so all agree on a misfit
+  const long long W = pre[u];
+  auto first_of = [&](int r) -> int {  // first i with pre[i] * C >= r * W
+    int lo = 0, hi = u;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (static_cast<long long>(pre[mid]) * C >= static_cast<long long>(r) * W)
+        hi = mid;
+      else
+        lo = mid + 1;
+    }
+    return lo;
+  };
+  const long long avail = kTailSmem - kTailFixed;
+  if (threadIdx.x < static_cast<unsigned>(C)) {
+    const int r = threadIdx.x;
+    const int a0 = first_of(r), a1 = r + 1 < C ? first_of(r + 1) : u;
+    if (2ll * (pre[a1] - pre[a0]) + 16 > avail) atomicOr(&sc[3], 1u);
+  }
+  __syncthreads();
+  if (sc[3]) {
+    if (rank == 0 && threadIdx.x == 0) atomicExch(&ctl->err, 2);
+    return;  // no cluster barrier or remote access has happened yet
+  }
+  const int lo = first_of(rank), hi = rank + 1 < C ? first_of(rank + 1) : u;
+  const int o = hi - lo;
+  int* o_hint = o_gv + o;
+  unsigned* o_word = reinterpret_cast<unsigned*>(o_hint + o);
+  int* o_cnt = reinterpret_cast<int*>(o_word + o);
+  int* o_nwords = o_cnt + o;
+  unsigned short* lists = reinterpret_cast<unsigned short*>(o_nwords + o);
+  // list of owned vertex a at lists[pre[lo + a] - pre[lo] - kTailVertexWeight * a ..]
+  auto list_off = [&](int a) -> int { return pre[lo + a] - pre[lo] - kTailVertexWeight * a; };
+
+  // 3. owned lists in 16-bit local ids; neighbours fixed since the last pick
+  // go into B_v and leave the list
+  for (int a = warp; a < o; a += nwarps) {
+    const int v = uid(lo + a);
+    const long long s = A.row_ptr[v];
+    const long long deg = A.row_ptr[v + 1] - s;
+    const long long nw = (deg + 32) / 32;
+    unsigned* Bv = A.B + bstart(A.row_ptr, v);
+    const int id = A.ideg[v];
+    unsigned short* L = lists + list_off(a);
+    int kept = 0;
+    for (int j0 = 0; j0 < id; j0 += 32) {
+      const int j = j0 + lane;
+      const int w = j < id ? A.icol[s + j] : -1;
+      const unsigned x = w >= 0 ? static_cast<unsigned>(ld_relaxed(A.S + w)) : 0u;
+      const bool tent = w >= 0 && (x & kTent);
+      if (w >= 0 && !tent) {
+        const long long cc = static_cast<long long>(x & kColMask);
+        if (cc >= 1 && cc <= deg + 1) atomicOr(Bv + ((cc - 1) >> 5), 1u << ((cc - 1) & 31));
+      }
+      const unsigned m = __ballot_sync(kFull, tent);
+      if (tent) L[kept + __popc(m & lanemask_lt())] = static_cast<unsigned short>(lid[w]);
+      kept += __popc(m);
+    }
+    __syncwarp();
+    if (lane == 0) {
+      const int h = A.hint[v];
+      o_gv[a] = v;
+      o_hint[a] = h;
+      o_word[a] = __ldcg(Bv + h);
+      o_cnt[a] = kept;
+      o_nwords[a] = static_cast<int>(nw);
+    }
+  }
+  tail_sync();  // every replica complete before any remote write
+
+  // 4. iterations
+  const unsigned sc0 = tail_map(sc, 0);  // CTA 0's counters
+  int it = 0, local_max = 0;
+  for (;;) {
+    // pick: fixed neighbours into B_v (the window word, or B_v above it),
+    // out of the list; draw the smallest free colour
+    if (rank == 0 && threadIdx.x == 0) sc[(it + 1) % 3] = 0u;
+    for (int a = warp; a < o; a += nwarps) {
+      const int i = lo + a;
+      if (!(st[i] & kTent)) continue;
+      unsigned short* L = lists + list_off(a);
+      const int cnt = o_cnt[a];
+      const int h0 = o_hint[a];
+      const int nw = o_nwords[a];
+      unsigned* Bv = A.B + bstart(A.row_ptr, o_gv[a]);
+      int kept = 0;
+      for (int j0 = 0; j0 < cnt; j0 += 32) {
+        const int k = j0 + lane;
+        const int j = k < cnt ? L[k] : -1;
+        const unsigned x = j >= 0 ? st[j] : 0u;
+        const bool tent = j >= 0 && (x & kTent);
+        if (j >= 0 && !tent) {
+          const int wi = static_cast<int>(((x & kColMask) - 1u) >> 5);
+          const unsigned bit = 1u << (((x & kColMask) - 1u) & 31);
+          if (wi == h0)
+            atomicOr(&o_word[a], bit);
+          else if (wi > h0 && wi < nw)
+            atomicOr(Bv + wi, bit);
+        }
+        const unsigned m = __ballot_sync(kFull, tent);
+        if (tent) L[kept + __popc(m & lanemask_lt())] = static_cast<unsigned short>(j);
+        kept += __popc(m);
+      }
+      __syncwarp();
+      int t = 0;
+      if (lane == 0) {
+        o_cnt[a] = kept;
+        int h = h0;
+        unsigned word = o_word[a];
+        while (word == kFull && h + 1 < nw) {
+          Bv[h] = word;
+          word = __ldcg(Bv + ++h);
+        }
+        o_word[a] = word;
+        o_hint[a] = h;
+        t = 32 * h + __ffs(~word);
+      }
+      t = __shfl_sync(kFull, t, 0);
+      if (lane < C) tail_st(tail_map(&st[i], lane), kTent | static_cast<unsigned>(t));
+    }
+    tail_sync();
+    // check: keep the draw unless a higher-key neighbour in U drew it too
+    unsigned rem = 0;
+    for (int a = warp; a < o; a += nwarps) {
+      const int i = lo + a;
+      const unsigned xi = st[i];
+      if (!(xi & kTent)) continue;
+      const unsigned t = xi & kColMask, hv = hk[i];
+      const unsigned short* L = lists + list_off(a);
+      const int cnt = o_cnt[a];
+      bool hit = false;
+      for (int k = lane; k < cnt && !hit; k += 32) {
+        const int j = L[k];
+        if ((st[j] & kColMask) == t && (hk[j] > hv || (hk[j] == hv && uid(j) > o_gv[a]))) hit = true;
+      }
+      const bool lose = __any_sync(kFull, hit);
+      if (!lose) {
+        if (lane < C) tail_st(tail_map(&st[i], lane), t);
+        if (lane == 0) st_relaxed(A.S + o_gv[a], state_word<Packed>(l, static_cast<int>(t)));
+        local_max = static_cast<int>(t) > local_max ? static_cast<int>(t) : local_max;
+      } else if (lane == 0) {
+        ++rem;
+      }
+    }
+    if (lane == 0 && rem) tail_add(sc0 + 4u * static_cast<unsigned>(it % 3), rem);
+    tail_sync();
+    const unsigned remaining = tail_ld(sc0 + 4u * static_cast<unsigned>(it % 3));
+    ++it;
+    if (remaining == 0u) break;
+    if (it > u) {  // cannot happen: every iteration keeps the highest key of U
+      if (rank == 0 && threadIdx.x == 0) atomicExch(&ctl->err, 2);
+      break;
+    }
+  }
+  tail_sync();  // no CTA leaves while another may still read its shared memory
+
+  local_max = warp_max(local_max);
+  if (lane == 0 && local_max > 0) atomicMax(&ctl->max_color, local_max);
+  if (rank == 0 && threadIdx.x == 0) {
+    atomicAdd(&ctl->iters, static_cast<unsigned long long>(it));
+    for (int z = 1; z <= 2; ++z) {  // slots slot+1, slot+2: empty, cursors at 0
+      const int q = (slot + z) % 3;
+      for (int f = 0; f < 4; ++f) ctl->cnt[q][f] = 0;
+      for (int f = 0; f < 4; ++f) ctl->cur[q][f] = 0;
+    }
+  }
+}
+
 __global__ void dec_strip_kernel(long long n, int* __restrict__ S) {
   for (long long v = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; v < n;
        v += static_cast<long long>(gridDim.x) * blockDim.x)
@@ -926,10 +1235,45 @@ __global__ void dec_strip_kernel(long long n, int* __restrict__ S) {
 
 size_t bitmap_words(long long n, long long nnz) { return static_cast<size_t>((nnz + n) / 32 + n + 2); }
 
+// CTAs of the tail cluster: the largest of 16, 8, 4, 2 that the device can
+// place with the tail's shared memory (0: none).
+int tail_cluster_size(gc_context* ctx) {
+  if (ctx->tail_cluster != 0) return ctx->tail_cluster > 0 ? ctx->tail_cluster : 0;
+  ctx->tail_cluster = -1;
+  for (auto k : {dec_tail_kernel<true>, dec_tail_kernel<false>}) {
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kTailSmem) != cudaSuccess ||
+        cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+  }
+  for (int cs = kTailClusterMax; cs >= 2; cs /= 2) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(kTailThreads);
+    cfg.dynamicSmemBytes = kTailSmem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, dec_tail_kernel<true>, &cfg) == cudaSuccess && ncl >= 1) {
+      ctx->tail_cluster = cs;
+      return cs;
+    }
+    cudaGetLastError();
+  }
+  return 0;
+}
+
 template <bool Packed>
 gc_status dec_loop(gc_context* ctx, const DecArgs& A, PartRange* part, const int* order, int rounds,
                    cudaStream_t s) {
   const int sms = ctx->num_sms;
+  const int tail_c = ctx->dec_tail ? tail_cluster_size(ctx) : 0;
   const int gx = resident_grid(dec_extract_kernel<Packed>, kDecThreads, sms);
   const int gk = resident_grid(dec_check_kernel, kDecThreads, sms);
   const int gp = resident_grid(dec_pick_kernel<Packed>, kDecThreads, sms);
@@ -961,10 +1305,34 @@ gc_status dec_loop(gc_context* ctx, const DecArgs& A, PartRange* part, const int
       }
       ctx->timer_end(s);
       GC_TRY_CUDA(cudaGetLastError());
-      GC_TRY_CUDA(cudaMemcpyAsync(pinned, A.ctl->cnt[slot % 3], 2 * sizeof(unsigned long long),
+      GC_TRY_CUDA(cudaMemcpyAsync(pinned, A.ctl->cnt[slot % 3], 4 * sizeof(unsigned long long),
                                   cudaMemcpyDeviceToHost, s));
       GC_TRY_CUDA(cudaStreamSynchronize(s));
-      if (pinned[0] + pinned[1] == 0) break;
+      const unsigned long long u = pinned[0] + pinned[1];
+      if (u == 0) break;
+      if (tail_c > 0 && u <= static_cast<unsigned long long>(kTailMax) &&
+          kTailFixed + tail_need(static_cast<long long>(u), static_cast<long long>(pinned[2]),
+                                 static_cast<long long>(pinned[3]), tail_c) <= kTailSmem) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = tail_c;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(tail_c);
+        cfg.blockDim = dim3(kTailThreads);
+        cfg.dynamicSmemBytes = kTailSmem;
+        cfg.stream = s;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        ctx->timer_begin(gc_context::kTDecIterate, s);
+        GC_TRY_CUDA(cudaLaunchKernelEx(&cfg, dec_tail_kernel<Packed>, A, slot, l));
+        ctx->timer_end(s);
+        ++g_launches;
+        ++ctx->stats.dec_tail_partitions;
+        ++slot;  // the tail leaves slots slot+1 and slot+2 empty
+        break;
+      }
       // one warp per warp-path vertex, one per 32 lane-path vertices
       const unsigned long long warps = pinned[0] + (pinned[1] + 31) / 32;
       const unsigned long long want = (warps + kDecThreads / 32 - 1) / (kDecThreads / 32);
@@ -980,7 +1348,7 @@ gc_status dec_loop(gc_context* ctx, const DecArgs& A, PartRange* part, const int
 size_t dec_scratch_bytes(long long n, long long nnz, int rounds) {
   const size_t nn = static_cast<size_t>(n > 0 ? n : 1);
   const size_t nr = static_cast<size_t>(rounds > 0 ? rounds : 0) + 1;
-  return 16 * 256 + sizeof(DecCtl) + sizeof(PartRange) * nr + 2 * 8 * 3 * nr + 4 * nr + 4 * 6 * nn + 8 * nn +
+  return 17 * 256 + sizeof(DecCtl) + sizeof(PartRange) * nr + 2 * 8 * 3 * nr + 4 * nr + 4 * 7 * nn + 8 * nn +
          4 * static_cast<size_t>(nnz > 0 ? nnz : 1) + 4 * bitmap_words(n, nnz);
 }
 
@@ -1008,6 +1376,8 @@ gc_status dec_itr_run(gc_context* ctx, Arena a, const gc_csr* g, const int* batc
   unsigned* B = a.take<unsigned>(bitmap_words(n, nnz));
   long long* hubpre = a.take<long long>(n);
   int* hdone = a.take<int>(n);
+  int* lid = a.take<int>(n);
+  if (!lid) return GC_ERR_OOM;
   if (!ctl || !part || !bins || !fill || !present || !order || !ideg || !hint || !ub0 || !ub1 || !icol || !B ||
       !hubpre || !hdone)
     return GC_ERR_OOM;
@@ -1045,6 +1415,7 @@ gc_status dec_itr_run(gc_context* ctx, Arena a, const gc_csr* g, const int* batc
   A.ucap = n;
   A.hubpre = hubpre;
   A.hdone = hdone;
+  A.lid = lid;
   A.ctl = ctl;
   A.seed = seed;
   if (packed)
@@ -1061,7 +1432,8 @@ gc_status dec_itr_run(gc_context* ctx, Arena a, const gc_csr* g, const int* batc
   GC_TRY_CUDA(cudaMemcpyAsync(ctx->pinned, ctl, sizeof(DecCtl), cudaMemcpyDeviceToHost, s));
   GC_TRY_CUDA(cudaStreamSynchronize(s));
   memcpy(&h, ctx->pinned, sizeof(DecCtl));
-  if (h.err) return GC_ERR_INVALID_ARG;
+  if (h.err == 1) return GC_ERR_INVALID_ARG;
+  if (h.err) return GC_ERR_CUDA;  // the tail found U larger than its shared memory: cannot happen
   *num_colors_out = h.max_color;
   *iters_out = static_cast<long long>(h.nonempty) + static_cast<long long>(h.iters);
   ctx->stats.dec_internal_edges = static_cast<int64_t>(h.internal);

@@ -177,6 +177,8 @@ struct gc_context {
   int stall_vertex = -1;
   bool fail_alloc = false;
   int core_cluster = 0;                   // CTAs of the core cluster (0: not chosen yet)
+  bool dec_tail = true;                   // DEC-ADG-ITR: finish small U in one cluster launch
+  int tail_cluster = 0;                   // CTAs of that cluster (0: not chosen yet, -1: none fits)
   int core_warps = 0;                     // warps per core CTA
   // scratch arena (device)
   void* scratch = nullptr;

@@ -62,7 +62,8 @@ class gc_stats(ctypes.Structure):
                 ("core_vertices", ctypes.c_int64), ("core_preds", ctypes.c_int64),
                 ("core_degree_sum", ctypes.c_int64), ("core_ctas", ctypes.c_int32),
                 ("sim_iterations", ctypes.c_int64), ("dec_internal_edges", ctypes.c_int64),
-                ("ms_dec_extract", ctypes.c_float), ("ms_dec_iterate", ctypes.c_float)]
+                ("ms_dec_extract", ctypes.c_float), ("ms_dec_iterate", ctypes.c_float),
+                ("dec_tail_partitions", ctypes.c_int64)]
 
 
 _lib = None

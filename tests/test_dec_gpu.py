@@ -35,6 +35,26 @@ def ctx():
     c.close()
 
 
+@pytest.fixture(scope="module")
+def ctx_notail():
+    # every SIM-COL iteration as GPU-wide launches (GC_DEC_TAIL is read when
+    # the context is created)
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import os
+    old = os.environ.get("GC_DEC_TAIL")
+    os.environ["GC_DEC_TAIL"] = "0"
+    try:
+        c = gcp.Context(0)
+    finally:
+        if old is None:
+            del os.environ["GC_DEC_TAIL"]
+        else:
+            os.environ["GC_DEC_TAIL"] = old
+    yield c
+    c.close()
+
+
 def dev(g):
     return gcp.DeviceGraph.from_host(g, "cuda:0")
 
@@ -145,3 +165,20 @@ def test_dec_itr_zero_vertices(ctx):
     out = torch.empty(0, dtype=torch.int32, device="cuda:0")
     assert ctx.gc_color_graph_dec_itr(dg, 1, 100, 42, out) == (0, 0)
     assert ctx.gc_dec_itr_color(dg, out, 1, 42, out) == 0
+
+
+TAIL_GRAPHS = [complete(300), complete(1100), gg.rmat(16, 16, seed=2), gg.rmat(18, 16, seed=9),
+               gg.barabasi_albert(2046, 14, 43), _twin_hubs(9000), gg.rmat(20, 16, seed=1)]
+
+
+@pytest.mark.parametrize("g", TAIL_GRAPHS, ids=lambda g: g.name)
+def test_dec_itr_tail_and_launch_paths(ctx, ctx_notail, g):
+    # the single-cluster tail and the GPU-wide iterations give the oracle's
+    # colouring; the dense graphs here do reach the tail
+    c1 = assert_dec_same(ctx, g)
+    tails = ctx.gc_get_stats().dec_tail_partitions
+    c2 = assert_dec_same(ctx_notail, g)
+    assert ctx_notail.gc_get_stats().dec_tail_partitions == 0
+    assert np.array_equal(c1, c2)
+    if g.name.startswith(("K300", "K1100", "rmat")):
+        assert tails >= 1, g.name

@@ -9,6 +9,8 @@ Functions (each cites the passage of the paper it follows in ``oracle.c``):
   adg(g, p, q)                   Algorithm 1, fresh degree sums every round
   adg_naive(g, p, q)             Algorithm 1 with D recomputed from scratch
   adg_m(g), adg_m_naive(g)       ADG-M (median; R = ceil(|U|/2) smallest (D, id))
+  adg_o(g, p, q)                 ADG-O (Algorithm 6: R sorted by D, total order rho)
+  jp_adg_o(g, p, q)              JP with rho_ADG-O
   tiebreak(seed, v)              SplitMix64-based random tie-break rho_R
   priority(batch, seed)          (batch << 32) | tiebreak, ties by vertex id
   priority_kind(g, kind, seed)   JP-R / FF / LF / LLF keys (kinds 0..3)
@@ -77,6 +79,8 @@ def _load():
         lib.oracle_jp_depth.argtypes = [i64, vp, vp, vp, vp]
         lib.oracle_degeneracy.restype = i64
         lib.oracle_degeneracy.argtypes = [i64, vp, vp, vp]
+        lib.oracle_adg_o.restype = ctypes.c_int
+        lib.oracle_adg_o.argtypes = [i64, vp, vp, u32, u32, vp, vp, vp, ctypes.POINTER(ctypes.c_int32)]
         lib.oracle_dec_adg_itr.restype = ctypes.c_int
         lib.oracle_dec_adg_itr.argtypes = [i64, vp, vp, vp, i32, u64, vp, vp, vp, vp]
         lib.oracle_chromatic_number.restype = i32
@@ -151,6 +155,27 @@ def adg_m_naive(g):
     rounds = ctypes.c_int32(0)
     _check(_load().oracle_adg_m_naive(n, _p(rp), _p(ci), _p(batch), ctypes.byref(rounds)), "adg_m_naive")
     return batch, rounds.value
+
+
+def adg_o(g, eps_p: int, eps_q: int):
+    """ADG-O (Algorithm 6).  Returns (batch, rho int64[n], rank int64[n],
+    num_rounds)."""
+    n, rp, ci = _csr(g)
+    batch = np.zeros(n, dtype=np.int32)
+    rho = np.zeros(n, dtype=np.int64)
+    rank = np.zeros(n, dtype=np.int64)
+    rounds = ctypes.c_int32(0)
+    _check(_load().oracle_adg_o(n, _p(rp), _p(ci), eps_p, eps_q, _p(batch), _p(rho), _p(rank),
+                                ctypes.byref(rounds)), "adg_o")
+    return batch, rho, rank, rounds.value
+
+
+def jp_adg_o(g, eps_p: int, eps_q: int):
+    """JP-ADG-O: JP with priority rho_ADG-O (a total order, no random
+    tie-break).  Returns (batch, rho, color, num_rounds, num_colors)."""
+    batch, rho, _, rounds = adg_o(g, eps_p, eps_q)
+    color, nc = jp_color(g, rho.astype(np.uint64))
+    return batch, rho, color, rounds, nc
 
 
 def jp_adg_m(g, seed: int):

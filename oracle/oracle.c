@@ -456,6 +456,102 @@ int64_t oracle_jp_depth(int64_t n, const int64_t *row_ptr, const int32_t *col_id
 }
 
 /* ------------------------------------------------------------------------- */
+/* ADG-O (Algorithm 6; Section 5, "Explicit Ordering in R" and "Detailed     */
+/* Algorithm Specifications"): ADG whose removed set R is sorted by           */
+/* increasing D before it is numbered, so that rho is a total order.         */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    int64_t d;
+    int64_t v;
+} dkey;
+
+static int dkey_asc(const void *a, const void *b)
+{
+    const dkey *x = (const dkey *)a, *y = (const dkey *)b;
+    if (x->d != y->d) return x->d < y->d ? -1 : 1;
+    if (x->v != y->v) return x->v < y->v ? -1 : 1;
+    return 0;
+}
+
+/*
+ * Inputs: CSR, eps = eps_p / eps_q.  Outputs: batch[v] = the iteration that
+ * removed v (1-based, as in Algorithm 1), rho[v] in 0..n-1 = Algorithm 6's
+ * rho_ADG (l + i for the i-th vertex of the sorted R, l = vertices removed
+ * before), rank[v] = its count of neighbours with a higher rho (Algorithm 6's
+ * UPDATEandPRIORITIZE), *num_rounds.
+ * Readings: R is sorted by increasing D with equal D in increasing vertex id
+ * (the paper leaves ties open; the sort is meant to make the order total);
+ * the threshold is Algorithm 1's, evaluated exactly in integers.
+ * Returns 0, 1 on bad arguments, 2 on allocation failure.
+ */
+int oracle_adg_o(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, uint32_t eps_p,
+                 uint32_t eps_q, int32_t *batch, int64_t *rho, int64_t *rank, int32_t *num_rounds)
+{
+    if (n < 0 || eps_q == 0) return 1;
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    int64_t *D = (int64_t *)malloc(sizeof(int64_t) * nn);
+    char *inU = (char *)malloc(nn);
+    dkey *R = (dkey *)malloc(sizeof(dkey) * nn);
+    if (!D || !inU || !R) { free(D); free(inU); free(R); return 2; }
+    /* D = degrees; U = V; l = 0; rho(v) = n for all v */
+    for (int64_t v = 0; v < n; ++v) {
+        D[v] = row_ptr[v + 1] - row_ptr[v];
+        inU[v] = 1;
+        rho[v] = n;
+        rank[v] = 0;
+        batch[v] = 0;
+    }
+    int64_t sizeU = n, l = 0;
+    int32_t round = 0;
+    while (sizeU > 0) {
+        ++round;
+        /* the average degree of U, as an exact threshold on D */
+        int64_t count = 0, cnt = 0;
+        for (int64_t v = 0; v < n; ++v)
+            if (inU[v]) { count += 1; cnt += D[v]; }
+        unsigned __int128 num = (unsigned __int128)(eps_q + (uint64_t)eps_p) * (uint64_t)cnt;
+        unsigned __int128 den = (unsigned __int128)eps_q * (uint64_t)count;
+        unsigned __int128 T = num / den;
+        /* PARTITION: R = {u in U : D[u] <= (1+eps) * average} */
+        int64_t sizeR = 0;
+        for (int64_t v = 0; v < n; ++v)
+            if (inU[v] && (unsigned __int128)D[v] <= T) { R[sizeR].d = D[v]; R[sizeR].v = v; ++sizeR; }
+        if (sizeR == 0) { free(D); free(inU); free(R); return 3; } /* cannot happen */
+        /* SORT(R, D) by increasing D */
+        qsort(R, (size_t)sizeR, sizeof(dkey), dkey_asc);
+        /* rho(r_i) = l + i */
+        for (int64_t i = 0; i < sizeR; ++i) {
+            rho[R[i].v] = l + i;
+            batch[R[i].v] = round;
+        }
+        /* &U = &U + |R| */
+        for (int64_t i = 0; i < sizeR; ++i) inU[R[i].v] = 0;
+        sizeU -= sizeR;
+        /* UPDATEandPRIORITIZE: for v in R, every neighbour w after v in the
+         * order loses one from D[w]; rank(v) counts them */
+        for (int64_t i = 0; i < sizeR; ++i) {
+            const int64_t v = R[i].v;
+            int64_t c = 0;
+            for (int64_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) {
+                const int32_t w = col_idx[k];
+                if (rho[w] > rho[v]) {
+                    D[w] -= 1;
+                    c += 1;
+                }
+            }
+            rank[v] = c;
+        }
+        l += sizeR;
+    }
+    *num_rounds = round;
+    free(D);
+    free(inU);
+    free(R);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
 /* DEC-ADG-ITR (Section 4.3): DEC-ADG's partition-by-partition colouring     */
 /* (Algorithm 4) with SIM-COL (Algorithm 5) changed to give every vertex of U */
 /* the smallest colour not in B_v instead of a random one.                    */

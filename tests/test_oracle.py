@@ -707,3 +707,68 @@ def test_dec_itr_bad_batch_rejected():
         oracle.dec_itr(g, np.array([1, 2, 3, 1], dtype=np.int32), 2, 42)
     color, nc, iters, _ = oracle.dec_itr(empty(0), np.zeros(0, dtype=np.int32), 0, 42)
     assert nc == 0 and iters == 0
+
+
+# ---------------------------------------------------------------- ADG-O
+
+def _adg_o_graphs():
+    yield complete(9)
+    yield star(12)
+    yield petersen()
+    yield wheel(20)
+    for s in range(3):
+        yield random_small(50, 0.15, s)
+    yield gg.erdos_renyi(2000, 9000, 4)
+    yield gg.rmat(11, 16, seed=6)
+    yield gg.barabasi_albert(1500, 4, 3)
+    yield gg.grid(20, 15)
+
+
+@pytest.mark.parametrize("g", list(_adg_o_graphs()), ids=lambda g: g.name)
+@pytest.mark.parametrize("p,q", [(1, 100), (1, 2), (0, 1)])
+def test_adg_o_against_definitions(g, p, q):
+    # Algorithm 6 removes the same sets as Algorithm 1 (its UPDATE also
+    # decrements vertices later in the same R, whose D no longer matters);
+    # rho numbers the vertices batch by batch, inside a batch by increasing
+    # degree in G[U] at removal (= neighbours in the same or a later batch),
+    # equal degrees by id; rank(v) counts the neighbours with a higher rho
+    b, rho, rank, r = oracle.adg_o(g, p, q)
+    ob, orr = oracle.adg(g, p, q)
+    assert r == orr and np.array_equal(b, ob)
+    assert sorted(rho.tolist()) == list(range(g.n))
+    geq = _geq_counts(g, b)
+    want = sorted(range(g.n), key=lambda v: (b[v], geq[v], v))
+    assert [int(x) for x in np.argsort(rho)] == want
+    src = np.repeat(np.arange(g.n), g.degrees())
+    assert np.array_equal(rank, np.bincount(src, weights=rho[g.col_idx] > rho[src], minlength=g.n))
+
+
+def test_adg_o_closed_forms():
+    # K_n: one batch of equal degrees, rho = id, rank(v) = n - 1 - v, and
+    # JP-ADG-O colours v with n - v
+    b, rho, rank, r = oracle.adg_o(complete(8), 1, 100)
+    assert r == 1 and list(rho) == list(range(8)) and list(rank) == list(range(7, -1, -1))
+    assert list(oracle.jp_adg_o(complete(8), 1, 100)[2]) == list(range(8, 0, -1))
+    # star K_{1,k}: leaves first in id order, then the centre
+    b, rho, rank, r = oracle.adg_o(star(6), 1, 100)
+    assert list(rho) == [6, 0, 1, 2, 3, 4, 5] and list(rank) == [0, 1, 1, 1, 1, 1, 1]
+    # P_n, n <= 100: batch l = {l-1, n-l} with equal degrees, so the smaller
+    # id comes first
+    for n in (6, 7, 40):
+        b, rho, rank, r = oracle.adg_o(path(n), 1, 100)
+        for v in range(n):
+            l = min(v, n - 1 - v)
+            assert rho[v] == 2 * l + (0 if v <= n - 1 - v else 1)
+
+
+@pytest.mark.parametrize("g", [gg.rmat(11, 16, seed=2), gg.erdos_renyi(3000, 15000, 8), gg.grid(30, 30, perm_seed=1)],
+                         ids=lambda g: g.name)
+def test_jp_adg_o_colours(g):
+    # JP with the total order rho: proper, each colour the smallest missing
+    # among the higher-rho neighbours, within 2(1+eps)d + 1 colours
+    d, _ = oracle.degeneracy(g)
+    b, rho, color, r, nc = oracle.jp_adg_o(g, 1, 100)
+    src = np.repeat(np.arange(g.n), g.degrees())
+    assert (color[src] != color[g.col_idx]).all() and color.max() == nc
+    assert nc <= (2 * 101 * d) // 100 + 1
+    assert np.array_equal(color, _jp_simulate(g, rho.astype(np.uint64), np.random.default_rng(3)))

@@ -171,7 +171,7 @@ class ClockSampler:
                 "samples": len(sms)}
 
 
-def cpu_baseline(w_name, seconds_target=10.0, median=False, dec=False):
+def cpu_baseline(w_name, seconds_target=10.0, median=False, dec=False, ordered=False):
     """The oracle as it stands, single-threaded, on a bounded sample of the
     same family (R-MAT scale 22 for the R-MAT workloads)."""
     import graphgen as gg
@@ -195,11 +195,14 @@ def cpu_baseline(w_name, seconds_target=10.0, median=False, dec=False):
             oracle.jp_adg_m(g, w["seed"])
         elif dec:
             oracle.dec_adg_itr(g, p, q, w["seed"])
+        elif ordered:
+            oracle.jp_adg_o(g, p, q)
         else:
             oracle.jp_adg(g, p, q, w["seed"])
         total += time.perf_counter() - t0
         reps += 1
-    what = "ADG-M + Greedy" if median else ("ADG + DEC-ADG-ITR" if dec else "ADG + Greedy")
+    what = ("ADG-M + Greedy" if median else "ADG + DEC-ADG-ITR" if dec else "ADG-O + Greedy" if ordered
+            else "ADG + Greedy")
     return {"value": g.m * reps / total, "unit": "edges/s", "cores": 1, "kind": "oracle",
             "sample": f"{desc}: n={g.n}, m={g.m}, {reps} run(s) of {what}, {total:.1f} s"}
 
@@ -644,8 +647,9 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat24")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--priority", choices=["adg", "adg-m"] + sorted(PRIORITIES), default="adg",
-                    help="JP priority: adg (JP-ADG, the default), adg-m (JP-ADG-M) or another JP variant")
+    ap.add_argument("--priority", choices=["adg", "adg-m", "adg-o"] + sorted(PRIORITIES), default="adg",
+                    help="JP priority: adg (JP-ADG, the default), adg-m (JP-ADG-M), adg-o (JP-ADG-O) or "
+                         "another JP variant")
     ap.add_argument("--algo", choices=["jp", "dec-itr"], default="jp",
                     help="colouring: jp (JP with --priority, the default) or dec-itr (DEC-ADG-ITR)")
     args = ap.parse_args()
@@ -665,7 +669,7 @@ def main():
     if args.priority != "adg":
         if WORKLOADS[args.workload]["kind"] in ("batch", "serve"):
             ap.error("--priority applies to the single-graph workloads")
-        if args.priority != "adg-m":
+        if args.priority not in ("adg-m", "adg-o"):
             return run_variant(args, rank, world)
     if WORKLOADS[args.workload]["kind"] == "batch":
         return run_batch(args, rank, world)
@@ -698,10 +702,13 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     median = args.priority == "adg-m"
+    ordered = args.priority == "adg-o"
 
     def colour_step():
         if median:  # JP-ADG-M: ADG-M has no eps
             return ctx.gc_color_graph_m(dg, seed, color, batch)
+        if ordered:  # JP-ADG-O: a total order, no tie-break seed
+            return ctx.gc_color_graph_o(dg, p, q, color, batch)
         return ctx.gc_color_graph(dg, p, q, seed, color, batch)
 
     for _ in range(args.warmup):
@@ -742,7 +749,7 @@ def main():
 
     # end to end through the public host-buffer entry point
     e2e = None
-    if not args.no_e2e and not median:
+    if not args.no_e2e and not median and not ordered:
         hcolor = torch.empty(n, dtype=torch.int32, pin_memory=True).numpy()
         ctx.gc_set_timing(False)
         ctx.gc_color_graph_host(g.row_ptr, g.col_idx, p, q, seed, hcolor)  # grows buffers once
@@ -785,7 +792,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": w["desc"] if not median else w["desc"].replace("eps=1/100", "JP-ADG-M (median)"),
+        "config": {"workload": (w["desc"].replace("eps=1/100", "JP-ADG-M (median)") if median else
+                                (w["desc"] + ", JP-ADG-O (R sorted by degree)" if ordered else w["desc"])),
                    "n": n, "m": m, "eps": f"{p}/{q}" if not median else None, "seed": seed,
                    "adg_rounds": nr, "num_colors": nc, "sum_U": sum_u, "decrements": dec,
                    "parallelism": "replicas" if world > 1 else "single GPU",
@@ -805,7 +813,7 @@ def main():
     if e2e:
         line["e2e"] = e2e
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.workload, median=median)
+        line["cpu_baseline"] = cpu_baseline(args.workload, median=median, ordered=ordered)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -201,6 +201,25 @@ gc_status gc_adg_m_partition(gc_context *ctx, const gc_csr *g, int32_t *batch_ou
 gc_status gc_color_graph_m(gc_context *ctx, const gc_csr *g, uint64_t seed, int32_t *color_out, int32_t *batch_out,
                            int32_t *num_colors_out, int32_t *num_rounds_out, gc_stream stream);
 
+/* ADG-O (Algorithm 6; Section 5, "Explicit Ordering in R"): the iterations
+ * of gc_adg_partition, each removed set R numbered in increasing order of its
+ * vertices' degree D in G[U] at removal, equal degrees in increasing id (a
+ * reading: the paper leaves ties open).  rho_out[v] (device, n int32) is
+ * rho_ADG(v) = (vertices removed in earlier iterations) + (v's place in its
+ * sorted R), a permutation of 0..n-1; batch_out (device, n int32, may be
+ * NULL) the iteration as in gc_adg_partition; rank_out (device, n int32, may
+ * be NULL) the number of neighbours with a higher rho (Algorithm 6's
+ * UPDATEandPRIORITIZE); *num_rounds_out (host, may be NULL) the number of
+ * iterations. */
+gc_status gc_adg_o_order(gc_context *ctx, const gc_csr *g, uint32_t eps_p, uint32_t eps_q, int32_t *batch_out,
+                         int32_t *rho_out, int32_t *rank_out, int32_t *num_rounds_out, gc_stream stream);
+
+/* JP-ADG-O: JP (Algorithm 3) with the total order rho_ADG-O as its priority
+ * (a higher rho is coloured first); no random tie-break, so no seed.
+ * Arguments as in gc_color_graph.  At most floor(2(1+eps)d) + 1 colours. */
+gc_status gc_color_graph_o(gc_context *ctx, const gc_csr *g, uint32_t eps_p, uint32_t eps_q, int32_t *color_out,
+                           int32_t *batch_out, int32_t *num_colors_out, int32_t *num_rounds_out, gc_stream stream);
+
 /* DEC-ADG-ITR colouring (Section 4.3) of given partitions
  * R(l) = {v : batch[v] = l}, l = 1..num_rounds (batch: device, n int32, any
  * partial order such as gc_adg_partition's or gc_adg_m_partition's):

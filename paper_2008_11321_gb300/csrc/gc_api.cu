@@ -429,6 +429,74 @@ gc_status gc_color_graph_m(gc_context* ctx, const gc_csr* g, uint64_t seed, int3
                             reinterpret_cast<cudaStream_t>(stream), true);
 }
 
+gc_status gc_adg_o_order(gc_context* ctx, const gc_csr* g, uint32_t eps_p, uint32_t eps_q, int32_t* batch_out,
+                         int32_t* rho_out, int32_t* rank_out, int32_t* num_rounds_out, gc_stream stream) {
+  if (!ctx) return GC_ERR_INVALID_ARG;
+  GC_TRY(check_graph_args(g));
+  GC_TRY(check_eps(eps_p, eps_q));
+  if (g->n > 0 && !rho_out) return GC_ERR_INVALID_ARG;
+  DeviceGuard guard(ctx->device);
+  CallScope scope(ctx);
+  if (!guard.ok) return GC_ERR_CUDA;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const long long n = g->n;
+  const size_t vb = static_cast<size_t>(n > 0 ? n : 1) * 4 + 256;
+  GC_TRY(ctx->reserve_vert(2 * vb));
+  int* D = static_cast<int*>(ctx->vbuf);
+  int* b = batch_out ? batch_out : reinterpret_cast<int*>(static_cast<char*>(ctx->vbuf) + vb);
+  GC_TRY(ctx->reserve(gc::adg_scratch_bytes(n, g->nnz)));
+  int rounds = 0;
+  GC_TRY(timing_begin(ctx, 0, s));
+  GC_TRY(gc::adg_run(ctx, ctx->arena(), g, eps_p, eps_q, b, D, &rounds, s));
+  GC_TRY(ctx->reserve(gc::adg_o_scratch_bytes(n)));
+  GC_TRY(gc::adg_o_order(ctx, ctx->arena(), g, b, D, rho_out, rank_out, s));
+  GC_TRY(timing_begin(ctx, 1, s));
+  GC_TRY_CUDA(cudaStreamSynchronize(s));
+  if (ctx->timing) ctx->stats.ms_adg = timing_ms(ctx, 0, 1);
+  if (num_rounds_out) *num_rounds_out = rounds;
+  return GC_OK;
+}
+
+gc_status gc_color_graph_o(gc_context* ctx, const gc_csr* g, uint32_t eps_p, uint32_t eps_q, int32_t* color_out,
+                           int32_t* batch_out, int32_t* num_colors_out, int32_t* num_rounds_out, gc_stream stream) {
+  if (!ctx) return GC_ERR_INVALID_ARG;
+  GC_TRY(check_graph_args(g));
+  GC_TRY(check_eps(eps_p, eps_q));
+  if (g->n > 0 && !color_out) return GC_ERR_INVALID_ARG;
+  DeviceGuard guard(ctx->device);
+  CallScope scope(ctx);
+  if (!guard.ok) return GC_ERR_CUDA;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const long long n = g->n;
+  const size_t vb = static_cast<size_t>(n > 0 ? n : 1) * 4 + 256;
+  GC_TRY(ctx->reserve_vert(2 * vb));
+  int* D = static_cast<int*>(ctx->vbuf);
+  int* b = batch_out ? batch_out : reinterpret_cast<int*>(static_cast<char*>(ctx->vbuf) + vb);
+  GC_TRY(ctx->reserve(gc::adg_scratch_bytes(n, g->nnz)));
+  int rounds = 0, colors = 0;
+  GC_TRY(timing_begin(ctx, 0, s));
+  GC_TRY(gc::adg_run(ctx, ctx->arena(), g, eps_p, eps_q, b, D, &rounds, s));
+  GC_TRY(timing_begin(ctx, 1, s));
+  // the key first in the arena (ADG's scratch is dead by now), JP after it
+  const size_t key_bytes = (static_cast<size_t>(n > 0 ? n : 1) * 8 + 255) & ~size_t(255);
+  GC_TRY(ctx->reserve(key_bytes + gc::jp_scratch_bytes(n, g->nnz)));
+  gc::Arena a = ctx->arena();
+  unsigned long long* key = a.take<unsigned long long>(n > 0 ? n : 1);
+  if (!key) return GC_ERR_OOM;
+  GC_TRY_CUDA(gc::adg_o_priority(b, D, n, key, ctx->num_sms, s));
+  GC_TRY(gc::jp_run_given(ctx, a, g, key, color_out, &colors, s));
+  GC_TRY(timing_begin(ctx, 2, s));
+  if (ctx->timing) {
+    GC_TRY_CUDA(cudaEventSynchronize(ctx->ev[2]));
+    ctx->stats.ms_adg = timing_ms(ctx, 0, 1);
+    ctx->stats.ms_jp = timing_ms(ctx, 1, 2);
+  }
+  ctx->stats.adg_rounds = rounds;
+  if (num_colors_out) *num_colors_out = colors;
+  if (num_rounds_out) *num_rounds_out = rounds;
+  return GC_OK;
+}
+
 gc_status gc_dec_itr_color(gc_context* ctx, const gc_csr* g, const int32_t* batch, int32_t num_rounds,
                            uint64_t seed, int32_t* color_out, int32_t* num_colors_out, gc_stream stream) {
   if (!ctx) return GC_ERR_INVALID_ARG;

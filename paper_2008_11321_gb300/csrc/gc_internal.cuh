@@ -135,6 +135,15 @@ gc_status jp_run_fused(gc_context* ctx, Arena a, const gc_csr* g, const int* bat
                        cudaStream_t s);
 gc_status jp_run_given(gc_context* ctx, Arena a, const gc_csr* g, const unsigned long long* prio,
                        int* color, int* num_colors_out, cudaStream_t s);
+// ADG-O (gc_adg_o.cu): rho (and, if rank is not null, the count of
+// higher-rho neighbours) from ADG's batches and degrees at removal; and
+// JP-ADG-O's key batch * 2^32 + D.
+size_t adg_o_scratch_bytes(long long n);
+gc_status adg_o_order(gc_context* ctx, Arena a, const gc_csr* g, const int* batch, const int* D, int* rho,
+                      int* rank, cudaStream_t s);
+cudaError_t adg_o_priority(const int* batch, const int* D, long long n, unsigned long long* key, int num_sms,
+                           cudaStream_t s);
+
 // DEC-ADG-ITR colouring of the partitions batch[] = 1..rounds (gc_dec.cu).
 // iters_out: SIM-COL iterations summed over the partitions.
 size_t dec_scratch_bytes(long long n, long long nnz, int rounds);

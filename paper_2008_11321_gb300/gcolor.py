@@ -26,7 +26,7 @@ EXPORTS = ("gc_status_str", "gc_create", "gc_destroy", "gc_get_stats", "gc_set_t
            "gc_validate_csr", "gc_adg_partition", "gc_make_priority", "gc_jp_color",
            "gc_color_graph", "gc_color_graph_host", "gc_adg_partition_noalloc", "gc_color_batch",
            "gc_color_batch_list", "gc_make_priority_kind", "gc_adg_m_partition", "gc_color_graph_m",
-           "gc_dec_itr_color", "gc_color_graph_dec_itr")
+           "gc_dec_itr_color", "gc_color_graph_dec_itr", "gc_adg_o_order", "gc_color_graph_o")
 
 # priority kinds of gc_make_priority_kind
 GC_PRIO_R, GC_PRIO_FF, GC_PRIO_LF, GC_PRIO_LLF = 0, 1, 2, 3
@@ -103,6 +103,10 @@ def load(path: str = LIB_PATH):
     lib.gc_adg_m_partition.argtypes = [vp, P(gc_csr), vp, P(i32), vp]
     lib.gc_color_graph_m.restype = ctypes.c_int
     lib.gc_color_graph_m.argtypes = [vp, P(gc_csr), u64, vp, vp, P(i32), P(i32), vp]
+    lib.gc_adg_o_order.restype = ctypes.c_int
+    lib.gc_adg_o_order.argtypes = [vp, P(gc_csr), u32, u32, vp, vp, vp, P(i32), vp]
+    lib.gc_color_graph_o.restype = ctypes.c_int
+    lib.gc_color_graph_o.argtypes = [vp, P(gc_csr), u32, u32, vp, vp, P(i32), P(i32), vp]
     lib.gc_dec_itr_color.restype = ctypes.c_int
     lib.gc_dec_itr_color.argtypes = [vp, P(gc_csr), vp, i32, u64, vp, P(i32), vp]
     lib.gc_color_graph_dec_itr.restype = ctypes.c_int
@@ -286,6 +290,25 @@ class Context:
         nc, nr = ctypes.c_int32(0), ctypes.c_int32(0)
         _check(self._lib.gc_color_graph_m(self.handle, ctypes.byref(c), seed, _ptr(color_out), _ptr(batch_out),
                                           ctypes.byref(nc), ctypes.byref(nr), _stream(stream)), "gc_color_graph_m")
+        return nc.value, nr.value
+
+    def gc_adg_o_order(self, g: DeviceGraph, eps_p: int, eps_q: int, rho_out, batch_out=None, rank_out=None,
+                       stream=None) -> int:
+        """ADG-O's total order rho (and batches, rank); returns the number of
+        iterations."""
+        c = g.csr()
+        nr = ctypes.c_int32(0)
+        _check(self._lib.gc_adg_o_order(self.handle, ctypes.byref(c), eps_p, eps_q, _ptr(batch_out), _ptr(rho_out),
+                                        _ptr(rank_out), ctypes.byref(nr), _stream(stream)), "gc_adg_o_order")
+        return nr.value
+
+    def gc_color_graph_o(self, g: DeviceGraph, eps_p: int, eps_q: int, color_out, batch_out=None, stream=None):
+        """JP-ADG-O; returns (num_colors, num_rounds)."""
+        c = g.csr()
+        nc, nr = ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(self._lib.gc_color_graph_o(self.handle, ctypes.byref(c), eps_p, eps_q, _ptr(color_out),
+                                          _ptr(batch_out), ctypes.byref(nc), ctypes.byref(nr), _stream(stream)),
+               "gc_color_graph_o")
         return nc.value, nr.value
 
     def gc_dec_itr_color(self, g: DeviceGraph, batch, num_rounds: int, seed: int, color_out, stream=None) -> int:

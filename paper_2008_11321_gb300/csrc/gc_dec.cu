@@ -159,40 +159,54 @@ dec_count_kernel(const long long* __restrict__ row_ptr, const int* __restrict__ 
                  bool packed, int* __restrict__ S, unsigned long long* __restrict__ bins, int* __restrict__ present,
                  DecCtl* ctl) {
   __shared__ unsigned sh[kDecBinsSmem];
+  __shared__ unsigned char sh_present[kDecBinsSmem / 3 + 1];
   __shared__ int any_iso;
   const long long nb = 3ll * (rounds + 1);
   const bool use_sh = nb <= kDecBinsSmem;
-  if (use_sh)
+  if (use_sh) {
     for (long long i = threadIdx.x; i < nb; i += blockDim.x) sh[i] = 0u;
+    for (long long i = threadIdx.x; i <= rounds; i += blockDim.x) sh_present[i] = 0;
+  }
   if (threadIdx.x == 0) any_iso = 0;
   __syncthreads();
   for (long long v = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; v < n;
        v += static_cast<long long>(gridDim.x) * blockDim.x) {
     const int b = batch[v];
     const long long d = row_ptr[v + 1] - row_ptr[v];
+    long long bin = -1;
     if (b < 1 || b > rounds) {
       atomicExch(&ctl->err, 1);
       S[v] = 0;
-      continue;
+    } else {
+      if (use_sh)
+        sh_present[b] = 1;
+      else
+        present[b] = 1;
+      const int word = packed ? static_cast<int>(static_cast<unsigned>(b) << 24) : 0;
+      if (d == 0) {  // isolated: B_v is empty and U has no neighbour, colour 1
+        S[v] = word | 1;
+        any_iso = 1;
+      } else {
+        S[v] = word;
+        bin = 3ll * b + bin_of(d);
+      }
     }
-    present[b] = 1;
-    const int word = packed ? static_cast<int>(static_cast<unsigned>(b) << 24) : 0;
-    if (d == 0) {  // isolated: B_v is empty and U has no neighbour, colour 1
-      S[v] = word | 1;
-      any_iso = 1;
-      continue;
+    // lanes with the same bin add once (the bins are few, so many coincide)
+    const unsigned peers = __match_any_sync(__activemask(), bin);
+    if (bin >= 0 && static_cast<int>(threadIdx.x & 31) == __ffs(peers) - 1) {
+      if (use_sh)
+        atomicAdd(&sh[bin], static_cast<unsigned>(__popc(peers)));
+      else
+        atomicAdd(&bins[bin], static_cast<unsigned long long>(__popc(peers)));
     }
-    S[v] = word;
-    const long long bin = 3ll * b + bin_of(d);
-    if (use_sh)
-      atomicAdd(&sh[bin], 1u);
-    else
-      atomicAdd(&bins[bin], 1ull);
   }
   __syncthreads();
-  if (use_sh)
+  if (use_sh) {
     for (long long i = threadIdx.x; i < nb; i += blockDim.x)
       if (sh[i]) atomicAdd(&bins[i], static_cast<unsigned long long>(sh[i]));
+    for (long long i = threadIdx.x; i <= rounds; i += blockDim.x)
+      if (sh_present[i]) present[i] = 1;
+  }
   if (threadIdx.x == 0 && any_iso) atomicMax(&ctl->max_color, 1);
 }
 
@@ -304,8 +318,7 @@ dec_place_kernel(const long long* __restrict__ row_ptr, const int* __restrict__ 
 
 // One block per partition (grid-stride over partitions): the chunk counts of
 // the partition's hubs as an inclusive prefix (hubpre, by position in
-// `order`), and the state their chunks accumulate into: B_v cleared, the
-// internal count and the count of finished chunks at 0.
+// `order`), and the internal count and the count of finished chunks at 0.
 __global__ void __launch_bounds__(kDecThreads)
 dec_hub_prep_kernel(const long long* __restrict__ row_ptr, const int* __restrict__ order, int rounds,
                     PartRange* __restrict__ part, long long* __restrict__ hubpre, int* __restrict__ hdone,
@@ -344,13 +357,26 @@ dec_hub_prep_kernel(const long long* __restrict__ row_ptr, const int* __restrict
       __syncthreads();
     }
     if (threadIdx.x == 0) p.hub_tasks = carry;
-    for (long long i = warp; i < nh; i += kWarps) {
+    __syncthreads();
+  }
+}
+
+// The hubs' bitmaps cleared before their chunks mark them: one warp per hub,
+// the whole GPU over every partition.
+__global__ void __launch_bounds__(kDecThreads)
+dec_hub_zero_kernel(const long long* __restrict__ row_ptr, const int* __restrict__ order, int rounds,
+                    const PartRange* __restrict__ part, unsigned* __restrict__ B) {
+  const int lane = threadIdx.x & 31;
+  const long long gw = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
+  for (int l = 1; l <= rounds; ++l) {
+    const long long nh = part[l].n_hub, off = part[l].off_hub;
+    for (long long i = gw; i < nh; i += nwarps) {
       const int v = order[off + i];
       const long long nw = (row_ptr[v + 1] - row_ptr[v] + 32) / 32;
       unsigned* Bv = B + bstart(row_ptr, v);
       for (long long j = lane; j < nw; j += 32) Bv[j] = 0u;
     }
-    __syncthreads();
   }
 }
 
@@ -1398,7 +1424,9 @@ gc_status dec_itr_run(gc_context* ctx, Arena a, const gc_csr* g, const int* batc
                                                                                             part, fill, order);
     const int hblocks = rounds < 4 * ctx->num_sms ? rounds : 4 * ctx->num_sms;
     dec_hub_prep_kernel<<<hblocks, kDecThreads, 0, s>>>(rp, order, rounds, part, hubpre, hdone, ideg, B);
-    g_launches += 4;
+    dec_hub_zero_kernel<<<resident_grid(dec_hub_zero_kernel, kDecThreads, ctx->num_sms), kDecThreads, 0, s>>>(
+        rp, order, rounds, part, B);
+    g_launches += 5;
     GC_TRY_CUDA(cudaGetLastError());
   }
   DecArgs A{};

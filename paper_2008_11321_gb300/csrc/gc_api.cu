@@ -477,14 +477,10 @@ gc_status gc_color_graph_o(gc_context* ctx, const gc_csr* g, uint32_t eps_p, uin
   GC_TRY(timing_begin(ctx, 0, s));
   GC_TRY(gc::adg_run(ctx, ctx->arena(), g, eps_p, eps_q, b, D, &rounds, s));
   GC_TRY(timing_begin(ctx, 1, s));
-  // the key first in the arena (ADG's scratch is dead by now), JP after it
+  // JP scratch (and a key array beyond 255 iterations) after ADG's, which is dead
   const size_t key_bytes = (static_cast<size_t>(n > 0 ? n : 1) * 8 + 255) & ~size_t(255);
   GC_TRY(ctx->reserve(key_bytes + gc::jp_scratch_bytes(n, g->nnz)));
-  gc::Arena a = ctx->arena();
-  unsigned long long* key = a.take<unsigned long long>(n > 0 ? n : 1);
-  if (!key) return GC_ERR_OOM;
-  GC_TRY_CUDA(gc::adg_o_priority(b, D, n, key, ctx->num_sms, s));
-  GC_TRY(gc::jp_run_given(ctx, a, g, key, color_out, &colors, s));
+  GC_TRY(gc::jp_run_ordered(ctx, ctx->arena(), g, b, D, rounds, color_out, &colors, s));
   GC_TRY(timing_begin(ctx, 2, s));
   if (ctx->timing) {
     GC_TRY_CUDA(cudaEventSynchronize(ctx->ev[2]));

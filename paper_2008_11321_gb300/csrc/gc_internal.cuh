@@ -135,6 +135,10 @@ gc_status jp_run_fused(gc_context* ctx, Arena a, const gc_csr* g, const int* bat
                        cudaStream_t s);
 gc_status jp_run_given(gc_context* ctx, Arena a, const gc_csr* g, const unsigned long long* prio,
                        int* color, int* num_colors_out, cudaStream_t s);
+// JP-ADG-O: JP in the exact order (batch, D, id) descending, D = degree at
+// removal from adg_run.  Scratch: jp_scratch_bytes(n, nnz) + 8n.
+gc_status jp_run_ordered(gc_context* ctx, Arena a, const gc_csr* g, const int* batch, const int* D, int rounds,
+                         int* color, int* num_colors_out, cudaStream_t s);
 // ADG-O (gc_adg_o.cu): rho (and, if rank is not null, the count of
 // higher-rho neighbours) from ADG's batches and degrees at removal; and
 // JP-ADG-O's key batch * 2^32 + D.

@@ -129,6 +129,31 @@ struct KeyPacked {  // JP-ADG over many disjoint graphs: rho_R precomputed per v
   __device__ __forceinline__ int cword(unsigned long long, int c) const { return c; }
 };
 
+// JP-ADG-O: the priority (batch, D at removal, id), with the batch kept in
+// the top 8 bits of the colour word as in KeyState; D is read only for a
+// neighbour of the same batch.
+struct KeyStateD {
+  const int* state;  // the colour array during JP-ADG-O
+  const int* D;
+  __device__ __forceinline__ unsigned long long operator()(int v) const {
+    return (static_cast<unsigned long long>(static_cast<unsigned>(__ldg(state + v)) >> 24) << 32) |
+           static_cast<unsigned>(__ldg(D + v));
+  }
+  using PG = int;
+  __device__ __forceinline__ PG pgather(int w, const int* color) const { return ld_relaxed(color + w); }
+  __device__ __forceinline__ bool pred_g(PG x, int w, unsigned long long kv, int v) const {
+    const unsigned bw = static_cast<unsigned>(x) >> 24, bv = static_cast<unsigned>(kv >> 32);
+    if (bw != bv) return bw > bv;
+    const unsigned dw = static_cast<unsigned>(__ldg(D + w)), dv = static_cast<unsigned>(kv);
+    return dw > dv || (dw == dv && w > v);
+  }
+  __device__ __forceinline__ int color_g(PG x, const int*, int) const { return x & 0xffffff; }
+  __device__ __forceinline__ int cmask() const { return 0xffffff; }
+  __device__ __forceinline__ int cword(unsigned long long kv, int c) const {
+    return static_cast<int>(static_cast<unsigned>(kv >> 32) << 24) | c;
+  }
+};
+
 struct KeyGiven {  // any priority array
   const unsigned long long* prio;
   __device__ __forceinline__ unsigned long long operator()(int v) const { return __ldg(prio + v); }
@@ -414,6 +439,26 @@ __global__ void jp_split_kernel(const int* __restrict__ order, const long long* 
       plist[pos[i]] = v;
     else
       plist[nbig + (i - pos[i])] = v;
+  }
+}
+
+// Ordered path: where each batch starts in the rest of the order (sorted by
+// batch), as positions in the warp-path list (pos) and the lane-path list
+// (i - pos); -1 for batches with no vertex there.
+__global__ void jpo_first_kernel(const int* __restrict__ order, long long n, const int* __restrict__ batch,
+                                 int* __restrict__ first) {
+  for (long long i = gtid(); i < n; i += gstride()) {
+    const int b = batch[static_cast<unsigned>(order[i]) & ~kBigBit];
+    if (i == 0 || batch[static_cast<unsigned>(order[i - 1]) & ~kBigBit] != b) first[b] = static_cast<int>(i);
+  }
+}
+
+__global__ void jpo_bounds_kernel(const int* __restrict__ first, const long long* __restrict__ pos, int rounds,
+                                  long long* __restrict__ bounds) {
+  for (long long b = gtid(); b <= rounds; b += gstride()) {
+    const int f = first[b];
+    bounds[2 * b] = f < 0 ? -1 : pos[f];
+    bounds[2 * b + 1] = f < 0 ? -1 : f - pos[f];
   }
 }
 
@@ -1158,6 +1203,17 @@ size_t jp_scratch_bytes(long long n, long long nnz) {
 }
 
 namespace {
+// KeyState: colour words start as batch << 24 (colour 0) and lose the batch
+// bits at the end.
+__global__ void state_init_kernel(const int* __restrict__ batch, long long n, int* __restrict__ color) {
+  for (long long v = gtid(); v < n; v += gstride())
+    color[v] = static_cast<int>(static_cast<unsigned>(batch[v]) << 24);
+}
+
+__global__ void state_strip_kernel(long long n, int* __restrict__ color) {
+  for (long long v = gtid(); v < n; v += gstride()) color[v] &= 0xffffff;
+}
+
 // Core of the generic path: the first kc entries of the sorted order (vertex
 // ids with the warp-path flag) as plain ids, and their core positions.
 __global__ void jp_core_from_sorted_kernel(const int* __restrict__ order, long long kc, int* __restrict__ corder,
@@ -1171,8 +1227,12 @@ __global__ void jp_core_from_sorted_kernel(const int* __restrict__ order, long l
 }
 }  // namespace
 
-gc_status jp_run_given(gc_context* ctx, Arena a, const gc_csr* g, const unsigned long long* prio,
-                       int* color, int* num_colors_out, cudaStream_t s) {
+// Exact order of `key` (radix sort), the top of it by the core cluster, the
+// rest by one bulk launch.  With `state` (KeyStateD), colour words start as
+// batch << 24 (state_batch) and lose those bits at the end.
+template <class Key>
+gc_status jp_run_exact(gc_context* ctx, Arena a, const gc_csr* g, const Key& key, const int* state_batch,
+                       const int* core_D, int* color, int* num_colors_out, cudaStream_t s, int rounds = 0) {
   const long long n = g->n;
   if (num_colors_out) *num_colors_out = 0;
   ctx->stats.num_colors = 0;
@@ -1201,10 +1261,13 @@ gc_status jp_run_given(gc_context* ctx, Arena a, const gc_csr* g, const unsigned
       !cb.lid || !cb.cbits || !cb.cap || !cb.toff || !cb.pcnt || !cb.task_i || !cb.task_start || !cb.task_len)
     return GC_ERR_OOM;
   const long long* rp = row_ptr_of(g);
-  const KeyGiven key{prio};
   const int blocks = ctx->num_sms * 8;
   jp_init_kernel<<<1, 1, 0, s>>>(ctl, ctx->wait_ns, ctx->stall_vertex);
   ++g_launches;
+  if (state_batch) {
+    state_init_kernel<<<blocks, 256, 0, s>>>(state_batch, n, color);
+    ++g_launches;
+  }
   jp_keys_kernel<<<blocks, 256, 0, s>>>(key, rp, n, sb.keys[0], sb.vals[0], ctl);
   ++g_launches;
   GC_TRY_CUDA(cudaGetLastError());
@@ -1222,12 +1285,12 @@ gc_status jp_run_given(gc_context* ctx, Arena a, const gc_csr* g, const unsigned
   const int* order = sb.vals[res];
   long long* pos = reinterpret_cast<long long*>(sb.keys[res ^ 1]);
   int* plist = sb.vals[res ^ 1];
-  GC_TRY_CUDA(cudaMemsetAsync(color, 0, sizeof(int) * n, s));
+  if (!state_batch) GC_TRY_CUDA(cudaMemsetAsync(color, 0, sizeof(int) * n, s));
   if (kc > 0) {  // the top kc vertices: exact order known, coloured by the core cluster
     jp_core_from_sorted_kernel<<<blocks, 256, 0, s>>>(order, kc, corder, cb.lid, ctl);
     ++g_launches;
     GC_TRY_CUDA(cudaGetLastError());
-    GC_TRY(run_core(ctx, g, corder, nullptr, kc, ctl, cb, color, s));
+    GC_TRY(run_core(ctx, g, corder, core_D, kc, ctl, cb, color, s));
   }
   // the rest: warp-path list first, then the lane-path list, each in order
   const long long nrest = n - kc;
@@ -1243,12 +1306,74 @@ gc_status jp_run_given(gc_context* ctx, Arena a, const gc_csr* g, const unsigned
     jp_count_kernel<<<1, 1, 0, s>>>(pos, nrest, ctl);
     ++g_launches;
     GC_TRY_CUDA(cudaGetLastError());
-    ctx->timer_begin(gc_context::kTBulk, s);
-    GC_TRY_CUDA(launch_bulk(ctx, ctl, &ctl->big_cursor, rp, g->col_idx, key, plist, -1, nullptr, 0, color, s));
-    ctx->timer_end(s);
-    ctx->stats.bulk_launches = 1;
+    if (rounds > 0) {
+      // ordered by batch first: one launch per batch from the top, so that a
+      // vertex only waits on earlier vertices of its own batch
+      int* first = a.take<int>(static_cast<size_t>(rounds) + 1);
+      long long* bounds = a.take<long long>(2 * (static_cast<size_t>(rounds) + 1));
+      unsigned long long* cur = a.take<unsigned long long>(2 * (static_cast<size_t>(rounds) + 1));
+      if (!first || !bounds || !cur) return GC_ERR_OOM;
+      GC_TRY_CUDA(cudaMemsetAsync(first, 0xff, sizeof(int) * (rounds + 1), s));
+      GC_TRY_CUDA(cudaMemsetAsync(cur, 0, sizeof(unsigned long long) * 2 * (rounds + 1), s));
+      jpo_first_kernel<<<blocks, 256, 0, s>>>(rest, nrest, state_batch, first);
+      jpo_bounds_kernel<<<(rounds + 256) / 256, 256, 0, s>>>(first, pos, rounds, bounds);
+      g_launches += 2;
+      GC_TRY_CUDA(cudaGetLastError());
+      std::vector<long long> hb(2 * (static_cast<size_t>(rounds) + 1));
+      GC_TRY_CUDA(cudaMemcpyAsync(hb.data(), bounds, sizeof(long long) * hb.size(), cudaMemcpyDeviceToHost, s));
+      GC_TRY_CUDA(cudaMemcpyAsync(ctx->pinned, ctl, sizeof(JpCtl), cudaMemcpyDeviceToHost, s));
+      GC_TRY_CUDA(cudaStreamSynchronize(s));
+      const long long nbig = static_cast<long long>(static_cast<JpCtl*>(ctx->pinned)->nbig);
+      const long long nsmall = nrest - nbig;
+      long long end_b = nbig, end_s = nsmall;  // ends of the next batch up's ranges
+      // batches from the lowest up, so each knows where the one below starts
+      std::vector<long long> lo_b(rounds + 1, -1), hi_b(rounds + 1), lo_s(rounds + 1), hi_s(rounds + 1);
+      for (int bt = 1; bt <= rounds; ++bt) {
+        if (hb[2 * bt] < 0) continue;
+        lo_b[bt] = hb[2 * bt];
+        lo_s[bt] = hb[2 * bt + 1];
+        hi_b[bt] = end_b;
+        hi_s[bt] = end_s;
+        end_b = lo_b[bt];
+        end_s = lo_s[bt];
+      }
+      ctx->stats.bulk_launches = 0;
+      for (int bt = rounds; bt >= 1; --bt) {
+        if (lo_b[bt] < 0) continue;
+        ctx->timer_begin(gc_context::kTBulk, s);
+        GC_TRY_CUDA(launch_bulk(ctx, ctl, cur + 2 * bt, rp, g->col_idx, key, plist + lo_b[bt], hi_b[bt] - lo_b[bt],
+                                plist + nbig + lo_s[bt], hi_s[bt] - lo_s[bt], color, s));
+        ctx->timer_end(s);
+        ++ctx->stats.bulk_launches;
+      }
+    } else {
+      ctx->timer_begin(gc_context::kTBulk, s);
+      GC_TRY_CUDA(launch_bulk(ctx, ctl, &ctl->big_cursor, rp, g->col_idx, key, plist, -1, nullptr, 0, color, s));
+      ctx->timer_end(s);
+      ctx->stats.bulk_launches = 1;
+    }
+  }
+  if (state_batch) {
+    state_strip_kernel<<<blocks, 256, 0, s>>>(n, color);
+    ++g_launches;
+    GC_TRY_CUDA(cudaGetLastError());
   }
   return finish_jp(ctx, ctl, num_colors_out, s);
+}
+
+gc_status jp_run_given(gc_context* ctx, Arena a, const gc_csr* g, const unsigned long long* prio,
+                       int* color, int* num_colors_out, cudaStream_t s) {
+  return jp_run_exact(ctx, a, g, KeyGiven{prio}, nullptr, nullptr, color, num_colors_out, s);
+}
+
+gc_status jp_run_ordered(gc_context* ctx, Arena a, const gc_csr* g, const int* batch, const int* D, int rounds,
+                         int* color, int* num_colors_out, cudaStream_t s) {
+  if (rounds <= 255)  // the batch fits the colour word
+    return jp_run_exact(ctx, a, g, KeyStateD{color, D}, batch, D, color, num_colors_out, s, rounds);
+  unsigned long long* key = a.take<unsigned long long>(g->n > 0 ? g->n : 1);
+  if (!key) return GC_ERR_OOM;
+  GC_TRY_CUDA(adg_o_priority(batch, D, g->n, key, ctx->num_sms, s));
+  return jp_run_exact(ctx, a, g, KeyGiven{key}, nullptr, D, color, num_colors_out, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -1267,17 +1392,6 @@ size_t jpadg_scratch_bytes(long long n, long long nnz, int rounds) {
 }
 
 namespace {
-// KeyState: colour words start as batch << 24 (colour 0) and lose the batch
-// bits at the end.
-__global__ void state_init_kernel(const int* __restrict__ batch, long long n, int* __restrict__ color) {
-  for (long long v = gtid(); v < n; v += gstride())
-    color[v] = static_cast<int>(static_cast<unsigned>(batch[v]) << 24);
-}
-
-__global__ void state_strip_kernel(long long n, int* __restrict__ color) {
-  for (long long v = gtid(); v < n; v += gstride()) color[v] &= 0xffffff;
-}
-
 template <class Key>
 gc_status jp_adg_impl(gc_context* ctx, Arena a, const gc_csr* g, const Key& key, const int* D,
                       int rounds, int* color, int* num_colors_out, cudaStream_t s) {

@@ -97,6 +97,8 @@ KERNEL_TRAFFIC = {
     ("rmat24", "jpf_core_solve_kernel"): 35.0e6,
     ("rmat24", "adg_update_kernel"): 350.5e6,
     ("rmat24", "jp_color_kernel"): 1125.5e6,
+    # profiles/launches_dec_itr_rmat24.md (mean over its 7 launches)
+    ("rmat24", "dec_extract_kernel"): 657.7e6,
 }
 
 
@@ -373,7 +375,8 @@ def run_dec(args, rank, world):
                    "internal_entries": inner,
                    "l2": f"inputs larger than L2 (col_idx {4 * nnz / 1e9:.2f} GB), no flush"},
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": KERNEL_TRAFFIC.get((args.workload, kname)),
                      "algorithmic_bytes_per_launch": gb[kname] / kl, "ms_per_launch": kms / kl,
                      "launches_per_step": kl,
                      "groups_ms": {"adg_update_kernel": mean("ms_adg_update"),

@@ -993,7 +993,7 @@ constexpr int kTailMax = 4096;  // |U| at most (16-bit local ids)
 constexpr int kTailThreads = 1024;
 constexpr int kTailClusterMax = 16;
 constexpr int kTailSmem = 200 * 1024;
-// replica, hashes and split prefix (4 B each per local id) and counters
+// replica, hashes and split prefix (4 B each per local id) and flag words
 constexpr int kTailFixed = 12 * kTailMax + 4 + 64;
 // per owned vertex: global id, window word index, window word, list length,
 // bitmap words (20 B), so a vertex with d list entries takes 2 (d + 10) bytes
@@ -1024,14 +1024,6 @@ __device__ __forceinline__ unsigned tail_map(const void* p, unsigned rank) {
 }
 __device__ __forceinline__ void tail_st(unsigned addr, unsigned v) {
   asm volatile("st.relaxed.cluster.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
-}
-__device__ __forceinline__ void tail_add(unsigned addr, unsigned v) {
-  asm volatile("red.relaxed.cluster.shared::cluster.add.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
-}
-__device__ __forceinline__ unsigned tail_ld(unsigned addr) {
-  unsigned v;
-  asm volatile("ld.relaxed.cluster.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
-  return v;
 }
 
 // Largest per-CTA shared memory for the owned vertices of a split of U (u
@@ -1156,12 +1148,10 @@ dec_tail_kernel(DecArgs A, int slot, int l) {
   tail_sync();  // every replica complete before any remote write
 
   // 4. iterations
-  const unsigned sc0 = tail_map(sc, 0);  // CTA 0's counters
   int it = 0, local_max = 0;
   for (;;) {
     // pick: fixed neighbours into B_v (the window word, or B_v above it),
     // out of the list; draw the smallest free colour
-    if (rank == 0 && threadIdx.x == 0) sc[(it + 1) % 3] = 0u;
     for (int a = warp; a < o; a += nwarps) {
       const int i = lo + a;
       if (!(st[i] & kTent)) continue;
@@ -1207,7 +1197,6 @@ dec_tail_kernel(DecArgs A, int slot, int l) {
     }
     tail_sync();
     // check: keep the draw unless a higher-key neighbour in U drew it too
-    unsigned rem = 0;
     for (int a = warp; a < o; a += nwarps) {
       const int i = lo + a;
       const unsigned xi = st[i];
@@ -1225,15 +1214,16 @@ dec_tail_kernel(DecArgs A, int slot, int l) {
         if (lane < C) tail_st(tail_map(&st[i], lane), t);
         if (lane == 0) st_relaxed(A.S + o_gv[a], state_word<Packed>(l, static_cast<int>(t)));
         local_max = static_cast<int>(t) > local_max ? static_cast<int>(t) : local_max;
-      } else if (lane == 0) {
-        ++rem;
       }
     }
-    if (lane == 0 && rem) tail_add(sc0 + 4u * static_cast<unsigned>(it % 3), rem);
     tail_sync();
-    const unsigned remaining = tail_ld(sc0 + 4u * static_cast<unsigned>(it % 3));
+    // every replica now holds the same flags: each CTA sees alone whether U
+    // is empty (the next pick rewrites only words that stay tentative)
+    int left = 0;
+    for (int i = threadIdx.x; i < u; i += blockDim.x) left |= static_cast<int>(st[i] & kTent);
+    left = __syncthreads_or(left);
     ++it;
-    if (remaining == 0u) break;
+    if (!left) break;
     if (it > u) {  // cannot happen: every iteration keeps the highest key of U
       if (rank == 0 && threadIdx.x == 0) atomicExch(&ctl->err, 2);
       break;

@@ -451,8 +451,10 @@ gc_status gc_adg_o_order(gc_context* ctx, const gc_csr* g, uint32_t eps_p, uint3
   GC_TRY(ctx->reserve(gc::adg_o_scratch_bytes(n)));
   GC_TRY(gc::adg_o_order(ctx, ctx->arena(), g, b, D, rho_out, rank_out, s));
   GC_TRY(timing_begin(ctx, 1, s));
-  GC_TRY_CUDA(cudaStreamSynchronize(s));
-  if (ctx->timing) ctx->stats.ms_adg = timing_ms(ctx, 0, 1);
+  if (ctx->timing) {
+    GC_TRY_CUDA(cudaEventSynchronize(ctx->ev[1]));
+    ctx->stats.ms_adg = timing_ms(ctx, 0, 1);
+  }
   if (num_rounds_out) *num_rounds_out = rounds;
   return GC_OK;
 }

@@ -49,6 +49,13 @@ def test_null_arguments_rejected_without_device_work(lib):
         gcp.GC_ERR_INVALID_ARG
     assert lib.gc_color_graph(None, None, 1, 100, 42, None, None, None, None, None) == gcp.GC_ERR_INVALID_ARG
     assert lib.gc_create(None, 0) == gcp.GC_ERR_INVALID_ARG
+    for call in (lambda: lib.gc_dec_itr_color(None, None, None, 1, 42, None, None, None),
+                 lambda: lib.gc_color_graph_dec_itr(None, None, 1, 100, 42, None, None, None, None, None),
+                 lambda: lib.gc_adg_o_order(None, None, 1, 100, None, None, None, None, None),
+                 lambda: lib.gc_color_graph_o(None, None, 1, 100, None, None, None, None, None),
+                 lambda: lib.gc_adg_m_partition(None, None, None, None, None),
+                 lambda: lib.gc_color_graph_m(None, None, 42, None, None, None, None, None)):
+        assert call() == gcp.GC_ERR_INVALID_ARG
     st = gcp.gcolor.gc_stats()
     assert lib.gc_get_stats(None, ctypes.byref(st)) == gcp.GC_ERR_INVALID_ARG
     lib.gc_destroy(None)  # a no-op

@@ -173,9 +173,11 @@ class ClockSampler:
                 "samples": len(sms)}
 
 
-def cpu_baseline(w_name, seconds_target=10.0, median=False, dec=False, ordered=False):
+def cpu_baseline(w_name, seconds_target=10.0, median=False, dec=False, ordered=False, itr=False):
     """The oracle as it stands, single-threaded, on a bounded sample of the
     same family (R-MAT scale 22 for the R-MAT workloads)."""
+    import numpy as np
+
     import graphgen as gg
     import oracle
     w = WORKLOADS[w_name]
@@ -195,6 +197,8 @@ def cpu_baseline(w_name, seconds_target=10.0, median=False, dec=False, ordered=F
         t0 = time.perf_counter()
         if median:
             oracle.jp_adg_m(g, w["seed"])
+        elif itr:
+            oracle.dec_itr(g, np.ones(g.n, dtype=np.int32), 1, w["seed"])
         elif dec:
             oracle.dec_adg_itr(g, p, q, w["seed"])
         elif ordered:
@@ -203,8 +207,8 @@ def cpu_baseline(w_name, seconds_target=10.0, median=False, dec=False, ordered=F
             oracle.jp_adg(g, p, q, w["seed"])
         total += time.perf_counter() - t0
         reps += 1
-    what = ("ADG-M + Greedy" if median else "ADG + DEC-ADG-ITR" if dec else "ADG-O + Greedy" if ordered
-            else "ADG + Greedy")
+    what = ("ADG-M + Greedy" if median else "ITR (one partition)" if itr else "ADG + DEC-ADG-ITR" if dec
+            else "ADG-O + Greedy" if ordered else "ADG + Greedy")
     return {"value": g.m * reps / total, "unit": "edges/s", "cores": 1, "kind": "oracle",
             "sample": f"{desc}: n={g.n}, m={g.m}, {reps} run(s) of {what}, {total:.1f} s"}
 
@@ -298,7 +302,9 @@ def run_variant(args, rank, world):
 def run_dec(args, rank, world):
     """DEC-ADG-ITR (Section 4.3): one step is gc_color_graph_dec_itr (ADG,
     then the partitions coloured from the top by SIM-COL in its ITR form) on
-    the resident graph."""
+    the resident graph.  --algo itr: the same colouring with every vertex in
+    one partition (plain ITR, the paper's point of comparison), through
+    gc_dec_itr_color."""
     import torch
     import torch.distributed as dist
     from paper_2008_11321_gb300 import _build
@@ -320,10 +326,18 @@ def run_dec(args, rank, world):
     dg = gcp.DeviceGraph(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col_idx).to(dev))
     color = torch.empty(n, dtype=torch.int32, device=dev)
     batch = torch.empty(n, dtype=torch.int32, device=dev)
+    itr = args.algo == "itr"
+    ones = torch.ones(n, dtype=torch.int32, device=dev)
     ctx = gcp.Context(local)
     stream = torch.cuda.current_stream(dev)
+
+    def colour_step():
+        if itr:
+            return ctx.gc_dec_itr_color(dg, ones, 1, seed, color), 1
+        return ctx.gc_color_graph_dec_itr(dg, p, q, seed, color, batch)
+
     for _ in range(args.warmup):
-        nc, nr = ctx.gc_color_graph_dec_itr(dg, p, q, seed, color, batch)
+        nc, nr = colour_step()
     ctx.gc_set_timing(True)
     sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
     sampler.start()
@@ -335,7 +349,7 @@ def run_dec(args, rank, world):
     ev0.record(stream)
     steps = []
     for _ in range(args.steps):
-        nc, nr = ctx.gc_color_graph_dec_itr(dg, p, q, seed, color, batch)
+        nc, nr = colour_step()
         st = ctx.gc_get_stats()
         steps.append({k: getattr(st, k) for k, _ in st._fields_})
     ev1.record(stream)
@@ -362,21 +376,26 @@ def run_dec(args, rank, world):
           "dec_extract_kernel": 24 * n_nonisolated + 8 * nnz + 4 * inner}
     groups = {"adg_update_kernel": (mean("ms_adg_update"), last["adg_rounds"]),
               "dec_extract_kernel": (mean("ms_dec_extract"), last["adg_rounds"])}
+    if itr:
+        groups.pop("adg_update_kernel")
     kname = max(groups, key=lambda k: groups[k][0])
     kms, kl = groups[kname]
+    if itr:
+        kl = 1
     achieved = gb[kname] / (kms / 1e3) / 1e9 if kms > 0 else 0.0
     line = {
         "metric": METRIC, "value": m * args.steps * world / t_max, "unit": "edges/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": w["desc"], "algorithm": "DEC-ADG-ITR", "n": n, "m": m, "eps": f"{p}/{q}",
+        "config": {"workload": w["desc"], "algorithm": "ITR (one partition)" if itr else "DEC-ADG-ITR", "n": n,
+                   "m": m, "eps": None if itr else f"{p}/{q}",
                    "seed": seed, "adg_rounds": nr, "num_colors": nc, "sim_iterations": last["sim_iterations"],
                    "internal_entries": inner,
                    "l2": f"inputs larger than L2 (col_idx {4 * nnz / 1e9:.2f} GB), no flush"},
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": KERNEL_TRAFFIC.get((args.workload, kname)),
+                     "traffic": None if itr else KERNEL_TRAFFIC.get((args.workload, kname)),
                      "algorithmic_bytes_per_launch": gb[kname] / kl, "ms_per_launch": kms / kl,
                      "launches_per_step": kl,
                      "groups_ms": {"adg_update_kernel": mean("ms_adg_update"),
@@ -387,7 +406,7 @@ def run_dec(args, rank, world):
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.workload, dec=True)
+        line["cpu_baseline"] = cpu_baseline(args.workload, dec=True, itr=itr)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -653,8 +672,9 @@ def main():
     ap.add_argument("--priority", choices=["adg", "adg-m", "adg-o"] + sorted(PRIORITIES), default="adg",
                     help="JP priority: adg (JP-ADG, the default), adg-m (JP-ADG-M), adg-o (JP-ADG-O) or "
                          "another JP variant")
-    ap.add_argument("--algo", choices=["jp", "dec-itr"], default="jp",
-                    help="colouring: jp (JP with --priority, the default) or dec-itr (DEC-ADG-ITR)")
+    ap.add_argument("--algo", choices=["jp", "dec-itr", "itr"], default="jp",
+                    help="colouring: jp (JP with --priority, the default), dec-itr (DEC-ADG-ITR) or itr "
+                         "(its SIM-COL on one partition: plain ITR)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: --warmup below 3 is outside the timing rules", file=sys.stderr)
@@ -665,7 +685,7 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args, rank, world)
-    if args.algo == "dec-itr":
+    if args.algo in ("dec-itr", "itr"):
         if WORKLOADS[args.workload]["kind"] in ("batch", "serve") or args.priority != "adg":
             ap.error("--algo dec-itr applies to the single-graph workloads, without --priority")
         return run_dec(args, rank, world)

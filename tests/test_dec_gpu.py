@@ -150,6 +150,15 @@ def test_dec_itr_given_partitions(ctx):
         assert np.array_equal(c, oc) and nc == onc and it == oit, g.name
 
 
+def test_itr_one_partition(ctx):
+    # every vertex in one partition: plain ITR, the paper's comparison point
+    for g in (gg.rmat(16, 16, seed=4), gg.barabasi_albert(20000, 8, 1), complete(200)):
+        ones = np.ones(g.n, dtype=np.int32)
+        oc, onc, oit, _ = oracle.dec_itr(g, ones, 1, 42)
+        c, nc, it = _given(ctx, g, ones, 1)
+        assert np.array_equal(c, oc) and nc == onc and it == oit, g.name
+
+
 def test_dec_itr_rejects_bad_partitions(ctx):
     g = path(6)
     for batch, rounds in (([1, 2, 3, 3, 2, 1], 2), ([0, 1, 1, 1, 1, 1], 3), ([1] * 6, 0)):

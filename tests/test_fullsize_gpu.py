@@ -1,7 +1,8 @@
 """Full-size workloads, in the configuration the benchmark times
 (gc_color_graph on a device-resident graph, eps = 1/100, tie-break seed 42),
 compared with the oracle on every vertex: batch ids, round count, colours
-and colour count bit for bit."""
+and colour count bit for bit; and R-MAT 24 through DEC-ADG-ITR and JP-ADG-O
+in the configurations of their benchmark modes."""
 from __future__ import annotations
 
 import numpy as np
@@ -44,9 +45,41 @@ def _check(ctx, g):
     assert np.array_equal(c, oc)
 
 
-def test_rmat24_full(ctx):
+@pytest.fixture(scope="module")
+def rmat24():
     # R-MAT scale 24, edge factor 16, (a,b,c,d) = (.57,.19,.19,.05)
-    _check(ctx, gg.rmat(24, 16, seed=1))
+    return gg.rmat(24, 16, seed=1)
+
+
+def test_rmat24_full(ctx, rmat24):
+    _check(ctx, rmat24)
+
+
+def test_rmat24_dec_itr_full(ctx, rmat24):
+    # bench.py --algo dec-itr: gc_color_graph_dec_itr, eps = 1/100, seed 42
+    g = rmat24
+    dg = gcp.DeviceGraph.from_host(g, "cuda:0")
+    color = torch.empty(g.n, dtype=torch.int32, device="cuda:0")
+    nc, nr = ctx.gc_color_graph_dec_itr(dg, 1, 100, 42, color)
+    it = ctx.gc_get_stats().sim_iterations
+    c = color.cpu().numpy()
+    del dg, color
+    _, oc, onr, onc, oit, _ = oracle.dec_adg_itr(g, 1, 100, 42)
+    assert (nr, nc, it) == (onr, onc, oit)
+    assert np.array_equal(c, oc)
+
+
+def test_rmat24_adg_o_full(ctx, rmat24):
+    # bench.py --priority adg-o: gc_color_graph_o, eps = 1/100
+    g = rmat24
+    dg = gcp.DeviceGraph.from_host(g, "cuda:0")
+    color = torch.empty(g.n, dtype=torch.int32, device="cuda:0")
+    nc, nr = ctx.gc_color_graph_o(dg, 1, 100, color)
+    c = color.cpu().numpy()
+    del dg, color
+    _, _, oc, onr, onc = oracle.jp_adg_o(g, 1, 100)
+    assert (nr, nc) == (onr, onc)
+    assert np.array_equal(c, oc)
 
 
 def test_grid256_permuted_full(ctx):

@@ -112,6 +112,33 @@ def load_peak():
         return 6800.0, "fallback"
 
 
+def sync_ranks(world, dev=None):
+    """Bracket of a timed region: a barrier across the ranks (when there are
+    several) and a synchronise of this rank's device."""
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.barrier()
+    if dev is not None:
+        torch.cuda.synchronize(dev)
+
+
+def max_over_ranks(seconds, world, device="cpu"):
+    """The slowest rank's time: every rank passes its own and gets the max."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_step, steps, world, t_max):
+    """Whole-job throughput of `world` replicas that each processed
+    units_per_step units per step for `steps` steps in t_max seconds."""
+    return units_per_step * steps * world / t_max
+
+
 def make_graph(w, pinned=False):
     import graphgen as gg
     if w["kind"] == "rmat":
@@ -249,9 +276,7 @@ def run_variant(args, rank, world):
     sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
     sampler.start()
     time.sleep(0.3)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
+    sync_ranks(world, dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     launches, bulk_ms = 0, 0.0
@@ -263,12 +288,9 @@ def run_variant(args, rank, world):
         launches += st.launches
         bulk_ms += st.ms_jp_color
     ev1.record(stream)
-    torch.cuda.synchronize(dev)
+    sync_ranks(world, dev)
     clocks = sampler.stop()
-    t = torch.tensor([ev0.elapsed_time(ev1) / 1e3], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    t_max = float(t.item())
+    t_max = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, world, dev)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -280,7 +302,7 @@ def run_variant(args, rank, world):
     kms = bulk_ms / args.steps
     achieved = kbytes / (kms / 1e3) / 1e9 if kms > 0 else 0.0
     line = {
-        "metric": METRIC, "value": m * args.steps * world / t_max, "unit": "edges/s", "n_gpus": world,
+        "metric": METRIC, "value": job_rate(m, args.steps, world, t_max), "unit": "edges/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
@@ -342,9 +364,7 @@ def run_dec(args, rank, world):
     sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
     sampler.start()
     time.sleep(0.3)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
+    sync_ranks(world, dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     steps = []
@@ -353,12 +373,9 @@ def run_dec(args, rank, world):
         st = ctx.gc_get_stats()
         steps.append({k: getattr(st, k) for k, _ in st._fields_})
     ev1.record(stream)
-    torch.cuda.synchronize(dev)
+    sync_ranks(world, dev)
     clocks = sampler.stop()
-    t = torch.tensor([ev0.elapsed_time(ev1) / 1e3], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    t_max = float(t.item())
+    t_max = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, world, dev)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -384,7 +401,7 @@ def run_dec(args, rank, world):
         kl = 1
     achieved = gb[kname] / (kms / 1e3) / 1e9 if kms > 0 else 0.0
     line = {
-        "metric": METRIC, "value": m * args.steps * world / t_max, "unit": "edges/s", "n_gpus": world,
+        "metric": METRIC, "value": job_rate(m, args.steps, world, t_max), "unit": "edges/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
@@ -500,14 +517,19 @@ def run_batch(args, rank, world):
     same GPU (graphs/s both ways, colourings checked identical)."""
     import numpy as np
     import torch
+    import torch.distributed as dist
     import graphgen as gg
     from paper_2008_11321_gb300 import _build
-    if rank == 0:
-        _build.build()
-    import paper_2008_11321_gb300 as gcp
-    w = WORKLOADS[args.workload]
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
+    if world > 1:  # replicas: every rank colours its own copy of the batch
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    import paper_2008_11321_gb300 as gcp
+    w = WORKLOADS[args.workload]
     G = w["count"]
     g, off = gg.batch(G, w["n_lo"], w["n_hi"], w["seed"], pinned=True)
     p, q = w["eps"]
@@ -524,16 +546,16 @@ def run_batch(args, rank, world):
     sampler.start()
     time.sleep(0.3)
     launches = 0
-    torch.cuda.synchronize(dev)
+    sync_ranks(world, dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
         ctx.gc_color_batch(db, jobs, color, None, ncol)
         launches += ctx.gc_get_stats().launches
     e1.record(stream)
-    torch.cuda.synchronize(dev)
+    sync_ranks(world, dev)
     clocks = sampler.stop()
-    t_batch = e0.elapsed_time(e1) / 1e3 / args.steps
+    t_batch = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, dev) / args.steps
     # per-graph plain launches of the same graphs (local ids), one pass
     rp, ci = g.row_ptr, g.col_idx
     graphs = []
@@ -564,9 +586,14 @@ def run_batch(args, rank, world):
         ctx.gc_color_batch(db2, jobs, color, None, ncol)
         hcolor.copy_(color, non_blocking=True)
     e1.record(stream)
-    torch.cuda.synchronize(dev)
-    t_e2e = e0.elapsed_time(e1) / 1e3 / args.steps
-    line = {"metric": METRIC, "value": G / t_batch, "unit": "graphs/s", "n_gpus": world, "steps": args.steps,
+    sync_ranks(world, dev)
+    t_e2e = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, dev) / args.steps
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    line = {"metric": METRIC, "value": job_rate(G, 1, world, t_batch), "unit": "graphs/s", "n_gpus": world,
+            "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_batch * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": w["desc"], "graphs": G, "n": db.n, "m": db.nnz // 2,
@@ -574,12 +601,16 @@ def run_batch(args, rank, world):
             "per_graph": {"value": G / t_single, "unit": "graphs/s", "ms_total": t_single * 1e3,
                           "identical_colourings": identical},
             "speedup_vs_per_graph": t_single / t_batch,
-            "edges_per_s": (db.nnz // 2) / t_batch,
-            "e2e": {"value": G / t_e2e, "unit": "graphs/s",
+            "edges_per_s": job_rate(db.nnz // 2, 1, world, t_batch),
+            "e2e": {"value": job_rate(G, 1, world, t_e2e), "unit": "graphs/s",
                     "h2d_bytes_per_step": 8 * (db.n + 1) + 4 * db.nnz + 8 * (G + 1),
                     "d2h_bytes_per_step": 4 * db.n},
             "gpu_launches": launches, "clocks": clocks}
+    if world > 1:
+        line["config"]["parallelism"] = "replicas"
     print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
     return 0
 
 
@@ -609,13 +640,18 @@ def run_serve(args, rank, world):
     submission to colours on the host."""
     import numpy as np
     import torch
+    import torch.distributed as dist
     from paper_2008_11321_gb300 import _build
-    if rank == 0:
-        _build.build()
-    from paper_2008_11321_gb300.serve import ColoringServer, latency_summary
-    w = WORKLOADS[args.workload]
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
+    if world > 1:  # replicas: every rank serves its own copy of the request stream
+        dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2008_11321_gb300.serve import ColoringServer, latency_summary
+    w = WORKLOADS[args.workload]
     reqs_in = serve_requests(w)
     edges = sum(g.m for g, _, _ in reqs_in)
     with ColoringServer(dev, memory_budget=w["budget"]) as srv:
@@ -636,6 +672,7 @@ def run_serve(args, rank, world):
         sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
         sampler.start()
         n_batches0 = len(srv.batches)
+        sync_ranks(world)
         t0 = time.perf_counter()
         rs = []
         for g, e, sd in reqs_in:
@@ -646,8 +683,14 @@ def run_serve(args, rank, world):
         t_open = time.perf_counter() - t0
         clocks = sampler.stop()
         batches = srv.batches[n_batches0:]
+    # the job's time is the slowest replica's (host clocks: latency is a host-side quantity)
+    t_open = max_over_ranks(t_open, world, torch.device("cuda", dev))
     lat = latency_summary(rs)
-    line = {"metric": METRIC, "value": edges / t_open, "unit": "edges/s", "n_gpus": world,
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    line = {"metric": METRIC, "value": job_rate(edges, 1, world, t_open), "unit": "edges/s", "n_gpus": world,
             "steps": 1, "warmup": 1, "ms_per_step": t_open * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": w["desc"], "requests": len(reqs_in), "edges": edges,
@@ -656,7 +699,11 @@ def run_serve(args, rank, world):
             "capacity": {"requests_per_s": cap, "edges_per_s": edges / t_closed},
             "batches": {"count": len(batches), "mean_graphs": float(np.mean([b[0] for b in batches]))},
             "clocks": clocks}
+    if world > 1:
+        line["config"]["parallelism"] = "replicas; latency of rank 0"
     print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
     return 0
 
 
@@ -749,9 +796,7 @@ def main():
 
     steps = []
     n_nonisolated = int((g.degrees() > 0).sum())
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
+    sync_ranks(world, dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
@@ -759,16 +804,10 @@ def main():
         st = ctx.gc_get_stats()
         steps.append({k: getattr(st, k) for k, _ in st._fields_})
     ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        dist.barrier()
+    sync_ranks(world, dev)
     clocks = sampler.stop()
-    elapsed = ev0.elapsed_time(ev1) / 1e3
-    t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    t_max = float(t.item())
-    value = m * args.steps * world / t_max
+    t_max = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, world, dev)
+    value = job_rate(m, args.steps, world, t_max)
 
     # end to end through the public host-buffer entry point
     e2e = None
@@ -776,20 +815,16 @@ def main():
         hcolor = torch.empty(n, dtype=torch.int32, pin_memory=True).numpy()
         ctx.gc_set_timing(False)
         ctx.gc_color_graph_host(g.row_ptr, g.col_idx, p, q, seed, hcolor)  # grows buffers once
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
+        sync_ranks(world, dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
             ctx.gc_color_graph_host(g.row_ptr, g.col_idx, p, q, seed, hcolor)
         e1.record(stream)
-        torch.cuda.synchronize(dev)
-        te = torch.tensor([e0.elapsed_time(e1) / 1e3], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        sync_ranks(world, dev)
+        te = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, dev)
         assert (hcolor == color.cpu().numpy()).all(), "host entry point disagrees with device path"
-        e2e = {"value": m * args.steps * world / float(te.item()), "unit": "edges/s",
+        e2e = {"value": job_rate(m, args.steps, world, te), "unit": "edges/s",
                "h2d_bytes_per_step": 8 * (n + 1) + 4 * nnz, "d2h_bytes_per_step": 4 * n}
 
     if rank != 0:

@@ -20,9 +20,13 @@
 //            its fixed internal neighbours to B_v, drops them from its
 //            internal list (in place), and draws the smallest colour not in
 //            B_v.
-// The full adjacency is read once per vertex, and a fixed neighbour once
-// more; the later iterations (hundreds on the dense top partition of a
-// power-law graph) touch only the edges of G(l) between vertices of U.
+//   tail     once U is small, the partition's remaining iterations run in one
+//            launch of one thread-block cluster on shared-memory replicas
+//            (see dec_tail_kernel).
+// The full adjacency is read once per vertex (hubs in chunks over several
+// warps), and a fixed neighbour once more; the later iterations (hundreds on
+// the dense top partition of a power-law graph) touch only the edges of G(l)
+// between vertices of U.
 //
 // State word of a vertex (the caller's colour array during the call):
 //   bits 24..31  its batch, when rho-bar <= 255 (one load of a neighbour's
@@ -105,7 +109,8 @@ struct DecCtl {  // read back whole into the context's 256-byte pinned buffer
   unsigned long long cnt[3][4];  // U of slot k % 3: [0] warp-path, [1] lane-path vertices, [2] list entries,
                                  // [3] the longest list
   unsigned long long cur[3][4];  // cursors of slot k % 3: pick warp/lane, check warp/lane
-  unsigned long long iters;      // pick launches that found U non-empty
+  unsigned long long iters;      // iterations after each partition's first: pick launches that
+                                 // found U non-empty, and the tail's
   unsigned long long internal;   // sum of the internal list lengths
   int max_color;
   int err;                       // 1: a batch outside 1..rounds; 2: the tail did not fit

@@ -200,7 +200,7 @@ class ClockSampler:
                 "samples": len(sms)}
 
 
-def cpu_baseline(w_name, seconds_target=10.0, median=False, dec=False, ordered=False, itr=False):
+def cpu_baseline(w_name, seconds_target=10.0, median=False, dec=False, ordered=False, itr=False, kind=None):
     """The oracle as it stands, single-threaded, on a bounded sample of the
     same family (R-MAT scale 22 for the R-MAT workloads)."""
     import numpy as np
@@ -222,7 +222,9 @@ def cpu_baseline(w_name, seconds_target=10.0, median=False, dec=False, ordered=F
     reps, total = 0, 0.0
     while total < seconds_target and reps < 50:
         t0 = time.perf_counter()
-        if median:
+        if kind is not None:
+            oracle.jp_color(g, oracle.priority_kind(g, kind, w["seed"]))
+        elif median:
             oracle.jp_adg_m(g, w["seed"])
         elif itr:
             oracle.dec_itr(g, np.ones(g.n, dtype=np.int32), 1, w["seed"])
@@ -235,7 +237,8 @@ def cpu_baseline(w_name, seconds_target=10.0, median=False, dec=False, ordered=F
         total += time.perf_counter() - t0
         reps += 1
     what = ("ADG-M + Greedy" if median else "ITR (one partition)" if itr else "ADG + DEC-ADG-ITR" if dec
-            else "ADG-O + Greedy" if ordered else "ADG + Greedy")
+            else "ADG-O + Greedy" if ordered else f"priority kind {kind} + Greedy" if kind is not None
+            else "ADG + Greedy")
     return {"value": g.m * reps / total, "unit": "edges/s", "cores": 1, "kind": "oracle",
             "sample": f"{desc}: n={g.n}, m={g.m}, {reps} run(s) of {what}, {total:.1f} s"}
 
@@ -315,6 +318,8 @@ def run_variant(args, rank, world):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload, kind=kind)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -260,8 +260,10 @@ def test_three_calls_equal_one(ctx):
     assert torch.equal(c1, c2)
 
 
-def test_host_entry_point(ctx):
-    g = gg.rmat(15, 16, seed=4)
+@pytest.mark.parametrize("scale", [15, 20])
+def test_host_entry_point(ctx, scale):
+    # scale 20: a 126 MB col_idx upload
+    g = gg.rmat(scale, 16, seed=4)
     color = np.zeros(g.n, dtype=np.int32)
     batch = np.zeros(g.n, dtype=np.int32)
     nc, nr = ctx.gc_color_graph_host(g.row_ptr, g.col_idx, 1, 100, 42, color, batch)

@@ -15,8 +15,8 @@ import pytest
 
 import graphgen as gg
 import oracle
-from _fixtures import (complete, complete_bipartite, cycle, empty, path, petersen, random_small, star,
-                       wheel)
+from _fixtures import (case_graph, complete, complete_bipartite, cycle, empty, ints, path, petersen, random_small,
+                       read_cases, star, wheel)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -101,6 +101,15 @@ DEC_GRAPHS += [star(12345), wheel(9000), _twin_hubs(9000), gg.rmat(18, 16, seed=
 @pytest.mark.parametrize("p,q", [(1, 100), (1, 2)])
 def test_dec_itr_matches_oracle(ctx, g, p, q):
     assert_dec_same(ctx, g, p, q)
+
+
+@pytest.mark.parametrize("case", read_cases("dec_itr_small.txt"), ids=lambda c: c["name"])
+def test_dec_itr_golden(ctx, case):
+    # the hand-worked cases: colours and iterations as derived in the fixture
+    g = case_graph(case)
+    b, c, nr, nc, it, _ = dec_graph(ctx, g, 1, 100, 42)
+    assert nr == int(case["rounds"]) and np.array_equal(b, ints(case["batch"]))
+    assert np.array_equal(c, ints(case["color"])) and it == int(case["iterations"])
 
 
 def test_dec_itr_clique_beyond_window(ctx):

@@ -772,3 +772,14 @@ def test_jp_adg_o_colours(g):
     assert (color[src] != color[g.col_idx]).all() and color.max() == nc
     assert nc <= (2 * 101 * d) // 100 + 1
     assert np.array_equal(color, _jp_simulate(g, rho.astype(np.uint64), np.random.default_rng(3)))
+
+
+@pytest.mark.parametrize("case", read_cases("dec_itr_small.txt"), ids=lambda c: c["name"])
+def test_golden_dec_itr_small(case):
+    g = case_graph(case)
+    for v in range(g.n):  # the hash values the hand derivation used
+        assert oracle.tiebreak(42, v) == [3184996902, 686809907, 1196582743, 1478287871, 163338330][v]
+    batch, color, rounds, nc, iters, _ = oracle.dec_adg_itr(g, 1, 100, 42)
+    assert rounds == int(case["rounds"]) and np.array_equal(batch, ints(case["batch"]))
+    assert np.array_equal(color, ints(case["color"]))
+    assert iters == int(case["iterations"]) and nc == int(max(ints(case["color"])))

@@ -10,7 +10,8 @@ import pytest
 
 import graphgen as gg
 import oracle
-from _fixtures import complete, complete_bipartite, cycle, empty, path, petersen, random_small, star
+from _fixtures import (case_graph, complete, complete_bipartite, cycle, empty, ints, path, petersen, random_small,
+                       read_cases, star)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -58,6 +59,19 @@ def test_adg_o_matches_oracle(ctx, g, p, q):
     _, _, oc, _, onc = oracle.jp_adg_o(g, p, q)
     assert nr2 == onr and np.array_equal(b2.cpu().numpy(), ob), g.name
     assert nc == onc and np.array_equal(color.cpu().numpy(), oc), g.name
+
+
+@pytest.mark.parametrize("case", read_cases("adg_o_small.txt"), ids=lambda c: c["name"])
+def test_adg_o_golden(ctx, case):
+    # the hand-worked cases: rho, rank and the JP-ADG-O colours
+    g = case_graph(case)
+    dg = dev(g)
+    rho, rank, color = i32(g.n), i32(g.n), i32(g.n)
+    ctx.gc_adg_o_order(dg, 1, 100, rho, None, rank)
+    ctx.gc_color_graph_o(dg, 1, 100, color)
+    assert np.array_equal(rho.cpu().numpy(), ints(case["rho"]))
+    assert np.array_equal(rank.cpu().numpy(), ints(case["rank"]))
+    assert np.array_equal(color.cpu().numpy(), ints(case["color"]))
 
 
 @pytest.mark.parametrize("n", [520, 1500])

@@ -783,3 +783,13 @@ def test_golden_dec_itr_small(case):
     assert rounds == int(case["rounds"]) and np.array_equal(batch, ints(case["batch"]))
     assert np.array_equal(color, ints(case["color"]))
     assert iters == int(case["iterations"]) and nc == int(max(ints(case["color"])))
+
+
+@pytest.mark.parametrize("case", read_cases("adg_o_small.txt"), ids=lambda c: c["name"])
+def test_golden_adg_o_small(case):
+    g = case_graph(case)
+    batch, rho, rank, rounds = oracle.adg_o(g, 1, 100)
+    assert np.array_equal(rho, ints(case["rho"]))
+    assert np.array_equal(rank, ints(case["rank"]))
+    _, _, color, _, nc = oracle.jp_adg_o(g, 1, 100)
+    assert np.array_equal(color, ints(case["color"])) and nc == int(max(ints(case["color"])))

@@ -64,3 +64,43 @@ def test_null_arguments_rejected_without_device_work(lib):
 def test_library_links_cuda_sm103a_only(lib):
     # the build compiles for exactly one real architecture
     assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def _prototypes():
+    """{name: [parameter declarations]} from the header's prototypes."""
+    text = re.sub(r"/\*.*?\*/", " ", open(HEADER).read(), flags=re.S)
+    out = {}
+    for name, params in re.findall(r"\b(?:gc_status|void|const char\s*\*)\s*(gc_\w+)\s*\(([^;]*?)\)\s*;", text,
+                                   flags=re.S):
+        ps = [" ".join(p.split()) for p in params.split(",")]
+        out[name] = [] if ps == ["void"] or ps == [""] else ps
+    return out
+
+
+def _ctype_kind(t):
+    """'ptr' for pointer-sized arguments, else the integer width and sign."""
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or (isinstance(t, type) and issubclass(t, ctypes._Pointer)):
+        return "ptr"
+    return {ctypes.c_int32: "i32", ctypes.c_uint32: "u32", ctypes.c_int64: "i64", ctypes.c_uint64: "u64"}.get(t, t)
+
+
+def _decl_kind(decl):
+    if "*" in decl or decl.startswith("gc_stream"):
+        return "ptr"
+    base = decl.rsplit(" ", 1)[0].replace("const ", "")
+    return {"int": "i32", "int32_t": "i32", "uint32_t": "u32", "int64_t": "i64", "uint64_t": "u64",
+            "gc_status": "i32"}[base]
+
+
+def test_binding_signatures_match_header(lib):
+    # the ctypes argument lists the binding installs have the header's arity
+    # and, parameter by parameter, its pointer/integer kind and width
+    protos = _prototypes()
+    assert set(protos) == set(gcp.EXPORTS)
+    for name, decls in protos.items():
+        argtypes = getattr(lib, name).argtypes
+        assert argtypes is not None and len(argtypes) == len(decls), (name, decls)
+        for decl, t in zip(decls, argtypes):
+            kind = _ctype_kind(t)
+            want = _decl_kind(decl)
+            assert kind == want or (want == "i32" and t is ctypes.c_int), (name, decl, t)

@@ -264,11 +264,14 @@ def pred_count(g, prio: np.ndarray) -> np.ndarray:
     return cnt
 
 
-def jp_depth(g, prio: np.ndarray) -> int:
+def jp_depth(g, prio: np.ndarray, per_vertex: bool = False):
+    """Longest path (in vertices) of G_rho; with per_vertex, also depth[v],
+    the length of the longest path of G_rho that ends at v."""
     n, rp, ci = _csr(g)
     pr = np.ascontiguousarray(prio, dtype=np.uint64)
     depth = np.zeros(n, dtype=np.int32)
-    return int(_load().oracle_jp_depth(n, _p(rp), _p(ci), _p(pr), _p(depth)))
+    best = int(_load().oracle_jp_depth(n, _p(rp), _p(ci), _p(pr), _p(depth)))
+    return (best, depth) if per_vertex else best
 
 
 def degeneracy(g):

@@ -14,8 +14,10 @@ Renyi, Barabasi-Albert and regular grids of the same scale are generated.
 from __future__ import annotations
 
 import ctypes
+import hashlib
 import math
 import os
+import platform
 import subprocess
 from dataclasses import dataclass
 
@@ -30,12 +32,22 @@ RMAT_ABC = (0.57, 0.19, 0.19)  # d = 0.05
 
 
 def build(force: bool = False) -> str:
-    """Compile libgraphgen.so next to the source (host C++ only)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    """Compile libgraphgen.so next to the source (host C++ only) unless a
+    stamp beside it holds the hash of the source, the command and the host
+    architecture."""
+    cmd = ["g++", "-O3", "-std=c++17", "-shared", "-fPIC", "-pthread", _SRC]
+    h = hashlib.sha256(platform.machine().encode() + "\0".join(cmd).encode())
+    with open(_SRC, "rb") as f:
+        h.update(f.read())
+    digest = h.hexdigest()
+    stamp = _LIB + ".stamp"
+    fresh = os.path.exists(_LIB) and os.path.exists(stamp) and open(stamp).read().strip() == digest
+    if force or not fresh:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["g++", "-O3", "-std=c++17", "-shared", "-fPIC", "-pthread",
-                               _SRC, "-o", tmp])
+        subprocess.check_call(cmd + ["-o", tmp])
         os.replace(tmp, _LIB)
+        with open(stamp, "w") as f:
+            f.write(digest + "\n")
     return _LIB
 
 

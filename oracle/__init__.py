@@ -27,7 +27,9 @@ Functions (each cites the passage of the paper it follows in ``oracle.c``):
 from __future__ import annotations
 
 import ctypes
+import hashlib
 import os
+import platform
 import subprocess
 
 import numpy as np
@@ -39,10 +41,21 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    """Compile liboracle.so unless a stamp beside it holds the hash of the
+    source, the command and the host architecture."""
+    cmd = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", _SRC]
+    h = hashlib.sha256(platform.machine().encode() + "\0".join(cmd).encode())
+    with open(_SRC, "rb") as f:
+        h.update(f.read())
+    digest = h.hexdigest()
+    stamp = _LIB + ".stamp"
+    fresh = os.path.exists(_LIB) and os.path.exists(stamp) and open(stamp).read().strip() == digest
+    if force or not fresh:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", _SRC, "-o", tmp])
+        subprocess.check_call(cmd + ["-o", tmp])
         os.replace(tmp, _LIB)
+        with open(stamp, "w") as f:
+            f.write(digest + "\n")
     return _LIB
 
 

@@ -2,12 +2,17 @@
 
 Each translation unit is compiled in parallel, then linked as a shared
 library against the shared CUDA runtime (the same libcudart.so.13 PyTorch
-loads).  The result is written next to this file.
+loads).  The result is written next to this file.  A step is redone unless a
+stamp file beside its output holds the hash of its inputs (sources, headers,
+flags, host architecture): file times are not trusted, so a library copied
+from another machine is rebuilt.
 """
 from __future__ import annotations
 
 import concurrent.futures as cf
+import hashlib
 import os
+import platform
 import shutil
 import subprocess
 
@@ -34,26 +39,48 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def _stale(target: str, deps) -> bool:
-    if not os.path.exists(target):
-        return True
-    t = os.path.getmtime(target)
-    return any(os.path.getmtime(d) > t for d in deps)
+def _digest(paths, cmd) -> str:
+    """Hash of the inputs of one build step: file contents, the command line
+    and the host architecture (a library built on another machine type is
+    never reused)."""
+    h = hashlib.sha256()
+    h.update(platform.machine().encode())
+    h.update("\0".join(cmd).encode())
+    for p in paths:
+        h.update(p.encode())
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def _fresh(target: str, digest: str) -> bool:
+    stamp = target + ".stamp"
+    if not (os.path.exists(target) and os.path.exists(stamp)):
+        return False
+    with open(stamp) as f:
+        return f.read().strip() == digest
+
+
+def _stamp(target: str, digest: str) -> None:
+    with open(target + ".stamp", "w") as f:
+        f.write(digest + "\n")
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
     srcs = sources()
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
-    headers += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
-    if not force and not _stale(LIB, srcs + headers + [__file__]):
+    headers = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h")))
+    headers += sorted(os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h"))
+    cc = nvcc()
+    lib_digest = _digest(srcs + headers + [__file__], [cc, *ARCH, *NVCC_FLAGS])
+    if not force and _fresh(LIB, lib_digest):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
-    cc = nvcc()
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        if force or _stale(obj, [src] + headers + [__file__]):
-            cmd = [cc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+        cmd = [cc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+        digest = _digest([src] + headers + [__file__], cmd)
+        if force or verbose or not _fresh(obj, digest):
             if verbose:
                 cmd.insert(1, "-Xptxas=-v")
             r = subprocess.run(cmd, capture_output=True, text=True)
@@ -61,6 +88,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
             if verbose:
                 print(r.stderr)
+            _stamp(obj, digest)
         return obj
 
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
@@ -73,6 +101,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    _stamp(LIB, lib_digest)
     return LIB
 
 

@@ -103,32 +103,68 @@ typedef struct {
   float ms_dec_extract;    /* DEC-ADG-ITR: per-partition extraction launches   */
   float ms_dec_iterate;    /* DEC-ADG-ITR: the later SIM-COL iterations        */
   int64_t dec_tail_partitions; /* DEC-ADG-ITR: partitions finished by the
-                              single-cluster tail (see GC_DEC_TAIL)            */
+                              single-cluster tail (gc_options.dec_tail)      */
+  int32_t adg_pull_rounds; /* ADG rounds whose UPDATE pulled (update_mode)     */
 } gc_stats;
 
 /* Human-readable name of a status code (static storage). */
 const char *gc_status_str(gc_status s);
 
-/* Create a context bound to CUDA device `device`.  Allocates nothing large
- * until the first call needs scratch.  *ctx is NULL on failure.
+/* ADG's UPDATE direction (gc_options.update_mode).  Push (Algorithm 1's
+ * UPDATE): every vertex removed this round decrements the degree of each
+ * neighbour still in U.  Pull (Section 5, "Push vs. Pull", the CREW variant
+ * of Algorithm 2): every vertex still in U subtracts the number of its
+ * neighbours removed this round, with no contended atomics.  AUTO chooses per
+ * round from the edges each direction must sweep (see pull_percent).  The
+ * results are identical in every mode. */
+enum { GC_UPDATE_AUTO = 0, GC_UPDATE_PUSH = 1, GC_UPDATE_PULL = 2 };
+
+/* Tunables of a context.  Fill one with gc_options_init(), change fields,
+ * and pass it to gc_create() (NULL there means every default).  Each field
+ * changes speed only: every call gives identical results for every valid
+ * setting.  struct_size versions the struct: a caller built against an
+ * older, shorter gc_options sets its own size and the library takes defaults
+ * for the fields it does not have. */
+typedef struct {
+  uint32_t struct_size;    /* sizeof(gc_options) as the caller knows it      */
+  int32_t core_target;     /* JP core size in vertices, 0..32768; 0: no core
+                              (default 16384)                                */
+  int32_t core_cluster;    /* at most this many CTAs in the core's thread-block
+                              cluster, 1..16 (default 16; fewer if the device
+                              cannot place them)                             */
+  int32_t core_warps;      /* warps per core CTA, 1..32 (default 8)           */
+  int32_t dec_tail;        /* DEC-ADG-ITR: 1 finishes a partition's last
+                              SIM-COL iterations in one cluster launch
+                              (default), 0 runs every iteration GPU-wide     */
+  int32_t update_mode;     /* GC_UPDATE_AUTO (default), _PUSH or _PULL       */
+  int32_t pull_percent;    /* AUTO pulls a round when the rows of U' hold at
+                              most pull_percent % of the entries the rows of
+                              R hold, 0..100000 (default 100)                */
+  int32_t bulk_blocks_per_sm; /* resident blocks per SM of JP's bulk colouring
+                              kernel, 0 = as many as fit (default), 1..32    */
+  uint32_t wait_limit_ms;  /* bound of every device-side wait, 1..600000 ms
+                              (default 4000); a wait that runs out ends the
+                              call with GC_ERR_TIMEOUT, context usable       */
+} gc_options;
+
+/* Fill *opt with the defaults (and struct_size = sizeof(gc_options)). */
+gc_status gc_options_init(gc_options *opt);
+
+/* Create a context bound to CUDA device `device` with options `opt` (NULL:
+ * defaults; GC_ERR_INVALID_ARG if a field is out of range).  Allocates
+ * nothing large until the first call needs scratch.  *ctx is NULL on
+ * failure.
  *
- * The environment is read here, once per context:
- *   GC_CORE_TARGET    JP-ADG core size in vertices (default 16384, at most
- *                     32768; 0: no core);
- *   GC_CORE_CLUSTER   at most this many CTAs in the core cluster (1..16);
- *   GC_CORE_WARPS     warps per core CTA (1..32, default 8);
- *   GC_DEC_TAIL       0: DEC-ADG-ITR runs every SIM-COL iteration as two
- *                     GPU-wide launches, also once U is small (default: the
- *                     last iterations of a partition run in one cluster);
- *   GC_WAIT_LIMIT_MS  bound of every wait on a colour outside the core
- *                     (default 4000; the core's waits are bounded by 4 s);
- *                     a wait that runs out ends the call with
- *                     GC_ERR_TIMEOUT and leaves the context usable;
- * and, to test those error paths, failure injection:
- *   GC_INJECT_STALL   id of a vertex outside the core whose colour is never
- *                     published, so that its successors' waits run out;
+ * The environment is read here only for failure injection, to test the
+ * error paths:
+ *   GC_INJECT_STALL   id of a vertex whose colour is never published, so
+ *                     that the waits of its successors run out (inside or
+ *                     outside the JP core);
  *   GC_INJECT_OOM     non-zero: every scratch allocation fails (GC_ERR_OOM). */
-gc_status gc_create(gc_context **ctx, int device);
+gc_status gc_create(gc_context **ctx, int device, const gc_options *opt);
+
+/* The options the context runs with (defaults filled in). */
+gc_status gc_get_options(const gc_context *ctx, gc_options *out);
 
 /* Release the context's scratch memory and the context itself (NULL ok). */
 void gc_destroy(gc_context *ctx);
@@ -172,10 +208,14 @@ gc_status gc_adg_partition(gc_context *ctx, const gc_csr *g, uint32_t eps_p, uin
  * graphs return GC_ERR_OVERFLOW without touching the device.
  * Runs on the calling thread's current device (g and batch_out must live
  * there).  The first call on each device looks up the array's device
- * address; make that first call before any stream capture.  All calls share
- * the one array and each call starts by resetting the state it reads, so
- * calls whose work could overlap on the GPU (other streams, other threads)
- * race with each other and must be serialised by the caller. */
+ * address; make that first call before any stream capture.  The address is
+ * kept for the rest of the process: after cudaDeviceReset() on a device it is
+ * stale, so do not call this entry point on that device again.  Each ADG
+ * round ends by reading |U| back into host memory, which synchronises
+ * `stream` once per round.  All calls share the one array and each call
+ * starts by resetting the state it reads, so calls whose work could overlap
+ * on the GPU (other streams, other threads) race with each other and must be
+ * serialised by the caller. */
 gc_status gc_adg_partition_noalloc(const gc_csr *g, uint32_t eps_p, uint32_t eps_q,
                                    int32_t *batch_out, int32_t *num_rounds_out, gc_stream stream);
 

@@ -14,6 +14,14 @@
 //   finalize   Sigma' = Sigma - Sigma_R - cut (Section 5, "Caching Sums of
 //              Degrees"), |U| = |U'|, next T, l = l + 1.
 //
+// A round may pull instead of push (Section 5, "Push vs. Pull"; the CREW
+// form of Algorithm 2): every survivor v in U' recounts D[v] as the number of
+// its neighbours still live after the partition, so no two threads update
+// the same word with contention, and Sigma' is the sum of the recounts (the
+// cut follows as Sigma - Sigma_R - Sigma').  Push sweeps the rows of R, pull
+// the rows of U'; the direction is chosen per round on the device
+// (adg_pulls) from the two row sums, which the partition and finalize carry.
+//
 // Round 1 reads U = V implicitly (no list) and writes D only for survivors.
 //
 // UPDATE tests "w still in U" on a bitmap (n bits) rather than on batch[]
@@ -45,13 +53,17 @@ __device__ __forceinline__ int adg_threshold(unsigned long long sigma, int size_
   return t > static_cast<unsigned __int128>(INT_MAX) ? INT_MAX : static_cast<int>(t);
 }
 
-__global__ void adg_init_kernel(AdgCtl* ctl, long long n, long long nnz, unsigned p, unsigned q) {
+__global__ void adg_init_kernel(AdgCtl* ctl, long long n, long long nnz, unsigned p, unsigned q, int mode,
+                                int pull_percent) {
   AdgCtl c{};
   c.sigma = static_cast<unsigned long long>(nnz);
+  c.rows_U = static_cast<unsigned long long>(nnz);
   c.size_U = static_cast<int>(n);
   c.round = 1;
   c.p = p;
   c.q = q;
+  c.mode = mode;
+  c.pull_percent = pull_percent;
   c.T = adg_threshold(c.sigma, c.size_U, p, q);
   *ctl = c;
 }
@@ -69,7 +81,7 @@ adg_partition_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row
   const long long size_u = first ? first_round_n : ctl->size_U;
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
-  unsigned long long sum_r = 0;
+  unsigned long long sum_r = 0, rows_r = 0;
   const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
   for (long long base = static_cast<long long>(blockIdx.x) * blockDim.x; base < size_u; base += stride) {
     const long long i = base + threadIdx.x;
@@ -112,13 +124,17 @@ adg_partition_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row
       batch[u] = round;
       sum_r += static_cast<unsigned long long>(d);
     }
-    if (first) continue;  // round 1's UPDATE sweeps vertex tiles, no task list
+    if (first) {  // round 1's UPDATE sweeps vertex tiles, no task list
+      if (in_r) rows_r += static_cast<unsigned long long>(re - rs);
+      continue;
+    }
     // removed -> UPDATE tasks of at most kChunk edges, written by the warp
     int nt = 0;
     if (in_r) {
       rs = row_ptr[u];
       re = row_ptr[u + 1];
       nt = static_cast<int>((re - rs + kChunk - 1) / kChunk);
+      rows_r += static_cast<unsigned long long>(re - rs);
     }
     const int incl = warp_inclusive_scan(nt);
     const int tot = __shfl_sync(kFull, incl, 31);
@@ -144,7 +160,9 @@ adg_partition_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row
     }
   }
   sum_r = warp_sum(sum_r);
+  rows_r = warp_sum(rows_r);
   if (lane == 0 && sum_r) atomicAdd(&ctl->sum_R, sum_r);
+  if (lane == 0 && rows_r) atomicAdd(&ctl->rows_R, rows_r);
 }
 
 // Round 1 (vertex_tiles != 0): lane l of a warp owns vertex 32*tile + l and
@@ -157,8 +175,9 @@ adg_update_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row_pt
                   const unsigned* __restrict__ live, const long long* __restrict__ task_start,
                   const int* __restrict__ task_len, long long vertex_tiles_n) {
   // The last round leaves U empty: no neighbour can still be in U, so there
-  // is nothing to decrement (and the cut is not needed any more).
-  if (ctl->size_Unext == 0) return;
+  // is nothing to decrement (and the cut is not needed any more).  A pull
+  // round recounts instead (adg_pull_*).
+  if (ctl->size_Unext == 0 || adg_pulls(*ctl)) return;
   const int round = ctl->round;
   const unsigned long long ntasks =
       vertex_tiles_n > 0 ? static_cast<unsigned long long>(vertex_tiles_n) : ctl->ntasks;
@@ -194,17 +213,124 @@ adg_update_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row_pt
   if (lane == 0 && cut) atomicAdd(&ctl->cut, cut);
 }
 
+// Pull round, step 1: every survivor v of U' (the list the partition wrote)
+// gets D[v] = 0 and its row cut into tasks of at most kChunk entries
+// (vertex, start, length), appended warp by warp.
+__global__ void __launch_bounds__(kAdgThreads)
+adg_pull_tasks_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row_ptr, int* __restrict__ D,
+                      const int* __restrict__ u_next, long long* __restrict__ task_start,
+                      int* __restrict__ task_len, int* __restrict__ task_v) {
+  if (!adg_pulls(*ctl)) return;
+  const long long size_un = ctl->size_Unext;
+  const int lane = threadIdx.x & 31;
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  for (long long base = static_cast<long long>(blockIdx.x) * blockDim.x; base < size_un; base += stride) {
+    const long long i = base + threadIdx.x;
+    int v = 0, nt = 0;
+    long long rs = 0, re = 0;
+    if (i < size_un) {
+      v = u_next[i];
+      D[v] = 0;
+      rs = row_ptr[v];
+      re = row_ptr[v + 1];
+      nt = static_cast<int>((re - rs + kChunk - 1) / kChunk);
+    }
+    const int incl = warp_inclusive_scan(nt);
+    const int tot = __shfl_sync(kFull, incl, 31);
+    const int excl = incl - nt;
+    unsigned long long tbase = 0;
+    if (lane == 31 && tot) tbase = atomicAdd(&ctl->ntasks_pull, static_cast<unsigned long long>(tot));
+    tbase = __shfl_sync(kFull, tbase, 31);
+    for (int b = 0; b < tot; b += 32) {
+      const int x = b + lane;
+      int j = 0;  // owner: the largest lane j with excl_j <= x
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int c = j + step;
+        if (__shfl_sync(kFull, excl, c) <= x) j = c;
+      }
+      const long long st = __shfl_sync(kFull, rs, j) +
+                           static_cast<long long>(x - __shfl_sync(kFull, excl, j)) * kChunk;
+      const long long rej = __shfl_sync(kFull, re, j);
+      const int vj = __shfl_sync(kFull, v, j);
+      if (x < tot) {
+        task_start[tbase + x] = st;
+        task_len[tbase + x] = static_cast<int>(rej - st < kChunk ? rej - st : kChunk);
+        task_v[tbase + x] = vj;
+      }
+    }
+  }
+}
+
+// Pull round, step 2: each task counts its row's live neighbours (the
+// bitmap already excludes this round's R); counts of the same task are
+// merged by the warp in shared memory, then added to D[v] once per task.
+// The sum of all counts is Sigma' = sum of D over U'.
+__global__ void __launch_bounds__(kAdgThreads)
+adg_pull_count_kernel(AdgCtl* __restrict__ ctl, const int* __restrict__ col, int* __restrict__ D,
+                      const unsigned* __restrict__ live, const long long* __restrict__ task_start,
+                      const int* __restrict__ task_len, const int* __restrict__ task_v) {
+  __shared__ int s_cnt[kAdgThreads / 32][32];
+  if (!adg_pulls(*ctl)) return;
+  const unsigned long long ntasks = ctl->ntasks_pull;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned long long gwarp = (static_cast<unsigned long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long nwarps = (static_cast<unsigned long long>(gridDim.x) * blockDim.x) >> 5;
+  int* cnt = s_cnt[warp];
+  unsigned long long total = 0;
+  for (unsigned long long tile = gwarp; tile * 32 < ntasks; tile += nwarps) {
+    const unsigned long long t = tile * 32 + lane;
+    long long st = 0;
+    int len = 0;
+    if (t < ntasks) {
+      st = task_start[t];
+      len = task_len[t];
+    }
+    cnt[lane] = 0;
+    __syncwarp();
+    sweep_tile(
+        st, len, lane, col, [&](int w, int) { return (__ldg(live + (w >> 5)) >> (w & 31)) & 1u; },
+        [&](int, int j, unsigned lv) {
+          // lanes of this step holding edges of the same task add once
+          const unsigned act = __activemask();
+          const unsigned lm = __ballot_sync(act, lv != 0u);
+          const unsigned grp = __match_any_sync(act, j);
+          const unsigned mine = grp & lm;
+          if (lv && (mine & lanemask_lt()) == 0) atomicAdd(&cnt[j], __popc(mine));
+        });
+    __syncwarp();
+    const int c = cnt[lane];
+    if (t < ntasks && c) {
+      atomicAdd(&D[task_v[t]], c);
+      total += static_cast<unsigned long long>(c);
+    }
+    __syncwarp();
+  }
+  total = warp_sum(total);
+  if (lane == 0 && total) atomicAdd(&ctl->pull_sigma, total);
+}
+
 __global__ void adg_finalize_kernel(AdgCtl* ctl) {
   AdgCtl c = *ctl;
   c.total_U += static_cast<unsigned long long>(c.size_U);
+  if (adg_pulls(c)) {  // Sigma' is the recount; the cut follows from it
+    c.cut = c.sigma - c.sum_R - c.pull_sigma;
+    c.sigma = c.pull_sigma;
+    ++c.pull_rounds;
+  } else {
+    c.sigma = c.sigma - c.sum_R - c.cut;
+  }
   c.total_dec += c.cut;
-  c.sigma = c.sigma - c.sum_R - c.cut;
+  c.rows_U -= c.rows_R;
   c.size_U = c.size_Unext;
   c.round += 1;
   c.T = adg_threshold(c.sigma, c.size_U, c.p, c.q);
   c.sum_R = 0;
+  c.rows_R = 0;
   c.cut = 0;
+  c.pull_sigma = 0;
   c.ntasks = 0;
+  c.ntasks_pull = 0;
   c.size_Unext = 0;
   *ctl = c;
 }
@@ -214,7 +340,7 @@ __global__ void adg_finalize_kernel(AdgCtl* ctl) {
 // Excludes D (n ints), which the caller provides.
 size_t adg_scratch_bytes(long long n, long long nnz) {
   const long long ntask = n + nnz / kChunk + 1;
-  return 2 * (static_cast<size_t>(n) * 4 + 256) + static_cast<size_t>(ntask) * 12 +
+  return 2 * (static_cast<size_t>(n) * 4 + 256) + static_cast<size_t>(ntask) * 16 + 3 * 256 +
          static_cast<size_t>((n + 31) / 32) * 4 + 256 + 2048;
 }
 
@@ -229,16 +355,19 @@ gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigne
   const long long ntask = n + nnz / kChunk + 1;
   long long* task_start = a.take<long long>(ntask);
   int* task_len = a.take<int>(ntask);
+  int* task_v = a.take<int>(ntask);
   unsigned* live = a.take<unsigned>((n + 31) / 32);
-  if (!ctl || !D || !ubuf[0] || !ubuf[1] || !task_start || !task_len || !live) return GC_ERR_OOM;
+  if (!ctl || !D || !ubuf[0] || !ubuf[1] || !task_start || !task_len || !task_v || !live) return GC_ERR_OOM;
 
+  const int mode = ctx->opt.update_mode;
   GC_TRY_CUDA(cudaMemsetAsync(batch, 0, sizeof(int) * n, s));  // batch 0 = still in U
-  adg_init_kernel<<<1, 1, 0, s>>>(ctl, n, nnz, p, q);
+  adg_init_kernel<<<1, 1, 0, s>>>(ctl, n, nnz, p, q, mode, ctx->opt.pull_percent);
   ++g_launches;
   GC_TRY_CUDA(cudaGetLastError());
 
   const int max_blocks = ctx->num_sms * 8;
   const int upd_blocks = resident_grid(adg_update_kernel, kAdgThreads, ctx->num_sms);
+  const int pull_blocks = resident_grid(adg_pull_count_kernel, kAdgThreads, ctx->num_sms);
   long long size_u = n;
   int cur = 0;
   int* pinned = static_cast<int*>(ctx->pinned);
@@ -253,9 +382,19 @@ gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigne
     ++g_launches;
     GC_TRY_CUDA(cudaGetLastError());
     ctx->timer_begin(gc_context::kTUpdate, s);
-    adg_update_kernel<<<upd_blocks, kAdgThreads, 0, s>>>(ctl, row_ptr_of(g), g->col_idx, D, batch, live,
-                                                          task_start, task_len, round == 1 ? n : 0);
-    ++g_launches;
+    if (mode != GC_UPDATE_PULL) {  // each direction's kernels return at once if not chosen
+      adg_update_kernel<<<upd_blocks, kAdgThreads, 0, s>>>(ctl, row_ptr_of(g), g->col_idx, D, batch, live,
+                                                            task_start, task_len, round == 1 ? n : 0);
+      ++g_launches;
+    }
+    if (mode != GC_UPDATE_PUSH) {
+      const long long wantp = (size_u + kAdgThreads - 1) / kAdgThreads;
+      adg_pull_tasks_kernel<<<static_cast<int>(wantp < max_blocks ? wantp : max_blocks), kAdgThreads, 0, s>>>(
+          ctl, row_ptr_of(g), D, ubuf[cur], task_start, task_len, task_v);
+      adg_pull_count_kernel<<<pull_blocks, kAdgThreads, 0, s>>>(ctl, g->col_idx, D, live, task_start, task_len,
+                                                                 task_v);
+      g_launches += 2;
+    }
     ctx->timer_end(s);
     GC_TRY_CUDA(cudaGetLastError());
     adg_finalize_kernel<<<1, 1, 0, s>>>(ctl);
@@ -269,13 +408,13 @@ gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigne
     cur ^= 1;
   }
   // statistics
-  unsigned long long tot[2];
-  GC_TRY_CUDA(cudaMemcpyAsync(pinned, &ctl->total_U, 2 * sizeof(unsigned long long),
-                              cudaMemcpyDeviceToHost, s));
+  GC_TRY_CUDA(cudaMemcpyAsync(pinned, ctl, sizeof(AdgCtl), cudaMemcpyDeviceToHost, s));
   GC_TRY_CUDA(cudaStreamSynchronize(s));
-  memcpy(tot, pinned, sizeof(tot));
-  ctx->stats.sum_U = static_cast<int64_t>(tot[0]);
-  ctx->stats.sum_decrements = static_cast<int64_t>(tot[1]);
+  AdgCtl h;
+  memcpy(&h, pinned, sizeof(h));
+  ctx->stats.sum_U = static_cast<int64_t>(h.total_U);
+  ctx->stats.sum_decrements = static_cast<int64_t>(h.total_dec);
+  ctx->stats.adg_pull_rounds = h.pull_rounds;
   ctx->stats.adg_rounds = round;
   *rounds_out = round;
   return GC_OK;
@@ -406,7 +545,7 @@ gc_status adg_m_run(gc_context* ctx, Arena a, const gc_csr* g, int* batch, int* 
   const int max_blocks = ctx->num_sms * 8;
   const int upd_blocks = resident_grid(adg_update_kernel, kAdgThreads, ctx->num_sms);
   GC_TRY_CUDA(cudaMemsetAsync(batch, 0, sizeof(int) * n, s));
-  adg_init_kernel<<<1, 1, 0, s>>>(ctl, n, nnz, 0, 1);  // (its threshold is not used here)
+  adg_init_kernel<<<1, 1, 0, s>>>(ctl, n, nnz, 0, 1, GC_UPDATE_PUSH, 0);  // (its threshold is not used here)
   ++g_launches;
   adg_m_init_kernel<<<max_blocks, kAdgThreads, 0, s>>>(rp, n, D, ubuf[0], live);
   ++g_launches;
@@ -443,14 +582,14 @@ gc_status adg_m_run(gc_context* ctx, Arena a, const gc_csr* g, int* batch, int* 
     cur ^= 1;
   }
   // one read-back at the end: the totals, and |U| = 0 as a check
-  GC_TRY_CUDA(cudaMemcpyAsync(pinned, &ctl->total_U, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-  GC_TRY_CUDA(cudaMemcpyAsync(pinned + 4, &ctl->size_U, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GC_TRY_CUDA(cudaMemcpyAsync(pinned, ctl, sizeof(AdgCtl), cudaMemcpyDeviceToHost, s));
   GC_TRY_CUDA(cudaStreamSynchronize(s));
-  if (pinned[4] != 0) return GC_ERR_CUDA;  // cannot happen
-  unsigned long long tot[2];
-  memcpy(tot, pinned, sizeof(tot));
-  ctx->stats.sum_U = static_cast<int64_t>(tot[0]);
-  ctx->stats.sum_decrements = static_cast<int64_t>(tot[1]);
+  AdgCtl h;
+  memcpy(&h, pinned, sizeof(h));
+  if (h.size_U != 0) return GC_ERR_CUDA;  // cannot happen
+  ctx->stats.sum_U = static_cast<int64_t>(h.total_U);
+  ctx->stats.sum_decrements = static_cast<int64_t>(h.total_dec);
+  ctx->stats.adg_pull_rounds = 0;
   ctx->stats.adg_rounds = round;
   *rounds_out = round;
   return GC_OK;
@@ -537,7 +676,7 @@ extern "C" gc_status gc_adg_partition_noalloc(const gc_csr* g, uint32_t eps_p, u
   // Every buffer above is written before it is read within a call; the
   // control block, the only state carried between kernels, is reset here.
   GC_TRY_CUDA(cudaMemsetAsync(batch_out, 0, sizeof(int) * n, s));
-  adg_init_kernel<<<1, 1, 0, s>>>(ctl, n, nnz, eps_p, eps_q);
+  adg_init_kernel<<<1, 1, 0, s>>>(ctl, n, nnz, eps_p, eps_q, GC_UPDATE_PUSH, 0);
   GC_TRY_CUDA(cudaGetLastError());
   const int max_blocks = num_sms * 8;
   const int upd_blocks = gc::resident_grid(gc::adg_update_kernel, gc::kAdgThreads, num_sms);

@@ -202,9 +202,40 @@ const char* gc_status_str(gc_status s) {
   return "GC_ERR_UNKNOWN";
 }
 
-gc_status gc_create(gc_context** out, int device) {
+gc_status gc_options_init(gc_options* opt) {
+  if (!opt) return GC_ERR_INVALID_ARG;
+  gc_options o{};
+  o.struct_size = sizeof(gc_options);
+  o.core_target = static_cast<int32_t>(gc::kCoreDefault);
+  o.core_cluster = 16;
+  o.core_warps = 8;
+  o.dec_tail = 1;
+  o.update_mode = GC_UPDATE_AUTO;
+  o.pull_percent = 100;
+  o.bulk_blocks_per_sm = 0;
+  o.wait_limit_ms = static_cast<uint32_t>(gc::kWaitLimitNs / 1000000ull);
+  *opt = o;
+  return GC_OK;
+}
+
+gc_status gc_create(gc_context** out, int device, const gc_options* opt) {
   if (!out) return GC_ERR_INVALID_ARG;
   *out = nullptr;
+  // options: defaults, overwritten by the prefix of the struct the caller knows
+  gc_options o;
+  gc_options_init(&o);
+  if (opt) {
+    if (opt->struct_size < sizeof(uint32_t) || opt->struct_size > sizeof(gc_options)) return GC_ERR_INVALID_ARG;
+    memcpy(reinterpret_cast<char*>(&o) + sizeof(uint32_t), reinterpret_cast<const char*>(opt) + sizeof(uint32_t),
+           opt->struct_size - sizeof(uint32_t));
+    o.struct_size = sizeof(gc_options);
+  }
+  if (o.core_target < 0 || o.core_target > gc::kCoreMax || o.core_cluster < 1 || o.core_cluster > 16 ||
+      o.core_warps < 1 || o.core_warps > 32 || (o.dec_tail != 0 && o.dec_tail != 1) ||
+      o.update_mode < GC_UPDATE_AUTO || o.update_mode > GC_UPDATE_PULL || o.pull_percent < 0 ||
+      o.pull_percent > 100000 || o.bulk_blocks_per_sm < 0 || o.bulk_blocks_per_sm > 32 || o.wait_limit_ms < 1 ||
+      o.wait_limit_ms > 600000)
+    return GC_ERR_INVALID_ARG;
   int count = 0;
   if (cudaGetDeviceCount(&count) != cudaSuccess) {
     cudaGetLastError();
@@ -216,13 +247,11 @@ gc_status gc_create(gc_context** out, int device) {
   gc_context* ctx = new (std::nothrow) gc_context();
   if (!ctx) return GC_ERR_OOM;
   ctx->device = device;
-  if (const char* env = getenv("GC_CORE_TARGET")) ctx->core_target = atoll(env);
-  if (const char* env = getenv("GC_DEC_TAIL")) ctx->dec_tail = env[0] != '\0' && env[0] != '0';
+  ctx->opt = o;
+  ctx->core_target = o.core_target;
+  ctx->dec_tail = o.dec_tail != 0;
+  ctx->wait_ns = static_cast<unsigned long long>(o.wait_limit_ms) * 1000000ull;
   // failure injection for tests of the error paths (see gc_context)
-  if (const char* env = getenv("GC_WAIT_LIMIT_MS")) {
-    const long long ms = atoll(env);
-    if (ms >= 1 && ms <= 600000) ctx->wait_ns = static_cast<unsigned long long>(ms) * 1000000ull;
-  }
   if (const char* env = getenv("GC_INJECT_STALL")) ctx->stall_vertex = atoi(env);
   if (const char* env = getenv("GC_INJECT_OOM")) ctx->fail_alloc = env[0] != '\0' && env[0] != '0';
   if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
@@ -265,6 +294,12 @@ void gc_destroy(gc_context* ctx) {
   for (auto& ev : ctx->tev)
     if (ev) cudaEventDestroy(ev);
   delete ctx;
+}
+
+gc_status gc_get_options(const gc_context* ctx, gc_options* out) {
+  if (!ctx || !out) return GC_ERR_INVALID_ARG;
+  *out = ctx->opt;
+  return GC_OK;
 }
 
 gc_status gc_get_stats(const gc_context* ctx, gc_stats* out) {

@@ -42,14 +42,36 @@ struct AdgCtl {
   unsigned long long ntasks;     // this round: UPDATE tasks appended
   unsigned long long total_U;    // sum over rounds of |U|
   unsigned long long total_dec;  // sum over rounds of the cut
+  unsigned long long rows_U;     // sum of the row lengths (CSR entries) over U
+  unsigned long long rows_R;     // this round: sum of the row lengths over R
+  unsigned long long pull_sigma; // pull round: sum of the recounted D over U'
+  unsigned long long ntasks_pull;// pull round: tasks over U' appended
   int size_U;                    // |U| of the current round
   int size_Unext;                // this round: survivors appended
   int T;                         // threshold of the current round (clamped)
   int round;                     // l (1-based) of the current round
   unsigned p, q;                 // eps = p / q
+  int mode;                      // GC_UPDATE_AUTO / _PUSH / _PULL
+  int pull_percent;              // AUTO: pull when rows(U') <= pull_percent % of rows(R)
+  int pull_rounds;               // rounds that pulled
   int err;
-  int pad;
 };
+
+static_assert(sizeof(AdgCtl) <= 256, "AdgCtl must fit the pinned read-back buffer");
+
+// Direction of this round's UPDATE, decided on the device after the
+// partition from the entries each direction must sweep: push sweeps the rows
+// of R, pull the rows of U'.  Every kernel of the round evaluates it on the
+// same control block, so they agree without a host round trip.
+#ifdef __CUDACC__
+__device__ __forceinline__ bool adg_pulls(const AdgCtl& c) {
+  if (c.size_Unext == 0 || c.mode == GC_UPDATE_PUSH) return false;
+  if (c.mode == GC_UPDATE_PULL) return true;
+  const unsigned long long rows_up = c.rows_U - c.rows_R;
+  return static_cast<unsigned __int128>(rows_up) * 100u <=
+         static_cast<unsigned __int128>(c.rows_R) * static_cast<unsigned>(c.pull_percent);
+}
+#endif
 
 // Control block of one JP run (must fit the context's 256-byte pinned buffer).
 struct JpCtl {
@@ -181,12 +203,12 @@ struct gc_context {
   int num_sms = 0;
   int coop = 0;
   int timing = 0;
+  gc_options opt{};                       // the options of gc_create, defaults filled in
   long long core_target = kCoreDefault_;  // JP-ADG core size (vertices)
-  // Failure injection, for tests of the error paths (set from the
-  // environment at gc_create): the bound of every device-side wait, a
-  // vertex whose colour is never published (so that its successors' waits
-  // run out), and allocation failure.
-  unsigned long long wait_ns = gc::kWaitLimitNs;
+  unsigned long long wait_ns = gc::kWaitLimitNs;  // bound of every device-side wait
+  // Failure injection, for tests of the error paths (read from the
+  // environment at gc_create): a vertex whose colour is never published (so
+  // that its successors' waits run out), and allocation failure.
   int stall_vertex = -1;
   bool fail_alloc = false;
   int core_cluster = 0;                   // CTAs of the core cluster (0: not chosen yet)

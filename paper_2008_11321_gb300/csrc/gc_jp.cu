@@ -881,13 +881,22 @@ jpf_core_solve_kernel(const int* __restrict__ order, const long long* __restrict
   unsigned short* def = s_def + warp * kDeferLane * 32 + lane;
   const unsigned col_r = lane < nctas ? cluster_map(s_col, lane) : 0u;  // copy in CTA `lane`
   const uint4* groups = reinterpret_cast<const uint4*>(stream);
+  // the wait bound (counted from the kernel's start) and the injected stall,
+  // kept in shared memory: the inner loops are sensitive to every register
+  __shared__ unsigned long long s_wait_ns;
+  __shared__ int s_stall;
+  if (threadIdx.x == 0) {
+    s_wait_ns = ctl->wait_ns;
+    s_stall = ctl->stall;
+  }
+  __syncthreads();
   const unsigned long long t0 = global_ns();
   bool timed_out = false;
-  // (the core's waits keep the fixed bound: its inner loops are sensitive to
-  // every register, and a stalled vertex is injected outside the core)
-  auto expired = [&]() { return timed_out || ld_relaxed(&ctl->err) != 0 || global_ns() - t0 > kWaitLimitNs; };
+  auto expired = [&]() { return timed_out || ld_relaxed(&ctl->err) != 0 || global_ns() - t0 > s_wait_ns; };
   int local_max = 0;
   for (int i = nwc * rank + warp; i < kc; i += nwc * nctas) {
+    // an injected fault: this vertex never publishes its colour
+    const bool stalled = s_stall >= 0 && __ldg(order + i) == s_stall;
     const long long a = qoff[i], b = qoff[i + 1];
     const int np = static_cast<int>(b - a);
     const int nw = np / 32 + 1 < kBitWords ? np / 32 + 1 : kBitWords;
@@ -988,7 +997,7 @@ jpf_core_solve_kernel(const int* __restrict__ order, const long long* __restrict
       }
       timed_out = __any_sync(kFull, timed_out);
     }
-    if (lane < nctas) st_cluster_u16(col_r + 2u * static_cast<unsigned>(i), static_cast<unsigned short>(c));
+    if (lane < nctas && !stalled) st_cluster_u16(col_r + 2u * static_cast<unsigned>(i), static_cast<unsigned short>(c));
     local_max = c > local_max ? c : local_max;
   }
   local_max = warp_max(local_max);
@@ -1003,20 +1012,17 @@ jpf_core_solve_kernel(const int* __restrict__ order, const long long* __restrict
   }
 }
 
-// Shape of the core cluster: warps per CTA (GC_CORE_WARPS, default
+// Shape of the core cluster: warps per CTA (gc_options.core_warps, default
 // kCoreWarpsDefault) and the largest cluster (16, 8, ..., 1 CTAs) the device
-// can place with the core's largest shared-memory footprint; GC_CORE_CLUSTER
-// may ask for fewer CTAs.
+// can place with the core's largest shared-memory footprint;
+// gc_options.core_cluster may ask for fewer CTAs.
 cudaError_t core_cluster_size(gc_context* ctx, int* out) {
   if (ctx->core_cluster > 0) {
     *out = ctx->core_cluster;
     return cudaSuccess;
   }
-  int warps = kCoreWarpsDefault;
-  if (const char* env = getenv("GC_CORE_WARPS")) {
-    const int v = atoi(env);
-    if (v >= 1 && v <= kCoreWarps) warps = v;
-  }
+  const int warps = ctx->opt.core_warps >= 1 && ctx->opt.core_warps <= kCoreWarps ? ctx->opt.core_warps
+                                                                                  : kCoreWarpsDefault;
   ctx->core_warps = warps;
   const size_t smem_max = core_smem_bytes(warps, kCoreMax);
   cudaError_t e = cudaFuncSetAttribute(jpf_core_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1025,10 +1031,7 @@ cudaError_t core_cluster_size(gc_context* ctx, int* out) {
   e = cudaFuncSetAttribute(jpf_core_solve_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
   int limit = kCoreClusterMax;
-  if (const char* env = getenv("GC_CORE_CLUSTER")) {
-    const int v = atoi(env);
-    if (v >= 1 && v < limit) limit = v;
-  }
+  if (ctx->opt.core_cluster >= 1 && ctx->opt.core_cluster < limit) limit = ctx->opt.core_cluster;
   int best = 1;
   for (int cs = 1; cs <= limit; cs *= 2) {
     cudaLaunchConfig_t cfg = {};
@@ -1061,6 +1064,7 @@ cudaError_t launch_bulk(gc_context* ctx, JpCtl* ctl, unsigned long long* cursors
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jp_color_kernel<Key>, kJpThreads, 0);
   if (e != cudaSuccess) return e;
+  if (ctx->opt.bulk_blocks_per_sm > 0 && ctx->opt.bulk_blocks_per_sm < per_sm) per_sm = ctx->opt.bulk_blocks_per_sm;
   if (per_sm < 1) per_sm = 1;
   jp_color_kernel<Key><<<ctx->num_sms * per_sm, kJpThreads, 0, s>>>(ctl, cursors, row_ptr, col, key, big, nbig,
                                                                    small, nsmall, color);

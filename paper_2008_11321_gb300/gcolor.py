@@ -22,7 +22,8 @@ GC_OK, GC_ERR_INVALID_ARG, GC_ERR_INVALID_GRAPH, GC_ERR_OOM = 0, 1, 2, 3
 GC_ERR_CUDA, GC_ERR_TIMEOUT, GC_ERR_OVERFLOW = 4, 5, 6
 
 # Every symbol declared in include/gcolor.h.
-EXPORTS = ("gc_status_str", "gc_create", "gc_destroy", "gc_get_stats", "gc_set_timing",
+EXPORTS = ("gc_status_str", "gc_options_init", "gc_create", "gc_get_options", "gc_destroy", "gc_get_stats",
+           "gc_set_timing",
            "gc_validate_csr", "gc_adg_partition", "gc_make_priority", "gc_jp_color",
            "gc_color_graph", "gc_color_graph_host", "gc_adg_partition_noalloc", "gc_color_batch",
            "gc_color_batch_list", "gc_make_priority_kind", "gc_adg_m_partition", "gc_color_graph_m",
@@ -30,6 +31,8 @@ EXPORTS = ("gc_status_str", "gc_create", "gc_destroy", "gc_get_stats", "gc_set_t
 
 # priority kinds of gc_make_priority_kind
 GC_PRIO_R, GC_PRIO_FF, GC_PRIO_LF, GC_PRIO_LLF = 0, 1, 2, 3
+# ADG UPDATE directions (gc_options.update_mode)
+GC_UPDATE_AUTO, GC_UPDATE_PUSH, GC_UPDATE_PULL = 0, 1, 2
 
 
 class GcError(RuntimeError):
@@ -52,6 +55,27 @@ class gc_job(ctypes.Structure):
     _fields_ = [("eps_p", ctypes.c_uint32), ("eps_q", ctypes.c_uint32), ("seed", ctypes.c_uint64)]
 
 
+class gc_options(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("core_target", ctypes.c_int32),
+                ("core_cluster", ctypes.c_int32), ("core_warps", ctypes.c_int32), ("dec_tail", ctypes.c_int32),
+                ("update_mode", ctypes.c_int32), ("pull_percent", ctypes.c_int32),
+                ("bulk_blocks_per_sm", ctypes.c_int32), ("wait_limit_ms", ctypes.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "struct_size"}
+
+
+def make_options(**fields) -> gc_options:
+    """gc_options with the library's defaults, then the given fields."""
+    o = gc_options()
+    _check(load().gc_options_init(ctypes.byref(o)), "gc_options_init")
+    for k, v in fields.items():
+        if k not in dict(gc_options._fields_) or k == "struct_size":
+            raise KeyError(f"gc_options has no field {k!r}")
+        setattr(o, k, int(v))
+    return o
+
+
 class gc_stats(ctypes.Structure):
     _fields_ = [("adg_rounds", ctypes.c_int32), ("num_colors", ctypes.c_int32),
                 ("sum_U", ctypes.c_int64), ("sum_decrements", ctypes.c_int64),
@@ -63,7 +87,7 @@ class gc_stats(ctypes.Structure):
                 ("core_degree_sum", ctypes.c_int64), ("core_ctas", ctypes.c_int32),
                 ("sim_iterations", ctypes.c_int64), ("dec_internal_edges", ctypes.c_int64),
                 ("ms_dec_extract", ctypes.c_float), ("ms_dec_iterate", ctypes.c_float),
-                ("dec_tail_partitions", ctypes.c_int64)]
+                ("dec_tail_partitions", ctypes.c_int64), ("adg_pull_rounds", ctypes.c_int32)]
 
 
 _lib = None
@@ -83,8 +107,12 @@ def load(path: str = LIB_PATH):
     P = ctypes.POINTER
     lib.gc_status_str.restype = ctypes.c_char_p
     lib.gc_status_str.argtypes = [ctypes.c_int]
+    lib.gc_options_init.restype = ctypes.c_int
+    lib.gc_options_init.argtypes = [P(gc_options)]
     lib.gc_create.restype = ctypes.c_int
-    lib.gc_create.argtypes = [P(vp), ctypes.c_int]
+    lib.gc_create.argtypes = [P(vp), ctypes.c_int, P(gc_options)]
+    lib.gc_get_options.restype = ctypes.c_int
+    lib.gc_get_options.argtypes = [vp, P(gc_options)]
     lib.gc_destroy.restype = None
     lib.gc_destroy.argtypes = [vp]
     lib.gc_get_stats.restype = ctypes.c_int
@@ -223,12 +251,16 @@ class DeviceBatch:
 
 
 class Context:
-    """Owns a gc_context (scratch memory on one device)."""
+    """Owns a gc_context (scratch memory on one device).  `options` is a
+    gc_options, a dict of its fields, or None for the defaults."""
 
-    def __init__(self, device: int = 0):
+    def __init__(self, device: int = 0, options=None):
         self._lib = load()
+        if isinstance(options, dict):
+            options = make_options(**options)
         h = ctypes.c_void_p()
-        _check(self._lib.gc_create(ctypes.byref(h), device), "gc_create")
+        _check(self._lib.gc_create(ctypes.byref(h), device, ctypes.byref(options) if options is not None else None),
+               "gc_create")
         self.handle = h
         self.device = device
 
@@ -250,6 +282,11 @@ class Context:
         self.close()
 
     # -- the C ABI, one method per entry point ------------------------------
+    def gc_get_options(self) -> gc_options:
+        o = gc_options()
+        _check(self._lib.gc_get_options(self.handle, ctypes.byref(o)), "gc_get_options")
+        return o
+
     def gc_set_timing(self, enable: bool):
         _check(self._lib.gc_set_timing(self.handle, int(enable)), "gc_set_timing")
 

@@ -48,7 +48,7 @@ def test_null_arguments_rejected_without_device_work(lib):
     assert lib.gc_adg_partition(None, ctypes.byref(csr), 1, 100, None, ctypes.byref(rounds), None) == \
         gcp.GC_ERR_INVALID_ARG
     assert lib.gc_color_graph(None, None, 1, 100, 42, None, None, None, None, None) == gcp.GC_ERR_INVALID_ARG
-    assert lib.gc_create(None, 0) == gcp.GC_ERR_INVALID_ARG
+    assert lib.gc_create(None, 0, None) == gcp.GC_ERR_INVALID_ARG
     for call in (lambda: lib.gc_dec_itr_color(None, None, None, 1, 42, None, None, None),
                  lambda: lib.gc_color_graph_dec_itr(None, None, 1, 100, 42, None, None, None, None, None),
                  lambda: lib.gc_adg_o_order(None, None, 1, 100, None, None, None, None, None),
@@ -104,3 +104,29 @@ def test_binding_signatures_match_header(lib):
             kind = _ctype_kind(t)
             want = _decl_kind(decl)
             assert kind == want or (want == "i32" and t is ctypes.c_int), (name, decl, t)
+
+
+def test_options_defaults_and_range_checks(lib):
+    # defaults come from the library; out-of-range fields are rejected by
+    # gc_create before it touches any device
+    o = gcp.make_options()
+    assert o.struct_size == ctypes.sizeof(gcp.gc_options)
+    assert o.as_dict() == {"core_target": 16384, "core_cluster": 16, "core_warps": 8, "dec_tail": 1,
+                           "update_mode": gcp.GC_UPDATE_AUTO, "pull_percent": 100, "bulk_blocks_per_sm": 0,
+                           "wait_limit_ms": 4000}
+    h = ctypes.c_void_p()
+    bad = [dict(core_target=-1), dict(core_target=32769), dict(core_cluster=0), dict(core_cluster=17),
+           dict(core_warps=0), dict(core_warps=33), dict(dec_tail=2), dict(update_mode=3),
+           dict(pull_percent=-1), dict(bulk_blocks_per_sm=33), dict(wait_limit_ms=0),
+           dict(wait_limit_ms=600001)]
+    for fields in bad:
+        o = gcp.make_options(**fields)
+        assert lib.gc_create(ctypes.byref(h), 0, ctypes.byref(o)) == gcp.GC_ERR_INVALID_ARG, fields
+        assert not h.value
+    o = gcp.make_options()
+    o.struct_size = ctypes.sizeof(gcp.gc_options) + 4  # newer than the library
+    assert lib.gc_create(ctypes.byref(h), 0, ctypes.byref(o)) == gcp.GC_ERR_INVALID_ARG
+    with pytest.raises(KeyError):
+        gcp.make_options(no_such_field=1)
+    assert lib.gc_options_init(None) == gcp.GC_ERR_INVALID_ARG
+    assert lib.gc_get_options(None, ctypes.byref(o)) == gcp.GC_ERR_INVALID_ARG

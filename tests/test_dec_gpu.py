@@ -37,20 +37,10 @@ def ctx():
 
 @pytest.fixture(scope="module")
 def ctx_notail():
-    # every SIM-COL iteration as GPU-wide launches (GC_DEC_TAIL is read when
-    # the context is created)
+    # every SIM-COL iteration as GPU-wide launches
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    import os
-    old = os.environ.get("GC_DEC_TAIL")
-    os.environ["GC_DEC_TAIL"] = "0"
-    try:
-        c = gcp.Context(0)
-    finally:
-        if old is None:
-            del os.environ["GC_DEC_TAIL"]
-        else:
-            os.environ["GC_DEC_TAIL"] = old
+    c = gcp.Context(0, {"dec_tail": 0})
     yield c
     c.close()
 

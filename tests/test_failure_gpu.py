@@ -23,8 +23,9 @@ pytestmark = pytest.mark.gpu
 import paper_2008_11321_gb300 as gcp  # noqa: E402
 
 
-def context(env):
-    """A context created with `env` set (the library reads it at gc_create)."""
+def context(env, options=None):
+    """A context created with `env` set (the library reads its failure
+    injection variables at gc_create) and the given gc_options fields."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2008_11321_gb300 import _build
@@ -32,7 +33,7 @@ def context(env):
     old = {k: os.environ.get(k) for k in env}
     os.environ.update(env)
     try:
-        return gcp.Context(0)
+        return gcp.Context(0, options)
     finally:
         for k, v in old.items():
             if v is None:
@@ -57,9 +58,9 @@ def colour(ctx, g):
 
 
 def test_no_core_matches_oracle(graph):
-    # GC_CORE_TARGET=0: every vertex goes through the bulk kernels
+    # core_target = 0: every vertex goes through the bulk kernels
     g, _, oc, onc = graph
-    with context({"GC_CORE_TARGET": "0"}) as ctx:
+    with context({}, {"core_target": 0}) as ctx:
         nc, c = colour(ctx, g)
         assert nc == onc and np.array_equal(c, oc)
         assert ctx.gc_get_stats().core_vertices == 0
@@ -72,8 +73,7 @@ def test_wait_runs_out_and_device_stays_usable(graph):
     deg = g.degrees()
     cand = np.flatnonzero(deg > 0)
     v = int(cand[np.lexsort((cand, key[cand]))[-1]])
-    env = {"GC_CORE_TARGET": "0", "GC_WAIT_LIMIT_MS": "200", "GC_INJECT_STALL": str(v)}
-    with context(env) as ctx:
+    with context({"GC_INJECT_STALL": str(v)}, {"core_target": 0, "wait_limit_ms": 200}) as ctx:
         t0 = time.perf_counter()
         with pytest.raises(gcp.GcError) as err:
             colour(ctx, g)
@@ -94,3 +94,40 @@ def test_allocation_failure_reported(graph):
     with context({}) as ctx:
         nc, c = colour(ctx, g)
         assert nc == onc and np.array_equal(c, oc)
+
+
+def test_core_wait_runs_out_and_device_stays_usable(graph):
+    # a stalled vertex inside the core (the default core of 16384 vertices
+    # holds the top of the priority order): the core cluster's waits on it
+    # run out after the limit, the call returns GC_ERR_TIMEOUT, and the
+    # device and a fresh context then colour correctly
+    g, ob, oc, onc = graph
+    key = oracle.priority(ob, 42)
+    deg = g.degrees()
+    cand = np.flatnonzero(deg > 0)
+    v = int(cand[np.lexsort((cand, key[cand]))[-1]])  # the first vertex of the core
+    with context({"GC_INJECT_STALL": str(v)}, {"wait_limit_ms": 300}) as ctx:
+        t0 = time.perf_counter()
+        with pytest.raises(gcp.GcError) as err:
+            colour(ctx, g)
+        elapsed = time.perf_counter() - t0
+        assert err.value.status == gcp.GC_ERR_TIMEOUT
+        assert ctx.gc_get_stats().core_vertices > 0
+        assert elapsed < 5.0
+    with context({}) as ctx:
+        nc, c = colour(ctx, g)
+        assert nc == onc and np.array_equal(c, oc)
+
+
+def test_two_contexts_with_different_options_agree(graph):
+    # tunables change speed only: two contexts with different options colour
+    # the same graph identically, and as the oracle does
+    g, ob, oc, onc = graph
+    with context({}, {"core_target": 1024, "core_cluster": 4, "core_warps": 4, "update_mode": gcp.GC_UPDATE_PULL,
+                      "bulk_blocks_per_sm": 1}) as a, \
+            context({}, {"core_target": 32768, "update_mode": gcp.GC_UPDATE_PUSH}) as b:
+        assert a.gc_get_options().core_target == 1024
+        for ctx in (a, b):
+            nc, c = colour(ctx, g)
+            assert nc == onc and np.array_equal(c, oc)
+        assert a.gc_get_stats().adg_pull_rounds > 0 and b.gc_get_stats().adg_pull_rounds == 0

@@ -325,3 +325,57 @@ def test_invalid_eps_rejected(ctx):
         with pytest.raises(gcp.GcError) as e:
             ctx.gc_color_graph(g, p, q, 42, color)
         assert e.value.status == gcp.GC_ERR_INVALID_ARG
+
+
+# ---------------------------------------------------------------- UPDATE direction
+
+@pytest.fixture(scope="module")
+def ctx_push():
+    c = gcp.Context(0, {"update_mode": gcp.GC_UPDATE_PUSH})
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def ctx_pull():
+    c = gcp.Context(0, {"update_mode": gcp.GC_UPDATE_PULL})
+    yield c
+    c.close()
+
+
+DIRECTION_GRAPHS = [gg.rmat(14, 16, seed=3), gg.barabasi_albert(20000, 8, 5), gg.erdos_renyi(30000, 150000, 9),
+                    gg.grid(120, 130), star(5000), complete(300), path(60), empty(40)]
+
+
+@pytest.mark.parametrize("g", DIRECTION_GRAPHS, ids=lambda g: g.name)
+@pytest.mark.parametrize("p,q", [(1, 100), (1, 2)])
+def test_push_pull_auto_identical(ctx, ctx_push, ctx_pull, g, p, q):
+    # Section 5, "Push vs. Pull": a pull round recounts every survivor's
+    # degree instead of decrementing it; batches, rounds, colours and the
+    # statistics the degree-sum rule carries (sum |U|, decrements) are the
+    # same in every direction and equal the oracle's
+    ob, oc, onr, onc = oracle.jp_adg(g, p, q, 42)
+    _, _, log = oracle.adg(g, p, q, log=True)
+    src = np.repeat(np.arange(g.n), g.degrees())
+    stats = []
+    for c in (ctx, ctx_push, ctx_pull):
+        b, col, nr, nc = color_graph(c, g, p, q, 42)
+        assert nr == onr and np.array_equal(b, ob)
+        assert nc == onc and np.array_equal(col, oc)
+        stats.append(c.gc_get_stats())
+    assert len({(s.sum_U, s.sum_decrements) for s in stats}) == 1
+    assert stats[0].sum_U == int(log["U"].sum())
+    assert stats[0].sum_decrements == int(np.sum(ob[g.col_idx] > ob[src]))
+    assert stats[1].adg_pull_rounds == 0
+    if g.nnz > 0 and onr > 1:
+        assert stats[2].adg_pull_rounds >= 1
+
+
+def test_auto_pulls_when_r_outweighs_u(ctx):
+    # eps = 1/2 on a Barabasi-Albert graph removes most of U every round:
+    # the rows of U' hold fewer entries than the rows of R, so AUTO pulls
+    g = gg.barabasi_albert(50000, 4, 11)
+    b, c, nr, nc = color_graph(ctx, g, 1, 2, 42)
+    ob, oc, onr, onc = oracle.jp_adg(g, 1, 2, 42)
+    assert np.array_equal(b, ob) and np.array_equal(c, oc)
+    assert 0 < ctx.gc_get_stats().adg_pull_rounds < nr

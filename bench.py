@@ -270,7 +270,7 @@ def run_variant(args, rank, world):
     dg = gcp.DeviceGraph(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col_idx).to(dev))
     key = torch.empty(n, dtype=torch.int64, device=dev)
     color = torch.empty(n, dtype=torch.int32, device=dev)
-    ctx = gcp.Context(local)
+    ctx = gcp.Context(local, args.options)
     stream = torch.cuda.current_stream(dev)
     for _ in range(args.warmup):
         ctx.gc_make_priority_kind(dg, kind, seed, key)
@@ -355,7 +355,7 @@ def run_dec(args, rank, world):
     batch = torch.empty(n, dtype=torch.int32, device=dev)
     itr = args.algo == "itr"
     ones = torch.ones(n, dtype=torch.int32, device=dev)
-    ctx = gcp.Context(local)
+    ctx = gcp.Context(local, args.options)
     stream = torch.cuda.current_stream(dev)
 
     def colour_step():
@@ -543,7 +543,7 @@ def run_batch(args, rank, world):
                          torch.from_numpy(off).to(dev))
     color = torch.empty(db.n, dtype=torch.int32, device=dev)
     ncol = torch.empty(G, dtype=torch.int32, device=dev)
-    ctx = gcp.Context(dev.index)
+    ctx = gcp.Context(dev.index, args.options)
     stream = torch.cuda.current_stream(dev)
     for _ in range(args.warmup):
         ctx.gc_color_batch(db, jobs, color, None, ncol)
@@ -724,10 +724,14 @@ def main():
     ap.add_argument("--priority", choices=["adg", "adg-m", "adg-o"] + sorted(PRIORITIES), default="adg",
                     help="JP priority: adg (JP-ADG, the default), adg-m (JP-ADG-M), adg-o (JP-ADG-O) or "
                          "another JP variant")
+    ap.add_argument("--options", default=None,
+                    help="gc_options fields for the context, as JSON (e.g. '{\"jp_state16\": 0}'); default: "
+                         "the library's defaults")
     ap.add_argument("--algo", choices=["jp", "dec-itr", "itr"], default="jp",
                     help="colouring: jp (JP with --priority, the default), dec-itr (DEC-ADG-ITR) or itr "
                          "(its SIM-COL on one partition: plain ITR)")
     args = ap.parse_args()
+    args.options = json.loads(args.options) if args.options else None
     if args.warmup < 3:
         print("warning: --warmup below 3 is outside the timing rules", file=sys.stderr)
 
@@ -773,7 +777,7 @@ def main():
     dg = gcp.DeviceGraph(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col_idx).to(dev))
     color = torch.empty(n, dtype=torch.int32, device=dev)
     batch = torch.empty(n, dtype=torch.int32, device=dev)
-    ctx = gcp.Context(local)
+    ctx = gcp.Context(local, args.options)
     stream = torch.cuda.current_stream(dev)
 
     median = args.priority == "adg-m"
@@ -860,6 +864,8 @@ def main():
                    "n": n, "m": m, "eps": f"{p}/{q}" if not median else None, "seed": seed,
                    "adg_rounds": nr, "num_colors": nc, "sum_U": sum_u, "decrements": dec,
                    "parallelism": "replicas" if world > 1 else "single GPU",
+                   "options": ctx.gc_get_options().as_dict(), "jp_state_bits": last["jp_state_bits"],
+                   "adg_pull_rounds": last["adg_pull_rounds"],
                    "l2": f"inputs larger than L2 (col_idx {4 * nnz / 1e9:.2f} GB), no flush"},
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,

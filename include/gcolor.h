@@ -105,6 +105,7 @@ typedef struct {
   int64_t dec_tail_partitions; /* DEC-ADG-ITR: partitions finished by the
                               single-cluster tail (gc_options.dec_tail)      */
   int32_t adg_pull_rounds; /* ADG rounds whose UPDATE pulled (update_mode)     */
+  int32_t jp_state_bits;   /* JP-ADG state word of the last call: 16 or 32     */
 } gc_stats;
 
 /* Human-readable name of a status code (static storage). */
@@ -145,6 +146,10 @@ typedef struct {
   uint32_t wait_limit_ms;  /* bound of every device-side wait, 1..600000 ms
                               (default 4000); a wait that runs out ends the
                               call with GC_ERR_TIMEOUT, context usable       */
+  int32_t jp_state16;      /* 1 (default): JP-ADG keeps each vertex's batch and
+                              colour in a 16-bit word when both fit (the
+                              colour bound is 1 + the largest degree at
+                              removal); 0: always a 32-bit word              */
 } gc_options;
 
 /* Fill *opt with the defaults (and struct_size = sizeof(gc_options)). */

@@ -82,6 +82,7 @@ adg_partition_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
   unsigned long long sum_r = 0, rows_r = 0;
+  int max_d = 0;
   const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
   for (long long base = static_cast<long long>(blockIdx.x) * blockDim.x; base < size_u; base += stride) {
     const long long i = base + threadIdx.x;
@@ -123,6 +124,7 @@ adg_partition_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row
     if (in_r) {
       batch[u] = round;
       sum_r += static_cast<unsigned long long>(d);
+      max_d = d > max_d ? d : max_d;
     }
     if (first) {  // round 1's UPDATE sweeps vertex tiles, no task list
       if (in_r) rows_r += static_cast<unsigned long long>(re - rs);
@@ -163,6 +165,8 @@ adg_partition_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row
   rows_r = warp_sum(rows_r);
   if (lane == 0 && sum_r) atomicAdd(&ctl->sum_R, sum_r);
   if (lane == 0 && rows_r) atomicAdd(&ctl->rows_R, rows_r);
+  max_d = warp_max(max_d);
+  if (lane == 0 && max_d > 0) atomicMax(&ctl->max_removal_degree, max_d);
 }
 
 // Round 1 (vertex_tiles != 0): lane l of a warp owns vertex 32*tile + l and
@@ -349,6 +353,7 @@ gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigne
   const long long n = g->n, nnz = g->nnz;
   *rounds_out = 0;
   ctx->stats.adg_rounds = 0;
+  ctx->adg_max_removal_degree = -1;
   if (n == 0) return GC_OK;
   AdgCtl* ctl = a.take<AdgCtl>(1);
   int* ubuf[2] = {a.take<int>(n), a.take<int>(n)};
@@ -415,6 +420,7 @@ gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigne
   ctx->stats.sum_U = static_cast<int64_t>(h.total_U);
   ctx->stats.sum_decrements = static_cast<int64_t>(h.total_dec);
   ctx->stats.adg_pull_rounds = h.pull_rounds;
+  ctx->adg_max_removal_degree = h.max_removal_degree;
   ctx->stats.adg_rounds = round;
   *rounds_out = round;
   return GC_OK;
@@ -520,6 +526,7 @@ gc_status adg_m_run(gc_context* ctx, Arena a, const gc_csr* g, int* batch, int* 
   const long long n = g->n, nnz = g->nnz;
   *rounds_out = 0;
   ctx->stats.adg_rounds = 0;
+  ctx->adg_max_removal_degree = -1;
   if (n == 0) return GC_OK;
   AdgCtl* ctl = a.take<AdgCtl>(1);
   int* ubuf[2] = {a.take<int>(n), a.take<int>(n)};
@@ -590,6 +597,7 @@ gc_status adg_m_run(gc_context* ctx, Arena a, const gc_csr* g, int* batch, int* 
   ctx->stats.sum_U = static_cast<int64_t>(h.total_U);
   ctx->stats.sum_decrements = static_cast<int64_t>(h.total_dec);
   ctx->stats.adg_pull_rounds = 0;
+  ctx->adg_max_removal_degree = h.max_removal_degree;
   ctx->stats.adg_rounds = round;
   *rounds_out = round;
   return GC_OK;

@@ -54,7 +54,9 @@ struct AdgCtl {
   int mode;                      // GC_UPDATE_AUTO / _PUSH / _PULL
   int pull_percent;              // AUTO: pull when rows(U') <= pull_percent % of rows(R)
   int pull_rounds;               // rounds that pulled
-  int err;
+  int max_removal_degree;        // largest D at removal so far: every colour of
+                                 // JP-ADG is at most this + 1 (a vertex's
+                                 // predecessors are among the neighbours D counts)
 };
 
 static_assert(sizeof(AdgCtl) <= 256, "AdgCtl must fit the pinned read-back buffer");
@@ -215,6 +217,7 @@ struct gc_context {
   bool dec_tail = true;                   // DEC-ADG-ITR: finish small U in one cluster launch
   int tail_cluster = 0;                   // CTAs of that cluster (0: not chosen yet, -1: none fits)
   int core_warps = 0;                     // warps per core CTA
+  int adg_max_removal_degree = -1;        // of the last ADG run (-1: unknown)
   // scratch arena (device)
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
@@ -334,6 +337,16 @@ __device__ __forceinline__ int ld_relaxed(const int* p) {
 
 __device__ __forceinline__ void st_relaxed(int* p, int v) {
   asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_relaxed(const unsigned short* p) {
+  unsigned short v;
+  asm volatile("ld.relaxed.gpu.global.u16 %0, [%1];" : "=h"(v) : "l"(p) : "memory");
+  return static_cast<int>(v);
+}
+
+__device__ __forceinline__ void st_relaxed(unsigned short* p, int v) {
+  asm volatile("st.relaxed.gpu.global.u16 [%0], %1;" ::"l"(p), "h"(static_cast<unsigned short>(v)) : "memory");
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {

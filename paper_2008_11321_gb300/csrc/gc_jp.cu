@@ -65,6 +65,7 @@ __device__ __forceinline__ bool precedes(unsigned long long kw, int w, unsigned 
 // x & cmask().
 
 struct KeyFused {  // JP-ADG: (batch << 32) | rho_R(v), rho_R from one seed
+  using W = int;  // the colour word
   const int* batch;
   unsigned long long seed;
   __device__ __forceinline__ int bat(int v) const { return __ldg(batch + v); }
@@ -88,6 +89,7 @@ struct KeyFused {  // JP-ADG: (batch << 32) | rho_R(v), rho_R from one seed
 // neighbour's word gives both its priority and its colour, and the randomly
 // read state is one n-word array instead of two.
 struct KeyState {
+  using W = int;
   const int* state;  // the colour array during JP-ADG
   unsigned long long seed;
   // a coherent load: colour bits of the array change while JP runs (the
@@ -111,7 +113,38 @@ struct KeyState {
   }
 };
 
+// KeyState in a 16-bit word: batch << cb | colour, with cb colour bits.  It
+// applies when the batch fits 16 - cb bits and every colour fits cb bits:
+// a colour is at most 1 + |pred(v)|, and pred(v) lies among the neighbours
+// that ADG's degree at removal D[v] counts (those in the same or a later
+// batch), so colour <= 1 + max D[v].  On R-MAT scale 24 (7 batches, max D
+// 2,901) 3 + 13 bits suffice, and the randomly read state of the bulk shrinks
+// from 67 MB to 33.5 MB, well inside L2.
+struct KeyState16 {
+  using W = unsigned short;
+  const unsigned short* state;  // the 16-bit state array during JP-ADG
+  unsigned long long seed;
+  int cb;  // colour bits
+  __device__ __forceinline__ int bat(int v) const { return static_cast<int>(static_cast<unsigned>(state[v]) >> cb); }
+  __device__ __forceinline__ unsigned tie(int v) const { return tie_hash(seed, static_cast<unsigned>(v)); }
+  __device__ __forceinline__ unsigned long long operator()(int v) const {
+    return (static_cast<unsigned long long>(static_cast<unsigned>(bat(v))) << 32) | tie(v);
+  }
+  using PG = int;
+  __device__ __forceinline__ PG pgather(int w, const unsigned short* color) const { return ld_relaxed(color + w); }
+  __device__ __forceinline__ bool pred_g(PG x, int w, unsigned long long kv, int v) const {
+    const unsigned long long kw = (static_cast<unsigned long long>(static_cast<unsigned>(x) >> cb) << 32) | tie(w);
+    return precedes(kw, w, kv, v);
+  }
+  __device__ __forceinline__ int color_g(PG x, const unsigned short*, int) const { return x & cmask(); }
+  __device__ __forceinline__ int cmask() const { return (1 << cb) - 1; }
+  __device__ __forceinline__ int cword(unsigned long long kv, int c) const {
+    return static_cast<int>(static_cast<unsigned>(kv >> 32) << cb) | c;
+  }
+};
+
 struct KeyPacked {  // JP-ADG over many disjoint graphs: rho_R precomputed per vertex
+  using W = int;
   const int* batch;
   const unsigned* tiev;
   __device__ __forceinline__ int bat(int v) const { return __ldg(batch + v); }
@@ -133,6 +166,7 @@ struct KeyPacked {  // JP-ADG over many disjoint graphs: rho_R precomputed per v
 // the top 8 bits of the colour word as in KeyState; D is read only for a
 // neighbour of the same batch.
 struct KeyStateD {
+  using W = int;
   const int* state;  // the colour array during JP-ADG-O
   const int* D;
   __device__ __forceinline__ unsigned long long operator()(int v) const {
@@ -155,6 +189,7 @@ struct KeyStateD {
 };
 
 struct KeyGiven {  // any priority array
+  using W = int;
   const unsigned long long* prio;
   __device__ __forceinline__ unsigned long long operator()(int v) const { return __ldg(prio + v); }
   using PG = unsigned long long;
@@ -184,7 +219,8 @@ struct JpLimits {
 // ---------------------------------------------------------------------------
 // Waiting on a colour word (global memory), bounded, with backoff.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int wait_color(const int* p, int cmask, JpCtl* ctl, const JpLimits& lim,
+template <class Wd>
+__device__ __forceinline__ int wait_color(const Wd* p, int cmask, JpCtl* ctl, const JpLimits& lim,
                                           unsigned long long& spins) {
   int c = ld_relaxed(p) & cmask;
   if (c != 0) return c;
@@ -213,7 +249,7 @@ __device__ __forceinline__ int wait_color(const int* p, int cmask, JpCtl* ctl, c
 // position mask and waited on after the scan.
 template <class Key>
 __device__ int color_lane(int v, const long long* __restrict__ row_ptr, const int* __restrict__ col,
-                          const Key& key, int* color, JpCtl* ctl, const JpLimits& lim,
+                          const Key& key, typename Key::W* color, JpCtl* ctl, const JpLimits& lim,
                           unsigned long long& spins) {
   constexpr int U = 4;
   const unsigned long long kv = key(v);
@@ -258,7 +294,7 @@ __device__ int color_lane(int v, const long long* __restrict__ row_ptr, const in
 // are scanned again for the next window.
 template <class Key>
 __device__ int color_warp(int v, unsigned* bm, const long long* __restrict__ row_ptr,
-                          const int* __restrict__ col, const Key& key, int* color, JpCtl* ctl,
+                          const int* __restrict__ col, const Key& key, typename Key::W* color, JpCtl* ctl,
                           const JpLimits& lim, unsigned long long& spins) {
   const int lane = threadIdx.x & 31;
   const unsigned long long kv = key(v);
@@ -328,10 +364,10 @@ __device__ int color_warp(int v, unsigned* bm, const long long* __restrict__ row
 // the two counters cursors[0] and cursors[1].  nbig < 0 means: counts from
 // ctl, small list right after the big one.
 template <class Key>
-__global__ void __launch_bounds__(kJpThreads)
+__global__ void __launch_bounds__(kJpThreads, 5)
 jp_color_kernel(JpCtl* ctl, unsigned long long* cursors, const long long* __restrict__ row_ptr,
                 const int* __restrict__ col, Key key, const int* __restrict__ big, long long nbig,
-                const int* __restrict__ small, long long nsmall, int* color) {
+                const int* __restrict__ small, long long nsmall, typename Key::W* color) {
   __shared__ unsigned s_bm[kJpWarps][kColorWin / 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (nbig < 0) {
@@ -494,16 +530,16 @@ __device__ __forceinline__ long long bucket_of(int batch, unsigned h, const Buck
 template <class Key>
 __global__ void __launch_bounds__(256)
 jpf_hist_kernel(Key key, const long long* __restrict__ row_ptr, long long n, BucketPlan bp,
-                unsigned long long* __restrict__ cnt, int* __restrict__ color, JpCtl* ctl) {
+                unsigned long long* __restrict__ cnt, typename Key::W* __restrict__ color, JpCtl* ctl) {
   bool isolated = false;
   for (long long v = gtid(); v < n; v += gstride()) {
     const long long deg = row_ptr[v + 1] - row_ptr[v];
     if (deg == 0) {
-      color[v] = key.cword(key(static_cast<int>(v)), 1);  // isolated: no predecessor, smallest colour
+      color[v] = static_cast<typename Key::W>(key.cword(key(static_cast<int>(v)), 1));  // isolated: colour 1
       isolated = true;
       continue;
     }
-    color[v] = key.cword(key(static_cast<int>(v)), 0);
+    color[v] = static_cast<typename Key::W>(key.cword(key(static_cast<int>(v)), 0));
     const long long b = bucket_of(key.bat(static_cast<int>(v)), key.tie(static_cast<int>(v)), bp);
     const long long cls = deg > kSmallDeg ? 0 : 1;
     atomicAdd(&cnt[cls * (bp.B + 1) + b], 1ull);
@@ -817,14 +853,20 @@ __global__ void jpf_compact_kernel(const int* __restrict__ preds, const long lon
 // until every vertex is done.
 //
 // Used colours are marked in per-lane bitmaps (word q of lane l at q*32 + l,
-// so a warp's marks never collide in a bank and need no atomics), then OR-ed
-// across lanes with a rotated read; a pass covers a 512-colour window and
-// only ceil((|pred|+1)/32) words of it can hold the answer.
+// so a warp's marks never collide in a bank and need no atomics) while the
+// list is scanned, then OR-ed across lanes (a rotated read) into the warp's
+// merged words BEFORE it waits on the set-aside predecessors: those mark the
+// merged words directly as they arrive, so once the last one lands only one
+// word per lane is read to find the smallest free colour -- the 32-way OR is
+// off the dependency chain.  A pass covers a 512-colour window and only
+// ceil((|pred|+1)/32) words of it can hold the answer.
 constexpr int kBitWords = 16;       // 512-colour window per pass
 constexpr int kDeferLane = 40;      // predecessors a lane sets aside per vertex
 constexpr int kCoreClusterMax = 16;
-// shared memory of one core warp: its bitmaps and set-aside predecessors
-constexpr size_t kCoreWarpBytes = kBitWords * 32 * sizeof(unsigned) + kDeferLane * 32 * sizeof(unsigned short);
+// shared memory of one core warp: its bitmaps, merged words and set-aside
+// predecessors
+constexpr size_t kCoreWarpBytes = kBitWords * 32 * sizeof(unsigned) + kBitWords * sizeof(unsigned) +
+                                  kDeferLane * 32 * sizeof(unsigned short);
 
 size_t core_smem_bytes(int warps, long long kc) {
   return static_cast<size_t>(warps) * kCoreWarpBytes + static_cast<size_t>(kc) * sizeof(unsigned short);
@@ -861,13 +903,15 @@ __device__ __forceinline__ void st_cluster_u16(unsigned addr, unsigned short v) 
   asm volatile("st.relaxed.cluster.shared::cluster.u16 [%0], %1;" ::"r"(addr), "h"(v) : "memory");
 }
 
+template <class W>
 __global__ void __launch_bounds__(kCoreThreads, 1)
 jpf_core_solve_kernel(const int* __restrict__ order, const long long* __restrict__ qoff,
-                      const unsigned short* __restrict__ stream, JpCtl* ctl, int* color) {
+                      const unsigned short* __restrict__ stream, JpCtl* ctl, W* color) {
   extern __shared__ __align__(16) unsigned char s_dyn[];
   const int nwc = blockDim.x >> 5;  // warps per CTA
   unsigned* s_bits = reinterpret_cast<unsigned*>(s_dyn);  // [warp][word][lane]
-  unsigned short* s_def = reinterpret_cast<unsigned short*>(s_bits + nwc * kBitWords * 32);  // [warp][slot][lane]
+  unsigned* s_merged = s_bits + nwc * kBitWords * 32;      // [warp][word]
+  unsigned short* s_def = reinterpret_cast<unsigned short*>(s_merged + nwc * kBitWords);  // [warp][slot][lane]
   unsigned short* s_col = s_def + nwc * kDeferLane * 32;
   const int kc = static_cast<int>(ctl->ncore);
   const int rank = static_cast<int>(cluster_rank()), nctas = static_cast<int>(cluster_ctas());
@@ -878,6 +922,7 @@ jpf_core_solve_kernel(const int* __restrict__ order, const long long* __restrict
 
   volatile unsigned short* vcol = s_col;
   unsigned* bits = s_bits + warp * kBitWords * 32;
+  unsigned* merged = s_merged + warp * kBitWords;
   unsigned short* def = s_def + warp * kDeferLane * 32 + lane;
   const unsigned col_r = lane < nctas ? cluster_map(s_col, lane) : 0u;  // copy in CTA `lane`
   const uint4* groups = reinterpret_cast<const uint4*>(stream);
@@ -904,9 +949,15 @@ jpf_core_solve_kernel(const int* __restrict__ order, const long long* __restrict
     for (int base = 0; !timed_out; base += 32 * nw) {
       for (int q = 0; q < nw; ++q) bits[q * 32 + lane] = 0u;
       int nd = 0;
+      bool late = false;  // after the merge: marks go to the merged words
       auto put = [&](int cj) {
         const int x = cj - base - 1;
-        if (x >= 0 && x < 32 * nw) bits[(x >> 5) * 32 + lane] |= 1u << (x & 31);
+        if (x >= 0 && x < 32 * nw) {
+          if (!late)
+            bits[(x >> 5) * 32 + lane] |= 1u << (x & 31);
+          else
+            atomicOr(&merged[x >> 5], 1u << (x & 31));
+        }
       };
       // marks the set-aside predecessors coloured by now and keeps the rest
       auto sweep = [&]() {
@@ -980,13 +1031,27 @@ jpf_core_solve_kernel(const int* __restrict__ order, const long long* __restrict
           }
         }
       }
-      drain(0);
       __syncwarp();
       // lane q < nw ORs word q over all lanes (rotated so no bank repeats)
-      unsigned word = 0u;
-      if (lane < nw)
+      // into the merged words, while set-aside predecessors may still be
+      // uncoloured
+      if (lane < nw) {
+        unsigned word = 0u;
         for (int l = 0; l < 32; ++l) word |= bits[lane * 32 + ((lane + l) & 31)];
-      const unsigned freeb = lane < nw ? ~word : 0u;
+        merged[lane] = word;
+      }
+      __syncwarp();
+      late = true;
+      drain(0);
+      __syncwarp();
+      // a wait that ran out on any lane ends this warp's colouring: agree on
+      // it before any warp-wide step, so that every lane leaves together and
+      // no collective below or in a later vertex runs with lanes missing
+      if (__any_sync(kFull, timed_out)) {
+        timed_out = true;
+        break;
+      }
+      const unsigned freeb = lane < nw ? ~merged[lane] : 0u;
       const unsigned fm = __ballot_sync(kFull, freeb != 0u);
       __syncwarp();
       if (fm) {
@@ -995,7 +1060,6 @@ jpf_core_solve_kernel(const int* __restrict__ order, const long long* __restrict
         c = base + f * 32 + __ffs(fb);
         break;
       }
-      timed_out = __any_sync(kFull, timed_out);
     }
     if (lane < nctas && !stalled) st_cluster_u16(col_r + 2u * static_cast<unsigned>(i), static_cast<unsigned short>(c));
     local_max = c > local_max ? c : local_max;
@@ -1008,7 +1072,7 @@ jpf_core_solve_kernel(const int* __restrict__ order, const long long* __restrict
   for (int t = threadIdx.x;; t += blockDim.x) {  // this CTA's vertices, increasing
     const int i = nwc * (rank + nctas * (t / nwc)) + t % nwc;
     if (i >= kc) break;
-    color[order[i]] |= s_col[i];  // the word holds 0 or the vertex's batch bits
+    color[order[i]] = static_cast<W>(color[order[i]] | s_col[i]);  // the word holds 0 or the batch bits
   }
 }
 
@@ -1025,11 +1089,14 @@ cudaError_t core_cluster_size(gc_context* ctx, int* out) {
                                                                                   : kCoreWarpsDefault;
   ctx->core_warps = warps;
   const size_t smem_max = core_smem_bytes(warps, kCoreMax);
-  cudaError_t e = cudaFuncSetAttribute(jpf_core_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem_max));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(jpf_core_solve_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
+  for (const void* k : {reinterpret_cast<const void*>(jpf_core_solve_kernel<int>),
+                        reinterpret_cast<const void*>(jpf_core_solve_kernel<unsigned short>)}) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_max));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
   int limit = kCoreClusterMax;
   if (ctx->opt.core_cluster >= 1 && ctx->opt.core_cluster < limit) limit = ctx->opt.core_cluster;
   int best = 1;
@@ -1046,7 +1113,7 @@ cudaError_t core_cluster_size(gc_context* ctx, int* out) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int ncl = 0;
-    if (cudaOccupancyMaxActiveClusters(&ncl, jpf_core_solve_kernel, &cfg) != cudaSuccess || ncl < 1) {
+    if (cudaOccupancyMaxActiveClusters(&ncl, jpf_core_solve_kernel<int>, &cfg) != cudaSuccess || ncl < 1) {
       cudaGetLastError();  // clear the query's error; keep the last size that fits
       break;
     }
@@ -1060,7 +1127,7 @@ cudaError_t core_cluster_size(gc_context* ctx, int* out) {
 template <class Key>
 cudaError_t launch_bulk(gc_context* ctx, JpCtl* ctl, unsigned long long* cursors, const long long* row_ptr,
                         const int* col, const Key& key, const int* big, long long nbig, const int* small,
-                        long long nsmall, int* color, cudaStream_t s) {
+                        long long nsmall, typename Key::W* color, cudaStream_t s) {
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jp_color_kernel<Key>, kJpThreads, 0);
   if (e != cudaSuccess) return e;
@@ -1120,8 +1187,9 @@ struct CoreBufs {
   long long* temp;  // at least scan_temp_elems(kCoreMax + 1) elements
 };
 
+template <class W>
 gc_status run_core(gc_context* ctx, const gc_csr* g, const int* order, const int* D, long long kc, JpCtl* ctl,
-                   const CoreBufs& cb, int* color, cudaStream_t s) {
+                   const CoreBufs& cb, W* color, cudaStream_t s) {
   const long long n = g->n;
   const long long* rp = row_ptr_of(g);
   const int blocks = ctx->num_sms * 8;
@@ -1177,7 +1245,7 @@ gc_status run_core(gc_context* ctx, const gc_csr* g, const int* order, const int
     cfg.numAttrs = 1;
     ctx->stats.core_ctas = ncta;
     ctx->timer_begin(gc_context::kTCoreSolve, s);
-    GC_TRY_CUDA(cudaLaunchKernelEx(&cfg, jpf_core_solve_kernel, static_cast<const int*>(order),
+    GC_TRY_CUDA(cudaLaunchKernelEx(&cfg, jpf_core_solve_kernel<W>, static_cast<const int*>(order),
                                    static_cast<const long long*>(qoff), static_cast<const unsigned short*>(cpreds),
                                    ctl, color));
     ++g_launches;
@@ -1385,20 +1453,21 @@ gc_status jp_run_ordered(gc_context* ctx, Arena a, const gc_csr* g, const int* b
 // ---------------------------------------------------------------------------
 size_t jpadg_scratch_bytes(long long n, long long nnz, int rounds) {
   const BucketPlan bp = make_plan(n, rounds);
+  const size_t state16 = static_cast<size_t>(n) * 2 + 256;
   const size_t nb = static_cast<size_t>(bp.B + 1);
   const size_t kc = static_cast<size_t>(kCoreMax) + 1;
   const size_t ntask = kc + static_cast<size_t>(nnz / kChunk) + 1;
   const size_t sc = scan_temp_elems(static_cast<long long>(nb)) +
                     scan_temp_elems(static_cast<long long>(kc)) + 2;
   const size_t rb = (4 * (static_cast<size_t>(bp.rounds) + 1) * 8 + 512);
-  return rb + 256 + 3 * (nb * 8 + 256) + 2 * (static_cast<size_t>(n) * 4 + 256) + 2 * (kc * 8 + 256) +
+  return state16 + rb + 256 + 3 * (nb * 8 + 256) + 2 * (static_cast<size_t>(n) * 4 + 256) + 2 * (kc * 8 + 256) +
          (kc * 4 + 256) + ntask * 16 + 3 * 256 + sc * 8 + static_cast<size_t>((n + 31) / 32) * 4 + 256 + 4096;
 }
 
 namespace {
 template <class Key>
 gc_status jp_adg_impl(gc_context* ctx, Arena a, const gc_csr* g, const Key& key, const int* D,
-                      int rounds, int* color, int* num_colors_out, cudaStream_t s) {
+                      int rounds, typename Key::W* color, int* num_colors_out, cudaStream_t s) {
   const long long n = g->n, nnz = g->nnz;
   if (num_colors_out) *num_colors_out = 0;
   ctx->stats.num_colors = 0;
@@ -1504,13 +1573,54 @@ gc_status jp_adg_impl(gc_context* ctx, Arena a, const gc_csr* g, const Key& key,
 
 }  // namespace
 
+namespace {
+// KeyState16: state words start as batch << cb (colour 0); at the end the
+// colours are copied out to the caller's 32-bit array.
+__global__ void state16_init_kernel(const int* __restrict__ batch, long long n, int cb,
+                                    unsigned short* __restrict__ st) {
+  for (long long v = gtid(); v < n; v += gstride())
+    st[v] = static_cast<unsigned short>(static_cast<unsigned>(batch[v]) << cb);
+}
+
+__global__ void state16_strip_kernel(const unsigned short* __restrict__ st, long long n, int cmask,
+                                     int* __restrict__ color) {
+  for (long long v = gtid(); v < n; v += gstride()) color[v] = static_cast<int>(st[v]) & cmask;
+}
+}  // namespace
+
+// Colour bits of the 16-bit JP-ADG state word for `rounds` batches whose
+// colours are at most max_d + 1, or 0 if the word cannot hold both.
+int state16_colour_bits(int rounds, int max_d) {
+  if (rounds < 1 || max_d < 0) return 0;
+  int bb = 0;
+  while ((1 << bb) <= rounds) ++bb;  // bits of the largest batch id
+  const int cb = 16 - bb;
+  if (cb < 2 || static_cast<long long>(max_d) + 1 > (1ll << cb) - 1) return 0;
+  return cb;
+}
+
 gc_status jp_run_fused(gc_context* ctx, Arena a, const gc_csr* g, const int* batch, const int* D,
                        int rounds, unsigned long long seed, int* color, int* num_colors_out,
                        cudaStream_t s) {
   const long long n = g->n;
+  ctx->stats.jp_state_bits = 32;
   if (rounds > 255 || n == 0)
     return jp_adg_impl(ctx, a, g, KeyFused{batch, seed}, D, rounds, color, num_colors_out, s);
   const int blocks = ctx->num_sms * 8;
+  const int cb = ctx->opt.jp_state16 ? state16_colour_bits(rounds, ctx->adg_max_removal_degree) : 0;
+  ctx->stats.jp_state_bits = cb > 0 ? 16 : 32;
+  if (cb > 0) {
+    unsigned short* st = a.take<unsigned short>(n);
+    if (!st) return GC_ERR_OOM;
+    state16_init_kernel<<<blocks, 256, 0, s>>>(batch, n, cb, st);
+    ++g_launches;
+    GC_TRY_CUDA(cudaGetLastError());
+    GC_TRY(jp_adg_impl(ctx, a, g, KeyState16{st, seed, cb}, D, rounds, st, num_colors_out, s));
+    state16_strip_kernel<<<blocks, 256, 0, s>>>(st, n, (1 << cb) - 1, color);
+    ++g_launches;
+    GC_TRY_CUDA(cudaGetLastError());
+    return GC_OK;
+  }
   state_init_kernel<<<blocks, 256, 0, s>>>(batch, n, color);
   ++g_launches;
   GC_TRY_CUDA(cudaGetLastError());

@@ -59,7 +59,8 @@ class gc_options(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("core_target", ctypes.c_int32),
                 ("core_cluster", ctypes.c_int32), ("core_warps", ctypes.c_int32), ("dec_tail", ctypes.c_int32),
                 ("update_mode", ctypes.c_int32), ("pull_percent", ctypes.c_int32),
-                ("bulk_blocks_per_sm", ctypes.c_int32), ("wait_limit_ms", ctypes.c_uint32)]
+                ("bulk_blocks_per_sm", ctypes.c_int32), ("wait_limit_ms", ctypes.c_uint32),
+                ("jp_state16", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "struct_size"}
@@ -87,7 +88,8 @@ class gc_stats(ctypes.Structure):
                 ("core_degree_sum", ctypes.c_int64), ("core_ctas", ctypes.c_int32),
                 ("sim_iterations", ctypes.c_int64), ("dec_internal_edges", ctypes.c_int64),
                 ("ms_dec_extract", ctypes.c_float), ("ms_dec_iterate", ctypes.c_float),
-                ("dec_tail_partitions", ctypes.c_int64), ("adg_pull_rounds", ctypes.c_int32)]
+                ("dec_tail_partitions", ctypes.c_int64), ("adg_pull_rounds", ctypes.c_int32),
+                ("jp_state_bits", ctypes.c_int32)]
 
 
 _lib = None

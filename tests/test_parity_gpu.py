@@ -379,3 +379,41 @@ def test_auto_pulls_when_r_outweighs_u(ctx):
     ob, oc, onr, onc = oracle.jp_adg(g, 1, 2, 42)
     assert np.array_equal(b, ob) and np.array_equal(c, oc)
     assert 0 < ctx.gc_get_stats().adg_pull_rounds < nr
+
+
+# ---------------------------------------------------------------- 16-bit JP state
+
+@pytest.fixture(scope="module")
+def ctx_state32():
+    c = gcp.Context(0, {"jp_state16": 0})
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("g", [gg.rmat(15, 16, seed=7), gg.barabasi_albert(30000, 6, 2), complete(300),
+                               gg.grid(64, 64, 8, perm_seed=1)], ids=lambda g: g.name)
+def test_state_word_16_and_32_bits_identical(ctx, ctx_state32, g):
+    # the batch|colour word of JP-ADG in 16 bits (when the colour bound
+    # 1 + max degree at removal fits) or in 32 bits: identical colourings
+    ob, oc, onr, onc = oracle.jp_adg(g, 1, 100, 42)
+    for c, bits in ((ctx, 16), (ctx_state32, 32)):
+        b, col, nr, nc = color_graph(c, g, 1, 100, 42)
+        assert nr == onr and np.array_equal(b, ob)
+        assert nc == onc and np.array_equal(col, oc)
+        assert c.gc_get_stats().jp_state_bits == bits
+
+
+@pytest.mark.parametrize("n,bits", [(4000, 16), (4100, 32)])
+def test_state_word_switch_on_cliques(ctx, n, bits):
+    # JP-ADG-M on K_n takes floor(log2 n) + 1 = 12 or 13 rounds (4 batch
+    # bits), leaving 12 colour bits (at most 4095): K_4000's 4000 colours fit
+    # the 16-bit word, K_4100's 4100 do not and the call falls back to 32 bits
+    g = complete(n)
+    dg = dev(g)
+    color = torch.empty(g.n, dtype=torch.int32, device="cuda:0")
+    batch = torch.empty(g.n, dtype=torch.int32, device="cuda:0")
+    nc, nr = ctx.gc_color_graph_m(dg, 42, color, batch)
+    ob, oc, onr, onc = oracle.jp_adg_m(g, 42)
+    assert nr == onr and nc == onc == n
+    assert np.array_equal(batch.cpu().numpy(), ob) and np.array_equal(color.cpu().numpy(), oc)
+    assert ctx.gc_get_stats().jp_state_bits == bits

@@ -106,6 +106,7 @@ typedef struct {
                               single-cluster tail (gc_options.dec_tail)      */
   int32_t adg_pull_rounds; /* ADG rounds whose UPDATE pulled (update_mode)     */
   int32_t jp_state_bits;   /* JP-ADG state word of the last call: 16 or 32     */
+  int32_t batch_path;      /* gc_color_batch: GC_BATCH_SEGMENTED or _PERSISTENT */
 } gc_stats;
 
 /* Human-readable name of a status code (static storage). */
@@ -140,17 +141,28 @@ typedef struct {
   int32_t update_mode;     /* GC_UPDATE_AUTO (default), _PUSH or _PULL       */
   int32_t pull_percent;    /* AUTO pulls a round when the rows of U' hold at
                               most pull_percent % of the entries the rows of
-                              R hold, 0..100000 (default 100)                */
+                              R hold, 0..100000 (default 25)                 */
   int32_t bulk_blocks_per_sm; /* resident blocks per SM of JP's bulk colouring
                               kernel, 0 = as many as fit (default), 1..32    */
   uint32_t wait_limit_ms;  /* bound of every device-side wait, 1..600000 ms
                               (default 4000); a wait that runs out ends the
                               call with GC_ERR_TIMEOUT, context usable       */
-  int32_t jp_state16;      /* 1 (default): JP-ADG keeps each vertex's batch and
-                              colour in a 16-bit word when both fit (the
-                              colour bound is 1 + the largest degree at
-                              removal); 0: always a 32-bit word              */
+  int32_t jp_state16;      /* 1: JP-ADG keeps each vertex's batch and colour in
+                              a 16-bit word when both fit (the colour bound
+                              is 1 + the largest degree at removal); 0
+                              (default): always a 32-bit word                */
+  int32_t batch_mode;      /* gc_color_batch: GC_BATCH_AUTO (default),
+                              GC_BATCH_SEGMENTED or GC_BATCH_PERSISTENT      */
 } gc_options;
+
+/* How gc_color_batch runs (gc_options.batch_mode, gc_stats.batch_path):
+ * SEGMENTED runs ADG's rounds for all graphs together, one set of GPU-wide
+ * launches per round, then one JP over the union; PERSISTENT is one launch
+ * in which each thread block takes whole graphs from a queue (largest first)
+ * and runs ADG and JP on each graph alone.  AUTO takes PERSISTENT unless one
+ * graph holds more than 2^24 CSR entries or more than 4/num_SMs of the
+ * batch's.  Results are identical. */
+enum { GC_BATCH_AUTO = 0, GC_BATCH_SEGMENTED = 1, GC_BATCH_PERSISTENT = 2 };
 
 /* Fill *opt with the defaults (and struct_size = sizeof(gc_options)). */
 gc_status gc_options_init(gc_options *opt);

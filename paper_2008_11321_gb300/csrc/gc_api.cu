@@ -31,6 +31,7 @@ struct CallScope {
     ctx->stats.dec_internal_edges = 0;
     ctx->stats.dec_tail_partitions = 0;
     ctx->stats.jp_state_bits = 0;
+    ctx->stats.batch_path = 0;
   }
   ~CallScope() {
     if (!ctx) return;
@@ -212,10 +213,11 @@ gc_status gc_options_init(gc_options* opt) {
   o.core_warps = 8;
   o.dec_tail = 1;
   o.update_mode = GC_UPDATE_AUTO;
-  o.pull_percent = 100;
+  o.pull_percent = 25;
   o.bulk_blocks_per_sm = 0;
   o.wait_limit_ms = static_cast<uint32_t>(gc::kWaitLimitNs / 1000000ull);
-  o.jp_state16 = 1;
+  o.jp_state16 = 0;
+  o.batch_mode = GC_BATCH_AUTO;
   *opt = o;
   return GC_OK;
 }
@@ -236,7 +238,8 @@ gc_status gc_create(gc_context** out, int device, const gc_options* opt) {
       o.core_warps < 1 || o.core_warps > 32 || (o.dec_tail != 0 && o.dec_tail != 1) ||
       o.update_mode < GC_UPDATE_AUTO || o.update_mode > GC_UPDATE_PULL || o.pull_percent < 0 ||
       o.pull_percent > 100000 || o.bulk_blocks_per_sm < 0 || o.bulk_blocks_per_sm > 32 || o.wait_limit_ms < 1 ||
-      o.wait_limit_ms > 600000 || (o.jp_state16 != 0 && o.jp_state16 != 1))
+      o.wait_limit_ms > 600000 || (o.jp_state16 != 0 && o.jp_state16 != 1) || o.batch_mode < GC_BATCH_AUTO ||
+      o.batch_mode > GC_BATCH_PERSISTENT)
     return GC_ERR_INVALID_ARG;
   int count = 0;
   if (cudaGetDeviceCount(&count) != cudaSuccess) {

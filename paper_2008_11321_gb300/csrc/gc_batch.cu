@@ -321,6 +321,24 @@ gc_status batch_color(gc_context* ctx, const gc_batch_csr* b, const gc_job* jobs
   if (!ctl || !ubuf[0] || !ubuf[1] || !task_start || !task_len || !task_g) return GC_ERR_OOM;
 
   GC_TRY_CUDA(cudaMemcpyAsync(djobs, jobs, sizeof(gc_job) * G, cudaMemcpyHostToDevice, s));
+  // One persistent launch (a block per graph, gc_batch_persist.cu) when no
+  // graph is too large for one block: at most 4 times an SM's share of the
+  // batch's CSR entries, and at most 2^24 entries.
+  if (ctx->opt.batch_mode != GC_BATCH_SEGMENTED && n > 0) {
+    GC_TRY(ctx->reserve(batch_persistent_scratch_bytes(n, G)));
+    Arena pa = ctx->arena();
+    int* order = nullptr;
+    long long max_n = 0, max_nnz = 0;
+    GC_TRY(batch_order(ctx, pa, b, &order, &max_n, &max_nnz, s));
+    const bool fits = max_nnz <= (1ll << 24) && max_nnz * ctx->num_sms <= 4 * (nnz > 0 ? nnz : 1);
+    if (ctx->opt.batch_mode == GC_BATCH_PERSISTENT || fits) {
+      ctx->stats.batch_path = GC_BATCH_PERSISTENT;
+      ctx->stats.adg_rounds = 0;
+      return batch_color_persistent(ctx, pa, b, djobs, order, color_out, batch_out, num_colors_out, num_rounds_out,
+                                    s);
+    }
+  }
+  ctx->stats.batch_path = GC_BATCH_SEGMENTED;
   if (n > 0) GC_TRY_CUDA(cudaMemsetAsync(bat, 0, sizeof(int) * n, s));  // 0 = still in U
   const int blocks = ctx->num_sms * 8;
   const int upd_blocks = resident_grid(batch_update_kernel, kBThreads, ctx->num_sms);

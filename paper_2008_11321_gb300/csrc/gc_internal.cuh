@@ -186,6 +186,15 @@ gc_status batch_color(gc_context* ctx, const gc_batch_csr* b, const gc_job* jobs
 
 gc_status batch_color_list(gc_context* ctx, long long G, const gc_csr* graphs, const gc_job* jobs,
                            int32_t* const* color_out, cudaStream_t s);
+// The batch in one persistent launch, a block per graph (gc_batch_persist.cu):
+// batch_order sorts the graph ids by decreasing size and returns the largest
+// graph's vertices and CSR entries; djobs is a device copy of the jobs.
+size_t batch_persistent_scratch_bytes(long long n, long long G);
+gc_status batch_order(gc_context* ctx, Arena& a, const gc_batch_csr* b, int** order_out, long long* max_n,
+                      long long* max_nnz, cudaStream_t s);
+gc_status batch_color_persistent(gc_context* ctx, Arena a, const gc_batch_csr* b, const gc_job* djobs,
+                                 const int* order, int32_t* color_out, int32_t* batch_out, int32_t* num_colors_out,
+                                 int32_t* num_rounds_out, cudaStream_t s);
 
 // JP-ADG on the disjoint union of many graphs: tiev[v] is v's tie-break.
 gc_status jp_run_packed(gc_context* ctx, Arena a, const gc_csr* g, const int* batch, const unsigned* tiev,

@@ -33,6 +33,8 @@ EXPORTS = ("gc_status_str", "gc_options_init", "gc_create", "gc_get_options", "g
 GC_PRIO_R, GC_PRIO_FF, GC_PRIO_LF, GC_PRIO_LLF = 0, 1, 2, 3
 # ADG UPDATE directions (gc_options.update_mode)
 GC_UPDATE_AUTO, GC_UPDATE_PUSH, GC_UPDATE_PULL = 0, 1, 2
+# gc_color_batch paths (gc_options.batch_mode, gc_stats.batch_path)
+GC_BATCH_AUTO, GC_BATCH_SEGMENTED, GC_BATCH_PERSISTENT = 0, 1, 2
 
 
 class GcError(RuntimeError):
@@ -60,7 +62,7 @@ class gc_options(ctypes.Structure):
                 ("core_cluster", ctypes.c_int32), ("core_warps", ctypes.c_int32), ("dec_tail", ctypes.c_int32),
                 ("update_mode", ctypes.c_int32), ("pull_percent", ctypes.c_int32),
                 ("bulk_blocks_per_sm", ctypes.c_int32), ("wait_limit_ms", ctypes.c_uint32),
-                ("jp_state16", ctypes.c_int32)]
+                ("jp_state16", ctypes.c_int32), ("batch_mode", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "struct_size"}
@@ -89,7 +91,7 @@ class gc_stats(ctypes.Structure):
                 ("sim_iterations", ctypes.c_int64), ("dec_internal_edges", ctypes.c_int64),
                 ("ms_dec_extract", ctypes.c_float), ("ms_dec_iterate", ctypes.c_float),
                 ("dec_tail_partitions", ctypes.c_int64), ("adg_pull_rounds", ctypes.c_int32),
-                ("jp_state_bits", ctypes.c_int32)]
+                ("jp_state_bits", ctypes.c_int32), ("batch_path", ctypes.c_int32)]
 
 
 _lib = None

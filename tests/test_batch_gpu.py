@@ -1,6 +1,8 @@
 """gc_color_batch: every graph of a packed batch gets exactly the batches,
 round count, colours and colour count that the oracle (and gc_color_graph
-on the graph alone) give it with its own eps and seed."""
+on the graph alone) give it with its own eps and seed -- on both paths: the
+segmented one (GPU-wide launches per ADG round) and the persistent one (one
+launch, a thread block per graph)."""
 from __future__ import annotations
 
 import numpy as np
@@ -16,13 +18,17 @@ pytestmark = pytest.mark.gpu
 import paper_2008_11321_gb300 as gcp  # noqa: E402
 
 
-@pytest.fixture(scope="module")
-def ctx():
+MODES = {"auto": gcp.GC_BATCH_AUTO, "segmented": gcp.GC_BATCH_SEGMENTED, "persistent": gcp.GC_BATCH_PERSISTENT}
+
+
+@pytest.fixture(scope="module", params=sorted(MODES))
+def ctx(request):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2008_11321_gb300 import _build
     _build.build()
-    c = gcp.Context(0)
+    c = gcp.Context(0, {"batch_mode": MODES[request.param]})
+    c.mode = MODES[request.param]
     yield c
     c.close()
 
@@ -42,6 +48,8 @@ def _run(ctx, graphs, jobs):
     nrnd = torch.full((db.num_graphs,), -5, dtype=torch.int32, device="cuda:0")
     ctx.gc_color_batch(db, jobs, color, batch, ncol, nrnd)
     torch.cuda.synchronize()
+    path = ctx.gc_get_stats().batch_path
+    assert path == ctx.mode or (ctx.mode == gcp.GC_BATCH_AUTO and path in (1, 2)) or db.n == 0
     voff = db.graph_off.cpu().numpy()
     return color.cpu().numpy(), batch.cpu().numpy(), ncol.cpu().numpy(), nrnd.cpu().numpy(), voff
 
@@ -77,3 +85,32 @@ def test_batch_twice_same_result(ctx):
     b = _run(ctx, graphs, jobs)
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
+
+
+def test_batch_hard_cases(ctx):
+    # many ADG rounds (short paths, eps = 0), colours beyond the 1024-colour
+    # window of the warp path (K_1100), hubs (stars, a BA graph), isolated
+    # vertices and empty graphs, all in one batch
+    graphs = [path(60), path(99), complete(1100), star(3000), empty(1), empty(0), gg.barabasi_albert(5000, 7, 4),
+              gg.grid(40, 50, perm_seed=9), complete(33), gg.erdos_renyi(3000, 200, 2)]
+    jobs = [(0, 1, 5), (1, 100, 6), (1, 100, 7), (1, 2, 8), (1, 100, 9), (1, 100, 10), (3, 1, 11), (1, 100, 12),
+            (1, 100, 13), (1, 10, 14)]
+    color, batch, ncol, nrnd, voff = _run(ctx, graphs, jobs)
+    for i, g in enumerate(graphs):
+        p, q, sd = jobs[i]
+        ob, oc, onr, onc = oracle.jp_adg(g, p, q, sd)
+        sl = slice(voff[i], voff[i + 1])
+        assert np.array_equal(batch[sl], ob), i
+        assert np.array_equal(color[sl], oc), i
+        assert nrnd[i] == onr and ncol[i] == onc, (i, nrnd[i], onr, ncol[i], onc)
+
+
+def test_batch_list_entry_point(ctx):
+    # the separately-resident form the serving path uses
+    graphs = _mixed(16, 31)
+    jobs = [(1, 100, 3 + i) for i in range(len(graphs))]
+    dgs = [gcp.DeviceGraph.from_host(g, "cuda:0") for g in graphs]
+    outs = [torch.full((g.n,), -1, dtype=torch.int32, device="cuda:0") for g in graphs]
+    ctx.gc_color_batch_list(dgs, jobs, outs)
+    for g, (p, q, sd), o in zip(graphs, jobs, outs):
+        assert np.array_equal(o.cpu().numpy(), oracle.jp_adg(g, p, q, sd)[1])

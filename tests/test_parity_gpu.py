@@ -371,9 +371,11 @@ def test_push_pull_auto_identical(ctx, ctx_push, ctx_pull, g, p, q):
         assert stats[2].adg_pull_rounds >= 1
 
 
-def test_auto_pulls_when_r_outweighs_u(ctx):
+def test_auto_pulls_when_r_outweighs_u():
     # eps = 1/2 on a Barabasi-Albert graph removes most of U every round:
-    # the rows of U' hold fewer entries than the rows of R, so AUTO pulls
+    # the rows of U' hold fewer entries than the rows of R, so AUTO (here
+    # pulling at up to 100 %) pulls
+    ctx = gcp.Context(0, {"pull_percent": 100})
     g = gg.barabasi_albert(50000, 4, 11)
     b, c, nr, nc = color_graph(ctx, g, 1, 2, 42)
     ob, oc, onr, onc = oracle.jp_adg(g, 1, 2, 42)
@@ -390,13 +392,20 @@ def ctx_state32():
     c.close()
 
 
+@pytest.fixture(scope="module")
+def ctx_state16():
+    c = gcp.Context(0, {"jp_state16": 1})
+    yield c
+    c.close()
+
+
 @pytest.mark.parametrize("g", [gg.rmat(15, 16, seed=7), gg.barabasi_albert(30000, 6, 2), complete(300),
                                gg.grid(64, 64, 8, perm_seed=1)], ids=lambda g: g.name)
-def test_state_word_16_and_32_bits_identical(ctx, ctx_state32, g):
+def test_state_word_16_and_32_bits_identical(ctx_state16, ctx_state32, g):
     # the batch|colour word of JP-ADG in 16 bits (when the colour bound
     # 1 + max degree at removal fits) or in 32 bits: identical colourings
     ob, oc, onr, onc = oracle.jp_adg(g, 1, 100, 42)
-    for c, bits in ((ctx, 16), (ctx_state32, 32)):
+    for c, bits in ((ctx_state16, 16), (ctx_state32, 32)):
         b, col, nr, nc = color_graph(c, g, 1, 100, 42)
         assert nr == onr and np.array_equal(b, ob)
         assert nc == onc and np.array_equal(col, oc)
@@ -404,7 +413,8 @@ def test_state_word_16_and_32_bits_identical(ctx, ctx_state32, g):
 
 
 @pytest.mark.parametrize("n,bits", [(4000, 16), (4100, 32)])
-def test_state_word_switch_on_cliques(ctx, n, bits):
+def test_state_word_switch_on_cliques(ctx_state16, n, bits):
+    ctx = ctx_state16
     # JP-ADG-M on K_n takes floor(log2 n) + 1 = 12 or 13 rounds (4 batch
     # bits), leaving 12 colour bits (at most 4095): K_4000's 4000 colours fit
     # the 16-bit word, K_4100's 4100 do not and the call falls back to 32 bits

@@ -1,6 +1,7 @@
 """The continuous-batching service: requests arriving at random times while
-others are on the GPU are coloured in shared batches, and every result is the
-same as colouring that graph alone (gc_color_graph) and as the oracle."""
+others are on the GPU are coloured in shared batches, in compute slots whose
+work overlaps on the device, and every result is the same as colouring that
+graph alone (gc_color_graph) and as the oracle."""
 from __future__ import annotations
 
 import threading
@@ -61,7 +62,7 @@ def test_results_same_alone_and_in_the_mix():
             time.sleep(rng.exponential(0.002))
         results = [r.result(timeout=120) for r in reqs]
         batches = list(srv.batches)
-    assert sum(b[0] for b in batches) == len(reqs_in)
+    assert sum(b[1] for b in batches) == len(reqs_in)
     assert len(batches) < len(reqs_in)  # requests really shared batches
     for (g, eps, seed), col in zip(reqs_in, results):
         assert np.array_equal(col, _alone(g, eps, seed))
@@ -103,3 +104,24 @@ def test_concurrent_clients():
             t.join()
     for (g, eps, seed), col in zip(reqs_in, out):
         assert np.array_equal(col, oracle.jp_adg(g, eps[0], eps[1], seed)[1])
+
+
+def test_small_request_overtakes_a_running_large_one():
+    # a large graph is running in one slot when a small one arrives: the
+    # small one starts in the other slot at once and finishes first, both
+    # with the oracle's colours
+    big = gg.rmat(21, 16, seed=3)
+    small = gg.erdos_renyi(2000, 8000, 4)
+    with ColoringServer(0, slots=2) as srv:
+        srv.submit(small.row_ptr, small.col_idx, 1, 100, 1).result(timeout=60)  # warm both paths
+        rb = srv.submit(big.row_ptr, big.col_idx, 1, 100, 5)
+        t0 = time.perf_counter()
+        while rb.t_start is None and time.perf_counter() - t0 < 30:
+            time.sleep(0.0005)
+        rs = srv.submit(small.row_ptr, small.col_idx, 1, 100, 6)
+        cs, cb = rs.result(timeout=60), rb.result(timeout=120)
+        slots = {k for k, _, _ in srv.batches}
+    assert rs.t_done < rb.t_done
+    assert slots == {0, 1}
+    assert np.array_equal(cs, oracle.jp_adg(small, 1, 100, 6)[1])
+    assert np.array_equal(cb, oracle.jp_adg(big, 1, 100, 5)[1])

@@ -183,6 +183,28 @@ gc_status gc_create(gc_context **ctx, int device, const gc_options *opt);
 /* The options the context runs with (defaults filled in). */
 gc_status gc_get_options(const gc_context *ctx, gc_options *out);
 
+/* Replace the context's options (range-checked as in gc_create; the context
+ * is unchanged on GC_ERR_INVALID_ARG).  Scratch memory is kept. */
+gc_status gc_set_options(gc_context *ctx, const gc_options *opt);
+
+/* Autotuner (no counterpart in the paper, which tunes nothing): finds the
+ * options under which gc_color_graph(g, eps, seed) runs fastest on this
+ * device, by coordinate descent over the option fields -- UPDATE direction
+ * and pull threshold, JP state word, JP core size, warps and cluster, bulk
+ * blocks per SM -- each run timed with CUDA events on `stream` (median of
+ * `reps` runs after one warm-up run).  Every candidate's colouring is
+ * compared with the starting options' on the device; a difference is a
+ * library defect and returns GC_ERR_CUDA.  The search stops early once the
+ * timed runs add up to budget_ms (0: no limit).  On success the fastest
+ * options are applied to the context and written to *best_out, with their
+ * median time (ms) in *best_ms_out and the starting options' in
+ * *start_ms_out (both may be NULL).  Allocates two n-int device buffers for
+ * the comparison and frees them before returning. */
+gc_status gc_autotune(gc_context *ctx, const gc_csr *g, uint32_t eps_p, uint32_t eps_q, uint64_t seed,
+                      int32_t reps, float budget_ms, gc_options *best_out, float *best_ms_out,
+                      float *start_ms_out, gc_stream stream);
+
+
 /* Release the context's scratch memory and the context itself (NULL ok). */
 void gc_destroy(gc_context *ctx);
 
@@ -393,6 +415,12 @@ gc_status gc_color_batch(gc_context *ctx, const gc_batch_csr *b, const gc_job *j
  * the colours are written. */
 gc_status gc_color_batch_list(gc_context *ctx, int64_t num_graphs, const gc_csr *graphs,
                               const gc_job *jobs, int32_t *const *color_out, gc_stream stream);
+
+/* gc_autotune for gc_color_batch(b, jobs): also chooses between the
+ * persistent and the segmented batch path (batch_mode). */
+gc_status gc_autotune_batch(gc_context *ctx, const gc_batch_csr *b, const gc_job *jobs, int32_t reps,
+                            float budget_ms, gc_options *best_out, float *best_ms_out, float *start_ms_out,
+                            gc_stream stream);
 
 #ifdef __cplusplus
 }

@@ -5,6 +5,8 @@
 #include <cstring>
 #include <new>
 
+#include <functional>
+
 #include "gc_internal.cuh"
 
 namespace gc {
@@ -222,10 +224,12 @@ gc_status gc_options_init(gc_options* opt) {
   return GC_OK;
 }
 
-gc_status gc_create(gc_context** out, int device, const gc_options* opt) {
-  if (!out) return GC_ERR_INVALID_ARG;
-  *out = nullptr;
-  // options: defaults, overwritten by the prefix of the struct the caller knows
+}  // extern "C"
+
+namespace {
+// Options as the library uses them: defaults, overwritten by the prefix of
+// the struct the caller knows, then range-checked.
+gc_status read_options(const gc_options* opt, gc_options* out) {
   gc_options o;
   gc_options_init(&o);
   if (opt) {
@@ -241,6 +245,18 @@ gc_status gc_create(gc_context** out, int device, const gc_options* opt) {
       o.wait_limit_ms > 600000 || (o.jp_state16 != 0 && o.jp_state16 != 1) || o.batch_mode < GC_BATCH_AUTO ||
       o.batch_mode > GC_BATCH_PERSISTENT)
     return GC_ERR_INVALID_ARG;
+  *out = o;
+  return GC_OK;
+}
+}  // namespace
+
+extern "C" {
+
+gc_status gc_create(gc_context** out, int device, const gc_options* opt) {
+  if (!out) return GC_ERR_INVALID_ARG;
+  *out = nullptr;
+  gc_options o;
+  GC_TRY(read_options(opt, &o));
   int count = 0;
   if (cudaGetDeviceCount(&count) != cudaSuccess) {
     cudaGetLastError();
@@ -252,10 +268,7 @@ gc_status gc_create(gc_context** out, int device, const gc_options* opt) {
   gc_context* ctx = new (std::nothrow) gc_context();
   if (!ctx) return GC_ERR_OOM;
   ctx->device = device;
-  ctx->opt = o;
-  ctx->core_target = o.core_target;
-  ctx->dec_tail = o.dec_tail != 0;
-  ctx->wait_ns = static_cast<unsigned long long>(o.wait_limit_ms) * 1000000ull;
+  gc::apply_options(ctx, o);
   // failure injection for tests of the error paths (see gc_context)
   if (const char* env = getenv("GC_INJECT_STALL")) ctx->stall_vertex = atoi(env);
   if (const char* env = getenv("GC_INJECT_OOM")) ctx->fail_alloc = env[0] != '\0' && env[0] != '0';
@@ -305,6 +318,56 @@ gc_status gc_get_options(const gc_context* ctx, gc_options* out) {
   if (!ctx || !out) return GC_ERR_INVALID_ARG;
   *out = ctx->opt;
   return GC_OK;
+}
+
+gc_status gc_set_options(gc_context* ctx, const gc_options* opt) {
+  if (!ctx || !opt) return GC_ERR_INVALID_ARG;
+  gc_options o;
+  GC_TRY(read_options(opt, &o));
+  gc::apply_options(ctx, o);
+  return GC_OK;
+}
+
+gc_status gc_autotune(gc_context* ctx, const gc_csr* g, uint32_t eps_p, uint32_t eps_q, uint64_t seed, int32_t reps,
+                      float budget_ms, gc_options* best_out, float* best_ms_out, float* start_ms_out,
+                      gc_stream stream) {
+  if (!ctx || !best_out) return GC_ERR_INVALID_ARG;
+  GC_TRY(check_graph_args(g));
+  GC_TRY(check_eps(eps_p, eps_q));
+  DeviceGuard guard(ctx->device);
+  CallScope scope(ctx);
+  if (!guard.ok) return GC_ERR_CUDA;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int timing = ctx->timing;
+  ctx->timing = 0;
+  const gc_status st = gc::autotune(
+      ctx, g->n,
+      [&](int* out) { return color_graph_device(ctx, g, eps_p, eps_q, seed, out, nullptr, nullptr, nullptr, s); },
+      false, reps, budget_ms, best_out, best_ms_out, start_ms_out, nullptr, s);
+  ctx->timing = timing;
+  return st;
+}
+
+gc_status gc_autotune_batch(gc_context* ctx, const gc_batch_csr* b, const gc_job* jobs, int32_t reps,
+                            float budget_ms, gc_options* best_out, float* best_ms_out, float* start_ms_out,
+                            gc_stream stream) {
+  if (!ctx || !b || !jobs || !best_out || b->num_graphs < 1 || b->num_graphs > INT_MAX || !b->graph_off)
+    return GC_ERR_INVALID_ARG;
+  if (b->n < 0 || b->nnz < 0 || b->n > static_cast<int64_t>(INT_MAX) - 1) return GC_ERR_INVALID_ARG;
+  if (b->n > 0 && !b->row_ptr) return GC_ERR_INVALID_ARG;
+  if (b->nnz > 0 && !b->col_idx) return GC_ERR_INVALID_ARG;
+  for (int64_t g = 0; g < b->num_graphs; ++g) GC_TRY(check_eps(jobs[g].eps_p, jobs[g].eps_q));
+  DeviceGuard guard(ctx->device);
+  CallScope scope(ctx);
+  if (!guard.ok) return GC_ERR_CUDA;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int timing = ctx->timing;
+  ctx->timing = 0;
+  const gc_status st = gc::autotune(
+      ctx, b->n, [&](int* out) { return gc::batch_color(ctx, b, jobs, out, nullptr, nullptr, nullptr, s); }, true,
+      reps, budget_ms, best_out, best_ms_out, start_ms_out, nullptr, s);
+  ctx->timing = timing;
+  return st;
 }
 
 gc_status gc_get_stats(const gc_context* ctx, gc_stats* out) {

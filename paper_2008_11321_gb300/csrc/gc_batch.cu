@@ -38,6 +38,8 @@ struct BCtl {
   int round;        // global round (the round of every graph still running)
   int size_Unext;   // survivors over all graphs
   unsigned long long ntasks;
+  unsigned long long total_U;    // sum over graphs and rounds of |U|
+  unsigned long long total_dec;  // sum over graphs and rounds of the cut
 };
 
 __device__ __forceinline__ int threshold_of(unsigned long long sigma, int size_u, unsigned p, unsigned q) {
@@ -229,6 +231,8 @@ __global__ void batch_finalize_kernel(BCtl* ctl, BGraph* __restrict__ gs, int G)
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
     BGraph c = gs[g];
     if (c.size_U == 0) continue;
+    atomicAdd(&ctl->total_U, static_cast<unsigned long long>(c.size_U));
+    if (c.cut) atomicAdd(&ctl->total_dec, c.cut);
     c.sigma = c.sigma - c.sum_R - c.cut;
     c.size_U = c.size_Unext;
     if (c.size_U == 0)
@@ -376,6 +380,13 @@ gc_status batch_color(gc_context* ctx, const gc_batch_csr* b, const gc_job* jobs
   }
   ctx->timer_end(s);
   ctx->stats.adg_rounds = round;
+  {
+    unsigned long long* pl = static_cast<unsigned long long*>(ctx->pinned);
+    GC_TRY_CUDA(cudaMemcpyAsync(pl, &ctl->total_U, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    GC_TRY_CUDA(cudaStreamSynchronize(s));
+    ctx->stats.sum_U = static_cast<int64_t>(pl[0]);
+    ctx->stats.sum_decrements = static_cast<int64_t>(pl[1]);
+  }
   if (n == 0) return GC_OK;
   batch_tie_kernel<<<blocks, 256, 0, s>>>(gs, off, G, n, tiev);
   ++g_launches;

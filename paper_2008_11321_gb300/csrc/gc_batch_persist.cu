@@ -22,8 +22,11 @@
 //   always ready, so the rounds end (after the length of the longest path of
 //   G_rho), and the colouring is Greedy's in decreasing priority -- the one
 //   gc_color_graph gives the graph alone.  Vertices of degree <= 32 are
-//   handled one per thread (their colour is at most 33: a 64-bit mask),
-//   larger ones one per warp with a 1024-colour shared window.
+//   handled one per thread (their colour is at most 33: a 64-bit mask) and
+//   resume where they stopped: a vertex that meets an uncoloured predecessor
+//   keeps its row position (in D, free after ADG) and its colour mask, so
+//   each row is read once over all rounds.  Larger vertices go one per warp
+//   with a 1024-colour shared window.
 //
 // Per-vertex state lives in the union's arrays (graph g at offsets v0..v1),
 // so a block's working set is one graph's and stays in L2.  Everything this
@@ -46,7 +49,7 @@
 namespace gc {
 namespace {
 
-constexpr int kPThreads = 256;
+constexpr int kPThreads = 512;
 constexpr int kPWarps = kPThreads / kWarp;
 
 struct PGraphArgs {
@@ -63,9 +66,10 @@ struct PGraphArgs {
   int* ld;
   int* batch;                // n
   int* color;                // n
+  unsigned long long* used;  // n: JP lane path, colours seen so far (D then holds the row position)
   int* ncol;                 // G or null
   int* nrounds;              // G or null
-  unsigned long long* next;  // queue position
+  unsigned long long* next;  // [0] queue position, [1] error word, [2] sum of |U|, [3] decrements
   int* err;                  // set if a round made no progress
 };
 
@@ -93,7 +97,7 @@ __device__ __forceinline__ unsigned long long pkey(int bat, unsigned h) {
   return (static_cast<unsigned long long>(static_cast<unsigned>(bat)) << 32) | h;
 }
 
-__global__ void __launch_bounds__(kPThreads)
+__global__ void __launch_bounds__(kPThreads, 3)
 batch_persistent_kernel(PGraphArgs A) {
   __shared__ unsigned long long s_sigma, s_sumR, s_cut;
   __shared__ int s_g, s_nU, s_nUn, s_nR, s_T, s_round, s_max;
@@ -125,6 +129,7 @@ batch_persistent_kernel(PGraphArgs A) {
     }
     __syncthreads();
     int rounds = 0;
+    unsigned long long work_u = 0, work_dec = 0;  // (thread 0) sum of |U| and of the cuts
     while (n > 0) {
       if (tid == 0) {
         s_T = p_threshold(s_sigma, s_nU, p, q);
@@ -164,6 +169,7 @@ batch_persistent_kernel(PGraphArgs A) {
       __syncthreads();
       rounds = round;
       const int nUn = s_nUn, nR = s_nR;
+      work_u += static_cast<unsigned long long>(nU);
       if (nUn == 0) break;  // U is empty: nothing left to decrement
       if (nUn >= nU) {      // no vertex left U: cannot happen for a valid graph
         if (tid == 0) atomicExch(A.err, 1);
@@ -193,6 +199,7 @@ batch_persistent_kernel(PGraphArgs A) {
       if (lane == 0 && cut) atomicAdd(&s_cut, cut);
       __syncthreads();
       if (tid == 0) {
+        work_dec += s_cut;
         s_sigma = s_sigma - s_sumR - s_cut;
         s_nU = nUn;
         s_round = round + 1;
@@ -226,6 +233,10 @@ batch_persistent_kernel(PGraphArgs A) {
         deg = A.row_ptr[v + 1] - A.row_ptr[v];
         A.color[v] = deg == 0 ? 1 : 0;  // isolated: no predecessor, colour 1
         if (deg == 0) local_max = 1;
+        if (deg > 0 && deg <= kSmallDeg) {  // lane path: start of the row, no colour seen
+          A.D[v] = 0;
+          A.used[v] = 0ull;
+        }
       }
       block_append(active && deg > 0 && deg <= kSmallDeg, v, Ls, &s_ns);
       block_append(active && deg > kSmallDeg, v, Lb, &s_nb);
@@ -249,8 +260,10 @@ batch_persistent_kernel(PGraphArgs A) {
           v = __ldcg(Ls + i);
           const unsigned long long kv = pkey(__ldcg(A.batch + v), tie_hash(seed, static_cast<unsigned>(v - v0)));
           const long long s = A.row_ptr[v], e = A.row_ptr[v + 1];
-          unsigned long long used = 0;
-          for (long long k = s; k < e; ++k) {
+          const int pos = __ldcg(A.D + v);
+          unsigned long long used = pos > 0 ? __ldcg(A.used + v) : 0ull;
+          long long k = s + pos;
+          for (; k < e; ++k) {
             const int w = __ldg(A.col + k);
             const unsigned long long kw = pkey(__ldcg(A.batch + w), tie_hash(seed, static_cast<unsigned>(w - v0)));
             if (kw > kv || (kw == kv && w > v)) {
@@ -262,7 +275,10 @@ batch_persistent_kernel(PGraphArgs A) {
               if (c <= 64) used |= 1ull << (c - 1);
             }
           }
-          if (!pending) {
+          if (pending) {  // resume here next round
+            A.D[v] = static_cast<int>(k - s);
+            A.used[v] = used;
+          } else {
             const int c = __ffsll(static_cast<long long>(~used));
             vcol[v] = c;
             local_max = c > local_max ? c : local_max;
@@ -338,6 +354,8 @@ batch_persistent_kernel(PGraphArgs A) {
     if (tid == 0) {
       if (A.ncol) A.ncol[g] = s_max;
       if (A.nrounds) A.nrounds[g] = rounds;
+      if (work_u) atomicAdd(A.next + 2, work_u);
+      if (work_dec) atomicAdd(A.next + 3, work_dec);
     }
     __syncthreads();
   }
@@ -372,8 +390,9 @@ __global__ void batch_order_keys_kernel(const long long* __restrict__ off, const
 size_t batch_persistent_scratch_bytes(long long n, long long G) {
   const size_t vb = (static_cast<size_t>(n > 0 ? n : 1) * 4 + 255) & ~size_t(255);
   const size_t gb = static_cast<size_t>(G) + 1;
-  // D, four lists and an internal batch array; the queue's sort buffers
-  return 6 * vb + 2 * (gb * 8 + 256) + 2 * (gb * 4 + 256) + sort_hist_elems(G) * 8 +
+  // D, four lists, an internal batch array, JP's colour masks; the queue's
+  // sort buffers
+  return 6 * vb + (static_cast<size_t>(n > 0 ? n : 1) * 8 + 256) + 2 * (gb * 8 + 256) + 2 * (gb * 4 + 256) + sort_hist_elems(G) * 8 +
          (scan_temp_elems(static_cast<long long>(sort_hist_elems(G))) + 1) * 8 + 4096;
 }
 
@@ -428,14 +447,15 @@ gc_status batch_color_persistent(gc_context* ctx, Arena a, const gc_batch_csr* b
   A.lc = a.take<int>(cnt);
   A.ld = a.take<int>(cnt);
   A.batch = batch_out ? batch_out : a.take<int>(cnt);
+  A.used = a.take<unsigned long long>(cnt);
   A.color = color_out;
   A.ncol = num_colors_out;
   A.nrounds = num_rounds_out;
-  A.next = a.take<unsigned long long>(2);
-  if (!A.D || !A.la || !A.lb || !A.lc || !A.ld || !A.batch || !A.next) return GC_ERR_OOM;
+  A.next = a.take<unsigned long long>(4);
+  if (!A.D || !A.la || !A.lb || !A.lc || !A.ld || !A.batch || !A.used || !A.next) return GC_ERR_OOM;
   A.err = reinterpret_cast<int*>(A.next + 1);
   if (n > 0) GC_TRY_CUDA(cudaMemsetAsync(A.batch, 0, sizeof(int) * n, s));
-  GC_TRY_CUDA(cudaMemsetAsync(A.next, 0, 2 * sizeof(unsigned long long), s));
+  GC_TRY_CUDA(cudaMemsetAsync(A.next, 0, 4 * sizeof(unsigned long long), s));
   int per_sm = 0;
   GC_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_persistent_kernel, kPThreads, 0));
   if (per_sm < 1) per_sm = 1;
@@ -446,10 +466,12 @@ gc_status batch_color_persistent(gc_context* ctx, Arena a, const gc_batch_csr* b
   ++g_launches;
   ctx->timer_end(s);
   GC_TRY_CUDA(cudaGetLastError());
-  int* pin = static_cast<int*>(ctx->pinned);
-  GC_TRY_CUDA(cudaMemcpyAsync(pin, A.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  unsigned long long* pin = static_cast<unsigned long long*>(ctx->pinned);
+  GC_TRY_CUDA(cudaMemcpyAsync(pin, A.next, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   GC_TRY_CUDA(cudaStreamSynchronize(s));
-  return *pin ? GC_ERR_CUDA : GC_OK;
+  ctx->stats.sum_U = static_cast<int64_t>(pin[2]);
+  ctx->stats.sum_decrements = static_cast<int64_t>(pin[3]);
+  return *reinterpret_cast<int*>(pin + 1) ? GC_ERR_CUDA : GC_OK;
 }
 
 }  // namespace gc

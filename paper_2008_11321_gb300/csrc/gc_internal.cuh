@@ -199,6 +199,16 @@ gc_status batch_color_persistent(gc_context* ctx, Arena a, const gc_batch_csr* b
 // JP-ADG on the disjoint union of many graphs: tiev[v] is v's tie-break.
 gc_status jp_run_packed(gc_context* ctx, Arena a, const gc_csr* g, const int* batch, const unsigned* tiev,
                         const int* D, int rounds, int* color, int* num_colors_out, cudaStream_t s);
+// Options (gc_tune.cu): apply range-checked options to a context; the
+// autotuner times run() (one colouring into its argument, n ints) under
+// candidate options and leaves the fastest applied.
+void apply_options(gc_context* ctx, const gc_options& o);
+}  // namespace gc
+#include <functional>
+namespace gc {
+gc_status autotune(gc_context* ctx, long long n, const std::function<gc_status(int*)>& run, bool batch, int reps,
+                   float budget_ms, gc_options* best_out, float* best_ms_out, float* start_ms_out, int* trials_out,
+                   cudaStream_t s);
 cudaError_t make_priority(const int* batch, long long n, unsigned long long seed,
                           unsigned long long* key, int num_sms, cudaStream_t s);
 // JP-R / FF / LF / LLF keys (gc_make_priority_kind); kind already checked.

@@ -22,8 +22,8 @@ GC_OK, GC_ERR_INVALID_ARG, GC_ERR_INVALID_GRAPH, GC_ERR_OOM = 0, 1, 2, 3
 GC_ERR_CUDA, GC_ERR_TIMEOUT, GC_ERR_OVERFLOW = 4, 5, 6
 
 # Every symbol declared in include/gcolor.h.
-EXPORTS = ("gc_status_str", "gc_options_init", "gc_create", "gc_get_options", "gc_destroy", "gc_get_stats",
-           "gc_set_timing",
+EXPORTS = ("gc_status_str", "gc_options_init", "gc_create", "gc_get_options", "gc_set_options", "gc_autotune",
+           "gc_autotune_batch", "gc_destroy", "gc_get_stats", "gc_set_timing",
            "gc_validate_csr", "gc_adg_partition", "gc_make_priority", "gc_jp_color",
            "gc_color_graph", "gc_color_graph_host", "gc_adg_partition_noalloc", "gc_color_batch",
            "gc_color_batch_list", "gc_make_priority_kind", "gc_adg_m_partition", "gc_color_graph_m",
@@ -117,6 +117,13 @@ def load(path: str = LIB_PATH):
     lib.gc_create.argtypes = [P(vp), ctypes.c_int, P(gc_options)]
     lib.gc_get_options.restype = ctypes.c_int
     lib.gc_get_options.argtypes = [vp, P(gc_options)]
+    lib.gc_set_options.restype = ctypes.c_int
+    lib.gc_set_options.argtypes = [vp, P(gc_options)]
+    f32 = ctypes.c_float
+    lib.gc_autotune.restype = ctypes.c_int
+    lib.gc_autotune.argtypes = [vp, P(gc_csr), u32, u32, u64, i32, f32, P(gc_options), P(f32), P(f32), vp]
+    lib.gc_autotune_batch.restype = ctypes.c_int
+    lib.gc_autotune_batch.argtypes = [vp, P(gc_batch_csr), P(gc_job), i32, f32, P(gc_options), P(f32), P(f32), vp]
     lib.gc_destroy.restype = None
     lib.gc_destroy.argtypes = [vp]
     lib.gc_get_stats.restype = ctypes.c_int
@@ -290,6 +297,33 @@ class Context:
         o = gc_options()
         _check(self._lib.gc_get_options(self.handle, ctypes.byref(o)), "gc_get_options")
         return o
+
+    def gc_set_options(self, options):
+        """options: a gc_options or a dict of its fields (the rest default)."""
+        if isinstance(options, dict):
+            options = make_options(**options)
+        _check(self._lib.gc_set_options(self.handle, ctypes.byref(options)), "gc_set_options")
+
+    def gc_autotune(self, g: DeviceGraph, eps_p: int, eps_q: int, seed: int, reps: int = 3, budget_ms: float = 0.0,
+                    stream=None):
+        """Returns (best gc_options, best ms, starting ms); the best options
+        are left applied to the context."""
+        c = g.csr()
+        best = gc_options()
+        bm, sm = ctypes.c_float(0), ctypes.c_float(0)
+        _check(self._lib.gc_autotune(self.handle, ctypes.byref(c), eps_p, eps_q, seed, reps, budget_ms,
+                                     ctypes.byref(best), ctypes.byref(bm), ctypes.byref(sm), _stream(stream)),
+               "gc_autotune")
+        return best, bm.value, sm.value
+
+    def gc_autotune_batch(self, b: "DeviceBatch", jobs, reps: int = 3, budget_ms: float = 0.0, stream=None):
+        c = b.csr()
+        arr = (gc_job * b.num_graphs)(*[gc_job(int(p), int(q), int(sd)) for p, q, sd in jobs])
+        best = gc_options()
+        bm, sm = ctypes.c_float(0), ctypes.c_float(0)
+        _check(self._lib.gc_autotune_batch(self.handle, ctypes.byref(c), arr, reps, budget_ms, ctypes.byref(best),
+                                           ctypes.byref(bm), ctypes.byref(sm), _stream(stream)), "gc_autotune_batch")
+        return best, bm.value, sm.value
 
     def gc_set_timing(self, enable: bool):
         _check(self._lib.gc_set_timing(self.handle, int(enable)), "gc_set_timing")

@@ -81,7 +81,8 @@ def _ctype_kind(t):
     """'ptr' for pointer-sized arguments, else the integer width and sign."""
     if t in (ctypes.c_void_p, ctypes.c_char_p) or (isinstance(t, type) and issubclass(t, ctypes._Pointer)):
         return "ptr"
-    return {ctypes.c_int32: "i32", ctypes.c_uint32: "u32", ctypes.c_int64: "i64", ctypes.c_uint64: "u64"}.get(t, t)
+    return {ctypes.c_int32: "i32", ctypes.c_uint32: "u32", ctypes.c_int64: "i64", ctypes.c_uint64: "u64",
+            ctypes.c_float: "f32"}.get(t, t)
 
 
 def _decl_kind(decl):
@@ -89,7 +90,7 @@ def _decl_kind(decl):
         return "ptr"
     base = decl.rsplit(" ", 1)[0].replace("const ", "")
     return {"int": "i32", "int32_t": "i32", "uint32_t": "u32", "int64_t": "i64", "uint64_t": "u64",
-            "gc_status": "i32"}[base]
+            "gc_status": "i32", "float": "f32"}[base]
 
 
 def test_binding_signatures_match_header(lib):
@@ -132,3 +133,6 @@ def test_options_defaults_and_range_checks(lib):
         gcp.make_options(no_such_field=1)
     assert lib.gc_options_init(None) == gcp.GC_ERR_INVALID_ARG
     assert lib.gc_get_options(None, ctypes.byref(o)) == gcp.GC_ERR_INVALID_ARG
+    assert lib.gc_set_options(None, ctypes.byref(o)) == gcp.GC_ERR_INVALID_ARG
+    assert lib.gc_autotune(None, None, 1, 100, 42, 3, 0.0, None, None, None, None) == gcp.GC_ERR_INVALID_ARG
+    assert lib.gc_autotune_batch(None, None, None, 3, 0.0, None, None, None, None) == gcp.GC_ERR_INVALID_ARG

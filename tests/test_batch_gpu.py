@@ -58,6 +58,8 @@ def test_batch_matches_oracle_per_graph(ctx):
     graphs = _mixed(40, 7) + [empty(0), empty(5), complete(30), star(40), path(7), gg.rmat(12, 8, seed=3)]
     jobs = [((1, 100) if i % 3 else (1, 10)) + (42 + i,) for i in range(len(graphs))]
     color, batch, ncol, nrnd, voff = _run(ctx, graphs, jobs)
+    st = ctx.gc_get_stats()
+    sum_u = dec = 0
     for i, g in enumerate(graphs):
         p, q, sd = jobs[i]
         ob, oc, onr, onc = oracle.jp_adg(g, p, q, sd)
@@ -65,6 +67,13 @@ def test_batch_matches_oracle_per_graph(ctx):
         assert np.array_equal(batch[sl], ob), i
         assert np.array_equal(color[sl], oc), i
         assert nrnd[i] == onr and ncol[i] == onc, (i, nrnd[i], onr, ncol[i], onc)
+        if g.n:
+            sum_u += int(oracle.adg(g, p, q, log=True)[2]["U"].sum())
+            src = np.repeat(np.arange(g.n), g.degrees())
+            dec += int(np.sum(ob[g.col_idx] > ob[src]))
+    # ADG's work counters over the batch: sum of |U| over graphs and rounds,
+    # and the degree decrements (edges into a later batch)
+    assert st.sum_U == sum_u and st.sum_decrements == dec
 
 
 def test_batch_equals_single_graph_calls(ctx):

@@ -48,11 +48,12 @@ WORKLOADS = {
                     desc="3D 7-point grid 256^3, seeded vertex permutation, eps=1/100, seed 42"),
     "er": dict(kind="er", n=16384, m=81920, gen_seed=1, eps=(1, 100), seed=42,
                desc="Erdos-Renyi G(n=16384, m=81920), eps=1/100, seed 42"),
-    "serve": dict(kind="serve", requests=64, n_lo=1000, n_hi=2_000_000, seed=42, budget=40 << 30,
+    "serve": dict(kind="serve", requests=1000, pool=48, n_lo=1000, n_hi=2_000_000, seed=42, budget=40 << 30,
                   load=0.5,
-                  desc="serving: Poisson arrivals at half the measured capacity; graphs n log-uniform in "
-                       "[1000, 2000000], R-MAT (.57,.19,.19,.05, edge factor 8-32) or Barabasi-Albert "
-                       "(m 2-16) 50/50, eps 1/100 or 1/10 50/50, 40 GB device-memory budget"),
+                  desc="serving: 1000 requests, Poisson arrivals at half the measured capacity; graphs drawn from "
+                       "a pool of 48 generated ones, n log-uniform in [1000, 2000000], R-MAT (.57,.19,.19,.05, "
+                       "edge factor 8-32) or Barabasi-Albert (m 2-16) 50/50; eps 1/100 or 1/10 50/50, seed per "
+                       "request; 40 GB device-memory budget"),
     "batch4096": dict(kind="batch", count=4096, n_lo=100, n_hi=200_000, seed=42, eps=(1, 100),
                       desc="4096 graphs, n log-uniform in [100, 200000], Erdos-Renyi (avg deg 8) / "
                            "Barabasi-Albert (m=4) / 2D grid, packed as one disjoint union, eps=1/100, "
@@ -89,17 +90,26 @@ def path_bytes(n, nnz, sum_u, decrements):
     return adg + jp
 
 
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# reported kernel from an ncu capture of the current code, by (workload,
-# kernel); empty until such a capture exists for the current kernels.
-KERNEL_TRAFFIC = {
-    # R-MAT scale 24 defaults, profiles/launches_rmat24.md (DRAM bytes per launch)
-    ("rmat24", "jpf_core_solve_kernel"): 35.0e6,
-    ("rmat24", "adg_update_kernel"): 350.5e6,
-    ("rmat24", "jp_color_kernel"): 1125.5e6,
-    # profiles/launches_dec_itr_rmat24.md (mean over its 7 launches)
-    ("rmat24", "dec_extract_kernel"): 657.7e6,
-}
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
+# kernel, from a one-kernel ncu capture, keyed by (workload, kernel).  Each
+# entry carries the SHA-256 prefix of the source file the kernel was built
+# from at capture time; once that file changes the figure no longer
+# describes the kernel and kernel_traffic() reports None.
+KERNEL_TRAFFIC = {}
+
+
+def kernel_traffic(workload, kernel):
+    ent = KERNEL_TRAFFIC.get((workload, kernel))
+    if not ent:
+        return None
+    nbytes, src, sha = ent
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "paper_2008_11321_gb300", "csrc", src), "rb") as f:
+            cur = hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return nbytes if cur == sha else None
 
 
 def load_peak():
@@ -200,15 +210,23 @@ class ClockSampler:
                 "samples": len(sms)}
 
 
-def cpu_baseline(w_name, seconds_target=10.0, median=False, dec=False, ordered=False, itr=False, kind=None):
-    """The oracle as it stands, single-threaded, on a bounded sample of the
-    same family (R-MAT scale 22 for the R-MAT workloads)."""
+def cpu_baseline(w_name, seconds_target=10.0, median=False, dec=False, ordered=False, itr=False, kind=None,
+                 graph=None):
+    """The oracle as it stands, single-threaded: on the benchmark's own
+    R-MAT scale 24 graph (one run, about 8 s) for the default JP-ADG line,
+    else on a bounded sample of the same family (R-MAT scale 22 for the
+    R-MAT workloads)."""
     import numpy as np
 
     import graphgen as gg
     import oracle
     w = WORKLOADS[w_name]
-    if w["kind"] == "rmat":
+    plain = not (median or dec or ordered or itr or kind is not None)
+    if graph is not None and plain and w_name == "rmat24":
+        g = graph
+        desc = w["desc"] + " (the benchmarked graph itself)"
+        seconds_target = 0.0  # one run
+    elif w["kind"] == "rmat":
         sample = dict(w, scale=min(w["scale"], 22))
         g = make_graph(sample)
         desc = f"R-MAT scale {sample['scale']} edge factor {w['ef']} (same a,b,c,d), eps=1/100"
@@ -220,7 +238,7 @@ def cpu_baseline(w_name, seconds_target=10.0, median=False, dec=False, ordered=F
         desc = w["desc"]
     p, q = w["eps"]
     reps, total = 0, 0.0
-    while total < seconds_target and reps < 50:
+    while (reps == 0 or total < seconds_target) and reps < 50:
         t0 = time.perf_counter()
         if kind is not None:
             oracle.jp_color(g, oracle.priority_kind(g, kind, w["seed"]))
@@ -417,7 +435,7 @@ def run_dec(args, rank, world):
                    "l2": f"inputs larger than L2 (col_idx {4 * nnz / 1e9:.2f} GB), no flush"},
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None if itr else KERNEL_TRAFFIC.get((args.workload, kname)),
+                     "traffic": None if itr else kernel_traffic(args.workload, kname),
                      "algorithmic_bytes_per_launch": gb[kname] / kl, "ms_per_launch": kms / kl,
                      "launches_per_step": kl,
                      "groups_ms": {"adg_update_kernel": mean("ms_adg_update"),
@@ -442,7 +460,8 @@ def run_reference(args, rank, world):
     import oracle
     w = WORKLOADS[args.workload]
     if w["kind"] == "serve":  # each step: the oracle on the 8 smallest requests
-        reqs = sorted(serve_requests(w), key=lambda r: r[0].nnz)[:8]
+        pool, stream = serve_requests(w)
+        reqs = sorted([(pool[k], e, sd) for k, e, sd in stream], key=lambda r: r[0].nnz)[:8]
         for _ in range(args.warmup):
             oracle.jp_adg(reqs[0][0], *reqs[0][1], reqs[0][2])
         t0 = time.perf_counter()
@@ -485,9 +504,9 @@ def run_reference(args, rank, world):
                           "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": 0,
                                   "d2h_bytes_per_step": 0}}), flush=True)
         return 0
-    # each step: the oracle on a bounded sample (R-MAT scale 20 for R-MAT)
+    # each step: the oracle on a bounded sample (R-MAT scale 22 for R-MAT)
     if w["kind"] == "rmat":
-        sample = dict(w, scale=min(w["scale"], 20))
+        sample = dict(w, scale=min(w["scale"], 22))
         desc = f"R-MAT scale {sample['scale']} edge factor {w['ef']}"
     elif w["kind"] == "grid3":
         sample = dict(w, k=min(w["k"], 96))
@@ -516,25 +535,27 @@ def run_reference(args, rank, world):
     return 0
 
 
-def run_batch(args, rank, world):
-    """Batched form: one gc_color_batch call colours every graph of the
-    packed batch; the comparison is one gc_color_graph call per graph on the
-    same GPU (graphs/s both ways, colourings checked identical)."""
+def _timed(stream, fn, steps):
+    """Device time (s) of `steps` calls of fn on `stream`, CUDA events."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def measure_batch(w, dev, steps, warmup, options=None, world=1, tune_cache=None):
+    """The batched workload: the persistent path (one launch), the segmented
+    path, the autotuned options, and one gc_color_graph call per graph on
+    the same graphs; colourings checked identical.  Returns a dict."""
     import numpy as np
     import torch
-    import torch.distributed as dist
     import graphgen as gg
-    from paper_2008_11321_gb300 import _build
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
-    torch.cuda.set_device(dev)
-    if world > 1:  # replicas: every rank colours its own copy of the batch
-        dist.init_process_group("nccl", device_id=dev)
-    if rank == 0:
-        _build.build()
-    if world > 1:
-        dist.barrier()
     import paper_2008_11321_gb300 as gcp
-    w = WORKLOADS[args.workload]
+    from paper_2008_11321_gb300 import tuning
     G = w["count"]
     g, off = gg.batch(G, w["n_lo"], w["n_hi"], w["seed"], pinned=True)
     p, q = w["eps"]
@@ -543,74 +564,117 @@ def run_batch(args, rank, world):
                          torch.from_numpy(off).to(dev))
     color = torch.empty(db.n, dtype=torch.int32, device=dev)
     ncol = torch.empty(G, dtype=torch.int32, device=dev)
-    ctx = gcp.Context(dev.index, args.options)
     stream = torch.cuda.current_stream(dev)
-    for _ in range(args.warmup):
+    ctx = gcp.Context(dev.index, options)
+    res = {}
+    launches = {}
+    for name, mode in (("persistent", gcp.GC_BATCH_PERSISTENT), ("segmented", gcp.GC_BATCH_SEGMENTED)):
+        ctx.gc_set_options(dict(ctx.gc_get_options().as_dict(), batch_mode=mode))
+        for _ in range(warmup):
+            ctx.gc_color_batch(db, jobs, color, None, ncol)
+        ctx.gc_set_timing(True)
+        t = _timed(stream, lambda: ctx.gc_color_batch(db, jobs, color, None, ncol), steps) / steps
+        st = ctx.gc_get_stats()
+        ctx.gc_set_timing(False)
+        res[name] = {"ms_per_step": t * 1e3, "graphs_per_s": G / t, "kernel_ms": st.ms_adg_update,
+                     "launches_per_step": st.launches}
+        launches[name] = st.launches * steps
+        ref_color = color.clone() if name == "persistent" else ref_color
+    identical_paths = bool(torch.equal(ref_color, color))
+    sum_u, dec = st.sum_U, st.sum_decrements
+    # the autotuner's choice for this batch class (searched unless cached)
+    ctx.gc_set_options(options or {})
+    rec = tuning.tune_batch(ctx, db, jobs, cache=tune_cache, reps=2)
+    for _ in range(warmup):
         ctx.gc_color_batch(db, jobs, color, None, ncol)
-    sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
-    sampler.start()
-    time.sleep(0.3)
-    launches = 0
     sync_ranks(world, dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        ctx.gc_color_batch(db, jobs, color, None, ncol)
-        launches += ctx.gc_get_stats().launches
-    e1.record(stream)
-    sync_ranks(world, dev)
-    clocks = sampler.stop()
-    t_batch = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, dev) / args.steps
+    t_tuned = max_over_ranks(_timed(stream, lambda: ctx.gc_color_batch(db, jobs, color, None, ncol), steps),
+                             world, dev) / steps
+    launches["tuned"] = ctx.gc_get_stats().launches * steps
+    identical_tuned = bool(torch.equal(ref_color, color))
     # per-graph plain launches of the same graphs (local ids), one pass
     rp, ci = g.row_ptr, g.col_idx
     graphs = []
     for i in range(G):
         a, b = int(off[i]), int(off[i + 1])
-        lrp = torch.from_numpy(rp[a:b + 1] - rp[a]).to(dev)
-        lci = torch.from_numpy(ci[rp[a]:rp[b]] - np.int32(a)).to(dev)
-        graphs.append(gcp.DeviceGraph(lrp, lci))
+        graphs.append(gcp.DeviceGraph(torch.from_numpy(rp[a:b + 1] - rp[a]).to(dev),
+                                      torch.from_numpy(ci[rp[a]:rp[b]] - np.int32(a)).to(dev)))
     single = torch.empty(db.n, dtype=torch.int32, device=dev)
     for i in range(min(8, G)):
         ctx.gc_color_graph(graphs[i], p, q, w["seed"] + i, single[int(off[i]):int(off[i + 1])])
-    torch.cuda.synchronize(dev)
-    e0.record(stream)
-    for i in range(G):
-        ctx.gc_color_graph(graphs[i], p, q, w["seed"] + i, single[int(off[i]):int(off[i + 1])])
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    t_single = e0.elapsed_time(e1) / 1e3
-    identical = bool(torch.equal(single, color))
+    t_single = _timed(stream, lambda: [ctx.gc_color_graph(graphs[i], p, q, w["seed"] + i,
+                                                          single[int(off[i]):int(off[i + 1])]) for i in range(G)], 1)
+    identical_single = bool(torch.equal(single, ref_color))
     # end to end: packed CSR host -> device, batch call, colours device -> host
     hcolor = torch.empty(db.n, dtype=torch.int32, pin_memory=True)
     rp_h, ci_h, off_h = torch.from_numpy(g.row_ptr), torch.from_numpy(g.col_idx), torch.from_numpy(off)
-    torch.cuda.synchronize(dev)
-    e0.record(stream)
-    for _ in range(args.steps):
+
+    def e2e_step():
         db2 = gcp.DeviceBatch(rp_h.to(dev, non_blocking=True), ci_h.to(dev, non_blocking=True),
                               off_h.to(dev, non_blocking=True))
         ctx.gc_color_batch(db2, jobs, color, None, ncol)
         hcolor.copy_(color, non_blocking=True)
-    e1.record(stream)
     sync_ranks(world, dev)
-    t_e2e = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, dev) / args.steps
+    t_e2e = max_over_ranks(_timed(stream, e2e_step, steps), world, dev) / steps
+    ctx.close()
+    peak, peak_kind = load_peak()
+    pb = path_bytes(db.n, db.nnz, sum_u, dec)
+    kms = res["persistent"]["kernel_ms"]
+    achieved = pb / (kms / 1e3) / 1e9 if kms > 0 else 0.0
+    return {
+        "graphs": G, "n": db.n, "m": db.nnz // 2, "t_tuned": t_tuned, "t_e2e": t_e2e,
+        "graphs_per_s": G / t_tuned, "edges_per_s": (db.nnz // 2) / t_tuned,
+        "paths": res, "identical_colourings": identical_paths and identical_tuned and identical_single,
+        "tuned": {"options": rec["options"], "searched": rec["searched"], "best_ms": rec["best_ms"],
+                  "start_ms": rec["start_ms"]},
+        "per_graph": {"value": G / t_single, "unit": "graphs/s", "ms_total": t_single * 1e3},
+        "speedup_vs_per_graph": t_single / t_tuned,
+        "e2e": {"value": G / t_e2e, "unit": "graphs/s", "h2d_bytes_per_step": 8 * (db.n + 1) + 4 * db.nnz + 8 * (G + 1),
+                "d2h_bytes_per_step": 4 * db.n},
+        "roofline": {"bound": "hbm", "kernel": "batch_persistent_kernel", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "algorithmic_bytes_per_launch": pb, "ms_per_launch": kms, "launches_per_step": 1},
+        "path": {"algorithmic_bytes_per_step": pb, "sum_U": sum_u, "decrements": dec},
+        "gpu_launches": launches["tuned"],
+    }
+
+
+def run_batch(args, rank, world):
+    """Batched form: gc_color_batch colours every graph of the packed batch
+    (with the autotuned options: the persistent one-launch path or the
+    segmented one); the comparison is one gc_color_graph call per graph on
+    the same GPU (graphs/s both ways, colourings checked identical)."""
+    import torch
+    import torch.distributed as dist
+    from paper_2008_11321_gb300 import _build, tuning
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    if world > 1:  # replicas: every rank colours its own copy of the batch
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    w = WORKLOADS[args.workload]
+    sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+    sampler.start()
+    b = measure_batch(w, dev, args.steps, args.warmup, args.options, world, tuning.TuningCache(args.tune_cache))
+    clocks = sampler.stop()
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return 0
-    line = {"metric": METRIC, "value": job_rate(G, 1, world, t_batch), "unit": "graphs/s", "n_gpus": world,
-            "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_batch * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": w["desc"], "graphs": G, "n": db.n, "m": db.nnz // 2,
-                       "l2": f"inputs larger than L2 (col_idx {4 * db.nnz / 1e9:.2f} GB), no flush"},
-            "per_graph": {"value": G / t_single, "unit": "graphs/s", "ms_total": t_single * 1e3,
-                          "identical_colourings": identical},
-            "speedup_vs_per_graph": t_single / t_batch,
-            "edges_per_s": job_rate(db.nnz // 2, 1, world, t_batch),
-            "e2e": {"value": job_rate(G, 1, world, t_e2e), "unit": "graphs/s",
-                    "h2d_bytes_per_step": 8 * (db.n + 1) + 4 * db.nnz + 8 * (G + 1),
-                    "d2h_bytes_per_step": 4 * db.n},
-            "gpu_launches": launches, "clocks": clocks}
+    line = {"metric": METRIC, "value": job_rate(b["graphs"], 1, world, b["t_tuned"]), "unit": "graphs/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": b["t_tuned"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": w["desc"], "graphs": b["graphs"], "n": b["n"], "m": b["m"],
+                       "options": b["tuned"]["options"],
+                       "l2": f"inputs larger than L2 (col_idx {8 * b['m'] / 1e9:.2f} GB), no flush"},
+            "paths": b["paths"], "tuned": b["tuned"], "identical_colourings": b["identical_colourings"],
+            "per_graph": b["per_graph"], "speedup_vs_per_graph": b["speedup_vs_per_graph"],
+            "edges_per_s": job_rate(b["m"], 1, world, b["t_tuned"]),
+            "e2e": dict(b["e2e"], value=job_rate(b["graphs"], 1, world, b["t_e2e"])),
+            "roofline": b["roofline"], "path": b["path"], "gpu_launches": b["gpu_launches"], "clocks": clocks}
     if world > 1:
         line["config"]["parallelism"] = "replicas"
     print(json.dumps(line), flush=True)
@@ -620,30 +684,94 @@ def run_batch(args, rank, world):
 
 
 def serve_requests(w):
-    """The serving workload's request list: (graph, eps, seed) per request."""
+    """The serving workload: a pool of generated graphs (n log-uniform in
+    [n_lo, n_hi]; R-MAT with edge factor 8-32 or Barabasi-Albert with m 2-16,
+    50/50) and the request stream drawn from it (graph, eps 1/100 or 1/10,
+    seed).  Returns (pool, [(pool index, eps, seed)])."""
     import math
     import numpy as np
     import graphgen as gg
     rng = np.random.default_rng(w["seed"])
-    out = []
+    pool = []
     lo, hi = math.log(w["n_lo"]), math.log(w["n_hi"])
-    for i in range(w["requests"]):
+    for i in range(w["pool"]):
         n = int(round(math.exp(lo + rng.random() * (hi - lo))))
         if rng.random() < 0.5:
             scale = max(1, int(round(math.log2(n))))
-            g = gg.rmat(scale, int(rng.integers(8, 33)), seed=w["seed"] + i)
+            pool.append(gg.rmat(scale, int(rng.integers(8, 33)), seed=w["seed"] + i))
         else:
-            g = gg.barabasi_albert(n, int(rng.integers(2, 17)), w["seed"] + i)
-        eps = (1, 100) if rng.random() < 0.5 else (1, 10)
-        out.append((g, eps, w["seed"] + i))
-    return out
+            pool.append(gg.barabasi_albert(n, int(rng.integers(2, 17)), w["seed"] + i))
+    reqs = [(int(rng.integers(len(pool))), (1, 100) if rng.random() < 0.5 else (1, 10), w["seed"] + 1000 + i)
+            for i in range(w["requests"])]
+    return pool, reqs
+
+
+def measure_serve(w, dev_index, world=1, slots=2):
+    """Continuous batching: the capacity with every request submitted at
+    once, then Poisson arrivals at `load` x capacity (latency from submission
+    to colours on the host), and the same requests as one gc_color_graph call
+    each on resident graphs (device time)."""
+    import numpy as np
+    import torch
+    import paper_2008_11321_gb300 as gcp
+    from paper_2008_11321_gb300.serve import ColoringServer, latency_summary
+    pool, reqs_in = serve_requests(w)
+    edges = sum(pool[k].m for k, _, _ in reqs_in)
+    with ColoringServer(dev_index, memory_budget=w["budget"], slots=slots) as srv:
+        # warm-up: single requests, then one closed loop (the contexts'
+        # buffers grow once)
+        for k, e, sd in reqs_in[:4]:
+            srv.submit(pool[k].row_ptr, pool[k].col_idx, e[0], e[1], sd).result()
+        for r in [srv.submit(pool[k].row_ptr, pool[k].col_idx, e[0], e[1], sd) for k, e, sd in reqs_in]:
+            r.result()
+        t0 = time.perf_counter()
+        rs = [srv.submit(pool[k].row_ptr, pool[k].col_idx, e[0], e[1], sd) for k, e, sd in reqs_in]
+        for r in rs:
+            r.result()
+        t_closed = time.perf_counter() - t0
+        cap = len(reqs_in) / t_closed
+        rng = np.random.default_rng(w["seed"] + 1)
+        rate = w["load"] * cap
+        n_batches0 = len(srv.batches)
+        srv.reset_occupancy()
+        sync_ranks(world)
+        t0 = time.perf_counter()
+        rs = []
+        for k, e, sd in reqs_in:
+            rs.append(srv.submit(pool[k].row_ptr, pool[k].col_idx, e[0], e[1], sd))
+            time.sleep(rng.exponential(1.0 / rate))
+        for r in rs:
+            r.result()
+        t_open = time.perf_counter() - t0
+        occ = srv.occupancy()
+        batches = srv.batches[n_batches0:]
+        served = {i: r.result() for i, r in enumerate(rs[:16])}
+    # the same requests, one gc_color_graph call each on resident graphs
+    dev = torch.device("cuda", dev_index)
+    dpool = [gcp.DeviceGraph.from_host(gr, dev) for gr in pool]
+    out = [torch.empty(gr.n, dtype=torch.int32, device=dev) for gr in pool]
+    stream = torch.cuda.current_stream(dev)
+    with gcp.Context(dev_index) as ctx:
+        for k, e, sd in reqs_in[:4]:
+            ctx.gc_color_graph(dpool[k], e[0], e[1], sd, out[k])
+        t_single = _timed(stream, lambda: [ctx.gc_color_graph(dpool[k], e[0], e[1], sd, out[k])
+                                           for k, e, sd in reqs_in], 1)
+        identical = True
+        for i in range(16):
+            k, e, sd = reqs_in[i]
+            ctx.gc_color_graph(dpool[k], e[0], e[1], sd, out[k])
+            identical &= bool(np.array_equal(out[k].cpu().numpy(), served[i]))
+    return {"requests": len(reqs_in), "pool_graphs": len(pool), "edges": edges, "t_open": t_open,
+            "arrival_rate_per_s": rate, "latency": latency_summary(rs), "requests_per_s": len(reqs_in) / t_open,
+            "edges_per_s": edges / t_open,
+            "capacity": {"requests_per_s": cap, "edges_per_s": edges / t_closed},
+            "per_graph": {"requests_per_s": len(reqs_in) / t_single, "edges_per_s": edges / t_single,
+                          "unit": "device time of one gc_color_graph call per request, graphs resident"},
+            "identical_colourings": identical, "slots": slots, "occupancy": occ,
+            "batches": {"count": len(batches), "mean_graphs": float(np.mean([b[1] for b in batches]))}}
 
 
 def run_serve(args, rank, world):
-    """Continuous batching: first the capacity with every request submitted
-    at once, then Poisson arrivals at `load` x capacity; latency from
-    submission to colours on the host."""
-    import numpy as np
     import torch
     import torch.distributed as dist
     from paper_2008_11321_gb300 import _build
@@ -655,54 +783,25 @@ def run_serve(args, rank, world):
         _build.build()
     if world > 1:
         dist.barrier()
-    from paper_2008_11321_gb300.serve import ColoringServer, latency_summary
     w = WORKLOADS[args.workload]
-    reqs_in = serve_requests(w)
-    edges = sum(g.m for g, _, _ in reqs_in)
-    with ColoringServer(dev, memory_budget=w["budget"]) as srv:
-        # warm-up: single requests, then one closed loop (the context's
-        # buffers grow to the largest batch once)
-        for g, e, sd in reqs_in[:min(4, len(reqs_in))]:
-            srv.submit(g.row_ptr, g.col_idx, e[0], e[1], sd).result()
-        for r in [srv.submit(g.row_ptr, g.col_idx, e[0], e[1], sd) for g, e, sd in reqs_in]:
-            r.result()
-        t0 = time.perf_counter()
-        rs = [srv.submit(g.row_ptr, g.col_idx, e[0], e[1], sd) for g, e, sd in reqs_in]
-        for r in rs:
-            r.result()
-        t_closed = time.perf_counter() - t0
-        cap = len(reqs_in) / t_closed
-        rng = np.random.default_rng(w["seed"] + 1)
-        rate = w["load"] * cap
-        sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
-        sampler.start()
-        n_batches0 = len(srv.batches)
-        sync_ranks(world)
-        t0 = time.perf_counter()
-        rs = []
-        for g, e, sd in reqs_in:
-            rs.append(srv.submit(g.row_ptr, g.col_idx, e[0], e[1], sd))
-            time.sleep(rng.exponential(1.0 / rate))
-        for r in rs:
-            r.result()
-        t_open = time.perf_counter() - t0
-        clocks = sampler.stop()
-        batches = srv.batches[n_batches0:]
+    sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+    sampler.start()
+    r = measure_serve(w, dev, world)
+    clocks = sampler.stop()
     # the job's time is the slowest replica's (host clocks: latency is a host-side quantity)
-    t_open = max_over_ranks(t_open, world, torch.device("cuda", dev))
-    lat = latency_summary(rs)
+    t_open = max_over_ranks(r["t_open"], world, torch.device("cuda", dev))
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return 0
-    line = {"metric": METRIC, "value": job_rate(edges, 1, world, t_open), "unit": "edges/s", "n_gpus": world,
+    line = {"metric": METRIC, "value": job_rate(r["edges"], 1, world, t_open), "unit": "edges/s", "n_gpus": world,
             "steps": 1, "warmup": 1, "ms_per_step": t_open * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": w["desc"], "requests": len(reqs_in), "edges": edges,
-                       "arrival_rate_per_s": rate, "budget_bytes": w["budget"]},
-            "latency": lat, "requests_per_s": len(reqs_in) / t_open,
-            "capacity": {"requests_per_s": cap, "edges_per_s": edges / t_closed},
-            "batches": {"count": len(batches), "mean_graphs": float(np.mean([b[0] for b in batches]))},
+            "config": {"workload": w["desc"], "requests": r["requests"], "pool_graphs": r["pool_graphs"],
+                       "edges": r["edges"], "arrival_rate_per_s": r["arrival_rate_per_s"],
+                       "budget_bytes": w["budget"], "slots": r["slots"]},
+            **{k: r[k] for k in ("latency", "requests_per_s", "capacity", "per_graph", "identical_colourings",
+                                 "occupancy", "batches")},
             "clocks": clocks}
     if world > 1:
         line["config"]["parallelism"] = "replicas; latency of rank 0"
@@ -724,6 +823,11 @@ def main():
     ap.add_argument("--priority", choices=["adg", "adg-m", "adg-o"] + sorted(PRIORITIES), default="adg",
                     help="JP priority: adg (JP-ADG, the default), adg-m (JP-ADG-M), adg-o (JP-ADG-O) or "
                          "another JP variant")
+    ap.add_argument("--tune-cache", default=None,
+                    help="JSON file of autotuned options (default: GC_TUNING_CACHE or ~/.cache/gcolor/tuning.json)")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner: time the given/default options")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="R-MAT 24 line only: leave out the batch4096 and serve sub-objects")
     ap.add_argument("--options", default=None,
                     help="gc_options fields for the context, as JSON (e.g. '{\"jp_state16\": 0}'); default: "
                          "the library's defaults")
@@ -792,6 +896,14 @@ def main():
 
     for _ in range(args.warmup):
         nc, nr = colour_step()
+    tuned = None
+    if not args.no_tune and not median and not ordered:
+        # the autotuner's options for this graph class (searched unless
+        # cached), applied to the context; then warm up again
+        from paper_2008_11321_gb300 import tuning
+        tuned = tuning.tune_graph(ctx, dg, p, q, seed, cache=tuning.TuningCache(args.tune_cache), reps=3)
+        for _ in range(args.warmup):
+            nc, nr = colour_step()
     ctx.gc_set_timing(True)
 
     try:
@@ -869,7 +981,7 @@ def main():
                    "l2": f"inputs larger than L2 (col_idx {4 * nnz / 1e9:.2f} GB), no flush"},
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": KERNEL_TRAFFIC.get((args.workload, kname)),
+                     "traffic": kernel_traffic(args.workload, kname),
                      "algorithmic_bytes_per_launch": gb[kname] / kl, "ms_per_launch": kms / kl,
                      "launches_per_step": kl,
                      "groups_ms": {k: v[0] for k, v in groups.items()}},
@@ -879,10 +991,33 @@ def main():
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if tuned:
+        line["tuned"] = {"searched": tuned["searched"], "best_ms": tuned["best_ms"], "start_ms": tuned["start_ms"]}
     if e2e:
         line["e2e"] = e2e
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.workload, median=median, ordered=ordered)
+        line["cpu_baseline"] = cpu_baseline(args.workload, median=median, ordered=ordered, graph=g)
+    if world == 1 and not args.no_extras and args.workload == "rmat24" and not median and not ordered:
+        # the batched and served forms, measured in the same run (compact)
+        from paper_2008_11321_gb300 import tuning
+        ctx.close()
+        b = measure_batch(WORKLOADS["batch4096"], dev, 3, 3, args.options, 1, tuning.TuningCache(args.tune_cache))
+        line["batch4096"] = {"workload": WORKLOADS["batch4096"]["desc"], "graphs_per_s": b["graphs_per_s"],
+                             "edges_per_s": b["edges_per_s"], "per_graph_graphs_per_s": b["per_graph"]["value"],
+                             "speedup_vs_per_graph": b["speedup_vs_per_graph"],
+                             "identical_colourings": b["identical_colourings"],
+                             "paths_graphs_per_s": {k: v["graphs_per_s"] for k, v in b["paths"].items()},
+                             "tuned_batch_mode": b["tuned"]["options"]["batch_mode"], "e2e_graphs_per_s":
+                             b["e2e"]["value"], "roofline_frac": b["roofline"]["frac"]}
+        r = measure_serve(WORKLOADS["serve"], local)
+        line["serve"] = {"workload": WORKLOADS["serve"]["desc"], "requests": r["requests"],
+                         "p50_ms": r["latency"].get("p50_ms"), "p99_ms": r["latency"].get("p99_ms"),
+                         "requests_per_s": r["requests_per_s"], "edges_per_s": r["edges_per_s"],
+                         "capacity_requests_per_s": r["capacity"]["requests_per_s"],
+                         "per_graph_requests_per_s": r["per_graph"]["requests_per_s"],
+                         "identical_colourings": r["identical_colourings"],
+                         "requests_in_flight_mean": r["occupancy"]["requests_in_flight_mean"],
+                         "busy_slots_mean": r["occupancy"]["busy_slots_mean"], "slots": r["slots"]}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -535,6 +535,14 @@ def run_reference(args, rank, world):
     return 0
 
 
+def _phase(name):
+    """Synchronises the device and notes on stderr that a phase ended, so an
+    asynchronous CUDA error surfaces in the phase that caused it."""
+    import torch
+    torch.cuda.synchronize()
+    print(f"[bench] {name} done", file=sys.stderr, flush=True)
+
+
 def _timed(stream, fn, steps):
     """Device time (s) of `steps` calls of fn on `stream`, CUDA events."""
     import torch
@@ -578,6 +586,7 @@ def measure_batch(w, dev, steps, warmup, options=None, world=1, tune_cache=None)
         ctx.gc_set_timing(False)
         res[name] = {"ms_per_step": t * 1e3, "graphs_per_s": G / t, "kernel_ms": st.ms_adg_update,
                      "launches_per_step": st.launches}
+        _phase(f"batch {name}")
         launches[name] = st.launches * steps
         ref_color = color.clone() if name == "persistent" else ref_color
     identical_paths = bool(torch.equal(ref_color, color))
@@ -585,6 +594,7 @@ def measure_batch(w, dev, steps, warmup, options=None, world=1, tune_cache=None)
     # the autotuner's choice for this batch class (searched unless cached)
     ctx.gc_set_options(options or {})
     rec = tuning.tune_batch(ctx, db, jobs, cache=tune_cache, reps=2)
+    _phase("batch tuning")
     for _ in range(warmup):
         ctx.gc_color_batch(db, jobs, color, None, ncol)
     sync_ranks(world, dev)
@@ -592,6 +602,7 @@ def measure_batch(w, dev, steps, warmup, options=None, world=1, tune_cache=None)
                              world, dev) / steps
     launches["tuned"] = ctx.gc_get_stats().launches * steps
     identical_tuned = bool(torch.equal(ref_color, color))
+    _phase("batch tuned")
     # per-graph plain launches of the same graphs (local ids), one pass
     rp, ci = g.row_ptr, g.col_idx
     graphs = []
@@ -605,6 +616,7 @@ def measure_batch(w, dev, steps, warmup, options=None, world=1, tune_cache=None)
     t_single = _timed(stream, lambda: [ctx.gc_color_graph(graphs[i], p, q, w["seed"] + i,
                                                           single[int(off[i]):int(off[i + 1])]) for i in range(G)], 1)
     identical_single = bool(torch.equal(single, ref_color))
+    _phase("batch per-graph")
     # end to end: packed CSR host -> device, batch call, colours device -> host
     hcolor = torch.empty(db.n, dtype=torch.int32, pin_memory=True)
     rp_h, ci_h, off_h = torch.from_numpy(g.row_ptr), torch.from_numpy(g.col_idx), torch.from_numpy(off)
@@ -617,6 +629,7 @@ def measure_batch(w, dev, steps, warmup, options=None, world=1, tune_cache=None)
     sync_ranks(world, dev)
     t_e2e = max_over_ranks(_timed(stream, e2e_step, steps), world, dev) / steps
     ctx.close()
+    _phase("batch e2e")
     peak, peak_kind = load_peak()
     pb = path_bytes(db.n, db.nnz, sum_u, dec)
     kms = res["persistent"]["kernel_ms"]
@@ -730,6 +743,7 @@ def measure_serve(w, dev_index, world=1, slots=2):
             r.result()
         t_closed = time.perf_counter() - t0
         cap = len(reqs_in) / t_closed
+        _phase("serve closed loop")
         rng = np.random.default_rng(w["seed"] + 1)
         rate = w["load"] * cap
         n_batches0 = len(srv.batches)
@@ -745,6 +759,7 @@ def measure_serve(w, dev_index, world=1, slots=2):
         t_open = time.perf_counter() - t0
         occ = srv.occupancy()
         batches = srv.batches[n_batches0:]
+        _phase("serve open loop")
         served = {i: r.result() for i, r in enumerate(rs[:16])}
     # the same requests, one gc_color_graph call each on resident graphs
     dev = torch.device("cuda", dev_index)

@@ -153,6 +153,10 @@ batch_persistent_kernel(PGraphArgs A) {
             A.D[u] = d;
           } else {
             u = __ldcg(U + i);
+            if (u < v0 || u >= v1) {  // not this graph's vertex: record it, skip it
+              atomicExch(A.err, 2);
+              u = static_cast<int>(v0);
+            }
             d = __ldcg(A.D + u);
           }
         }
@@ -183,8 +187,12 @@ batch_persistent_kernel(PGraphArgs A) {
         int len = 0;
         if (t < nR) {
           const int v = __ldcg(R + t);
-          st = A.row_ptr[v];
-          len = static_cast<int>(A.row_ptr[v + 1] - st);
+          if (v >= v0 && v < v1) {
+            st = A.row_ptr[v];
+            len = static_cast<int>(A.row_ptr[v + 1] - st);
+          } else {
+            atomicExch(A.err, 2);
+          }
         }
         sweep_tile(
             st, len, 0, A.col, [&](int w, int) { return __ldcg(A.batch + w); },
@@ -258,9 +266,17 @@ batch_persistent_kernel(PGraphArgs A) {
         int v = 0;
         if (i < ns) {
           v = __ldcg(Ls + i);
+          if (v < v0 || v >= v1) {  // not this graph's vertex: record it, skip it
+            atomicExch(A.err, 2);
+            v = static_cast<int>(v0);
+          }
           const unsigned long long kv = pkey(__ldcg(A.batch + v), tie_hash(seed, static_cast<unsigned>(v - v0)));
           const long long s = A.row_ptr[v], e = A.row_ptr[v + 1];
-          const int pos = __ldcg(A.D + v);
+          int pos = __ldcg(A.D + v);
+          if (pos < 0 || pos > e - s) {  // a resume position outside the row: record it, restart
+            atomicExch(A.err, 3);
+            pos = 0;
+          }
           unsigned long long used = pos > 0 ? __ldcg(A.used + v) : 0ull;
           long long k = s + pos;
           for (; k < e; ++k) {
@@ -289,7 +305,11 @@ batch_persistent_kernel(PGraphArgs A) {
       // warp path: one vertex per warp
       unsigned* win = s_win[warp];
       for (int i = warp; i < nb; i += kPWarps) {
-        const int v = __ldcg(Lb + i);
+        int v = __ldcg(Lb + i);
+        if (v < v0 || v >= v1) {
+          if (lane == 0) atomicExch(A.err, 2);
+          v = static_cast<int>(v0);
+        }
         const unsigned long long kv = pkey(__ldcg(A.batch + v), tie_hash(seed, static_cast<unsigned>(v - v0)));
         const long long s = A.row_ptr[v], e = A.row_ptr[v + 1];
         int c = 0;
@@ -471,6 +491,8 @@ gc_status batch_color_persistent(gc_context* ctx, Arena a, const gc_batch_csr* b
   GC_TRY_CUDA(cudaStreamSynchronize(s));
   ctx->stats.sum_U = static_cast<int64_t>(pin[2]);
   ctx->stats.sum_decrements = static_cast<int64_t>(pin[3]);
+  // 1: a round without progress, 2: a list entry outside its graph, 3: a
+  // resume position outside its row -- none can happen for a valid batch
   return *reinterpret_cast<int*>(pin + 1) ? GC_ERR_CUDA : GC_OK;
 }
 

@@ -13,7 +13,8 @@ Functions (each cites the passage of the paper it follows in ``oracle.c``):
   jp_adg_o(g, p, q)              JP with rho_ADG-O
   tiebreak(seed, v)              SplitMix64-based random tie-break rho_R
   priority(batch, seed)          (batch << 32) | tiebreak, ties by vertex id
-  priority_kind(g, kind, seed)   JP-R / FF / LF / LLF keys (kinds 0..3)
+  priority_kind(g, kind, seed)   JP-R / FF / LF / LLF / SL keys (kinds 0..4)
+  smallest_last(g)               SL order: minimum (current degree, id) first
   greedy(g, order)               Greedy colouring in a given order
   jp_color(g, priority)          JP (Algorithm 3) == Greedy by decreasing key
   jp_adg(g, p, q, seed)          ADG then JP with <rho_ADG, rho_R>
@@ -88,6 +89,8 @@ def _load():
         lib.oracle_jp_adg.argtypes = [i64, vp, vp, u32, u32, u64, vp, vp, vp, vp]
         lib.oracle_pred_count.restype = None
         lib.oracle_pred_count.argtypes = [i64, vp, vp, vp, vp]
+        lib.oracle_smallest_last.restype = ctypes.c_int
+        lib.oracle_smallest_last.argtypes = [i64, vp, vp, vp]
         lib.oracle_jp_depth.restype = i64
         lib.oracle_jp_depth.argtypes = [i64, vp, vp, vp, vp]
         lib.oracle_degeneracy.restype = i64
@@ -210,10 +213,25 @@ PRIO_R, PRIO_FF, PRIO_LF, PRIO_LLF = 0, 1, 2, 3
 
 
 def priority_kind(g, kind: int, seed: int) -> np.ndarray:
+    """Keys of the JP variants: 0 JP-R, 1 JP-FF, 2 JP-LF, 3 JP-LLF (from the
+    degrees and the seeded hash), 4 JP-SL (the smallest-last removal index:
+    vertices removed later are coloured first; no seed)."""
     n, rp, _ = _csr(g)
     key = np.zeros(n, dtype=np.uint64)
+    if kind == 4:
+        key[smallest_last(g)] = np.arange(n, dtype=np.uint64)
+        return key
     _check(_load().oracle_priority_kind(n, _p(rp), kind, seed, _p(key)), "priority_kind")
     return key
+
+
+def smallest_last(g) -> np.ndarray:
+    """int64[n]: the vertices in smallest-last removal order (minimum
+    current degree first, then minimum id)."""
+    n, rp, ci = _csr(g)
+    order = np.zeros(n, dtype=np.int64)
+    _check(_load().oracle_smallest_last(n, _p(rp), _p(ci), _p(order)), "smallest_last")
+    return order
 
 
 def greedy(g, order: np.ndarray):

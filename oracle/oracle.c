@@ -798,3 +798,83 @@ int32_t oracle_chromatic_number(int64_t n, const int64_t *row_ptr, const int32_t
     }
     return (int32_t)n;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Smallest-last order for JP-SL (Section 4.1 lists SL among the orderings   */
+/* JP is combined with; Matula-Beck peeling): repeatedly remove a vertex of  */
+/* minimum degree in the remaining graph.  The paper fixes no tie rule; the  */
+/* reading taken is the vertex of minimum (current degree, id).  A binary    */
+/* heap of (degree, id) entries with lazy deletion: an entry is stale once   */
+/* its vertex is gone or its degree has dropped.  order[i] = i-th removed.   */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    int64_t d;
+    int64_t v;
+} sl_ent;
+
+static int sl_less(sl_ent a, sl_ent b)
+{
+    return a.d < b.d || (a.d == b.d && a.v < b.v);
+}
+
+static void sl_push(sl_ent *h, int64_t *size, sl_ent e)
+{
+    int64_t i = (*size)++;
+    h[i] = e;
+    while (i > 0) {
+        int64_t p = (i - 1) / 2;
+        if (!sl_less(h[i], h[p])) break;
+        sl_ent t = h[i]; h[i] = h[p]; h[p] = t;
+        i = p;
+    }
+}
+
+static sl_ent sl_pop(sl_ent *h, int64_t *size)
+{
+    sl_ent top = h[0];
+    h[0] = h[--(*size)];
+    int64_t i = 0;
+    for (;;) {
+        int64_t l = 2 * i + 1, r = l + 1, m = i;
+        if (l < *size && sl_less(h[l], h[m])) m = l;
+        if (r < *size && sl_less(h[r], h[m])) m = r;
+        if (m == i) break;
+        sl_ent t = h[i]; h[i] = h[m]; h[m] = t;
+        i = m;
+    }
+    return top;
+}
+
+int oracle_smallest_last(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, int64_t *order)
+{
+    if (n == 0) return 0;
+    const int64_t nnz = row_ptr[n];
+    int64_t *deg = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    char *gone = (char *)calloc((size_t)n, 1);
+    /* every vertex enters once, then once more per decrement: n + nnz/2 entries at most */
+    sl_ent *heap = (sl_ent *)malloc(sizeof(sl_ent) * (size_t)(n + nnz / 2 + 1));
+    if (!deg || !gone || !heap) { free(deg); free(gone); free(heap); return 2; }
+    int64_t size = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        deg[v] = row_ptr[v + 1] - row_ptr[v];
+        sl_ent e = {deg[v], v};
+        sl_push(heap, &size, e);
+    }
+    int64_t i = 0;
+    while (i < n) {
+        sl_ent e = sl_pop(heap, &size);
+        if (gone[e.v] || e.d != deg[e.v]) continue;  /* stale entry */
+        gone[e.v] = 1;
+        order[i++] = e.v;
+        for (int64_t k = row_ptr[e.v]; k < row_ptr[e.v + 1]; ++k) {
+            int64_t w = col_idx[k];
+            if (gone[w]) continue;
+            deg[w] -= 1;
+            sl_ent f = {deg[w], w};
+            sl_push(heap, &size, f);
+        }
+    }
+    free(deg); free(gone); free(heap);
+    return 0;
+}

@@ -152,3 +152,57 @@ def test_depth_brute_force_tiny(seed):
     g = random_small(n, 0.45, seed)
     for prio in (rng.integers(0, 4, size=n).astype(np.uint64), rng.permutation(n).astype(np.uint64)):
         assert oracle.jp_depth(g, prio) == _longest_path_brute_force(g, prio)
+
+
+# ----------------------------------------------------------- smallest-last order
+
+def _sl_naive(g):
+    """Smallest-last by recomputing every remaining degree from scratch at
+    each step and taking the minimum (degree, id)."""
+    left = set(range(g.n))
+    nb = [set(int(w) for w in neighbours(g, v)) for v in range(g.n)]
+    out = []
+    while left:
+        v = min(left, key=lambda u: (len(nb[u] & left), u))
+        out.append(v)
+        left.remove(v)
+    return out
+
+
+def test_sl_closed_forms():
+    from _fixtures import complete_bipartite, cycle
+    assert oracle.smallest_last(path(7)).tolist() == list(range(7))          # an end, then its neighbour...
+    assert oracle.smallest_last(cycle(6)).tolist() == list(range(6))         # vertex 0, then the path 1..5
+    assert oracle.smallest_last(complete(5)).tolist() == list(range(5))      # all degrees equal: by id
+    assert oracle.smallest_last(star(5)).tolist() == [1, 2, 3, 4, 0, 5]      # leaves until the centre ties at 1
+    assert oracle.smallest_last(empty(4)).tolist() == [0, 1, 2, 3]
+    # K_{2,5}: the degree-2 side goes until the other side is down to 2
+    assert oracle.smallest_last(complete_bipartite(2, 5)).tolist() == [2, 3, 4, 0, 5, 1, 6]
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_sl_matches_naive_peeling(seed):
+    rng = np.random.default_rng(seed)
+    g = random_small(int(rng.integers(5, 40)), float(rng.uniform(0.05, 0.5)), seed)
+    assert oracle.smallest_last(g).tolist() == _sl_naive(g)
+
+
+@pytest.mark.parametrize("g", [gg.rmat(12, 8, seed=1), gg.barabasi_albert(2000, 5, 2), gg.erdos_renyi(3000, 12000, 3),
+                               gg.grid(30, 40)], ids=lambda g: g.name)
+def test_sl_degeneracy_and_colour_bound(g):
+    # the largest degree at removal in a smallest-last order is the
+    # degeneracy d, and Greedy in reverse removal order (JP-SL) uses at most
+    # d + 1 colours
+    order = oracle.smallest_last(g)
+    assert sorted(order.tolist()) == list(range(g.n))
+    pos = np.empty(g.n, dtype=np.int64)
+    pos[order] = np.arange(g.n)
+    src = np.repeat(np.arange(g.n), g.degrees())
+    later = np.bincount(src[pos[g.col_idx] > pos[src]], minlength=g.n)  # degree at removal
+    d, _ = oracle.degeneracy(g)
+    assert later.max() == d
+    key = oracle.priority_kind(g, 4, 0)
+    assert np.array_equal(key[order], np.arange(g.n, dtype=np.uint64))
+    color, nc = oracle.jp_color(g, key)
+    assert nc <= d + 1
+    assert np.all(color[src] != color[g.col_idx])

@@ -261,7 +261,7 @@ def cpu_baseline(w_name, seconds_target=10.0, median=False, dec=False, ordered=F
             "sample": f"{desc}: n={g.n}, m={g.m}, {reps} run(s) of {what}, {total:.1f} s"}
 
 
-PRIORITIES = {"r": (0, "JP-R"), "ff": (1, "JP-FF"), "lf": (2, "JP-LF"), "llf": (3, "JP-LLF")}
+PRIORITIES = {"r": (0, "JP-R"), "ff": (1, "JP-FF"), "lf": (2, "JP-LF"), "llf": (3, "JP-LLF"), "sl": (4, "JP-SL")}
 
 
 def run_variant(args, rank, world):
@@ -719,7 +719,15 @@ def serve_requests(w):
     return pool, reqs
 
 
-def measure_serve(w, dev_index, world=1, slots=2):
+def _log_batch(slot, reqs, seconds, errors):
+    """--debug: one stderr line per serving batch."""
+    bad = [e for e in errors if e]
+    print(f"[serve] slot {slot} graphs {len(reqs)} n {sum(r.n for r in reqs)} nnz {sum(r.nnz for r in reqs)} "
+          f"max_nnz {max(r.nnz for r in reqs)} {seconds * 1e3:.1f} ms" + (f" ERROR {bad[0]}" if bad else ""),
+          file=sys.stderr, flush=True)
+
+
+def measure_serve(w, dev_index, world=1, slots=2, debug=False):
     """Continuous batching: the capacity with every request submitted at
     once, then Poisson arrivals at `load` x capacity (latency from submission
     to colours on the host), and the same requests as one gc_color_graph call
@@ -730,13 +738,16 @@ def measure_serve(w, dev_index, world=1, slots=2):
     from paper_2008_11321_gb300.serve import ColoringServer, latency_summary
     pool, reqs_in = serve_requests(w)
     edges = sum(pool[k].m for k, _, _ in reqs_in)
-    with ColoringServer(dev_index, memory_budget=w["budget"], slots=slots) as srv:
+    with ColoringServer(dev_index, memory_budget=w["budget"], slots=slots,
+                        on_batch=_log_batch if debug else None) as srv:
         # warm-up: single requests, then one closed loop (the contexts'
         # buffers grow once)
         for k, e, sd in reqs_in[:4]:
             srv.submit(pool[k].row_ptr, pool[k].col_idx, e[0], e[1], sd).result()
+        _phase("serve warm-up singles")
         for r in [srv.submit(pool[k].row_ptr, pool[k].col_idx, e[0], e[1], sd) for k, e, sd in reqs_in]:
             r.result()
+        _phase("serve warm-up closed loop")
         t0 = time.perf_counter()
         rs = [srv.submit(pool[k].row_ptr, pool[k].col_idx, e[0], e[1], sd) for k, e, sd in reqs_in]
         for r in rs:
@@ -801,7 +812,7 @@ def run_serve(args, rank, world):
     w = WORKLOADS[args.workload]
     sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
     sampler.start()
-    r = measure_serve(w, dev, world)
+    r = measure_serve(w, dev, world, debug=args.debug)
     clocks = sampler.stop()
     # the job's time is the slowest replica's (host clocks: latency is a host-side quantity)
     t_open = max_over_ranks(r["t_open"], world, torch.device("cuda", dev))
@@ -838,6 +849,8 @@ def main():
     ap.add_argument("--priority", choices=["adg", "adg-m", "adg-o"] + sorted(PRIORITIES), default="adg",
                     help="JP priority: adg (JP-ADG, the default), adg-m (JP-ADG-M), adg-o (JP-ADG-O) or "
                          "another JP variant")
+    ap.add_argument("--debug", action="store_true",
+                    help="diagnostics: CUDA_LAUNCH_BLOCKING=1 and a stderr line per serving batch")
     ap.add_argument("--tune-cache", default=None,
                     help="JSON file of autotuned options (default: GC_TUNING_CACHE or ~/.cache/gcolor/tuning.json)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner: time the given/default options")
@@ -851,6 +864,8 @@ def main():
                          "(its SIM-COL on one partition: plain ITR)")
     args = ap.parse_args()
     args.options = json.loads(args.options) if args.options else None
+    if args.debug:  # before CUDA is initialised: every launch synchronous, faults reported where they happen
+        os.environ["CUDA_LAUNCH_BLOCKING"] = "1"
     if args.warmup < 3:
         print("warning: --warmup below 3 is outside the timing rules", file=sys.stderr)
 

@@ -112,6 +112,12 @@ typedef struct {
 /* Human-readable name of a status code (static storage). */
 const char *gc_status_str(gc_status s);
 
+/* Where the last CUDA call that failed inside this library on the calling
+ * host thread was made, and the CUDA error ("file:line: name (message)");
+ * "" if none has failed.  Thread-local storage, valid until the thread's
+ * next library call. */
+const char *gc_last_error(void);
+
 /* ADG's UPDATE direction (gc_options.update_mode).  Push (Algorithm 1's
  * UPDATE): every vertex removed this round decrements the degree of each
  * neighbour still in U.  Pull (Section 5, "Push vs. Pull", the CREW variant
@@ -333,10 +339,18 @@ gc_status gc_color_graph_dec_itr(gc_context *ctx, const gc_csr *g, uint32_t eps_
  *   GC_PRIO_LF   JP-LF:  <deg(v), rho_R>            key = deg(v) << 32 | h_seed(v)
  *   GC_PRIO_LLF  JP-LLF: <ceil(log2 deg(v)), rho_R> key = ceil(log2 deg(v)) << 32 | h_seed(v)
  *                        (0 for degree 0 and 1)
+ *   GC_PRIO_SL   JP-SL:  smallest-last              key = the index at which v is
+ *                        removed when the vertex of minimum (degree in the
+ *                        remaining graph, id) is removed repeatedly
+ *                        (Matula-Beck peeling; the paper leaves ties open);
+ *                        the vertex removed last is coloured first; no seed.
+ *                        Inherently sequential: one thread block removes a
+ *                        vertex every few microseconds.  n <= 2^25, else
+ *                        GC_ERR_OVERFLOW.
  * with h_seed as in gc_make_priority; equal keys fall back to the vertex id
  * in gc_jp_color.  key_out is device, n uint64.  GC_ERR_INVALID_ARG for an
  * unknown kind. */
-enum { GC_PRIO_R = 0, GC_PRIO_FF = 1, GC_PRIO_LF = 2, GC_PRIO_LLF = 3 };
+enum { GC_PRIO_R = 0, GC_PRIO_FF = 1, GC_PRIO_LF = 2, GC_PRIO_LLF = 3, GC_PRIO_SL = 4 };
 gc_status gc_make_priority_kind(gc_context *ctx, const gc_csr *g, int32_t kind, uint64_t seed,
                                 uint64_t *key_out, gc_stream stream);
 

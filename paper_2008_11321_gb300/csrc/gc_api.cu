@@ -1,6 +1,7 @@
 // C ABI entry points (gcolor.h): context management, argument checks, CSR
 // validation, and the orchestration of the ADG and JP kernels.
 #include <climits>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -11,6 +12,13 @@
 
 namespace gc {
 thread_local int g_launches = 0;
+thread_local char g_last_error[256] = "";
+
+void note_cuda_error(cudaError_t e, const char* file, int line) {
+  const char* base = strrchr(file, '/');
+  snprintf(g_last_error, sizeof(g_last_error), "%s:%d: %s (%s)", base ? base + 1 : file, line, cudaGetErrorName(e),
+           cudaGetErrorString(e));
+}
 }  // namespace gc
 
 namespace {
@@ -192,6 +200,8 @@ gc_status gc_context::reserve_aux(size_t bytes) { return fail_alloc ? GC_ERR_OOM
 gc_status gc_context::reserve_pack(size_t bytes) { return fail_alloc ? GC_ERR_OOM : grow(&pack, &pack_bytes, bytes); }
 
 extern "C" {
+
+const char* gc_last_error(void) { return gc::g_last_error; }
 
 const char* gc_status_str(gc_status s) {
   switch (s) {
@@ -450,11 +460,17 @@ gc_status gc_make_priority_kind(gc_context* ctx, const gc_csr* g, int32_t kind, 
                                 gc_stream stream) {
   if (!ctx) return GC_ERR_INVALID_ARG;
   GC_TRY(check_graph_args(g));
-  if (kind < GC_PRIO_R || kind > GC_PRIO_LLF) return GC_ERR_INVALID_ARG;
+  if (kind < GC_PRIO_R || kind > GC_PRIO_SL) return GC_ERR_INVALID_ARG;
   if (g->n > 0 && !key_out) return GC_ERR_INVALID_ARG;
+  if (kind == GC_PRIO_SL && g->n > (1ll << 25)) return GC_ERR_OVERFLOW;
   DeviceGuard guard(ctx->device);
   CallScope scope(ctx);
   if (!guard.ok) return GC_ERR_CUDA;
+  if (kind == GC_PRIO_SL) {
+    GC_TRY(ctx->reserve(gc::sl_scratch_bytes(g->n)));
+    return gc::sl_priority(ctx, ctx->arena(), g, reinterpret_cast<unsigned long long*>(key_out),
+                           reinterpret_cast<cudaStream_t>(stream));
+  }
   GC_TRY_CUDA(gc::make_priority_kind(row_ptr_of(g), g->n, kind, seed, reinterpret_cast<unsigned long long*>(key_out),
                                      ctx->num_sms, reinterpret_cast<cudaStream_t>(stream)));
   return GC_OK;

@@ -211,6 +211,9 @@ gc_status autotune(gc_context* ctx, long long n, const std::function<gc_status(i
                    cudaStream_t s);
 cudaError_t make_priority(const int* batch, long long n, unsigned long long seed,
                           unsigned long long* key, int num_sms, cudaStream_t s);
+// JP-SL keys (gc_sl.cu): the smallest-last removal index of every vertex.
+size_t sl_scratch_bytes(long long n);
+gc_status sl_priority(gc_context* ctx, Arena a, const gc_csr* g, unsigned long long* prio, cudaStream_t s);
 // JP-R / FF / LF / LLF keys (gc_make_priority_kind); kind already checked.
 cudaError_t make_priority_kind(const long long* row_ptr, long long n, int kind, unsigned long long seed,
                                unsigned long long* key, int num_sms, cudaStream_t s);
@@ -318,10 +321,18 @@ inline gc_status gc_cuda_status(cudaError_t e) {
   return GC_ERR_CUDA;
 }
 
+namespace gc {
+// Where the last failing CUDA call of this host thread was made (gc_last_error).
+void note_cuda_error(cudaError_t e, const char* file, int line);
+}  // namespace gc
+
 #define GC_TRY_CUDA(expr)                              \
   do {                                                 \
     cudaError_t e_ = (expr);                           \
-    if (e_ != cudaSuccess) return gc_cuda_status(e_);  \
+    if (e_ != cudaSuccess) {                           \
+      gc::note_cuda_error(e_, __FILE__, __LINE__);     \
+      return gc_cuda_status(e_);                       \
+    }                                                  \
   } while (0)
 
 #define GC_TRY(expr)                 \

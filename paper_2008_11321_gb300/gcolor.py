@@ -22,7 +22,7 @@ GC_OK, GC_ERR_INVALID_ARG, GC_ERR_INVALID_GRAPH, GC_ERR_OOM = 0, 1, 2, 3
 GC_ERR_CUDA, GC_ERR_TIMEOUT, GC_ERR_OVERFLOW = 4, 5, 6
 
 # Every symbol declared in include/gcolor.h.
-EXPORTS = ("gc_status_str", "gc_options_init", "gc_create", "gc_get_options", "gc_set_options", "gc_autotune",
+EXPORTS = ("gc_status_str", "gc_last_error", "gc_options_init", "gc_create", "gc_get_options", "gc_set_options", "gc_autotune",
            "gc_autotune_batch", "gc_destroy", "gc_get_stats", "gc_set_timing",
            "gc_validate_csr", "gc_adg_partition", "gc_make_priority", "gc_jp_color",
            "gc_color_graph", "gc_color_graph_host", "gc_adg_partition_noalloc", "gc_color_batch",
@@ -30,7 +30,7 @@ EXPORTS = ("gc_status_str", "gc_options_init", "gc_create", "gc_get_options", "g
            "gc_dec_itr_color", "gc_color_graph_dec_itr", "gc_adg_o_order", "gc_color_graph_o")
 
 # priority kinds of gc_make_priority_kind
-GC_PRIO_R, GC_PRIO_FF, GC_PRIO_LF, GC_PRIO_LLF = 0, 1, 2, 3
+GC_PRIO_R, GC_PRIO_FF, GC_PRIO_LF, GC_PRIO_LLF, GC_PRIO_SL = 0, 1, 2, 3, 4
 # ADG UPDATE directions (gc_options.update_mode)
 GC_UPDATE_AUTO, GC_UPDATE_PUSH, GC_UPDATE_PULL = 0, 1, 2
 # gc_color_batch paths (gc_options.batch_mode, gc_stats.batch_path)
@@ -40,7 +40,8 @@ GC_BATCH_AUTO, GC_BATCH_SEGMENTED, GC_BATCH_PERSISTENT = 0, 1, 2
 class GcError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
-        super().__init__(f"{what}: {status_str(status)}")
+        where = load().gc_last_error().decode() if status == GC_ERR_CUDA else ""
+        super().__init__(f"{what}: {status_str(status)}" + (f" at {where}" if where else ""))
 
 
 class gc_csr(ctypes.Structure):
@@ -111,6 +112,8 @@ def load(path: str = LIB_PATH):
     P = ctypes.POINTER
     lib.gc_status_str.restype = ctypes.c_char_p
     lib.gc_status_str.argtypes = [ctypes.c_int]
+    lib.gc_last_error.restype = ctypes.c_char_p
+    lib.gc_last_error.argtypes = []
     lib.gc_options_init.restype = ctypes.c_int
     lib.gc_options_init.argtypes = [P(gc_options)]
     lib.gc_create.restype = ctypes.c_int

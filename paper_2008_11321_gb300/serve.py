@@ -124,8 +124,11 @@ class CudaEngine:
 
 class ColoringServer:
     def __init__(self, device: int = 0, memory_budget: int = 40 << 30, max_batch_graphs: int = 4096,
-                 slots: int = 2, options=None, engine=None):
+                 slots: int = 2, options=None, engine=None, on_batch=None):
+        """on_batch(slot, requests, seconds, errors): called after every
+        batch (for logging), errors being one string or None per request."""
         self.engine = engine if engine is not None else CudaEngine(device, slots, options)
+        self.on_batch = on_batch
         self.slots = slots
         self.budget = memory_budget
         self.max_batch = max_batch_graphs
@@ -277,6 +280,8 @@ class ColoringServer:
                 r.t_start = t0
             results = self._colour(slot, batch)
             t1 = time.perf_counter()
+            if self.on_batch is not None:
+                self.on_batch(slot, batch, t1 - t0, [e for _, e in results])
             with self._cv:
                 self._account()
                 self._busy -= 1

@@ -37,6 +37,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_status_strings(lib):
+    assert lib.gc_last_error() == b""
     assert gcp.status_str(gcp.GC_OK) == "GC_OK"
     assert gcp.status_str(gcp.GC_ERR_TIMEOUT) == "GC_ERR_TIMEOUT"
     assert gcp.status_str(99) == "GC_ERR_UNKNOWN"

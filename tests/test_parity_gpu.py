@@ -194,9 +194,10 @@ VARIANT_GRAPHS = [gg.erdos_renyi(20000, 100000, seed=3), gg.rmat(16, 16, seed=2)
                   gg.grid(64, 64, 16, perm_seed=3), gg.barabasi_albert(30000, 4, 5), star(5000), empty(50)]
 
 
-@pytest.mark.parametrize("kind", [0, 1, 2, 3], ids=["R", "FF", "LF", "LLF"])
+@pytest.mark.parametrize("kind", [0, 1, 2, 3, 4], ids=["R", "FF", "LF", "LLF", "SL"])
 def test_jp_variants(ctx, kind):
-    # JP-R / FF / LF / LLF (Section 4.1): keys bit for bit, then the colouring
+    # JP-R / FF / LF / LLF / SL (Section 4.1): keys bit for bit, then the
+    # colouring; SL's key is the smallest-last removal index
     for g in VARIANT_GRAPHS:
         dg = dev(g)
         key = torch.zeros(g.n, dtype=torch.int64, device="cuda:0")
@@ -427,3 +428,20 @@ def test_state_word_switch_on_cliques(ctx_state16, n, bits):
     assert nr == onr and nc == onc == n
     assert np.array_equal(batch.cpu().numpy(), ob) and np.array_equal(color.cpu().numpy(), oc)
     assert ctx.gc_get_stats().jp_state_bits == bits
+
+
+def test_jp_sl_small_graphs_and_limit(ctx):
+    # the smallest-last order on the hand-derived cases and a graph with
+    # several chunks of 2048 vertices, then the size limit
+    from _fixtures import complete_bipartite
+    for g in (path(7), cycle(6), complete(5), star(5), complete_bipartite(2, 5), gg.rmat(13, 8, seed=4)):
+        dg = dev(g)
+        key = torch.zeros(g.n, dtype=torch.int64, device="cuda:0")
+        ctx.gc_make_priority_kind(dg, gcp.GC_PRIO_SL, 0, key)
+        order = np.argsort(key.cpu().numpy())
+        assert np.array_equal(order, oracle.smallest_last(g)), g.name
+    big = gcp.DeviceGraph(torch.zeros((1 << 25) + 2, dtype=torch.int64, device="cuda:0"),
+                          torch.zeros(0, dtype=torch.int32, device="cuda:0"))
+    with pytest.raises(gcp.GcError) as err:
+        ctx.gc_make_priority_kind(big, gcp.GC_PRIO_SL, 0, torch.empty(1, dtype=torch.int64, device="cuda:0"))
+    assert err.value.status == gcp.GC_ERR_OVERFLOW

@@ -314,16 +314,6 @@ gc_status batch_color(gc_context* ctx, const gc_batch_csr* b, const gc_job* jobs
   unsigned* tiev = reinterpret_cast<unsigned*>(vbase + 2 * vb);
   BGraph* gs = reinterpret_cast<BGraph*>(vbase + 3 * vb);
   gc_job* djobs = reinterpret_cast<gc_job*>(vbase + 3 * vb + gb);
-  GC_TRY(ctx->reserve(batch_adg_scratch_bytes(n, nnz, G)));
-  Arena a = ctx->arena();
-  BCtl* ctl = a.take<BCtl>(1);
-  int* ubuf[2] = {a.take<int>(n > 0 ? n : 1), a.take<int>(n > 0 ? n : 1)};
-  const long long ntask = n + nnz / kChunk + 1;
-  long long* task_start = a.take<long long>(ntask);
-  int* task_len = a.take<int>(ntask);
-  int* task_g = a.take<int>(ntask);
-  if (!ctl || !ubuf[0] || !ubuf[1] || !task_start || !task_len || !task_g) return GC_ERR_OOM;
-
   GC_TRY_CUDA(cudaMemcpyAsync(djobs, jobs, sizeof(gc_job) * G, cudaMemcpyHostToDevice, s));
   // One persistent launch (a block per graph, gc_batch_persist.cu) when no
   // graph is too large for one block: at most 4 times an SM's share of the
@@ -343,6 +333,17 @@ gc_status batch_color(gc_context* ctx, const gc_batch_csr* b, const gc_job* jobs
     }
   }
   ctx->stats.batch_path = GC_BATCH_SEGMENTED;
+  // the segmented path's scratch is taken only now: the check above may have
+  // grown (reallocated) the scratch arena
+  GC_TRY(ctx->reserve(batch_adg_scratch_bytes(n, nnz, G)));
+  Arena a = ctx->arena();
+  BCtl* ctl = a.take<BCtl>(1);
+  int* ubuf[2] = {a.take<int>(n > 0 ? n : 1), a.take<int>(n > 0 ? n : 1)};
+  const long long ntask = n + nnz / kChunk + 1;
+  long long* task_start = a.take<long long>(ntask);
+  int* task_len = a.take<int>(ntask);
+  int* task_g = a.take<int>(ntask);
+  if (!ctl || !ubuf[0] || !ubuf[1] || !task_start || !task_len || !task_g) return GC_ERR_OOM;
   if (n > 0) GC_TRY_CUDA(cudaMemsetAsync(bat, 0, sizeof(int) * n, s));  // 0 = still in U
   const int blocks = ctx->num_sms * 8;
   const int upd_blocks = resident_grid(batch_update_kernel, kBThreads, ctx->num_sms);

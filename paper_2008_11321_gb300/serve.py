@@ -293,13 +293,18 @@ class ColoringServer:
 
     def _colour(self, slot, batch):
         """[(colours, error)] per request: the batch in one call, or, if that
-        call fails, each request alone so that the error stays with the
-        requests that cause it."""
+        call fails with an error a request can cause (bad input, no memory),
+        each request alone so that the error stays with the requests that
+        cause it.  A CUDA error of the device itself fails the whole batch
+        with that first error: retrying on a broken device cannot help."""
         try:
             return [(c, None) for c in self.engine.colour(slot, batch)]
         except Exception as e:
-            if len(batch) == 1:
-                return [(None, str(e))]
+            first = str(e)
+            status = getattr(e, "status", None)
+            device_error = status == gcolor.GC_ERR_CUDA or (status is None and "CUDA error" in first)
+            if len(batch) == 1 or device_error:
+                return [(None, first)] * len(batch)
         out = []
         for r in batch:
             try:

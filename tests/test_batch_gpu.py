@@ -123,3 +123,20 @@ def test_batch_list_entry_point(ctx):
     ctx.gc_color_batch_list(dgs, jobs, outs)
     for g, (p, q, sd), o in zip(graphs, jobs, outs):
         assert np.array_equal(o.cpu().numpy(), oracle.jp_adg(g, p, q, sd)[1])
+
+
+def test_auto_falls_back_to_segmented_on_a_fresh_context():
+    # AUTO with one graph too large for a block (more than 4/num_SMs of the
+    # batch) in a multi-graph batch, on a fresh context: the persistent
+    # path's check grows the scratch, then the segmented path runs on the
+    # grown scratch
+    graphs = [gg.rmat(16, 16, seed=8), path(9), complete(6), gg.erdos_renyi(300, 900, 2)]
+    jobs = [(1, 100, 70 + i) for i in range(len(graphs))]
+    with gcp.Context(0) as c:
+        c.mode = gcp.GC_BATCH_AUTO
+        color, batch, ncol, nrnd, voff = _run(c, graphs, jobs)
+        assert c.gc_get_stats().batch_path == gcp.GC_BATCH_SEGMENTED
+    for i, g in enumerate(graphs):
+        ob, oc, onr, onc = oracle.jp_adg(g, *jobs[i])
+        sl = slice(voff[i], voff[i + 1])
+        assert np.array_equal(batch[sl], ob) and np.array_equal(color[sl], oc), i

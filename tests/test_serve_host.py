@@ -144,3 +144,23 @@ def test_invalid_requests_rejected_at_submit():
         with pytest.raises(RuntimeError, match="budget"):
             r.result(1)
     assert eng.calls == []
+
+
+def test_device_error_fails_the_batch_without_retries():
+    # a CUDA error of the device (not of one request) is not retried request
+    # by request: every request of the batch reports that first error
+    class BrokenDevice(FakeEngine):
+        def colour(self, slot, reqs):
+            self.calls.append((slot, [r.id for r in reqs]))
+            time.sleep(0.03)
+            raise RuntimeError("CUDA error: an illegal memory access was encountered")
+    eng = BrokenDevice()
+    with ColoringServer(slots=1, engine=eng) as srv:
+        srv.submit(GRAPHS[0].row_ptr, GRAPHS[0].col_idx, 1, 100, 1)
+        time.sleep(0.01)
+        rs = [srv.submit(g.row_ptr, g.col_idx, 1, 100, 2 + i) for i, g in enumerate(GRAPHS[1:4])]
+        for r in rs:
+            with pytest.raises(RuntimeError, match="illegal memory access"):
+                r.result(10)
+    assert len(eng.calls) == 2  # one call per batch, no per-request retries
+    assert srv.used == 0

@@ -159,6 +159,12 @@ typedef struct {
                               (default): always a 32-bit word                */
   int32_t batch_mode;      /* gc_color_batch: GC_BATCH_AUTO (default),
                               GC_BATCH_SEGMENTED or GC_BATCH_PERSISTENT      */
+  int32_t update_hubs;     /* ADG's push UPDATE merges the decrements aimed at
+                              up to this many highest-degree vertices (degree
+                              >= a power of two >= 256) in shared memory
+                              before they reach their degree words, 0..4096
+                              (default 1024; 0: every decrement is an atomic
+                              on its word)                                   */
 } gc_options;
 
 /* How gc_color_batch runs (gc_options.batch_mode, gc_stats.batch_path):

@@ -24,6 +24,16 @@
 //
 // Round 1 reads U = V implicitly (no list) and writes D only for survivors.
 //
+// Hubs.  Rounds 2-5 of a power-law graph send most decrements to a few
+// thousand high-degree vertices, and atomics on one word serialise in its L2
+// slice.  Before round 1 a degree histogram picks a power-of-two degree
+// threshold that marks at most `update_hubs` vertices (gc_options) as hubs;
+// their bit sits beside the liveness bit (one 8-byte gather per edge gives
+// both), and UPDATE counts decrements aimed at hubs first per warp step
+// (__match_any_sync), then per block in a shared-memory hash table, and adds
+// each hub's count to D once per block at the end.  The decrements are the
+// same, only merged: D, the cut and every result are unchanged.
+//
 // UPDATE tests "w still in U" on a bitmap (n bits) rather than on batch[]
 // (n ints): the test is a random gather per edge, and a 2 MB bitmap for 2^24
 // vertices stays in L2 next to the decremented D words, where a 64 MB array
@@ -43,6 +53,7 @@ namespace gc {
 namespace {
 
 constexpr int kAdgThreads = 256;
+constexpr int kMaxHubs = 4096;  // gc_options.update_hubs at most
 
 __device__ __forceinline__ int adg_threshold(unsigned long long sigma, int size_u, unsigned p,
                                              unsigned q) {
@@ -64,19 +75,48 @@ __global__ void adg_init_kernel(AdgCtl* ctl, long long n, long long nnz, unsigne
   c.q = q;
   c.mode = mode;
   c.pull_percent = pull_percent;
+  c.hub_min_degree = INT_MAX;
   c.T = adg_threshold(c.sigma, c.size_U, p, q);
   *ctl = c;
+}
+
+// Hub threshold: counts of vertices by floor(log2 degree), then the smallest
+// power of two 2^k >= 256 with at most max_hubs vertices of degree >= 2^k.
+__global__ void adg_hub_hist_kernel(const long long* __restrict__ row_ptr, long long n,
+                                    unsigned long long* __restrict__ hist) {
+  __shared__ unsigned s_h[64];
+  if (threadIdx.x < 64) s_h[threadIdx.x] = 0u;
+  __syncthreads();
+  for (long long v = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; v < n;
+       v += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const unsigned long long d = static_cast<unsigned long long>(row_ptr[v + 1] - row_ptr[v]);
+    if (d >= 256) atomicAdd(&s_h[63 - __clzll(d)], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x < 64 && s_h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], s_h[threadIdx.x]);
+}
+
+__global__ void adg_hub_pick_kernel(const unsigned long long* __restrict__ hist, int max_hubs, AdgCtl* ctl) {
+  unsigned long long above = 0;
+  int k = 64;
+  while (k > 8 && above + hist[k - 1] <= static_cast<unsigned long long>(max_hubs)) {
+    above += hist[k - 1];
+    --k;
+  }
+  // vertices of degree >= 2^k number `above` <= max_hubs
+  ctl->hub_min_degree = (k >= 31 || above == 0) ? INT_MAX : (1 << k);
 }
 
 __global__ void __launch_bounds__(kAdgThreads)
 adg_partition_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row_ptr,
                      int* __restrict__ D, int* __restrict__ batch, const int* __restrict__ u_in,
                      int* __restrict__ u_out, long long* __restrict__ task_start,
-                     int* __restrict__ task_len, unsigned* __restrict__ live, int first_round_n,
+                     int* __restrict__ task_len, uint2* __restrict__ live, int first_round_n,
                      const unsigned long long* __restrict__ mkeys = nullptr,
                      const unsigned long long* __restrict__ kstar = nullptr) {
   const int round = ctl->round;
   const int T = ctl->T;
+  const int hub_min = ctl->hub_min_degree;
   const bool first = first_round_n > 0;
   const long long size_u = first ? first_round_n : ctl->size_U;
   const int lane = threadIdx.x & 31;
@@ -110,12 +150,14 @@ adg_partition_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row
     if (lane == 0 && km) kbase = atomicAdd(&ctl->size_Unext, __popc(km));
     kbase = __shfl_sync(kFull, kbase, 0);
     if (keep) u_out[kbase + __popc(km & lt)] = u;
-    // liveness bitmap: round 1 writes the warp's word (vertices i = 32 j ..
-    // 32 j + 31, since blocks start at multiples of 32); later rounds clear
+    // liveness bitmap: round 1 writes the warp's word pair (vertices
+    // i = 32 j .. 32 j + 31, since blocks start at multiples of 32: live bits,
+    // hub bits); later rounds clear live bits
     if (first) {
-      if (lane == 0 && active) live[i >> 5] = km;
+      const unsigned hm = __ballot_sync(kFull, active && d >= hub_min);
+      if (lane == 0 && active) live[i >> 5] = make_uint2(km, hm);
     } else if (in_r) {
-      atomicAnd(&live[u >> 5], ~(1u << (u & 31)));
+      atomicAnd(&live[u >> 5].x, ~(1u << (u & 31)));
     }
     // D[u] is written for every vertex in round 1; for a removed vertex it then
     // keeps its degree at removal, |{w in N(u) : batch(w) >= batch(u)}|, which
@@ -172,16 +214,44 @@ adg_partition_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row
 // Round 1 (vertex_tiles != 0): lane l of a warp owns vertex 32*tile + l and
 // sweeps its row if it was removed in round 1 (degree <= T_1, no chunking
 // needed since T_1 is the average degree bound).  Later rounds sweep the task
-// list written by the partition.
+// list written by the partition.  With hub_slots > 0 (a power of two, twice
+// the hub count at least) decrements aimed at hubs go through the block's
+// shared hash table (hub_slots keys, then hub_slots counts).
+__device__ __forceinline__ void hub_add(int* tkey, int* tcnt, int slots, int w, int c, int* D) {
+  unsigned slot = (static_cast<unsigned>(w) * 2654435761u) & static_cast<unsigned>(slots - 1);
+  volatile int* vkey = tkey;
+  for (int probe = 0; probe < slots; ++probe) {
+    int k = vkey[slot];
+    if (k == -1) {
+      k = atomicCAS(&tkey[slot], -1, w);
+      if (k == -1) k = w;
+    }
+    if (k == w) {
+      atomicAdd(&tcnt[slot], c);
+      return;
+    }
+    slot = (slot + 1) & static_cast<unsigned>(slots - 1);
+  }
+  atomicSub(&D[w], c);  // table full (cannot happen with <= slots/2 hubs)
+}
+
 __global__ void __launch_bounds__(kAdgThreads)
 adg_update_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row_ptr,
                   const int* __restrict__ col, int* __restrict__ D, const int* __restrict__ batch,
-                  const unsigned* __restrict__ live, const long long* __restrict__ task_start,
-                  const int* __restrict__ task_len, long long vertex_tiles_n) {
+                  const uint2* __restrict__ live, const long long* __restrict__ task_start,
+                  const int* __restrict__ task_len, long long vertex_tiles_n, int hub_slots) {
+  extern __shared__ int s_hub[];
   // The last round leaves U empty: no neighbour can still be in U, so there
   // is nothing to decrement (and the cut is not needed any more).  A pull
   // round recounts instead (adg_pull_*).
   if (ctl->size_Unext == 0 || adg_pulls(*ctl)) return;
+  int* tkey = s_hub;
+  int* tcnt = s_hub + hub_slots;
+  for (int i = threadIdx.x; i < hub_slots; i += blockDim.x) {
+    tkey[i] = -1;
+    tcnt[i] = 0;
+  }
+  __syncthreads();
   const int round = ctl->round;
   const unsigned long long ntasks =
       vertex_tiles_n > 0 ? static_cast<unsigned long long>(vertex_tiles_n) : ctl->ntasks;
@@ -205,16 +275,30 @@ adg_update_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row_pt
       }
     }
     sweep_tile(
-        st, len, 0, col, [&](int w, int) { return (__ldg(live + (w >> 5)) >> (w & 31)) & 1u; },
-        [&](int w, int, unsigned lv) {
-          if (lv) {  // w is still in U
-            ++cut;
+        st, len, 0, col,
+        [&](int w, int) {
+          const uint2 lw = __ldg(live + (w >> 5));
+          return ((lw.x >> (w & 31)) & 1u) | (((lw.y >> (w & 31)) & 1u) << 1);
+        },
+        [&](int w, int, unsigned g) {
+          if (!(g & 1u)) return;  // w is no longer in U
+          ++cut;
+          if (hub_slots > 0 && (g & 2u)) {
+            // lanes of this step aiming at the same hub add once
+            const unsigned grp = __match_any_sync(__activemask(), w);
+            if ((grp & lanemask_lt()) == 0) hub_add(tkey, tcnt, hub_slots, w, __popc(grp), D);
+          } else {
             atomicSub(&D[w], 1);
           }
         });
   }
   cut = warp_sum(cut);
   if (lane == 0 && cut) atomicAdd(&ctl->cut, cut);
+  if (hub_slots > 0) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < hub_slots; i += blockDim.x)
+      if (tkey[i] >= 0 && tcnt[i] > 0) atomicSub(&D[tkey[i]], tcnt[i]);
+  }
 }
 
 // Pull round, step 1: every survivor v of U' (the list the partition wrote)
@@ -272,7 +356,7 @@ adg_pull_tasks_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ ro
 // The sum of all counts is Sigma' = sum of D over U'.
 __global__ void __launch_bounds__(kAdgThreads)
 adg_pull_count_kernel(AdgCtl* __restrict__ ctl, const int* __restrict__ col, int* __restrict__ D,
-                      const unsigned* __restrict__ live, const long long* __restrict__ task_start,
+                      const uint2* __restrict__ live, const long long* __restrict__ task_start,
                       const int* __restrict__ task_len, const int* __restrict__ task_v) {
   __shared__ int s_cnt[kAdgThreads / 32][32];
   if (!adg_pulls(*ctl)) return;
@@ -293,7 +377,7 @@ adg_pull_count_kernel(AdgCtl* __restrict__ ctl, const int* __restrict__ col, int
     cnt[lane] = 0;
     __syncwarp();
     sweep_tile(
-        st, len, lane, col, [&](int w, int) { return (__ldg(live + (w >> 5)) >> (w & 31)) & 1u; },
+        st, len, lane, col, [&](int w, int) { return (__ldg(live + (w >> 5)).x >> (w & 31)) & 1u; },
         [&](int, int j, unsigned lv) {
           // lanes of this step holding edges of the same task add once
           const unsigned act = __activemask();
@@ -345,7 +429,7 @@ __global__ void adg_finalize_kernel(AdgCtl* ctl) {
 size_t adg_scratch_bytes(long long n, long long nnz) {
   const long long ntask = n + nnz / kChunk + 1;
   return 2 * (static_cast<size_t>(n) * 4 + 256) + static_cast<size_t>(ntask) * 16 + 3 * 256 +
-         static_cast<size_t>((n + 31) / 32) * 4 + 256 + 2048;
+         static_cast<size_t>((n + 31) / 32) * 8 + 256 + 64 * 8 + 256 + 2048;
 }
 
 gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigned q, int* batch,
@@ -361,17 +445,42 @@ gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigne
   long long* task_start = a.take<long long>(ntask);
   int* task_len = a.take<int>(ntask);
   int* task_v = a.take<int>(ntask);
-  unsigned* live = a.take<unsigned>((n + 31) / 32);
-  if (!ctl || !D || !ubuf[0] || !ubuf[1] || !task_start || !task_len || !task_v || !live) return GC_ERR_OOM;
+  uint2* live = a.take<uint2>((n + 31) / 32);
+  unsigned long long* hub_hist = a.take<unsigned long long>(64);
+  if (!ctl || !D || !ubuf[0] || !ubuf[1] || !task_start || !task_len || !task_v || !live || !hub_hist)
+    return GC_ERR_OOM;
 
   const int mode = ctx->opt.update_mode;
   GC_TRY_CUDA(cudaMemsetAsync(batch, 0, sizeof(int) * n, s));  // batch 0 = still in U
   adg_init_kernel<<<1, 1, 0, s>>>(ctl, n, nnz, p, q, mode, ctx->opt.pull_percent);
   ++g_launches;
   GC_TRY_CUDA(cudaGetLastError());
+  // hubs: at most update_hubs vertices, merged in a table of twice as many slots
+  int hub_slots = 0;
+  if (ctx->opt.update_hubs > 0 && nnz > 0) {
+    hub_slots = 1;
+    while (hub_slots < 2 * ctx->opt.update_hubs) hub_slots <<= 1;
+    GC_TRY_CUDA(cudaMemsetAsync(hub_hist, 0, 64 * sizeof(unsigned long long), s));
+    adg_hub_hist_kernel<<<ctx->num_sms * 4, 256, 0, s>>>(row_ptr_of(g), n, hub_hist);
+    adg_hub_pick_kernel<<<1, 1, 0, s>>>(hub_hist, ctx->opt.update_hubs, ctl);
+    g_launches += 2;
+    GC_TRY_CUDA(cudaGetLastError());
+  }
+  const size_t hub_smem = static_cast<size_t>(hub_slots) * 2 * sizeof(int);
+  // the largest table any context may ask for (the attribute is the
+  // kernel's, shared by every context of the process)
+  GC_TRY_CUDA(cudaFuncSetAttribute(adg_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   static_cast<int>(2 * kMaxHubs * 2 * sizeof(int))));
 
   const int max_blocks = ctx->num_sms * 8;
-  const int upd_blocks = resident_grid(adg_update_kernel, kAdgThreads, ctx->num_sms);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adg_update_kernel, kAdgThreads, hub_smem) !=
+          cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  const int upd_blocks = ctx->num_sms * per_sm;
   const int pull_blocks = resident_grid(adg_pull_count_kernel, kAdgThreads, ctx->num_sms);
   long long size_u = n;
   int cur = 0;
@@ -388,8 +497,8 @@ gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigne
     GC_TRY_CUDA(cudaGetLastError());
     ctx->timer_begin(gc_context::kTUpdate, s);
     if (mode != GC_UPDATE_PULL) {  // each direction's kernels return at once if not chosen
-      adg_update_kernel<<<upd_blocks, kAdgThreads, 0, s>>>(ctl, row_ptr_of(g), g->col_idx, D, batch, live,
-                                                            task_start, task_len, round == 1 ? n : 0);
+      adg_update_kernel<<<upd_blocks, kAdgThreads, hub_smem, s>>>(
+          ctl, row_ptr_of(g), g->col_idx, D, batch, live, task_start, task_len, round == 1 ? n : 0, hub_slots);
       ++g_launches;
     }
     if (mode != GC_UPDATE_PUSH) {
@@ -447,7 +556,7 @@ struct SelState {
 };
 
 __global__ void adg_m_init_kernel(const long long* __restrict__ row_ptr, long long n, int* __restrict__ D,
-                                  int* __restrict__ U, unsigned* __restrict__ live) {
+                                  int* __restrict__ U, uint2* __restrict__ live) {
   const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
   const long long t0 = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   for (long long v = t0; v < n; v += stride) {
@@ -456,7 +565,7 @@ __global__ void adg_m_init_kernel(const long long* __restrict__ row_ptr, long lo
   }
   for (long long w = t0; w < (n + 31) / 32; w += stride) {
     const long long left = n - 32 * w;
-    live[w] = left >= 32 ? ~0u : ((1u << left) - 1u);
+    live[w] = make_uint2(left >= 32 ? ~0u : ((1u << left) - 1u), 0u);  // no hubs in ADG-M
   }
 }
 
@@ -533,7 +642,9 @@ gc_status adg_m_run(gc_context* ctx, Arena a, const gc_csr* g, int* batch, int* 
   const long long ntask = n + nnz / kChunk + 1;
   long long* task_start = a.take<long long>(ntask);
   int* task_len = a.take<int>(ntask);
-  unsigned* live = a.take<unsigned>((n + 31) / 32);
+  a.take<int>(ntask);  // (ADG's pull task list; ADG-M only pushes)
+  uint2* live = a.take<uint2>((n + 31) / 32);
+  a.take<unsigned long long>(64);
   unsigned long long* keys = a.take<unsigned long long>(n);
   SelState* st = a.take<SelState>(1);
   unsigned* hist = a.take<unsigned>(256);
@@ -578,7 +689,7 @@ gc_status adg_m_run(gc_context* ctx, Arena a, const gc_csr* g, int* batch, int* 
     GC_TRY_CUDA(cudaGetLastError());
     ctx->timer_begin(gc_context::kTUpdate, s);
     adg_update_kernel<<<upd_blocks, kAdgThreads, 0, s>>>(ctl, rp, g->col_idx, D, batch, live, task_start,
-                                                          task_len, 0);
+                                                          task_len, 0, 0);
     ++g_launches;
     ctx->timer_end(s);
     GC_TRY_CUDA(cudaGetLastError());
@@ -627,7 +738,7 @@ constexpr size_t kNaOffU1 = kNaOffU0 + align256(kNoAllocMaxN * sizeof(int));
 constexpr size_t kNaOffTs = kNaOffU1 + align256(kNoAllocMaxN * sizeof(int));
 constexpr size_t kNaOffTl = kNaOffTs + align256(kNoAllocTasks * sizeof(long long));
 constexpr size_t kNaOffLive = kNaOffTl + align256(kNoAllocTasks * sizeof(int));
-constexpr size_t kNoAllocBytes = kNaOffLive + align256(kNoAllocMaxN / 32 * sizeof(unsigned));  // about 6.5 MB
+constexpr size_t kNoAllocBytes = kNaOffLive + align256(kNoAllocMaxN / 32 * sizeof(uint2));  // about 6.5 MB
 
 constexpr int kNoAllocDevices = 64;
 std::mutex g_noalloc_mu;
@@ -679,7 +790,7 @@ extern "C" gc_status gc_adg_partition_noalloc(const gc_csr* g, uint32_t eps_p, u
   int* ubuf[2] = {reinterpret_cast<int*>(base + kNaOffU0), reinterpret_cast<int*>(base + kNaOffU1)};
   long long* task_start = reinterpret_cast<long long*>(base + kNaOffTs);
   int* task_len = reinterpret_cast<int*>(base + kNaOffTl);
-  unsigned* live = reinterpret_cast<unsigned*>(base + kNaOffLive);
+  uint2* live = reinterpret_cast<uint2*>(base + kNaOffLive);
 
   // Every buffer above is written before it is read within a call; the
   // control block, the only state carried between kernels, is reset here.
@@ -701,7 +812,7 @@ extern "C" gc_status gc_adg_partition_noalloc(const gc_csr* g, uint32_t eps_p, u
                                                         round == 1 ? static_cast<int>(n) : 0);
     GC_TRY_CUDA(cudaGetLastError());
     adg_update_kernel<<<upd_blocks, kAdgThreads, 0, s>>>(ctl, rp, g->col_idx, D, batch_out, live,
-                                                          task_start, task_len, round == 1 ? n : 0);
+                                                          task_start, task_len, round == 1 ? n : 0, 0);
     GC_TRY_CUDA(cudaGetLastError());
     adg_finalize_kernel<<<1, 1, 0, s>>>(ctl);
     GC_TRY_CUDA(cudaGetLastError());

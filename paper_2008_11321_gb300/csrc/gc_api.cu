@@ -230,6 +230,7 @@ gc_status gc_options_init(gc_options* opt) {
   o.wait_limit_ms = static_cast<uint32_t>(gc::kWaitLimitNs / 1000000ull);
   o.jp_state16 = 0;
   o.batch_mode = GC_BATCH_AUTO;
+  o.update_hubs = 1024;
   *opt = o;
   return GC_OK;
 }
@@ -253,7 +254,7 @@ gc_status read_options(const gc_options* opt, gc_options* out) {
       o.update_mode < GC_UPDATE_AUTO || o.update_mode > GC_UPDATE_PULL || o.pull_percent < 0 ||
       o.pull_percent > 100000 || o.bulk_blocks_per_sm < 0 || o.bulk_blocks_per_sm > 32 || o.wait_limit_ms < 1 ||
       o.wait_limit_ms > 600000 || (o.jp_state16 != 0 && o.jp_state16 != 1) || o.batch_mode < GC_BATCH_AUTO ||
-      o.batch_mode > GC_BATCH_PERSISTENT)
+      o.batch_mode > GC_BATCH_PERSISTENT || o.update_hubs < 0 || o.update_hubs > 4096)
     return GC_ERR_INVALID_ARG;
   *out = o;
   return GC_OK;

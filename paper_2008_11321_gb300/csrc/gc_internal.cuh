@@ -57,6 +57,8 @@ struct AdgCtl {
   int max_removal_degree;        // largest D at removal so far: every colour of
                                  // JP-ADG is at most this + 1 (a vertex's
                                  // predecessors are among the neighbours D counts)
+  int hub_min_degree;            // UPDATE merges decrements aimed at vertices of at
+                                 // least this degree (INT_MAX: none)
 };
 
 static_assert(sizeof(AdgCtl) <= 256, "AdgCtl must fit the pinned read-back buffer");

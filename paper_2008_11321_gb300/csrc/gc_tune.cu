@@ -6,8 +6,9 @@
 // Search: coordinate descent.  Starting from the context's options, each
 // dimension in turn (ADG's UPDATE direction and pull threshold -- the switch
 // between the frontier-sparse push sweep and the dense pull sweep --, the
-// JP state word, the JP core's size, warps and cluster, the bulk kernel's
-// blocks per SM, and for batches the persistent or segmented path) is set to
+// number of hubs whose decrements UPDATE merges, the JP state word, the JP
+// core's size, warps and cluster, the bulk kernel's blocks per SM, and for
+// batches the persistent or segmented path) is set to
 // each of its candidate values; a value is kept when its median time over
 // `reps` runs (after one warm-up run) beats the best so far by more than 1%.
 // The time of a run is taken with CUDA events on the caller's stream.
@@ -47,6 +48,7 @@ std::vector<Dim> dims_single(long long n) {
                  }
                },
                {-1, 25, 50, 100, 200}});
+  d.push_back({[](gc_options& o, int v) { o.update_hubs = v; }, {0, 512, 1024, 2048}});
   d.push_back({[](gc_options& o, int v) { o.jp_state16 = v; }, {0, 1}});
   std::vector<int> cores = {0, 4096, 8192, 16384, 24576, 32768};
   cores.erase(std::remove_if(cores.begin(), cores.end(), [n](int c) { return c > 0 && c / 2 >= n; }), cores.end());

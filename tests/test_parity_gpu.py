@@ -445,3 +445,22 @@ def test_jp_sl_small_graphs_and_limit(ctx):
     with pytest.raises(gcp.GcError) as err:
         ctx.gc_make_priority_kind(big, gcp.GC_PRIO_SL, 0, torch.empty(1, dtype=torch.int64, device="cuda:0"))
     assert err.value.status == gcp.GC_ERR_OVERFLOW
+
+
+# ---------------------------------------------------------------- UPDATE hub merging
+
+@pytest.mark.parametrize("hubs", [0, 1024, 4096])
+@pytest.mark.parametrize("g", [gg.rmat(16, 16, seed=12), gg.barabasi_albert(40000, 8, 3), star(5000), complete(300),
+                               gg.grid(90, 90), gg.erdos_renyi(20000, 100000, 6)], ids=lambda g: g.name)
+def test_hub_merging_identical(g, hubs):
+    # decrements aimed at hubs are merged in shared memory before they reach
+    # the degree words: batches, colours and ADG's statistics are unchanged
+    # (K_300: every vertex is a hub; star: the centre; grid: none)
+    with gcp.Context(0, {"update_hubs": hubs, "update_mode": gcp.GC_UPDATE_PUSH}) as c:
+        for p, q in ((1, 100), (1, 2)):
+            b, col, nr, nc = color_graph(c, g, p, q, 42)
+            ob, oc, onr, onc = oracle.jp_adg(g, p, q, 42)
+            assert nr == onr and np.array_equal(b, ob)
+            assert nc == onc and np.array_equal(col, oc)
+            src = np.repeat(np.arange(g.n), g.degrees())
+            assert c.gc_get_stats().sum_decrements == int(np.sum(ob[g.col_idx] > ob[src]))

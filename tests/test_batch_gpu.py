@@ -101,9 +101,9 @@ def test_batch_hard_cases(ctx):
     # window of the warp path (K_1100), hubs (stars, a BA graph), isolated
     # vertices and empty graphs, all in one batch
     graphs = [path(60), path(99), complete(1100), star(3000), empty(1), empty(0), gg.barabasi_albert(5000, 7, 4),
-              gg.grid(40, 50, perm_seed=9), complete(33), gg.erdos_renyi(3000, 200, 2)]
+              gg.grid(40, 50, perm_seed=9), complete(33), gg.erdos_renyi(3000, 200, 2), path(600)]
     jobs = [(0, 1, 5), (1, 100, 6), (1, 100, 7), (1, 2, 8), (1, 100, 9), (1, 100, 10), (3, 1, 11), (1, 100, 12),
-            (1, 100, 13), (1, 10, 14)]
+            (1, 100, 13), (1, 10, 14), (1, 1 << 20, 15)]  # the last: 300 rounds, beyond an 8-bit batch
     color, batch, ncol, nrnd, voff = _run(ctx, graphs, jobs)
     for i, g in enumerate(graphs):
         p, q, sd = jobs[i]

@@ -240,7 +240,7 @@ def test_adg_m_zero_vertices(ctx):
 def test_jp_variant_kind_rejected(ctx):
     dg = dev(path(5))
     key = torch.zeros(5, dtype=torch.int64, device="cuda:0")
-    for bad in (-1, 4):
+    for bad in (-1, 5):
         with pytest.raises(gcp.GcError) as e:
             ctx.gc_make_priority_kind(dg, bad, 1, key)
         assert e.value.status == gcp.GC_ERR_INVALID_ARG

@@ -165,6 +165,10 @@ typedef struct {
                               before they reach their degree words, 0..4096
                               (default 1024; 0: every decrement is an atomic
                               on its word)                                   */
+  int32_t host_upload;     /* gc_color_graph_host: 0 (default) copies the
+                              graph with the copy engine; 1 has the SMs read
+                              page-locked, mapped host buffers directly
+                              (16-byte aligned; others use the copy engine)  */
 } gc_options;
 
 /* How gc_color_batch runs (gc_options.batch_mode, gc_stats.batch_path):

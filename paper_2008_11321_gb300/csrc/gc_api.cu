@@ -1,6 +1,7 @@
 // C ABI entry points (gcolor.h): context management, argument checks, CSR
 // validation, and the orchestration of the ADG and JP kernels.
 #include <climits>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -141,6 +142,50 @@ float timing_ms(gc_context* ctx, int a, int b) {
   return ms;
 }
 
+// Upload by the SMs: 16-byte loads of mapped page-locked host memory (over
+// the CPU-GPU link), four in flight per thread, stored to device memory.
+__global__ void __launch_bounds__(256) host_copy_kernel(const uint4* __restrict__ src, uint4* __restrict__ dst,
+                                                        long long n16) {
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n16; i += 4 * stride) {
+    const uint4 a = src[i], b = src[i + stride], c = src[i + 2 * stride], d = src[i + 3 * stride];
+    dst[i] = a;
+    dst[i + stride] = b;
+    dst[i + 2 * stride] = c;
+    dst[i + 3 * stride] = d;
+  }
+  for (; i < n16; i += stride) dst[i] = src[i];
+}
+
+// Host -> device copy of `bytes`: by host_copy_kernel when asked for and the
+// host buffer is page-locked and mapped with 16-byte alignment, else by the
+// copy engine (cudaMemcpyAsync).
+gc_status upload(gc_context* ctx, void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return GC_OK;
+  if (ctx->opt.host_upload == 1) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, src) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer &&
+        (reinterpret_cast<uintptr_t>(at.devicePointer) & 15) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+      const long long n16 = static_cast<long long>(bytes / 16);
+      if (n16 > 0) {
+        host_copy_kernel<<<ctx->num_sms * 8, 256, 0, s>>>(static_cast<const uint4*>(at.devicePointer),
+                                                          static_cast<uint4*>(dst), n16);
+        ++gc::g_launches;
+        GC_TRY_CUDA(cudaGetLastError());
+      }
+      const size_t done = static_cast<size_t>(n16) * 16;
+      if (bytes > done)
+        GC_TRY_CUDA(cudaMemcpyAsync(static_cast<char*>(dst) + done, static_cast<const char*>(src) + done,
+                                    bytes - done, cudaMemcpyHostToDevice, s));
+      return GC_OK;
+    }
+    cudaGetLastError();  // (an unregistered pointer is not an error to keep)
+  }
+  GC_TRY_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
+  return GC_OK;
+}
+
 // Shared body of gc_color_graph and gc_color_graph_host.
 // JP-ADG (median = false) or JP-ADG-M (median = true, p and q unused).
 gc_status color_graph_device(gc_context* ctx, const gc_csr* g, uint32_t p, uint32_t q, uint64_t seed,
@@ -231,6 +276,7 @@ gc_status gc_options_init(gc_options* opt) {
   o.jp_state16 = 0;
   o.batch_mode = GC_BATCH_AUTO;
   o.update_hubs = 1024;
+  o.host_upload = 0;
   *opt = o;
   return GC_OK;
 }
@@ -254,7 +300,8 @@ gc_status read_options(const gc_options* opt, gc_options* out) {
       o.update_mode < GC_UPDATE_AUTO || o.update_mode > GC_UPDATE_PULL || o.pull_percent < 0 ||
       o.pull_percent > 100000 || o.bulk_blocks_per_sm < 0 || o.bulk_blocks_per_sm > 32 || o.wait_limit_ms < 1 ||
       o.wait_limit_ms > 600000 || (o.jp_state16 != 0 && o.jp_state16 != 1) || o.batch_mode < GC_BATCH_AUTO ||
-      o.batch_mode > GC_BATCH_PERSISTENT || o.update_hubs < 0 || o.update_hubs > 4096)
+      o.batch_mode > GC_BATCH_PERSISTENT || o.update_hubs < 0 || o.update_hubs > 4096 ||
+      (o.host_upload != 0 && o.host_upload != 1))
     return GC_ERR_INVALID_ARG;
   *out = o;
   return GC_OK;
@@ -711,11 +758,8 @@ gc_status gc_color_graph_host(gc_context* ctx, int64_t n, int64_t nnz, const int
   g.col_idx = reinterpret_cast<const int32_t*>(base + b_rp);
   int32_t* d_color = reinterpret_cast<int32_t*>(base + b_rp + b_ci);
   int32_t* d_batch = reinterpret_cast<int32_t*>(base + b_rp + b_ci + b_v);
-  GC_TRY_CUDA(cudaMemcpyAsync(const_cast<int64_t*>(g.row_ptr), row_ptr, static_cast<size_t>(n + 1) * 8,
-                              cudaMemcpyHostToDevice, s));
-  if (nnz > 0)
-    GC_TRY_CUDA(cudaMemcpyAsync(const_cast<int32_t*>(g.col_idx), col_idx, static_cast<size_t>(nnz) * 4,
-                                cudaMemcpyHostToDevice, s));
+  GC_TRY(upload(ctx, const_cast<int64_t*>(g.row_ptr), row_ptr, static_cast<size_t>(n + 1) * 8, s));
+  if (nnz > 0) GC_TRY(upload(ctx, const_cast<int32_t*>(g.col_idx), col_idx, static_cast<size_t>(nnz) * 4, s));
   GC_TRY(color_graph_device(ctx, &g, eps_p, eps_q, seed, d_color, d_batch, num_colors_out,
                             num_rounds_out, s));
   if (n > 0) {

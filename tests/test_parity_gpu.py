@@ -464,3 +464,19 @@ def test_hub_merging_identical(g, hubs):
             assert nc == onc and np.array_equal(col, oc)
             src = np.repeat(np.arange(g.n), g.degrees())
             assert c.gc_get_stats().sum_decrements == int(np.sum(ob[g.col_idx] > ob[src]))
+
+
+@pytest.mark.parametrize("misalign", [0, 1])
+def test_host_entry_point_kernel_upload(misalign):
+    # host_upload = 1: the SMs read the page-locked host CSR directly; a
+    # buffer that is not 16-byte aligned falls back to the copy engine
+    g = gg.rmat(18, 16, seed=6)
+    rp = torch.empty(g.n + 1 + 2 * misalign, dtype=torch.int64, pin_memory=True).numpy()[misalign:misalign + g.n + 1]
+    ci = torch.empty(g.nnz + 4 * misalign, dtype=torch.int32, pin_memory=True).numpy()[misalign:misalign + g.nnz]
+    rp[:] = g.row_ptr
+    ci[:] = g.col_idx
+    color = np.zeros(g.n, dtype=np.int32)
+    with gcp.Context(0, {"host_upload": 1}) as c:
+        nc, nr = c.gc_color_graph_host(rp, ci, 1, 100, 42, color)
+    ob, oc, onr, onc = oracle.jp_adg(g, 1, 100, 42)
+    assert (nc, nr) == (onc, onr) and np.array_equal(color, oc)

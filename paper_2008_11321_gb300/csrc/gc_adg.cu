@@ -218,7 +218,10 @@ adg_partition_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row
 // the hub count at least) decrements aimed at hubs go through the block's
 // shared hash table (hub_slots keys, then hub_slots counts).
 __device__ __forceinline__ void hub_add(int* tkey, int* tcnt, int slots, int w, int c, int* D) {
-  unsigned slot = (static_cast<unsigned>(w) * 2654435761u) & static_cast<unsigned>(slots - 1);
+  // Fibonacci hashing: the TOP bits of w times 2^32/phi (the low bits of the
+  // product depend only on w's low bits, and hub ids of a power-law graph
+  // share them)
+  unsigned slot = (static_cast<unsigned>(w) * 2654435769u) >> (__clz(slots) + 1);
   volatile int* vkey = tkey;
   for (int probe = 0; probe < slots; ++probe) {
     int k = vkey[slot];
@@ -235,6 +238,7 @@ __device__ __forceinline__ void hub_add(int* tkey, int* tcnt, int slots, int w, 
   atomicSub(&D[w], c);  // table full (cannot happen with <= slots/2 hubs)
 }
 
+template <bool kHubs>
 __global__ void __launch_bounds__(kAdgThreads)
 adg_update_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row_ptr,
                   const int* __restrict__ col, int* __restrict__ D, const int* __restrict__ batch,
@@ -247,11 +251,13 @@ adg_update_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row_pt
   if (ctl->size_Unext == 0 || adg_pulls(*ctl)) return;
   int* tkey = s_hub;
   int* tcnt = s_hub + hub_slots;
-  for (int i = threadIdx.x; i < hub_slots; i += blockDim.x) {
-    tkey[i] = -1;
-    tcnt[i] = 0;
+  if (kHubs) {
+    for (int i = threadIdx.x; i < hub_slots; i += blockDim.x) {
+      tkey[i] = -1;
+      tcnt[i] = 0;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   const int round = ctl->round;
   const unsigned long long ntasks =
       vertex_tiles_n > 0 ? static_cast<unsigned long long>(vertex_tiles_n) : ctl->ntasks;
@@ -283,7 +289,7 @@ adg_update_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row_pt
         [&](int w, int, unsigned g) {
           if (!(g & 1u)) return;  // w is no longer in U
           ++cut;
-          if (hub_slots > 0 && (g & 2u)) {
+          if (kHubs && (g & 2u)) {
             // lanes of this step aiming at the same hub add once
             const unsigned grp = __match_any_sync(__activemask(), w);
             if ((grp & lanemask_lt()) == 0) hub_add(tkey, tcnt, hub_slots, w, __popc(grp), D);
@@ -294,7 +300,7 @@ adg_update_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row_pt
   }
   cut = warp_sum(cut);
   if (lane == 0 && cut) atomicAdd(&ctl->cut, cut);
-  if (hub_slots > 0) {
+  if (kHubs) {
     __syncthreads();
     for (int i = threadIdx.x; i < hub_slots; i += blockDim.x)
       if (tkey[i] >= 0 && tcnt[i] > 0) atomicSub(&D[tkey[i]], tcnt[i]);
@@ -469,14 +475,16 @@ gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigne
   const size_t hub_smem = static_cast<size_t>(hub_slots) * 2 * sizeof(int);
   // the largest table any context may ask for (the attribute is the
   // kernel's, shared by every context of the process)
-  GC_TRY_CUDA(cudaFuncSetAttribute(adg_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  GC_TRY_CUDA(cudaFuncSetAttribute(adg_update_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    static_cast<int>(2 * kMaxHubs * 2 * sizeof(int))));
 
   const int max_blocks = ctx->num_sms * 8;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adg_update_kernel, kAdgThreads, hub_smem) !=
-          cudaSuccess ||
-      per_sm < 1) {
+  const cudaError_t oe =
+      hub_slots > 0
+          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adg_update_kernel<true>, kAdgThreads, hub_smem)
+          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adg_update_kernel<false>, kAdgThreads, 0);
+  if (oe != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
     per_sm = 1;
   }
@@ -497,8 +505,12 @@ gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigne
     GC_TRY_CUDA(cudaGetLastError());
     ctx->timer_begin(gc_context::kTUpdate, s);
     if (mode != GC_UPDATE_PULL) {  // each direction's kernels return at once if not chosen
-      adg_update_kernel<<<upd_blocks, kAdgThreads, hub_smem, s>>>(
-          ctl, row_ptr_of(g), g->col_idx, D, batch, live, task_start, task_len, round == 1 ? n : 0, hub_slots);
+      if (hub_slots > 0)
+        adg_update_kernel<true><<<upd_blocks, kAdgThreads, hub_smem, s>>>(
+            ctl, row_ptr_of(g), g->col_idx, D, batch, live, task_start, task_len, round == 1 ? n : 0, hub_slots);
+      else
+        adg_update_kernel<false><<<upd_blocks, kAdgThreads, 0, s>>>(
+            ctl, row_ptr_of(g), g->col_idx, D, batch, live, task_start, task_len, round == 1 ? n : 0, 0);
       ++g_launches;
     }
     if (mode != GC_UPDATE_PUSH) {
@@ -661,7 +673,7 @@ gc_status adg_m_run(gc_context* ctx, Arena a, const gc_csr* g, int* batch, int* 
 
   const long long* rp = row_ptr_of(g);
   const int max_blocks = ctx->num_sms * 8;
-  const int upd_blocks = resident_grid(adg_update_kernel, kAdgThreads, ctx->num_sms);
+  const int upd_blocks = resident_grid(adg_update_kernel<false>, kAdgThreads, ctx->num_sms);
   GC_TRY_CUDA(cudaMemsetAsync(batch, 0, sizeof(int) * n, s));
   adg_init_kernel<<<1, 1, 0, s>>>(ctl, n, nnz, 0, 1, GC_UPDATE_PUSH, 0);  // (its threshold is not used here)
   ++g_launches;
@@ -688,8 +700,8 @@ gc_status adg_m_run(gc_context* ctx, Arena a, const gc_csr* g, int* batch, int* 
     ++g_launches;
     GC_TRY_CUDA(cudaGetLastError());
     ctx->timer_begin(gc_context::kTUpdate, s);
-    adg_update_kernel<<<upd_blocks, kAdgThreads, 0, s>>>(ctl, rp, g->col_idx, D, batch, live, task_start,
-                                                          task_len, 0, 0);
+    adg_update_kernel<false><<<upd_blocks, kAdgThreads, 0, s>>>(ctl, rp, g->col_idx, D, batch, live, task_start,
+                                                                 task_len, 0, 0);
     ++g_launches;
     ctx->timer_end(s);
     GC_TRY_CUDA(cudaGetLastError());
@@ -798,7 +810,7 @@ extern "C" gc_status gc_adg_partition_noalloc(const gc_csr* g, uint32_t eps_p, u
   adg_init_kernel<<<1, 1, 0, s>>>(ctl, n, nnz, eps_p, eps_q, GC_UPDATE_PUSH, 0);
   GC_TRY_CUDA(cudaGetLastError());
   const int max_blocks = num_sms * 8;
-  const int upd_blocks = gc::resident_grid(gc::adg_update_kernel, gc::kAdgThreads, num_sms);
+  const int upd_blocks = gc::resident_grid(gc::adg_update_kernel<false>, gc::kAdgThreads, num_sms);
   const long long* rp = reinterpret_cast<const long long*>(g->row_ptr);
   long long size_u = n;
   int cur = 0, round = 0;
@@ -811,8 +823,8 @@ extern "C" gc_status gc_adg_partition_noalloc(const gc_csr* g, uint32_t eps_p, u
                                                         task_start, task_len, live,
                                                         round == 1 ? static_cast<int>(n) : 0);
     GC_TRY_CUDA(cudaGetLastError());
-    adg_update_kernel<<<upd_blocks, kAdgThreads, 0, s>>>(ctl, rp, g->col_idx, D, batch_out, live,
-                                                          task_start, task_len, round == 1 ? n : 0, 0);
+    adg_update_kernel<false><<<upd_blocks, kAdgThreads, 0, s>>>(ctl, rp, g->col_idx, D, batch_out, live,
+                                                                 task_start, task_len, round == 1 ? n : 0, 0);
     GC_TRY_CUDA(cudaGetLastError());
     adg_finalize_kernel<<<1, 1, 0, s>>>(ctl);
     GC_TRY_CUDA(cudaGetLastError());

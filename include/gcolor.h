@@ -159,12 +159,12 @@ typedef struct {
                               (default): always a 32-bit word                */
   int32_t batch_mode;      /* gc_color_batch: GC_BATCH_AUTO (default),
                               GC_BATCH_SEGMENTED or GC_BATCH_PERSISTENT      */
-  int32_t update_hubs;     /* ADG's push UPDATE merges the decrements aimed at
+  int32_t update_hubs;     /* ADG's push UPDATE counts the decrements aimed at
                               up to this many highest-degree vertices (degree
-                              >= a power of two >= 256) in shared memory
-                              before they reach their degree words, 0..4096
-                              (default 1024; 0: every decrement is an atomic
-                              on its word)                                   */
+                              >= a power of two >= 256) in a shared-memory
+                              array per thread block, added to their degree
+                              words once per block, 0..4096 (default 512; 0:
+                              every decrement is an atomic on its word)      */
   int32_t host_upload;     /* gc_color_graph_host: 0 (default) copies the
                               graph with the copy engine; 1 has the SMs read
                               page-locked, mapped host buffers directly

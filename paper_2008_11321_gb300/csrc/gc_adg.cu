@@ -105,6 +105,7 @@ __global__ void adg_hub_pick_kernel(const unsigned long long* __restrict__ hist,
   }
   // vertices of degree >= 2^k number `above` <= max_hubs
   ctl->hub_min_degree = (k >= 31 || above == 0) ? INT_MAX : (1 << k);
+  ctl->hub_cap = max_hubs;
 }
 
 __global__ void __launch_bounds__(kAdgThreads)
@@ -113,7 +114,8 @@ adg_partition_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row
                      int* __restrict__ u_out, long long* __restrict__ task_start,
                      int* __restrict__ task_len, uint2* __restrict__ live, int first_round_n,
                      const unsigned long long* __restrict__ mkeys = nullptr,
-                     const unsigned long long* __restrict__ kstar = nullptr) {
+                     const unsigned long long* __restrict__ kstar = nullptr, int* __restrict__ hub_base = nullptr,
+                     int* __restrict__ hub_vertex = nullptr) {
   const int round = ctl->round;
   const int T = ctl->T;
   const int hub_min = ctl->hub_min_degree;
@@ -156,6 +158,17 @@ adg_partition_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row
     if (first) {
       const unsigned hm = __ballot_sync(kFull, active && d >= hub_min);
       if (lane == 0 && active) live[i >> 5] = make_uint2(km, hm);
+      // hub ranks: the word's hubs take consecutive ranks from hub_base[word]
+      // on, in bit order (the hub of bit b has rank hub_base + popc(hm & (2^b - 1)))
+      if (hm && hub_base) {
+        int hb = 0;
+        if (lane == 0) {
+          hb = atomicAdd(&ctl->n_hubs, __popc(hm));
+          hub_base[i >> 5] = hb;
+        }
+        hb = __shfl_sync(kFull, hb, 0) + __popc(hm & lt);
+        if (((hm >> lane) & 1u) && hb < ctl->hub_cap) hub_vertex[hb] = u;
+      }
     } else if (in_r) {
       atomicAnd(&live[u >> 5].x, ~(1u << (u & 31)));
     }
@@ -214,48 +227,26 @@ adg_partition_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row
 // Round 1 (vertex_tiles != 0): lane l of a warp owns vertex 32*tile + l and
 // sweeps its row if it was removed in round 1 (degree <= T_1, no chunking
 // needed since T_1 is the average degree bound).  Later rounds sweep the task
-// list written by the partition.  With hub_slots > 0 (a power of two, twice
-// the hub count at least) decrements aimed at hubs go through the block's
-// shared hash table (hub_slots keys, then hub_slots counts).
-__device__ __forceinline__ void hub_add(int* tkey, int* tcnt, int slots, int w, int c, int* D) {
-  // Fibonacci hashing: the TOP bits of w times 2^32/phi (the low bits of the
-  // product depend only on w's low bits, and hub ids of a power-law graph
-  // share them)
-  unsigned slot = (static_cast<unsigned>(w) * 2654435769u) >> (__clz(slots) + 1);
-  volatile int* vkey = tkey;
-  for (int probe = 0; probe < slots; ++probe) {
-    int k = vkey[slot];
-    if (k == -1) {
-      k = atomicCAS(&tkey[slot], -1, w);
-      if (k == -1) k = w;
-    }
-    if (k == w) {
-      atomicAdd(&tcnt[slot], c);
-      return;
-    }
-    slot = (slot + 1) & static_cast<unsigned>(slots - 1);
-  }
-  atomicSub(&D[w], c);  // table full (cannot happen with <= slots/2 hubs)
-}
-
+// list written by the partition.  With kHubs, decrements aimed at hubs (the
+// second bit of the live word pair) are counted in the block's shared array
+// at the hub's rank (hub_base[w / 32] + the hubs below w in its word) and
+// reach D once per hub and block at the end.
 template <bool kHubs>
 __global__ void __launch_bounds__(kAdgThreads)
 adg_update_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row_ptr,
                   const int* __restrict__ col, int* __restrict__ D, const int* __restrict__ batch,
                   const uint2* __restrict__ live, const long long* __restrict__ task_start,
-                  const int* __restrict__ task_len, long long vertex_tiles_n, int hub_slots) {
+                  const int* __restrict__ task_len, long long vertex_tiles_n, const int* __restrict__ hub_base,
+                  const int* __restrict__ hub_vertex) {
   extern __shared__ int s_hub[];
   // The last round leaves U empty: no neighbour can still be in U, so there
   // is nothing to decrement (and the cut is not needed any more).  A pull
   // round recounts instead (adg_pull_*).
   if (ctl->size_Unext == 0 || adg_pulls(*ctl)) return;
-  int* tkey = s_hub;
-  int* tcnt = s_hub + hub_slots;
+  int nh = 0;
   if (kHubs) {
-    for (int i = threadIdx.x; i < hub_slots; i += blockDim.x) {
-      tkey[i] = -1;
-      tcnt[i] = 0;
-    }
+    nh = min(ctl->n_hubs, ctl->hub_cap);
+    for (int i = threadIdx.x; i < nh; i += blockDim.x) s_hub[i] = 0;
     __syncthreads();
   }
   const int round = ctl->round;
@@ -280,30 +271,38 @@ adg_update_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row_pt
         len = task_len[t];
       }
     }
+    // gathered per neighbour w: bit 0 live, bit 1 hub, bits 2.. the hubs
+    // below w in its word
     sweep_tile(
         st, len, 0, col,
         [&](int w, int) {
           const uint2 lw = __ldg(live + (w >> 5));
-          return ((lw.x >> (w & 31)) & 1u) | (((lw.y >> (w & 31)) & 1u) << 1);
+          const unsigned b = static_cast<unsigned>(w) & 31u;
+          unsigned r = (lw.x >> b) & 1u;
+          if (kHubs) r |= (((lw.y >> b) & 1u) << 1) | (static_cast<unsigned>(__popc(lw.y & ((1u << b) - 1u))) << 2);
+          return r;
         },
         [&](int w, int, unsigned g) {
           if (!(g & 1u)) return;  // w is no longer in U
           ++cut;
           if (kHubs && (g & 2u)) {
-            // lanes of this step aiming at the same hub add once
-            const unsigned grp = __match_any_sync(__activemask(), w);
-            if ((grp & lanemask_lt()) == 0) hub_add(tkey, tcnt, hub_slots, w, __popc(grp), D);
-          } else {
-            atomicSub(&D[w], 1);
+            const int h = __ldg(hub_base + (w >> 5)) + static_cast<int>(g >> 2);
+            if (h < nh) {
+              atomicAdd(&s_hub[h], 1);
+              return;
+            }
           }
+          atomicSub(&D[w], 1);
         });
   }
   cut = warp_sum(cut);
   if (lane == 0 && cut) atomicAdd(&ctl->cut, cut);
   if (kHubs) {
     __syncthreads();
-    for (int i = threadIdx.x; i < hub_slots; i += blockDim.x)
-      if (tkey[i] >= 0 && tcnt[i] > 0) atomicSub(&D[tkey[i]], tcnt[i]);
+    for (int i = threadIdx.x; i < nh; i += blockDim.x) {
+      const int c = s_hub[i];
+      if (c) atomicSub(&D[hub_vertex[i]], c);
+    }
   }
 }
 
@@ -435,7 +434,8 @@ __global__ void adg_finalize_kernel(AdgCtl* ctl) {
 size_t adg_scratch_bytes(long long n, long long nnz) {
   const long long ntask = n + nnz / kChunk + 1;
   return 2 * (static_cast<size_t>(n) * 4 + 256) + static_cast<size_t>(ntask) * 16 + 3 * 256 +
-         static_cast<size_t>((n + 31) / 32) * 8 + 256 + 64 * 8 + 256 + 2048;
+         static_cast<size_t>((n + 31) / 32) * 8 + 256 + 64 * 8 + 256 + static_cast<size_t>((n + 31) / 32) * 4 +
+         256 + kMaxHubs * 4 + 256 + 2048;
 }
 
 gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigned q, int* batch,
@@ -453,7 +453,10 @@ gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigne
   int* task_v = a.take<int>(ntask);
   uint2* live = a.take<uint2>((n + 31) / 32);
   unsigned long long* hub_hist = a.take<unsigned long long>(64);
-  if (!ctl || !D || !ubuf[0] || !ubuf[1] || !task_start || !task_len || !task_v || !live || !hub_hist)
+  int* hub_base = a.take<int>((n + 31) / 32);
+  int* hub_vertex = a.take<int>(kMaxHubs);
+  if (!ctl || !D || !ubuf[0] || !ubuf[1] || !task_start || !task_len || !task_v || !live || !hub_hist ||
+      !hub_base || !hub_vertex)
     return GC_ERR_OOM;
 
   const int mode = ctx->opt.update_mode;
@@ -461,27 +464,20 @@ gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigne
   adg_init_kernel<<<1, 1, 0, s>>>(ctl, n, nnz, p, q, mode, ctx->opt.pull_percent);
   ++g_launches;
   GC_TRY_CUDA(cudaGetLastError());
-  // hubs: at most update_hubs vertices, merged in a table of twice as many slots
-  int hub_slots = 0;
-  if (ctx->opt.update_hubs > 0 && nnz > 0) {
-    hub_slots = 1;
-    while (hub_slots < 2 * ctx->opt.update_hubs) hub_slots <<= 1;
+  // hubs: at most update_hubs vertices, one shared counter each
+  const int hubs = ctx->opt.update_hubs > 0 && nnz > 0 ? min(ctx->opt.update_hubs, kMaxHubs) : 0;
+  if (hubs > 0) {
     GC_TRY_CUDA(cudaMemsetAsync(hub_hist, 0, 64 * sizeof(unsigned long long), s));
     adg_hub_hist_kernel<<<ctx->num_sms * 4, 256, 0, s>>>(row_ptr_of(g), n, hub_hist);
     adg_hub_pick_kernel<<<1, 1, 0, s>>>(hub_hist, ctx->opt.update_hubs, ctl);
     g_launches += 2;
     GC_TRY_CUDA(cudaGetLastError());
   }
-  const size_t hub_smem = static_cast<size_t>(hub_slots) * 2 * sizeof(int);
-  // the largest table any context may ask for (the attribute is the
-  // kernel's, shared by every context of the process)
-  GC_TRY_CUDA(cudaFuncSetAttribute(adg_update_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   static_cast<int>(2 * kMaxHubs * 2 * sizeof(int))));
-
+  const size_t hub_smem = static_cast<size_t>(hubs) * sizeof(int);
   const int max_blocks = ctx->num_sms * 8;
   int per_sm = 0;
   const cudaError_t oe =
-      hub_slots > 0
+      hubs > 0
           ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adg_update_kernel<true>, kAdgThreads, hub_smem)
           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adg_update_kernel<false>, kAdgThreads, 0);
   if (oe != cudaSuccess || per_sm < 1) {
@@ -500,17 +496,19 @@ gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigne
     int blocks = static_cast<int>(want < max_blocks ? want : max_blocks);
     adg_partition_kernel<<<blocks, kAdgThreads, 0, s>>>(
         ctl, row_ptr_of(g), D, batch, round == 1 ? nullptr : ubuf[cur ^ 1], ubuf[cur], task_start,
-        task_len, live, round == 1 ? static_cast<int>(n) : 0);
+        task_len, live, round == 1 ? static_cast<int>(n) : 0, nullptr, nullptr, hub_base, hub_vertex);
     ++g_launches;
     GC_TRY_CUDA(cudaGetLastError());
     ctx->timer_begin(gc_context::kTUpdate, s);
     if (mode != GC_UPDATE_PULL) {  // each direction's kernels return at once if not chosen
-      if (hub_slots > 0)
+      if (hubs > 0)
         adg_update_kernel<true><<<upd_blocks, kAdgThreads, hub_smem, s>>>(
-            ctl, row_ptr_of(g), g->col_idx, D, batch, live, task_start, task_len, round == 1 ? n : 0, hub_slots);
+            ctl, row_ptr_of(g), g->col_idx, D, batch, live, task_start, task_len, round == 1 ? n : 0, hub_base,
+            hub_vertex);
       else
         adg_update_kernel<false><<<upd_blocks, kAdgThreads, 0, s>>>(
-            ctl, row_ptr_of(g), g->col_idx, D, batch, live, task_start, task_len, round == 1 ? n : 0, 0);
+            ctl, row_ptr_of(g), g->col_idx, D, batch, live, task_start, task_len, round == 1 ? n : 0, nullptr,
+            nullptr);
       ++g_launches;
     }
     if (mode != GC_UPDATE_PUSH) {
@@ -701,7 +699,7 @@ gc_status adg_m_run(gc_context* ctx, Arena a, const gc_csr* g, int* batch, int* 
     GC_TRY_CUDA(cudaGetLastError());
     ctx->timer_begin(gc_context::kTUpdate, s);
     adg_update_kernel<false><<<upd_blocks, kAdgThreads, 0, s>>>(ctl, rp, g->col_idx, D, batch, live, task_start,
-                                                                 task_len, 0, 0);
+                                                                 task_len, 0, nullptr, nullptr);
     ++g_launches;
     ctx->timer_end(s);
     GC_TRY_CUDA(cudaGetLastError());
@@ -824,7 +822,8 @@ extern "C" gc_status gc_adg_partition_noalloc(const gc_csr* g, uint32_t eps_p, u
                                                         round == 1 ? static_cast<int>(n) : 0);
     GC_TRY_CUDA(cudaGetLastError());
     adg_update_kernel<false><<<upd_blocks, kAdgThreads, 0, s>>>(ctl, rp, g->col_idx, D, batch_out, live,
-                                                                 task_start, task_len, round == 1 ? n : 0, 0);
+                                                                 task_start, task_len, round == 1 ? n : 0, nullptr,
+                                                                 nullptr);
     GC_TRY_CUDA(cudaGetLastError());
     adg_finalize_kernel<<<1, 1, 0, s>>>(ctl);
     GC_TRY_CUDA(cudaGetLastError());

@@ -275,7 +275,7 @@ gc_status gc_options_init(gc_options* opt) {
   o.wait_limit_ms = static_cast<uint32_t>(gc::kWaitLimitNs / 1000000ull);
   o.jp_state16 = 0;
   o.batch_mode = GC_BATCH_AUTO;
-  o.update_hubs = 1024;
+  o.update_hubs = 512;
   o.host_upload = 0;
   *opt = o;
   return GC_OK;

@@ -59,6 +59,8 @@ struct AdgCtl {
                                  // predecessors are among the neighbours D counts)
   int hub_min_degree;            // UPDATE merges decrements aimed at vertices of at
                                  // least this degree (INT_MAX: none)
+  int hub_cap;                   // hubs the rank table holds
+  int n_hubs;                    // hubs ranked by round 1's partition
 };
 
 static_assert(sizeof(AdgCtl) <= 256, "AdgCtl must fit the pinned read-back buffer");

@@ -48,7 +48,7 @@ std::vector<Dim> dims_single(long long n) {
                  }
                },
                {-1, 25, 50, 100, 200}});
-  d.push_back({[](gc_options& o, int v) { o.update_hubs = v; }, {0, 512, 1024, 2048}});
+  d.push_back({[](gc_options& o, int v) { o.update_hubs = v; }, {0, 256, 512, 1024, 4096}});
   d.push_back({[](gc_options& o, int v) { o.jp_state16 = v; }, {0, 1}});
   std::vector<int> cores = {0, 4096, 8192, 16384, 24576, 32768};
   cores.erase(std::remove_if(cores.begin(), cores.end(), [n](int c) { return c > 0 && c / 2 >= n; }), cores.end());

@@ -449,13 +449,15 @@ def test_jp_sl_small_graphs_and_limit(ctx):
 
 # ---------------------------------------------------------------- UPDATE hub merging
 
-@pytest.mark.parametrize("hubs", [0, 1024, 4096])
+@pytest.mark.parametrize("hubs", [0, 1, 512, 4096])
 @pytest.mark.parametrize("g", [gg.rmat(16, 16, seed=12), gg.barabasi_albert(40000, 8, 3), star(5000), complete(300),
                                gg.grid(90, 90), gg.erdos_renyi(20000, 100000, 6)], ids=lambda g: g.name)
 def test_hub_merging_identical(g, hubs):
-    # decrements aimed at hubs are merged in shared memory before they reach
-    # the degree words: batches, colours and ADG's statistics are unchanged
-    # (K_300: every vertex is a hub; star: the centre; grid: none)
+    # decrements aimed at hubs are counted per block in shared memory at the
+    # hub's rank before they reach the degree words: batches, colours and
+    # ADG's statistics are unchanged (K_300: every vertex is a hub, ranks
+    # spanning several bitmap words; star: the centre; grid: none; hubs=1:
+    # only vertices of the top degree class, if it holds one vertex)
     with gcp.Context(0, {"update_hubs": hubs, "update_mode": gcp.GC_UPDATE_PUSH}) as c:
         for p, q in ((1, 100), (1, 2)):
             b, col, nr, nc = color_graph(c, g, p, q, 42)

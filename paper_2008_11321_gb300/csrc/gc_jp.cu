@@ -1045,11 +1045,71 @@ jpf_core_solve_kernel(const int* __restrict__ order, const long long* __restrict
       }
       __syncwarp();
       late = true;
-      drain(0);
+      // Wait until at most one predecessor is left in the whole warp (each
+      // lane first down to one of its own).  That one is usually the
+      // previous vertex of the dependency chain: its colour cj decides
+      // between the two smallest colours c1 < c2 still free, c = (cj == c1 ?
+      // c2 : c1), so both are found before it lands and, once it does, the
+      // colour is stored at once.
+      drain(1);
       __syncwarp();
+      unsigned rem = __ballot_sync(kFull, nd > 0);
+      for (unsigned it = 0; __popc(rem) > 1; ++it) {
+        if (nd > 0) sweep();
+        rem = __ballot_sync(kFull, nd > 0);
+        if ((it & 255u) == 255u && __popc(rem) > 1 && __any_sync(kFull, expired())) {
+          timed_out = true;
+          nd = 0;
+          break;
+        }
+      }
       // a wait that ran out on any lane ends this warp's colouring: agree on
       // it before any warp-wide step, so that every lane leaves together and
       // no collective below or in a later vertex runs with lanes missing
+      if (__any_sync(kFull, timed_out)) {
+        timed_out = true;
+        break;
+      }
+      if (rem != 0u) {
+        __syncwarp();  // the other lanes' late marks are in the merged words
+        const unsigned fb0 = lane < nw ? ~merged[lane] : 0u;
+        const unsigned fm0 = __ballot_sync(kFull, fb0 != 0u);
+        int c1 = 0, c2 = 0;
+        if (fm0) {
+          const int f1 = __ffs(fm0) - 1;
+          const unsigned b1 = __shfl_sync(kFull, fb0, f1);
+          c1 = base + f1 * 32 + __ffs(b1);
+          const unsigned b1r = b1 & (b1 - 1u);
+          const unsigned fm1 = fm0 & ~(1u << f1);
+          const int f2 = fm1 ? __ffs(fm1) - 1 : 0;
+          const unsigned b2 = __shfl_sync(kFull, fb0, f2);
+          if (b1r)
+            c2 = base + f1 * 32 + __ffs(b1r);
+          else if (fm1)
+            c2 = base + f2 * 32 + __ffs(b2);
+        }
+        if (c2 != 0) {  // both inside this pass's window
+          const int j = __shfl_sync(kFull, static_cast<int>(def[0]), __ffs(rem) - 1);
+          unsigned got = 0u;
+          int cj = 0;
+          for (unsigned it = 0;; ++it) {
+            cj = vcol[j];
+            got = __ballot_sync(kFull, cj != 0);
+            if (got) break;
+            if ((it & 255u) == 255u && __any_sync(kFull, expired())) {
+              timed_out = true;
+              break;
+            }
+          }
+          nd = 0;
+          if (timed_out) break;
+          cj = __shfl_sync(kFull, cj, __ffs(got) - 1);
+          c = cj == c1 ? c2 : c1;
+          break;
+        }
+      }
+      drain(0);
+      __syncwarp();
       if (__any_sync(kFull, timed_out)) {
         timed_out = true;
         break;

@@ -140,7 +140,7 @@ typedef struct {
   int32_t core_cluster;    /* at most this many CTAs in the core's thread-block
                               cluster, 1..16 (default 16; fewer if the device
                               cannot place them)                             */
-  int32_t core_warps;      /* warps per core CTA, 1..32 (default 8)           */
+  int32_t core_warps;      /* warps per core CTA, 1..32 (default 12)          */
   int32_t dec_tail;        /* DEC-ADG-ITR: 1 finishes a partition's last
                               SIM-COL iterations in one cluster launch
                               (default), 0 runs every iteration GPU-wide     */

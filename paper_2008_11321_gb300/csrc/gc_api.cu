@@ -267,7 +267,7 @@ gc_status gc_options_init(gc_options* opt) {
   o.struct_size = sizeof(gc_options);
   o.core_target = static_cast<int32_t>(gc::kCoreDefault);
   o.core_cluster = 16;
-  o.core_warps = 8;
+  o.core_warps = 12;
   o.dec_tail = 1;
   o.update_mode = GC_UPDATE_AUTO;
   o.pull_percent = 25;

@@ -51,7 +51,7 @@ constexpr int kJpWarps = kJpThreads / kWarp;
 constexpr unsigned kBigBit = 0x80000000u;
 constexpr int kCoreThreads = 1024;  // largest core CTA
 constexpr int kCoreWarps = kCoreThreads / kWarp;
-constexpr int kCoreWarpsDefault = 8;
+constexpr int kCoreWarpsDefault = 12;
 
 __device__ __forceinline__ bool precedes(unsigned long long kw, int w, unsigned long long kv, int v) {
   return kw > kv || (kw == kv && w > v);
@@ -833,20 +833,22 @@ __global__ void jpf_compact_kernel(const int* __restrict__ preds, const long lon
 // SM) of W warps each.  Core vertex i belongs to CTA (i / W) mod C, warp
 // i mod W, so runs of W consecutive vertices (where many dependency steps
 // fall) share a CTA; every warp takes its vertices in increasing order.  W is
-// small (8 by default): warps that wait poll, and on a crowded SM their polls
+// small (12 by default): warps that wait poll, and on a crowded SM their polls
 // take the issue slots of the warps on the critical path.  Each CTA holds a full
 // copy of the core's colours (16-bit, so a core of at most 32768 vertices,
 // using at most 32768 colours) in its shared memory: a warp that colours
 // vertex i stores the colour into all C copies (lane r into CTA r, through
 // distributed shared memory), and waits for a predecessor by polling its own
 // CTA's copy.  A warp reads its vertex's predecessor list (the compact 16-bit
-// stream, core order) from global memory in 16-byte groups, marks the colours
-// already known and sets the others aside (up to kDeferLane per lane, in
-// shared memory) without waiting, so that the scan never stalls behind a
-// predecessor that is still being coloured; then it sweeps the set-aside
-// ones, marking those coloured meanwhile, until none is left (so that when
-// the last one is coloured, only it remains to be marked), and writes the
-// smallest colour none of the predecessors uses.  Predecessors
+// stream, core order) from global memory in 16-byte groups (the 8 colours of
+// a group are loaded together), marks the colours already known and sets the
+// others aside (up to kDeferLane per lane, in shared memory) without waiting,
+// so that the scan never stalls behind a predecessor that is still being
+// coloured; then it sweeps the set-aside ones, marking those coloured
+// meanwhile, until one is left in the warp.  The two smallest free colours
+// c1 < c2 are known by then, so the colour is (c1 if the last one's colour
+// differs from c1, else c2) and is stored the moment the last one lands.
+// Predecessors
 // precede their successors in the exact core order and every CTA of a
 // cluster is resident, so the warp holding the earliest unfinished vertex
 // always finds all of its predecessors coloured: the cluster makes progress
@@ -987,14 +989,30 @@ jpf_core_solve_kernel(const int* __restrict__ order, const long long* __restrict
           }
         }
       };
-      auto take = [&](int j) {
-        const int cj = vcol[j];
-        if (cj != 0) {
-          put(cj);
-          return;
+      // the 8 ids of a 16-byte group whose positions are in the list (bit e
+      // of `valid`): their colours are read first, all 8 loads in flight,
+      // then marked or set aside
+      auto take8 = [&](const uint4& v, unsigned valid) {
+        const unsigned wv[4] = {v.x, v.y, v.z, v.w};
+        int id[8], cj[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          id[e] = static_cast<int>((wv[e >> 1] >> (16 * (e & 1))) & 0xffffu);
+          cj[e] = ((valid >> e) & 1u) ? static_cast<int>(vcol[id[e]]) : -1;
         }
-        if (nd == kDeferLane) drain(kDeferLane - 1);
-        if (nd < kDeferLane) def[32 * nd++] = static_cast<unsigned short>(j);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          if (cj[e] > 0) {
+            put(cj[e]);
+          } else if (cj[e] == 0) {
+            if (nd == kDeferLane) drain(kDeferLane - 1);
+            if (nd < kDeferLane) def[32 * nd++] = static_cast<unsigned short>(id[e]);
+          }
+        }
+      };
+      auto mask8 = [&](long long p) -> unsigned {
+        const long long lo = a - p > 0 ? a - p : 0, hi = b - p < 8 ? b - p : 8;
+        return hi > lo ? ((1u << hi) - 1u) & ~((1u << lo) - 1u) : 0u;
       };
       // positions [a, b) of the stream, 8 per 16-byte group, two groups per
       // lane in flight
@@ -1002,37 +1020,8 @@ jpf_core_solve_kernel(const int* __restrict__ order, const long long* __restrict
         const bool has2 = (g + 32) * 8 < b;
         const uint4 v0 = __ldg(groups + g);
         const uint4 v1 = has2 ? __ldg(groups + g + 32) : make_uint4(0u, 0u, 0u, 0u);
-        const unsigned w0[4] = {v0.x, v0.y, v0.z, v0.w};
-        const unsigned w1[4] = {v1.x, v1.y, v1.z, v1.w};
-        const long long p0 = g * 8, p1 = (g + 32) * 8;
-        if (p0 >= a && p0 + 8 <= b) {
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            take(static_cast<int>(w0[e] & 0xffffu));
-            take(static_cast<int>(w0[e] >> 16));
-          }
-        } else {
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            if (p0 + 2 * e >= a && p0 + 2 * e < b) take(static_cast<int>(w0[e] & 0xffffu));
-            if (p0 + 2 * e + 1 >= a && p0 + 2 * e + 1 < b) take(static_cast<int>(w0[e] >> 16));
-          }
-        }
-        if (has2) {
-          if (p1 + 8 <= b) {
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              take(static_cast<int>(w1[e] & 0xffffu));
-              take(static_cast<int>(w1[e] >> 16));
-            }
-          } else {
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              if (p1 + 2 * e < b) take(static_cast<int>(w1[e] & 0xffffu));
-              if (p1 + 2 * e + 1 < b) take(static_cast<int>(w1[e] >> 16));
-            }
-          }
-        }
+        take8(v0, mask8(g * 8));
+        if (has2) take8(v1, mask8((g + 32) * 8));
       }
       __syncwarp();
       // lane q < nw ORs word q over all lanes (rotated so no bank repeats)

@@ -113,7 +113,7 @@ def test_options_defaults_and_range_checks(lib):
     # gc_create before it touches any device
     o = gcp.make_options()
     assert o.struct_size == ctypes.sizeof(gcp.gc_options)
-    assert o.as_dict() == {"core_target": 16384, "core_cluster": 16, "core_warps": 8, "dec_tail": 1,
+    assert o.as_dict() == {"core_target": 16384, "core_cluster": 16, "core_warps": 12, "dec_tail": 1,
                            "update_mode": gcp.GC_UPDATE_AUTO, "pull_percent": 25, "bulk_blocks_per_sm": 0,
                            "wait_limit_ms": 4000, "jp_state16": 0,
                            "batch_mode": gcp.GC_BATCH_AUTO, "update_hubs": 512,

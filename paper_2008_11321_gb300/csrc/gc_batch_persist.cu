@@ -219,17 +219,11 @@ batch_persistent_kernel(PGraphArgs A) {
     }
 
     // ---- JP ----------------------------------------------------------------
-    // lists: lane path (degree <= 32) in la/lb, warp path in lc/ld.  While
-    // JP runs, a graph of at most 255 rounds keeps each vertex's batch in the
-    // top 8 bits of its colour word (batch << 24 | colour; colours stay
-    // below 2^24), so one load of a neighbour's word gives both its priority
-    // and its colour; the batch bits are cleared at the end.
+    // lists: lane path (degree <= 32) in la/lb, warp path in lc/ld
     int* Ls = A.la + v0;
     int* Lsn = A.lb + v0;
     int* Lb = A.lc + v0;
     int* Lbn = A.ld + v0;
-    const bool packed = rounds <= 255;
-    const int cmask = packed ? 0xffffff : ~0;
     if (tid == 0) {
       s_ns = 0;
       s_nb = 0;
@@ -245,8 +239,7 @@ batch_persistent_kernel(PGraphArgs A) {
       if (active) {
         v = static_cast<int>(v0) + i;
         deg = A.row_ptr[v + 1] - A.row_ptr[v];
-        const int c0 = deg == 0 ? 1 : 0;  // isolated: no predecessor, colour 1
-        A.color[v] = packed ? static_cast<int>(static_cast<unsigned>(__ldcg(A.batch + v)) << 24) | c0 : c0;
+        A.color[v] = deg == 0 ? 1 : 0;  // isolated: no predecessor, colour 1
         if (deg == 0) local_max = 1;
         if (deg > 0 && deg <= kSmallDeg) {  // lane path: start of the row, no colour seen
           A.D[v] = 0;
@@ -258,10 +251,6 @@ batch_persistent_kernel(PGraphArgs A) {
     }
     __syncthreads();
     volatile int* vcol = A.color;
-    // a neighbour's batch: from its colour word when packed
-    auto batch_of = [&](int w, int x) {
-      return packed ? static_cast<int>(static_cast<unsigned>(x) >> 24) : __ldcg(A.batch + w);
-    };
     for (;;) {
       const int ns = s_ns, nb = s_nb;
       if (ns == 0 && nb == 0) break;
@@ -270,7 +259,7 @@ batch_persistent_kernel(PGraphArgs A) {
         s_nbn = 0;
       }
       __syncthreads();
-      // lane path: four neighbours' words in flight at a time
+      // lane path
       for (int base = 0; base < ns; base += kPThreads) {
         const int i = base + tid;
         bool pending = false;
@@ -281,8 +270,7 @@ batch_persistent_kernel(PGraphArgs A) {
             atomicExch(A.err, 2);
             v = static_cast<int>(v0);
           }
-          const int bv = __ldcg(A.batch + v);
-          const unsigned long long kv = pkey(bv, tie_hash(seed, static_cast<unsigned>(v - v0)));
+          const unsigned long long kv = pkey(__ldcg(A.batch + v), tie_hash(seed, static_cast<unsigned>(v - v0)));
           const long long s = A.row_ptr[v], e = A.row_ptr[v + 1];
           int pos = __ldcg(A.D + v);
           if (pos < 0 || pos > e - s) {  // a resume position outside the row: record it, restart
@@ -291,38 +279,24 @@ batch_persistent_kernel(PGraphArgs A) {
           }
           unsigned long long used = pos > 0 ? __ldcg(A.used + v) : 0ull;
           long long k = s + pos;
-          while (k < e) {
-            int w[4], x[4], bw[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) w[u] = k + u < e ? __ldg(A.col + k + u) : -1;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) x[u] = w[u] >= 0 ? vcol[w[u]] : 0;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) bw[u] = w[u] >= 0 ? batch_of(w[u], x[u]) : 0;
-            int u = 0;
-            for (; u < 4 && w[u] >= 0; ++u) {
-              const unsigned long long kw = pkey(bw[u], tie_hash(seed, static_cast<unsigned>(w[u] - v0)));
-              if (kw > kv || (kw == kv && w[u] > v)) {
-                const int c = x[u] & cmask;
-                if (c == 0) {
-                  pending = true;
-                  break;
-                }
-                if (c <= 64) used |= 1ull << (c - 1);
+          for (; k < e; ++k) {
+            const int w = __ldg(A.col + k);
+            const unsigned long long kw = pkey(__ldcg(A.batch + w), tie_hash(seed, static_cast<unsigned>(w - v0)));
+            if (kw > kv || (kw == kv && w > v)) {
+              const int c = vcol[w];
+              if (c == 0) {
+                pending = true;
+                break;
               }
+              if (c <= 64) used |= 1ull << (c - 1);
             }
-            if (pending) {
-              k += u;
-              break;
-            }
-            k += 4;
           }
           if (pending) {  // resume here next round
             A.D[v] = static_cast<int>(k - s);
             A.used[v] = used;
           } else {
             const int c = __ffsll(static_cast<long long>(~used));
-            vcol[v] = packed ? static_cast<int>(static_cast<unsigned>(bv) << 24) | c : c;
+            vcol[v] = c;
             local_max = c > local_max ? c : local_max;
           }
         }
@@ -336,8 +310,7 @@ batch_persistent_kernel(PGraphArgs A) {
           if (lane == 0) atomicExch(A.err, 2);
           v = static_cast<int>(v0);
         }
-        const int bv = __ldcg(A.batch + v);
-        const unsigned long long kv = pkey(bv, tie_hash(seed, static_cast<unsigned>(v - v0)));
+        const unsigned long long kv = pkey(__ldcg(A.batch + v), tie_hash(seed, static_cast<unsigned>(v - v0)));
         const long long s = A.row_ptr[v], e = A.row_ptr[v + 1];
         int c = 0;
         bool pending = false;
@@ -347,10 +320,9 @@ batch_persistent_kernel(PGraphArgs A) {
           bool miss = false;
           for (long long k = s + lane; k < e; k += 32) {
             const int w = __ldg(A.col + k);
-            const int x = vcol[w];
-            const unsigned long long kw = pkey(batch_of(w, x), tie_hash(seed, static_cast<unsigned>(w - v0)));
+            const unsigned long long kw = pkey(__ldcg(A.batch + w), tie_hash(seed, static_cast<unsigned>(w - v0)));
             if (kw > kv || (kw == kv && w > v)) {
-              const int cw = x & cmask;
+              const int cw = vcol[w];
               if (cw == 0) {
                 miss = true;
               } else if (cw > wbase && cw <= wbase + kColorWin) {
@@ -374,7 +346,7 @@ batch_persistent_kernel(PGraphArgs A) {
           if (pending) {
             Lbn[atomicAdd(&s_nbn, 1)] = v;
           } else {
-            vcol[v] = packed ? static_cast<int>(static_cast<unsigned>(bv) << 24) | c : c;
+            vcol[v] = c;
             local_max = c > local_max ? c : local_max;
           }
         }
@@ -395,9 +367,6 @@ batch_persistent_kernel(PGraphArgs A) {
       Lb = Lbn;
       Lbn = t2;
       __syncthreads();
-    }
-    if (packed) {  // the colours without the batch bits
-      for (int i = tid; i < n; i += kPThreads) vcol[v0 + i] = vcol[v0 + i] & 0xffffff;
     }
     local_max = warp_max(local_max);
     if (lane == 0 && local_max) atomicMax(&s_max, local_max);

@@ -162,6 +162,34 @@ struct KeyPacked {  // JP-ADG over many disjoint graphs: rho_R precomputed per v
   __device__ __forceinline__ int cword(unsigned long long, int c) const { return c; }
 };
 
+// JP-ADG over many disjoint graphs with the batch kept in the top 8 bits of
+// the colour word (batches up to 255) and rho_R precomputed per vertex (each
+// graph has its own seed): one load of a neighbour's word gives its batch and
+// colour, and its rho_R is read only when the batches are equal.
+struct KeyStateT {
+  using W = int;
+  const int* state;  // the colour array during JP
+  const unsigned* tiev;
+  __device__ __forceinline__ int bat(int v) const { return static_cast<int>(static_cast<unsigned>(state[v]) >> 24); }
+  __device__ __forceinline__ unsigned tie(int v) const { return __ldg(tiev + v); }
+  __device__ __forceinline__ unsigned long long operator()(int v) const {
+    return (static_cast<unsigned long long>(static_cast<unsigned>(bat(v))) << 32) | tie(v);
+  }
+  using PG = int;
+  __device__ __forceinline__ PG pgather(int w, const int* color) const { return ld_relaxed(color + w); }
+  __device__ __forceinline__ bool pred_g(PG x, int w, unsigned long long kv, int v) const {
+    const unsigned bw = static_cast<unsigned>(x) >> 24, bv = static_cast<unsigned>(kv >> 32);
+    if (bw != bv) return bw > bv;
+    const unsigned tw = tie(w), tv = static_cast<unsigned>(kv);
+    return tw > tv || (tw == tv && w > v);
+  }
+  __device__ __forceinline__ int color_g(PG x, const int*, int) const { return x & 0xffffff; }
+  __device__ __forceinline__ int cmask() const { return 0xffffff; }
+  __device__ __forceinline__ int cword(unsigned long long kv, int c) const {
+    return static_cast<int>(static_cast<unsigned>(kv >> 32) << 24) | c;
+  }
+};
+
 // JP-ADG-O: the priority (batch, D at removal, id), with the batch kept in
 // the top 8 bits of the colour word as in KeyState; D is read only for a
 // neighbour of the same batch.
@@ -1685,7 +1713,17 @@ gc_status jp_run_fused(gc_context* ctx, Arena a, const gc_csr* g, const int* bat
 
 gc_status jp_run_packed(gc_context* ctx, Arena a, const gc_csr* g, const int* batch, const unsigned* tiev,
                         const int* D, int rounds, int* color, int* num_colors_out, cudaStream_t s) {
-  return jp_adg_impl(ctx, a, g, KeyPacked{batch, tiev}, D, rounds, color, num_colors_out, s);
+  if (rounds > 255 || g->n == 0)
+    return jp_adg_impl(ctx, a, g, KeyPacked{batch, tiev}, D, rounds, color, num_colors_out, s);
+  const int blocks = ctx->num_sms * 8;
+  state_init_kernel<<<blocks, 256, 0, s>>>(batch, g->n, color);
+  ++g_launches;
+  GC_TRY_CUDA(cudaGetLastError());
+  GC_TRY(jp_adg_impl(ctx, a, g, KeyStateT{color, tiev}, D, rounds, color, num_colors_out, s));
+  state_strip_kernel<<<blocks, 256, 0, s>>>(g->n, color);
+  ++g_launches;
+  GC_TRY_CUDA(cudaGetLastError());
+  return GC_OK;
 }
 
 namespace {

@@ -165,10 +165,14 @@ typedef struct {
                               array per thread block, added to their degree
                               words once per block, 0..4096 (default 512; 0:
                               every decrement is an atomic on its word)      */
-  int32_t host_upload;     /* gc_color_graph_host: 0 (default) copies the
-                              graph with the copy engine; 1 has the SMs read
-                              page-locked, mapped host buffers directly
-                              (16-byte aligned; others use the copy engine)  */
+  int32_t host_upload;     /* gc_color_graph_host: 1 (default) has the SMs
+                              read page-locked, mapped host buffers directly
+                              (16-byte aligned; others use the copy engine);
+                              0 copies the graph with the copy engine.
+                              From 2^22 entries on, col_idx is copied in 8
+                              vertex ranges on a stream of the context and
+                              ADG's first round sweeps each range once it
+                              has arrived                                    */
 } gc_options;
 
 /* How gc_color_batch runs (gc_options.batch_mode, gc_stats.batch_path):

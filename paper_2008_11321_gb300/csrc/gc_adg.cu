@@ -237,7 +237,7 @@ adg_update_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row_pt
                   const int* __restrict__ col, int* __restrict__ D, const int* __restrict__ batch,
                   const uint2* __restrict__ live, const long long* __restrict__ task_start,
                   const int* __restrict__ task_len, long long vertex_tiles_n, const int* __restrict__ hub_base,
-                  const int* __restrict__ hub_vertex) {
+                  const int* __restrict__ hub_vertex, long long vertex_lo = 0) {
   extern __shared__ int s_hub[];
   // The last round leaves U empty: no neighbour can still be in U, so there
   // is nothing to decrement (and the cut is not needed any more).  A pull
@@ -250,8 +250,9 @@ adg_update_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row_pt
     __syncthreads();
   }
   const int round = ctl->round;
+  // round 1: the vertices [vertex_lo, vertex_tiles_n)
   const unsigned long long ntasks =
-      vertex_tiles_n > 0 ? static_cast<unsigned long long>(vertex_tiles_n) : ctl->ntasks;
+      vertex_tiles_n > 0 ? static_cast<unsigned long long>(vertex_tiles_n - vertex_lo) : ctl->ntasks;
   const int lane = threadIdx.x & 31;
   const unsigned long long gwarp = (static_cast<unsigned long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const unsigned long long nwarps = (static_cast<unsigned long long>(gridDim.x) * blockDim.x) >> 5;
@@ -262,9 +263,10 @@ adg_update_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row_pt
     int len = 0;
     if (t < ntasks) {
       if (vertex_tiles_n > 0) {
-        if (batch[t] == round) {
-          st = row_ptr[t];
-          len = static_cast<int>(row_ptr[t + 1] - st);
+        const long long x = vertex_lo + static_cast<long long>(t);
+        if (batch[x] == round) {
+          st = row_ptr[x];
+          len = static_cast<int>(row_ptr[x + 1] - st);
         }
       } else {
         st = task_start[t];
@@ -439,7 +441,7 @@ size_t adg_scratch_bytes(long long n, long long nnz) {
 }
 
 gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigned q, int* batch,
-                  int* D, int* rounds_out, cudaStream_t s) {
+                  int* D, int* rounds_out, cudaStream_t s, const ColChunks* chunks) {
   const long long n = g->n, nnz = g->nnz;
   *rounds_out = 0;
   ctx->stats.adg_rounds = 0;
@@ -500,16 +502,27 @@ gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigne
     ++g_launches;
     GC_TRY_CUDA(cudaGetLastError());
     ctx->timer_begin(gc_context::kTUpdate, s);
+    // round 1 sweeps vertex ranges, each once its column indices are on the
+    // device (one range: the whole graph, already there); later rounds sweep
+    // the partition's task list
+    const bool chunked = round == 1 && chunks != nullptr && chunks->k > 0;
+    if (chunked && mode == GC_UPDATE_PULL)  // nothing of round 1 reads col_idx before the pull count
+      for (int c = 0; c < chunks->k; ++c) GC_TRY_CUDA(cudaStreamWaitEvent(s, chunks->ready[c], 0));
     if (mode != GC_UPDATE_PULL) {  // each direction's kernels return at once if not chosen
-      if (hubs > 0)
-        adg_update_kernel<true><<<upd_blocks, kAdgThreads, hub_smem, s>>>(
-            ctl, row_ptr_of(g), g->col_idx, D, batch, live, task_start, task_len, round == 1 ? n : 0, hub_base,
-            hub_vertex);
-      else
-        adg_update_kernel<false><<<upd_blocks, kAdgThreads, 0, s>>>(
-            ctl, row_ptr_of(g), g->col_idx, D, batch, live, task_start, task_len, round == 1 ? n : 0, nullptr,
-            nullptr);
-      ++g_launches;
+      const int nr = chunked ? chunks->k : 1;
+      for (int c = 0; c < nr; ++c) {
+        const long long lo = chunked ? chunks->lo[c] : 0;
+        const long long hi = chunked ? chunks->lo[c + 1] : (round == 1 ? n : 0);
+        if (chunked) GC_TRY_CUDA(cudaStreamWaitEvent(s, chunks->ready[c], 0));
+        if (round == 1 && hi <= lo) continue;
+        if (hubs > 0)
+          adg_update_kernel<true><<<upd_blocks, kAdgThreads, hub_smem, s>>>(
+              ctl, row_ptr_of(g), g->col_idx, D, batch, live, task_start, task_len, hi, hub_base, hub_vertex, lo);
+        else
+          adg_update_kernel<false><<<upd_blocks, kAdgThreads, 0, s>>>(
+              ctl, row_ptr_of(g), g->col_idx, D, batch, live, task_start, task_len, hi, nullptr, nullptr, lo);
+        ++g_launches;
+      }
     }
     if (mode != GC_UPDATE_PUSH) {
       const long long wantp = (size_u + kAdgThreads - 1) / kAdgThreads;

@@ -9,6 +9,8 @@
 
 #include <functional>
 
+#include <algorithm>
+
 #include "gc_internal.cuh"
 
 namespace gc {
@@ -186,11 +188,29 @@ gc_status upload(gc_context* ctx, void* dst, const void* src, size_t bytes, cuda
   return GC_OK;
 }
 
+// gc_color_graph_host copies col_idx in ranges (on the context's copy stream)
+// from this many entries on.
+constexpr int64_t kChunkedUploadMin = int64_t(1) << 22;
+
+gc_status copy_stream_ready(gc_context* ctx) {
+  if (!ctx->copy_stream &&
+      cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    ctx->copy_stream = nullptr;
+    return gc_cuda_status(cudaGetLastError());
+  }
+  for (auto& e : ctx->copy_ev)
+    if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      e = nullptr;
+      return gc_cuda_status(cudaGetLastError());
+    }
+  return GC_OK;
+}
+
 // Shared body of gc_color_graph and gc_color_graph_host.
 // JP-ADG (median = false) or JP-ADG-M (median = true, p and q unused).
 gc_status color_graph_device(gc_context* ctx, const gc_csr* g, uint32_t p, uint32_t q, uint64_t seed,
                              int32_t* color, int32_t* batch, int32_t* ncol, int32_t* nrounds,
-                             cudaStream_t s, bool median = false) {
+                             cudaStream_t s, bool median = false, const gc::ColChunks* chunks = nullptr) {
   const long long n = g->n;
   const size_t vb = static_cast<size_t>(n > 0 ? n : 1) * 4 + 256;
   GC_TRY(ctx->reserve_vert(2 * vb));
@@ -202,7 +222,7 @@ gc_status color_graph_device(gc_context* ctx, const gc_csr* g, uint32_t p, uint3
   if (median)
     GC_TRY(gc::adg_m_run(ctx, ctx->arena(), g, b, D, &rounds, s));
   else
-    GC_TRY(gc::adg_run(ctx, ctx->arena(), g, p, q, b, D, &rounds, s));
+    GC_TRY(gc::adg_run(ctx, ctx->arena(), g, p, q, b, D, &rounds, s, chunks));
   GC_TRY(timing_begin(ctx, 1, s));
   GC_TRY(ctx->reserve(gc::jpadg_scratch_bytes(n, g->nnz, rounds)));
   GC_TRY(gc::jp_run_fused(ctx, ctx->arena(), g, b, D, rounds, seed, color, &colors, s));
@@ -276,7 +296,7 @@ gc_status gc_options_init(gc_options* opt) {
   o.jp_state16 = 0;
   o.batch_mode = GC_BATCH_AUTO;
   o.update_hubs = 512;
-  o.host_upload = 0;
+  o.host_upload = 1;
   *opt = o;
   return GC_OK;
 }
@@ -364,6 +384,9 @@ void gc_destroy(gc_context* ctx) {
   if (ctx->aux) cudaFree(ctx->aux);
   if (ctx->pack) cudaFree(ctx->pack);
   if (ctx->h_graph) cudaFree(ctx->h_graph);
+  for (auto& e : ctx->copy_ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   for (auto& ev : ctx->ev)
     if (ev) cudaEventDestroy(ev);
@@ -759,9 +782,48 @@ gc_status gc_color_graph_host(gc_context* ctx, int64_t n, int64_t nnz, const int
   int32_t* d_color = reinterpret_cast<int32_t*>(base + b_rp + b_ci);
   int32_t* d_batch = reinterpret_cast<int32_t*>(base + b_rp + b_ci + b_v);
   GC_TRY(upload(ctx, const_cast<int64_t*>(g.row_ptr), row_ptr, static_cast<size_t>(n + 1) * 8, s));
-  if (nnz > 0) GC_TRY(upload(ctx, const_cast<int32_t*>(g.col_idx), col_idx, static_cast<size_t>(nnz) * 4, s));
-  GC_TRY(color_graph_device(ctx, &g, eps_p, eps_q, seed, d_color, d_batch, num_colors_out,
-                            num_rounds_out, s));
+  // col_idx in vertex ranges of about equal size on the context's copy
+  // stream (by the copy engine, or by the SM copy with host_upload), so that
+  // ADG's first round starts on the ranges already copied; small graphs take
+  // one copy on s
+  gc::ColChunks chunks;
+  if (nnz >= kChunkedUploadMin) {
+    GC_TRY(copy_stream_ready(ctx));
+    GC_TRY_CUDA(cudaEventRecord(ctx->copy_ev[gc::kUploadChunks], s));  // earlier work on s is done with the buffers
+    GC_TRY_CUDA(cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_ev[gc::kUploadChunks], 0));
+    chunks.k = gc::kUploadChunks;
+    chunks.lo[0] = 0;
+    for (int c = 1; c < chunks.k; ++c) {
+      // the first vertex whose row starts at or after c/k of the entries
+      const int64_t target = nnz / chunks.k * c;
+      chunks.lo[c] = std::lower_bound(row_ptr, row_ptr + n + 1, target) - row_ptr;
+      if (chunks.lo[c] < chunks.lo[c - 1]) chunks.lo[c] = chunks.lo[c - 1];
+      if (chunks.lo[c] > n) chunks.lo[c] = n;
+    }
+    chunks.lo[chunks.k] = n;
+    // entry ranges: each range's first row start rounded up to 4 entries (16
+    // bytes, so the SM copy keeps its alignment; a range then also carries
+    // the first entries of the next one), kept within [0, nnz) and
+    // increasing, so that the copies cover the entries exactly once
+    // whatever row_ptr holds
+    int64_t pos[gc::kUploadChunks + 1];
+    pos[0] = 0;
+    pos[chunks.k] = nnz;
+    for (int c = 1; c < chunks.k; ++c)
+      pos[c] = std::min<int64_t>((std::max<int64_t>(row_ptr[chunks.lo[c]], pos[c - 1]) + 3) & ~int64_t(3), nnz);
+    for (int c = 0; c < chunks.k; ++c) {
+      const int64_t a = pos[c], b = pos[c + 1];
+      if (b > a)
+        GC_TRY(upload(ctx, const_cast<int32_t*>(g.col_idx) + a, col_idx + a, static_cast<size_t>(b - a) * 4,
+                      ctx->copy_stream));
+      GC_TRY_CUDA(cudaEventRecord(ctx->copy_ev[c], ctx->copy_stream));
+      chunks.ready[c] = ctx->copy_ev[c];
+    }
+  } else if (nnz > 0) {
+    GC_TRY(upload(ctx, const_cast<int32_t*>(g.col_idx), col_idx, static_cast<size_t>(nnz) * 4, s));
+  }
+  GC_TRY(color_graph_device(ctx, &g, eps_p, eps_q, seed, d_color, d_batch, num_colors_out, num_rounds_out, s,
+                            false, chunks.k > 0 ? &chunks : nullptr));
   if (n > 0) {
     GC_TRY_CUDA(cudaMemcpyAsync(color_out, d_color, static_cast<size_t>(n) * 4, cudaMemcpyDeviceToHost, s));
     if (batch_out)

@@ -144,9 +144,19 @@ int radix_sort_pairs(SortBufs& b, long long n, unsigned digit_mask, cudaStream_t
 
 // ADG rounds on the device (gc_adg.cu).  Scratch sized by adg_scratch_bytes.
 size_t adg_scratch_bytes(long long n, long long nnz);
+// The column indices of vertex ranges [lo[c], lo[c+1]) arriving on another
+// stream, range c complete when ready[c] fires: round 1's UPDATE sweeps each
+// range once its event has fired (round 1's partition needs row offsets only),
+// so the copy of col_idx overlaps ADG's first round.
+constexpr int kUploadChunks = 8;
+struct ColChunks {
+  int k = 0;
+  long long lo[kUploadChunks + 1] = {};
+  cudaEvent_t ready[kUploadChunks] = {};
+};
 // D (n ints) receives each vertex's degree at removal.
 gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigned q, int* batch,
-                  int* D, int* rounds_out, cudaStream_t s);
+                  int* D, int* rounds_out, cudaStream_t s, const ColChunks* chunks = nullptr);
 
 // ADG-M rounds (gc_adg.cu): median degree, R = the ceil(|U|/2) smallest
 // (D, id) of U.  D receives each vertex's degree at removal.
@@ -258,9 +268,11 @@ struct gc_context {
   // packed union of gc_color_batch_list
   void* pack = nullptr;
   size_t pack_bytes = 0;
-  // buffers owned for gc_color_graph_host
+  // buffers owned for gc_color_graph_host, and its copy stream and events
   void* h_graph = nullptr;
   size_t h_graph_bytes = 0;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copy_ev[gc::kUploadChunks + 1] = {};  // per range, then "the device buffers are free"
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   // kernel-group timers: event pairs recorded around launches when timing is
   // on, summed per group after the call's final synchronisation

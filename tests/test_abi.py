@@ -117,7 +117,7 @@ def test_options_defaults_and_range_checks(lib):
                            "update_mode": gcp.GC_UPDATE_AUTO, "pull_percent": 25, "bulk_blocks_per_sm": 0,
                            "wait_limit_ms": 4000, "jp_state16": 0,
                            "batch_mode": gcp.GC_BATCH_AUTO, "update_hubs": 512,
-                           "host_upload": 0}
+                           "host_upload": 1}
     h = ctypes.c_void_p()
     bad = [dict(core_target=-1), dict(core_target=32769), dict(core_cluster=0), dict(core_cluster=17),
            dict(core_warps=0), dict(core_warps=33), dict(dec_tail=2), dict(update_mode=3),

@@ -273,6 +273,29 @@ def test_host_entry_point(ctx, scale):
     assert np.array_equal(batch, ob) and np.array_equal(color, oc)
 
 
+@pytest.mark.parametrize("opts", [{}, {"host_upload": 0}, {"update_mode": gcp.GC_UPDATE_PULL}, {"update_hubs": 0}],
+                         ids=["auto", "copy-engine", "pull", "nohubs"])
+@pytest.mark.parametrize("g", [star(2_500_000), gg.rmat(18, 16, seed=8)], ids=lambda g: g.name)
+def test_host_entry_point_ranges(g, opts):
+    # from 2^22 entries on, col_idx is copied in vertex ranges on a copy
+    # stream (SM copy by default, copy engine with host_upload 0) and round
+    # 1's UPDATE sweeps each range once it has arrived (the star: one row
+    # holds half the entries, so several ranges are empty); page-locked and
+    # pageable buffers, three calls in a row
+    rp = torch.empty(g.n + 1, dtype=torch.int64, pin_memory=True).numpy()
+    ci = torch.empty(g.nnz, dtype=torch.int32, pin_memory=True).numpy()
+    rp[:] = g.row_ptr
+    ci[:] = g.col_idx
+    ob, oc, onr, onc = oracle.jp_adg(g, 1, 100, 42)
+    with gcp.Context(0, opts) as c:
+        for r, k in ((rp, ci), (g.row_ptr, g.col_idx), (rp, ci)):
+            color = np.zeros(g.n, dtype=np.int32)
+            batch = np.zeros(g.n, dtype=np.int32)
+            nc, nr = c.gc_color_graph_host(r, k, 1, 100, 42, color, batch)
+            assert (nc, nr) == (onc, onr)
+            assert np.array_equal(batch, ob) and np.array_equal(color, oc)
+
+
 def test_scratch_regrow_and_reuse(ctx):
     for g in (gg.rmat(10, 8, seed=1), gg.rmat(17, 16, seed=2), gg.rmat(11, 8, seed=3)):
         assert_same_as_oracle(ctx, g)

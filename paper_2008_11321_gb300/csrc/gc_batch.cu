@@ -50,19 +50,6 @@ __device__ __forceinline__ int threshold_of(unsigned long long sigma, int size_u
   return t > static_cast<unsigned __int128>(INT_MAX) ? INT_MAX : static_cast<int>(t);
 }
 
-// The graph owning vertex v: the largest g with off[g] <= v.
-__device__ __forceinline__ int graph_of(const long long* __restrict__ off, int G, long long v) {
-  int lo = 0, hi = G - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (__ldg(off + mid) <= v)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  return lo;
-}
-
 __global__ void batch_init_kernel(BGraph* __restrict__ gs, const gc_job* __restrict__ jobs, int G,
                                   const long long* __restrict__ off, const long long* __restrict__ row_ptr,
                                   BCtl* ctl) {
@@ -85,6 +72,13 @@ __global__ void batch_init_kernel(BGraph* __restrict__ gs, const gc_job* __restr
   }
 }
 
+// Graph id of every vertex (one block per graph writes its range), so that
+// the kernels below read a vertex's graph instead of searching graph_off.
+__global__ void batch_gid_kernel(const long long* __restrict__ off, int G, int* __restrict__ gid) {
+  for (int g = blockIdx.x; g < G; g += gridDim.x)
+    for (long long v = off[g] + threadIdx.x; v < off[g + 1]; v += blockDim.x) gid[v] = g;
+}
+
 // Sum of `x` over the lanes of `group` (a __match_any_sync class), 64-bit.
 __device__ __forceinline__ unsigned long long group_sum(unsigned group, unsigned long long x) {
   const unsigned lo = __reduce_add_sync(group, static_cast<unsigned>(x & 0xffffu));
@@ -95,11 +89,11 @@ __device__ __forceinline__ unsigned long long group_sum(unsigned group, unsigned
 }
 
 __global__ void __launch_bounds__(kBThreads)
-batch_partition_kernel(BCtl* __restrict__ ctl, BGraph* __restrict__ gs, const long long* __restrict__ off,
-                       int G, const long long* __restrict__ row_ptr, int* __restrict__ D,
+batch_partition_kernel(BCtl* __restrict__ ctl, BGraph* __restrict__ gs, const int* __restrict__ gid,
+                       const long long* __restrict__ row_ptr, int* __restrict__ D,
                        int* __restrict__ batch, const int* __restrict__ u_in, int* __restrict__ u_out,
                        long long* __restrict__ task_start, int* __restrict__ task_len,
-                       int* __restrict__ task_g, long long size_u) {
+                       int* __restrict__ task_g, long long size_u, unsigned* __restrict__ live) {
   const int round = ctl->round;
   const bool first = round == 1;
   const int lane = threadIdx.x & 31;
@@ -112,7 +106,7 @@ batch_partition_kernel(BCtl* __restrict__ ctl, BGraph* __restrict__ gs, const lo
     long long rs = 0, re = 0;
     if (active) {
       u = first ? static_cast<int>(i) : u_in[i];
-      g = graph_of(off, G, u);
+      g = gid[u];
       if (first) {
         rs = row_ptr[u];
         re = row_ptr[u + 1];
@@ -137,6 +131,17 @@ batch_partition_kernel(BCtl* __restrict__ ctl, BGraph* __restrict__ gs, const lo
     // removed -> batch id, per-graph sum of D
     const unsigned rm = __ballot_sync(kFull, in_r);
     const unsigned rgrp = grp & rm;
+    // liveness bitmap: round 1 writes the warp's word (vertices 32 j ..
+    // 32 j + 31: blocks start at multiples of 32), later rounds clear bits
+    if (first) {
+      if (lane == 0 && active) live[i >> 5] = km;
+    } else if (rm) {
+      // lanes clearing bits of one word (the list keeps ids mostly
+      // increasing) merge them: one atomic per word and warp
+      const unsigned wgrp = __match_any_sync(kFull, in_r ? (u >> 5) : -1 - lane);
+      const unsigned bits = __reduce_or_sync(wgrp, in_r ? 1u << (u & 31) : 0u);
+      if (in_r && (wgrp & lt) == 0) atomicAnd(&live[u >> 5], ~bits);
+    }
     const unsigned long long dsum = group_sum(grp, in_r ? static_cast<unsigned long long>(d) : 0ull);
     if (in_r) {
       batch[u] = round;
@@ -177,11 +182,11 @@ batch_partition_kernel(BCtl* __restrict__ ctl, BGraph* __restrict__ gs, const lo
 }
 
 __global__ void __launch_bounds__(kBThreads)
-batch_update_kernel(BCtl* __restrict__ ctl, BGraph* __restrict__ gs, const long long* __restrict__ off,
-                    int G, const long long* __restrict__ row_ptr, const int* __restrict__ col,
+batch_update_kernel(BCtl* __restrict__ ctl, BGraph* __restrict__ gs, const int* __restrict__ gid,
+                    const long long* __restrict__ row_ptr, const int* __restrict__ col,
                     int* __restrict__ D, const int* __restrict__ batch,
                     const long long* __restrict__ task_start, const int* __restrict__ task_len,
-                    const int* __restrict__ task_g, long long vertex_tiles_n) {
+                    const int* __restrict__ task_g, long long vertex_tiles_n, const unsigned* __restrict__ live) {
   const int round = ctl->round;
   const unsigned long long ntasks =
       vertex_tiles_n > 0 ? static_cast<unsigned long long>(vertex_tiles_n) : ctl->ntasks;
@@ -201,7 +206,7 @@ batch_update_kernel(BCtl* __restrict__ ctl, BGraph* __restrict__ gs, const long 
         if (batch[t] == round) {
           st = row_ptr[t];
           len = static_cast<int>(row_ptr[t + 1] - st);
-          tg = graph_of(off, G, static_cast<long long>(t));
+          tg = gid[t];
         }
       } else {
         st = task_start[t];
@@ -210,9 +215,9 @@ batch_update_kernel(BCtl* __restrict__ ctl, BGraph* __restrict__ gs, const long 
       }
     }
     sweep_tile(
-        st, len, tg, col, [&](int w, int) { return __ldg(batch + w); },
-        [&](int w, int g, int bw) {
-      if (bw == 0) {
+        st, len, tg, col, [&](int w, int) { return (__ldg(live + (w >> 5)) >> (w & 31)) & 1u; },
+        [&](int w, int g, unsigned lw) {
+      if (lw) {  // w is still in U
         atomicSub(&D[w], 1);
         if (g != cur_g) {
           if (cnt) atomicAdd(&gs[cur_g].cut, cnt);
@@ -253,17 +258,17 @@ __global__ void batch_next_round_kernel(BCtl* ctl) {
 }
 
 // rho_R of every vertex from its graph's seed and its id inside the graph.
-__global__ void batch_tie_kernel(const BGraph* __restrict__ gs, const long long* __restrict__ off, int G,
-                                 long long n, unsigned* __restrict__ tiev) {
+__global__ void batch_tie_kernel(const BGraph* __restrict__ gs, const long long* __restrict__ off,
+                                 const int* __restrict__ gid, long long n, unsigned* __restrict__ tiev) {
   for (long long v = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; v < n;
        v += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int g = graph_of(off, G, v);
+    const int g = gid[v];
     tiev[v] = tie_hash(gs[g].seed, static_cast<unsigned>(v - off[g]));
   }
 }
 
 // Largest colour and round count per graph.
-__global__ void batch_results_kernel(const BGraph* __restrict__ gs, const long long* __restrict__ off, int G,
+__global__ void batch_results_kernel(const BGraph* __restrict__ gs, const int* __restrict__ gid, int G,
                                      long long n, const int* __restrict__ color, int* __restrict__ ncol,
                                      int* __restrict__ nrounds) {
   const int lane = threadIdx.x & 31;
@@ -272,7 +277,7 @@ __global__ void batch_results_kernel(const BGraph* __restrict__ gs, const long l
        base += static_cast<long long>(gridDim.x) * blockDim.x) {
     const long long v = base + threadIdx.x;
     const bool active = v < n;
-    const int g = active ? graph_of(off, G, v) : -1;
+    const int g = active ? gid[v] : -1;
     const int c = active ? color[v] : 0;
     const unsigned grp = __match_any_sync(kFull, g);
     const int m = static_cast<int>(__reduce_max_sync(grp, static_cast<unsigned>(c)));
@@ -289,7 +294,8 @@ __global__ void batch_results_kernel(const BGraph* __restrict__ gs, const long l
 size_t batch_adg_scratch_bytes(long long n, long long nnz, long long G) {
   const long long ntask = n + nnz / kChunk + 1;
   return 2 * (static_cast<size_t>(n) * 4 + 256) + static_cast<size_t>(ntask) * 16 + 1024 +
-         static_cast<size_t>(G) * (sizeof(BGraph) + sizeof(gc_job)) + 2048;
+         static_cast<size_t>(G) * (sizeof(BGraph) + sizeof(gc_job)) + static_cast<size_t>((n + 31) / 32) * 4 + 256 +
+         2048;
 }
 
 }  // namespace gc
@@ -307,13 +313,14 @@ gc_status batch_color(gc_context* ctx, const gc_batch_csr* b, const gc_job* jobs
   const size_t vb = (static_cast<size_t>(n > 0 ? n : 1) * 4 + 255) & ~size_t(255);
   const size_t gb = (static_cast<size_t>(G) * sizeof(BGraph) + 255) & ~size_t(255);
   const size_t jb = (static_cast<size_t>(G) * sizeof(gc_job) + 255) & ~size_t(255);
-  GC_TRY(ctx->reserve_vert(3 * vb + gb + jb));
+  GC_TRY(ctx->reserve_vert(4 * vb + gb + jb));
   char* vbase = static_cast<char*>(ctx->vbuf);
   int* D = reinterpret_cast<int*>(vbase);
   int* bat = batch_out ? batch_out : reinterpret_cast<int*>(vbase + vb);
   unsigned* tiev = reinterpret_cast<unsigned*>(vbase + 2 * vb);
   BGraph* gs = reinterpret_cast<BGraph*>(vbase + 3 * vb);
   gc_job* djobs = reinterpret_cast<gc_job*>(vbase + 3 * vb + gb);
+  int* gid = reinterpret_cast<int*>(vbase + 3 * vb + gb + jb);
   GC_TRY_CUDA(cudaMemcpyAsync(djobs, jobs, sizeof(gc_job) * G, cudaMemcpyHostToDevice, s));
   // One persistent launch (a block per graph, gc_batch_persist.cu) when no
   // graph is too large for one block: at most 4 times an SM's share of the
@@ -343,11 +350,14 @@ gc_status batch_color(gc_context* ctx, const gc_batch_csr* b, const gc_job* jobs
   long long* task_start = a.take<long long>(ntask);
   int* task_len = a.take<int>(ntask);
   int* task_g = a.take<int>(ntask);
-  if (!ctl || !ubuf[0] || !ubuf[1] || !task_start || !task_len || !task_g) return GC_ERR_OOM;
+  unsigned* live = a.take<unsigned>((n + 31) / 32 + 1);
+  if (!ctl || !ubuf[0] || !ubuf[1] || !task_start || !task_len || !task_g || !live) return GC_ERR_OOM;
   if (n > 0) GC_TRY_CUDA(cudaMemsetAsync(bat, 0, sizeof(int) * n, s));  // 0 = still in U
   const int blocks = ctx->num_sms * 8;
   const int upd_blocks = resident_grid(batch_update_kernel, kBThreads, ctx->num_sms);
   batch_init_kernel<<<(G + 255) / 256, 256, 0, s>>>(gs, djobs, G, off, rp, ctl);
+  ++g_launches;
+  batch_gid_kernel<<<G < 65535 ? G : 65535, 256, 0, s>>>(off, G, gid);
   ++g_launches;
   GC_TRY_CUDA(cudaGetLastError());
 
@@ -360,12 +370,12 @@ gc_status batch_color(gc_context* ctx, const gc_batch_csr* b, const gc_job* jobs
     ++round;
     const long long want = (size_u + kBThreads - 1) / kBThreads;
     const int pblocks = static_cast<int>(want < blocks ? want : blocks);
-    batch_partition_kernel<<<pblocks, kBThreads, 0, s>>>(ctl, gs, off, G, rp, D, bat,
+    batch_partition_kernel<<<pblocks, kBThreads, 0, s>>>(ctl, gs, gid, rp, D, bat,
                                                          round == 1 ? nullptr : ubuf[cur ^ 1], ubuf[cur],
-                                                         task_start, task_len, task_g, size_u);
+                                                         task_start, task_len, task_g, size_u, live);
     ++g_launches;
-    batch_update_kernel<<<upd_blocks, kBThreads, 0, s>>>(ctl, gs, off, G, rp, b->col_idx, D, bat, task_start,
-                                                     task_len, task_g, round == 1 ? n : 0);
+    batch_update_kernel<<<upd_blocks, kBThreads, 0, s>>>(ctl, gs, gid, rp, b->col_idx, D, bat, task_start,
+                                                     task_len, task_g, round == 1 ? n : 0, live);
     ++g_launches;
     batch_finalize_kernel<<<(G + 255) / 256, 256, 0, s>>>(ctl, gs, G);
     ++g_launches;
@@ -389,7 +399,7 @@ gc_status batch_color(gc_context* ctx, const gc_batch_csr* b, const gc_job* jobs
     ctx->stats.sum_decrements = static_cast<int64_t>(pl[1]);
   }
   if (n == 0) return GC_OK;
-  batch_tie_kernel<<<blocks, 256, 0, s>>>(gs, off, G, n, tiev);
+  batch_tie_kernel<<<blocks, 256, 0, s>>>(gs, off, gid, n, tiev);
   ++g_launches;
   GC_TRY_CUDA(cudaGetLastError());
 
@@ -405,7 +415,7 @@ gc_status batch_color(gc_context* ctx, const gc_batch_csr* b, const gc_job* jobs
 
   if (num_colors_out || num_rounds_out) {
     if (num_colors_out) GC_TRY_CUDA(cudaMemsetAsync(num_colors_out, 0, sizeof(int) * G, s));
-    batch_results_kernel<<<blocks, 256, 0, s>>>(gs, off, G, n, color_out, num_colors_out, num_rounds_out);
+    batch_results_kernel<<<blocks, 256, 0, s>>>(gs, gid, G, n, color_out, num_colors_out, num_rounds_out);
     ++g_launches;
     GC_TRY_CUDA(cudaGetLastError());
     GC_TRY_CUDA(cudaStreamSynchronize(s));

@@ -652,6 +652,44 @@ def measure_batch(w, dev, steps, warmup, options=None, world=1, tune_cache=None)
     }
 
 
+def run_batch_path(args):
+    """One path of gc_color_batch on the batch workload, nothing else: W
+    warm-up calls, then K timed calls (CUDA events).  For profiling a path's
+    kernels; the default batch line compares both paths, the tuned options
+    and per-graph calls."""
+    import torch
+    import graphgen as gg
+    from paper_2008_11321_gb300 import _build
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    _build.build()
+    import paper_2008_11321_gb300 as gcp
+    w = WORKLOADS[args.workload]
+    G = w["count"]
+    g, off = gg.batch(G, w["n_lo"], w["n_hi"], w["seed"])
+    p, q = w["eps"]
+    jobs = [(p, q, w["seed"] + i) for i in range(G)]
+    db = gcp.DeviceBatch(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col_idx).to(dev),
+                         torch.from_numpy(off).to(dev))
+    color = torch.empty(db.n, dtype=torch.int32, device=dev)
+    ncol = torch.empty(G, dtype=torch.int32, device=dev)
+    mode = gcp.GC_BATCH_PERSISTENT if args.batch_path == "persistent" else gcp.GC_BATCH_SEGMENTED
+    ctx = gcp.Context(0, dict(args.options or {}, batch_mode=mode))
+    for _ in range(args.warmup):
+        ctx.gc_color_batch(db, jobs, color, None, ncol)
+    torch.cuda.synchronize()
+    t = _timed(torch.cuda.current_stream(dev), lambda: ctx.gc_color_batch(db, jobs, color, None, ncol),
+               args.steps) / args.steps
+    st = ctx.gc_get_stats()
+    ctx.close()
+    print(json.dumps({"metric": METRIC, "value": G / t, "unit": "graphs/s", "n_gpus": 1, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+                      "config": {"workload": w["desc"], "path": args.batch_path, "graphs": G, "n": db.n,
+                                 "m": db.nnz // 2},
+                      "gpu_launches": st.launches * args.steps}), flush=True)
+    return 0
+
+
 def run_batch(args, rank, world):
     """Batched form: gc_color_batch colours every graph of the packed batch
     (with the autotuned options: the persistent one-launch path or the
@@ -859,6 +897,9 @@ def main():
     ap.add_argument("--options", default=None,
                     help="gc_options fields for the context, as JSON (e.g. '{\"jp_state16\": 0}'); default: "
                          "the library's defaults")
+    ap.add_argument("--batch-path", choices=["persistent", "segmented"], default=None,
+                    help="batch workload only: time just this path of gc_color_batch (no tuning, no per-graph "
+                         "or end-to-end comparison), e.g. to profile it")
     ap.add_argument("--algo", choices=["jp", "dec-itr", "itr"], default="jp",
                     help="colouring: jp (JP with --priority, the default), dec-itr (DEC-ADG-ITR) or itr "
                          "(its SIM-COL on one partition: plain ITR)")
@@ -885,6 +926,10 @@ def main():
         if args.priority not in ("adg-m", "adg-o"):
             return run_variant(args, rank, world)
     if WORKLOADS[args.workload]["kind"] == "batch":
+        if args.batch_path:
+            if world > 1:
+                ap.error("--batch-path times one GPU")
+            return run_batch_path(args)
         return run_batch(args, rank, world)
     if WORKLOADS[args.workload]["kind"] == "serve":
         return run_serve(args, rank, world)

@@ -135,12 +135,8 @@ batch_partition_kernel(BCtl* __restrict__ ctl, BGraph* __restrict__ gs, const in
     // 32 j + 31: blocks start at multiples of 32), later rounds clear bits
     if (first) {
       if (lane == 0 && active) live[i >> 5] = km;
-    } else if (rm) {
-      // lanes clearing bits of one word (the list keeps ids mostly
-      // increasing) merge them: one atomic per word and warp
-      const unsigned wgrp = __match_any_sync(kFull, in_r ? (u >> 5) : -1 - lane);
-      const unsigned bits = __reduce_or_sync(wgrp, in_r ? 1u << (u & 31) : 0u);
-      if (in_r && (wgrp & lt) == 0) atomicAnd(&live[u >> 5], ~bits);
+    } else if (in_r) {
+      atomicAnd(&live[u >> 5], ~(1u << (u & 31)));
     }
     const unsigned long long dsum = group_sum(grp, in_r ? static_cast<unsigned long long>(d) : 0ull);
     if (in_r) {

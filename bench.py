@@ -95,7 +95,13 @@ def path_bytes(n, nnz, sum_u, decrements):
 # entry carries the SHA-256 prefix of the source file the kernel was built
 # from at capture time; once that file changes the figure no longer
 # describes the kernel and kernel_traffic() reports None.
-KERNEL_TRAFFIC = {}
+KERNEL_TRAFFIC = {
+    # R-MAT scale 24, the fourth call of `bench.py --steps 1 --warmup 3`; mean
+    # over the launches of one call (4 bulk, 7 UPDATE, 1 core)
+    ("rmat24", "jp_color_kernel"): (1129621952, "gc_jp.cu", "7e2afc01f602e17b"),
+    ("rmat24", "adg_update_kernel"): (354744137, "gc_adg.cu", "76112c885a71ecc2"),
+    ("rmat24", "jpf_core_solve_kernel"): (34953216, "gc_jp.cu", "7e2afc01f602e17b"),
+}
 
 
 def kernel_traffic(workload, kernel):

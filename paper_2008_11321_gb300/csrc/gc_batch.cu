@@ -52,8 +52,9 @@ __device__ __forceinline__ int threshold_of(unsigned long long sigma, int size_u
 
 __global__ void batch_init_kernel(BGraph* __restrict__ gs, const gc_job* __restrict__ jobs, int G,
                                   const long long* __restrict__ off, const long long* __restrict__ row_ptr,
-                                  BCtl* ctl) {
+                                  BCtl* ctl, unsigned long long* __restrict__ seeds) {
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+    seeds[g] = jobs[g].seed;
     BGraph b{};
     const long long n = off[g + 1] - off[g];
     b.sigma = static_cast<unsigned long long>(row_ptr[off[g + 1]] - row_ptr[off[g]]);
@@ -309,7 +310,8 @@ gc_status batch_color(gc_context* ctx, const gc_batch_csr* b, const gc_job* jobs
   const size_t vb = (static_cast<size_t>(n > 0 ? n : 1) * 4 + 255) & ~size_t(255);
   const size_t gb = (static_cast<size_t>(G) * sizeof(BGraph) + 255) & ~size_t(255);
   const size_t jb = (static_cast<size_t>(G) * sizeof(gc_job) + 255) & ~size_t(255);
-  GC_TRY(ctx->reserve_vert(4 * vb + gb + jb));
+  const size_t sb = (static_cast<size_t>(G) * sizeof(unsigned long long) + 255) & ~size_t(255);
+  GC_TRY(ctx->reserve_vert(4 * vb + gb + jb + sb));
   char* vbase = static_cast<char*>(ctx->vbuf);
   int* D = reinterpret_cast<int*>(vbase);
   int* bat = batch_out ? batch_out : reinterpret_cast<int*>(vbase + vb);
@@ -317,6 +319,7 @@ gc_status batch_color(gc_context* ctx, const gc_batch_csr* b, const gc_job* jobs
   BGraph* gs = reinterpret_cast<BGraph*>(vbase + 3 * vb);
   gc_job* djobs = reinterpret_cast<gc_job*>(vbase + 3 * vb + gb);
   int* gid = reinterpret_cast<int*>(vbase + 3 * vb + gb + jb);
+  unsigned long long* seeds = reinterpret_cast<unsigned long long*>(vbase + 4 * vb + gb + jb);
   GC_TRY_CUDA(cudaMemcpyAsync(djobs, jobs, sizeof(gc_job) * G, cudaMemcpyHostToDevice, s));
   // One persistent launch (a block per graph, gc_batch_persist.cu) when no
   // graph is too large for one block: at most 4 times an SM's share of the
@@ -351,7 +354,7 @@ gc_status batch_color(gc_context* ctx, const gc_batch_csr* b, const gc_job* jobs
   if (n > 0) GC_TRY_CUDA(cudaMemsetAsync(bat, 0, sizeof(int) * n, s));  // 0 = still in U
   const int blocks = ctx->num_sms * 8;
   const int upd_blocks = resident_grid(batch_update_kernel, kBThreads, ctx->num_sms);
-  batch_init_kernel<<<(G + 255) / 256, 256, 0, s>>>(gs, djobs, G, off, rp, ctl);
+  batch_init_kernel<<<(G + 255) / 256, 256, 0, s>>>(gs, djobs, G, off, rp, ctl, seeds);
   ++g_launches;
   batch_gid_kernel<<<G < 65535 ? G : 65535, 256, 0, s>>>(off, G, gid);
   ++g_launches;
@@ -395,9 +398,11 @@ gc_status batch_color(gc_context* ctx, const gc_batch_csr* b, const gc_job* jobs
     ctx->stats.sum_decrements = static_cast<int64_t>(pl[1]);
   }
   if (n == 0) return GC_OK;
-  batch_tie_kernel<<<blocks, 256, 0, s>>>(gs, off, gid, n, tiev);
-  ++g_launches;
-  GC_TRY_CUDA(cudaGetLastError());
+  if (round > 255) {  // the fallback key reads rho_R per vertex
+    batch_tie_kernel<<<blocks, 256, 0, s>>>(gs, off, gid, n, tiev);
+    ++g_launches;
+    GC_TRY_CUDA(cudaGetLastError());
+  }
 
   // JP on the union
   gc_csr u;
@@ -407,7 +412,7 @@ gc_status batch_color(gc_context* ctx, const gc_batch_csr* b, const gc_job* jobs
   u.col_idx = b->col_idx;
   GC_TRY(ctx->reserve(jpadg_scratch_bytes(n, nnz, round)));
   int colors = 0;
-  GC_TRY(jp_run_packed(ctx, ctx->arena(), &u, bat, tiev, D, round, color_out, &colors, s));
+  GC_TRY(jp_run_packed(ctx, ctx->arena(), &u, bat, gid, seeds, off, tiev, D, round, color_out, &colors, s));
 
   if (num_colors_out || num_rounds_out) {
     if (num_colors_out) GC_TRY_CUDA(cudaMemsetAsync(num_colors_out, 0, sizeof(int) * G, s));

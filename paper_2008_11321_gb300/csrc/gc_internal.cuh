@@ -210,9 +210,13 @@ gc_status batch_color_persistent(gc_context* ctx, Arena a, const gc_batch_csr* b
                                  const int* order, int32_t* color_out, int32_t* batch_out, int32_t* num_colors_out,
                                  int32_t* num_rounds_out, cudaStream_t s);
 
-// JP-ADG on the disjoint union of many graphs: tiev[v] is v's tie-break.
-gc_status jp_run_packed(gc_context* ctx, Arena a, const gc_csr* g, const int* batch, const unsigned* tiev,
-                        const int* D, int rounds, int* color, int* num_colors_out, cudaStream_t s);
+// JP-ADG on the disjoint union of many graphs.  Vertex v of graph gid[v]
+// (first vertex off[gid[v]]) has the tie-break rho_R of its own graph's seed,
+// seed[gid[v]], and its id inside the graph; runs of more than 255 rounds
+// need tiev[v], that tie-break precomputed (else tiev may be null).
+gc_status jp_run_packed(gc_context* ctx, Arena a, const gc_csr* g, const int* batch, const int* gid,
+                        const unsigned long long* seed, const long long* off, const unsigned* tiev, const int* D,
+                        int rounds, int* color, int* num_colors_out, cudaStream_t s);
 // Options (gc_tune.cu): apply range-checked options to a context; the
 // autotuner times run() (one colouring into its argument, n ints) under
 // candidate options and leaves the fastest applied.

@@ -163,15 +163,22 @@ struct KeyPacked {  // JP-ADG over many disjoint graphs: rho_R precomputed per v
 };
 
 // JP-ADG over many disjoint graphs with the batch kept in the top 8 bits of
-// the colour word (batches up to 255) and rho_R precomputed per vertex (each
-// graph has its own seed): one load of a neighbour's word gives its batch and
-// colour, and its rho_R is read only when the batches are equal.
-struct KeyStateT {
+// the colour word (batches up to 255): one load of a neighbour's word gives
+// its batch and colour.  rho_R of a vertex comes from its graph's seed and
+// its id inside the graph; a neighbour is in the same graph (no edge joins
+// two graphs), so its rho_R -- needed only when the batches are equal -- is
+// computed from the vertex's own graph, with no load of the neighbour's.
+struct KeyStateG {
   using W = int;
   const int* state;  // the colour array during JP
-  const unsigned* tiev;
+  const int* gid;    // graph of each vertex
+  const unsigned long long* seed;  // per graph
+  const long long* off;            // first vertex of each graph
   __device__ __forceinline__ int bat(int v) const { return static_cast<int>(static_cast<unsigned>(state[v]) >> 24); }
-  __device__ __forceinline__ unsigned tie(int v) const { return __ldg(tiev + v); }
+  __device__ __forceinline__ unsigned tie_in(int g, int v) const {
+    return tie_hash(__ldg(seed + g), static_cast<unsigned>(v - __ldg(off + g)));
+  }
+  __device__ __forceinline__ unsigned tie(int v) const { return tie_in(__ldg(gid + v), v); }
   __device__ __forceinline__ unsigned long long operator()(int v) const {
     return (static_cast<unsigned long long>(static_cast<unsigned>(bat(v))) << 32) | tie(v);
   }
@@ -180,7 +187,7 @@ struct KeyStateT {
   __device__ __forceinline__ bool pred_g(PG x, int w, unsigned long long kv, int v) const {
     const unsigned bw = static_cast<unsigned>(x) >> 24, bv = static_cast<unsigned>(kv >> 32);
     if (bw != bv) return bw > bv;
-    const unsigned tw = tie(w), tv = static_cast<unsigned>(kv);
+    const unsigned tw = tie_in(__ldg(gid + v), w), tv = static_cast<unsigned>(kv);
     return tw > tv || (tw == tv && w > v);
   }
   __device__ __forceinline__ int color_g(PG x, const int*, int) const { return x & 0xffffff; }
@@ -1711,15 +1718,18 @@ gc_status jp_run_fused(gc_context* ctx, Arena a, const gc_csr* g, const int* bat
   return GC_OK;
 }
 
-gc_status jp_run_packed(gc_context* ctx, Arena a, const gc_csr* g, const int* batch, const unsigned* tiev,
-                        const int* D, int rounds, int* color, int* num_colors_out, cudaStream_t s) {
-  if (rounds > 255 || g->n == 0)
+gc_status jp_run_packed(gc_context* ctx, Arena a, const gc_csr* g, const int* batch, const int* gid,
+                        const unsigned long long* seed, const long long* off, const unsigned* tiev, const int* D,
+                        int rounds, int* color, int* num_colors_out, cudaStream_t s) {
+  if (rounds > 255 || g->n == 0) {
+    if (!tiev && g->n > 0) return GC_ERR_INVALID_ARG;
     return jp_adg_impl(ctx, a, g, KeyPacked{batch, tiev}, D, rounds, color, num_colors_out, s);
+  }
   const int blocks = ctx->num_sms * 8;
   state_init_kernel<<<blocks, 256, 0, s>>>(batch, g->n, color);
   ++g_launches;
   GC_TRY_CUDA(cudaGetLastError());
-  GC_TRY(jp_adg_impl(ctx, a, g, KeyStateT{color, tiev}, D, rounds, color, num_colors_out, s));
+  GC_TRY(jp_adg_impl(ctx, a, g, KeyStateG{color, gid, seed, off}, D, rounds, color, num_colors_out, s));
   state_strip_kernel<<<blocks, 256, 0, s>>>(g->n, color);
   ++g_launches;
   GC_TRY_CUDA(cudaGetLastError());

@@ -334,8 +334,9 @@ gc_status gc_color_graph_o(gc_context *ctx, const gc_csr *g, uint32_t eps_p, uin
  * the same or a higher partition; *num_colors_out (host, may be NULL) the
  * largest.  gc_stats.sim_iterations counts the SIM-COL iterations.
  * GC_ERR_INVALID_ARG if num_rounds < 1 (n > 0) or a batch lies outside
- * 1..num_rounds (then color_out is undefined).  Scratch: about
- * 4 nnz + 24 n bytes. */
+ * 1..num_rounds (then color_out is undefined).  Empty partitions cost no
+ * launches (the non-empty ones are read back once).  Scratch: about
+ * 4 nnz + 24 n + 132 num_rounds bytes. */
 gc_status gc_dec_itr_color(gc_context *ctx, const gc_csr *g, const int32_t *batch, int32_t num_rounds,
                            uint64_t seed, int32_t *color_out, int32_t *num_colors_out, gc_stream stream);
 

@@ -48,6 +48,8 @@
 // launches iterations in growing chunks and reads |U| after each chunk.
 #include <cstring>
 
+#include <vector>
+
 #include "gc_internal.cuh"
 
 namespace gc {
@@ -1290,9 +1292,10 @@ int tail_cluster_size(gc_context* ctx) {
   return 0;
 }
 
+// levels: the non-empty partitions, highest first.
 template <bool Packed>
-gc_status dec_loop(gc_context* ctx, const DecArgs& A, PartRange* part, const int* order, int rounds,
-                   cudaStream_t s) {
+gc_status dec_loop(gc_context* ctx, const DecArgs& A, PartRange* part, const int* order,
+                   const std::vector<int>& levels, cudaStream_t s) {
   const int sms = ctx->num_sms;
   const int tail_c = ctx->dec_tail ? tail_cluster_size(ctx) : 0;
   const int gx = resident_grid(dec_extract_kernel<Packed>, kDecThreads, sms);
@@ -1300,7 +1303,7 @@ gc_status dec_loop(gc_context* ctx, const DecArgs& A, PartRange* part, const int
   const int gp = resident_grid(dec_pick_kernel<Packed>, kDecThreads, sms);
   unsigned long long* pinned = static_cast<unsigned long long*>(ctx->pinned);
   int slot = 0;
-  for (int l = rounds; l >= 1; --l) {
+  for (const int l : levels) {
     ctx->timer_begin(gc_context::kTDecExtract, s);
     dec_extract_kernel<Packed><<<gx, kDecThreads, 0, s>>>(A, part, l, order, slot);
     ctx->timer_end(s);
@@ -1424,6 +1427,16 @@ gc_status dec_itr_run(gc_context* ctx, Arena a, const gc_csr* g, const int* batc
     g_launches += 5;
     GC_TRY_CUDA(cudaGetLastError());
   }
+  // the partitions that hold vertices: a caller's batch array may leave many
+  // of 1..num_rounds empty, and each would still cost launches and a read-back
+  std::vector<int> levels;
+  {
+    std::vector<int> hp(static_cast<size_t>(rounds) + 1);
+    GC_TRY_CUDA(cudaMemcpyAsync(hp.data(), present, sizeof(int) * hp.size(), cudaMemcpyDeviceToHost, s));
+    GC_TRY_CUDA(cudaStreamSynchronize(s));
+    for (int l = rounds; l >= 1; --l)
+      if (hp[l]) levels.push_back(l);
+  }
   DecArgs A{};
   A.row_ptr = rp;
   A.col = g->col_idx;
@@ -1442,9 +1455,9 @@ gc_status dec_itr_run(gc_context* ctx, Arena a, const gc_csr* g, const int* batc
   A.ctl = ctl;
   A.seed = seed;
   if (packed)
-    GC_TRY(dec_loop<true>(ctx, A, part, order, rounds, s));
+    GC_TRY(dec_loop<true>(ctx, A, part, order, levels, s));
   else
-    GC_TRY(dec_loop<false>(ctx, A, part, order, rounds, s));
+    GC_TRY(dec_loop<false>(ctx, A, part, order, levels, s));
   if (packed) {
     const int grid = resident_grid(dec_strip_kernel, 256, ctx->num_sms);
     dec_strip_kernel<<<grid, 256, 0, s>>>(n, color);

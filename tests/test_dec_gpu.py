@@ -149,6 +149,23 @@ def test_dec_itr_given_partitions(ctx):
         assert np.array_equal(c, oc) and nc == onc and it == oit, g.name
 
 
+def test_dec_itr_sparse_partition_ids(ctx):
+    # 3 non-empty partitions numbered up to 200,000 of num_rounds = 250,000:
+    # only the partitions that hold vertices are visited (the call returns
+    # quickly), and the colouring is the one of the same partitions
+    # numbered 1..3, with the same iteration count
+    import time
+    g = gg.barabasi_albert(20000, 6, 5)
+    dense = (np.random.default_rng(5).integers(1, 4, g.n)).astype(np.int32)
+    sparse = np.array([0, 7, 90000, 200000], dtype=np.int32)[dense]
+    oc, onc, oit, _ = oracle.dec_itr(g, dense, 3, 11)
+    t0 = time.perf_counter()
+    c, nc, it = _given(ctx, g, sparse, 250000, 11)
+    elapsed = time.perf_counter() - t0
+    assert np.array_equal(c, oc) and nc == onc and it == oit
+    assert elapsed < 10.0
+
+
 def test_itr_one_partition(ctx):
     # every vertex in one partition: plain ITR, the paper's comparison point
     for g in (gg.rmat(16, 16, seed=4), gg.barabasi_albert(20000, 8, 1), complete(200)):

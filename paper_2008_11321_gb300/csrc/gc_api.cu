@@ -297,6 +297,7 @@ gc_status gc_options_init(gc_options* opt) {
   o.batch_mode = GC_BATCH_AUTO;
   o.update_hubs = 512;
   o.host_upload = 1;
+  o.round_graph = 1;
   *opt = o;
   return GC_OK;
 }
@@ -321,7 +322,7 @@ gc_status read_options(const gc_options* opt, gc_options* out) {
       o.pull_percent > 100000 || o.bulk_blocks_per_sm < 0 || o.bulk_blocks_per_sm > 32 || o.wait_limit_ms < 1 ||
       o.wait_limit_ms > 600000 || (o.jp_state16 != 0 && o.jp_state16 != 1) || o.batch_mode < GC_BATCH_AUTO ||
       o.batch_mode > GC_BATCH_PERSISTENT || o.update_hubs < 0 || o.update_hubs > 4096 ||
-      (o.host_upload != 0 && o.host_upload != 1))
+      (o.host_upload != 0 && o.host_upload != 1) || (o.round_graph != 0 && o.round_graph != 1))
     return GC_ERR_INVALID_ARG;
   *out = o;
   return GC_OK;
@@ -384,6 +385,7 @@ void gc_destroy(gc_context* ctx) {
   if (ctx->aux) cudaFree(ctx->aux);
   if (ctx->pack) cudaFree(ctx->pack);
   if (ctx->h_graph) cudaFree(ctx->h_graph);
+  gc::batch_graph_free(ctx);
   for (auto& e : ctx->copy_ev)
     if (e) cudaEventDestroy(e);
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
@@ -765,6 +767,7 @@ gc_status gc_color_graph_host(gc_context* ctx, int64_t n, int64_t nnz, const int
   const size_t need = b_rp + b_ci + 2 * b_v + 256;
   if (need > ctx->h_graph_bytes) {
     if (ctx->h_graph) cudaFree(ctx->h_graph);
+  gc::batch_graph_free(ctx);
     ctx->h_graph = nullptr;
     ctx->h_graph_bytes = 0;
     if (cudaMalloc(&ctx->h_graph, need) != cudaSuccess) {

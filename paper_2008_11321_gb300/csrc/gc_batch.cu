@@ -37,6 +37,8 @@ struct BGraph {
 struct BCtl {
   int round;        // global round (the round of every graph still running)
   int size_Unext;   // survivors over all graphs
+  int size_U;       // |U| over all graphs in the current round (from round 2 on)
+  int err;          // a round that removed no vertex (cannot happen)
   unsigned long long ntasks;
   unsigned long long total_U;    // sum over graphs and rounds of |U|
   unsigned long long total_dec;  // sum over graphs and rounds of the cut
@@ -52,7 +54,7 @@ __device__ __forceinline__ int threshold_of(unsigned long long sigma, int size_u
 
 __global__ void batch_init_kernel(BGraph* __restrict__ gs, const gc_job* __restrict__ jobs, int G,
                                   const long long* __restrict__ off, const long long* __restrict__ row_ptr,
-                                  BCtl* ctl, unsigned long long* __restrict__ seeds) {
+                                  BCtl* ctl, unsigned long long* __restrict__ seeds, long long n_total) {
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
     seeds[g] = jobs[g].seed;
     BGraph b{};
@@ -69,6 +71,7 @@ __global__ void batch_init_kernel(BGraph* __restrict__ gs, const gc_job* __restr
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     BCtl c{};
     c.round = 1;
+    c.size_U = static_cast<int>(n_total);
     *ctl = c;
   }
 }
@@ -96,6 +99,7 @@ batch_partition_kernel(BCtl* __restrict__ ctl, BGraph* __restrict__ gs, const in
                        long long* __restrict__ task_start, int* __restrict__ task_len,
                        int* __restrict__ task_g, long long size_u, unsigned* __restrict__ live) {
   const int round = ctl->round;
+  if (size_u < 0) size_u = ctl->size_U;  // the graph-launched rounds
   const bool first = round == 1;
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
@@ -248,10 +252,29 @@ __global__ void batch_finalize_kernel(BCtl* ctl, BGraph* __restrict__ gs, int G)
   }
 }
 
-__global__ void batch_next_round_kernel(BCtl* ctl) {
+// After a round: the survivors become U.  In the graph-launched loop the
+// kernel also decides whether the loop goes on (a round whose U was already
+// empty changed nothing and ends it; so does a round that removed no vertex,
+// which cannot happen and is reported).
+__device__ __forceinline__ bool next_round(BCtl* ctl) {
+  const int prev = ctl->size_U, next = ctl->size_Unext;
+  if (prev == 0) return false;
+  if (next >= prev) {
+    ctl->err = 1;
+    ctl->size_U = 0;
+    return false;
+  }
   ctl->round += 1;
+  ctl->size_U = next;
   ctl->size_Unext = 0;
   ctl->ntasks = 0;
+  return next > 0;
+}
+
+__global__ void batch_next_round_kernel(BCtl* ctl) { next_round(ctl); }
+
+__global__ void batch_next_round_graph_kernel(BCtl* ctl, cudaGraphConditionalHandle loop) {
+  cudaGraphSetConditional(loop, next_round(ctl) ? 1u : 0u);
 }
 
 // rho_R of every vertex from its graph's seed and its id inside the graph.
@@ -286,7 +309,128 @@ __global__ void batch_results_kernel(const BGraph* __restrict__ gs, const int* _
       nrounds[g] = gs[g].rounds;
 }
 
+// The ADG rounds from round 2 on as one CUDA graph: a while node whose body
+// holds two rounds (partition, UPDATE, finalize, next round), the first
+// reading U from ubuf[0] and writing U' to ubuf[1], the second the other way
+// round, so every kernel argument is fixed; the partition reads |U| from the
+// control block, and each round's last kernel sets the loop condition.  A
+// round whose U is already empty is a no-op.  The instantiated graph is kept
+// by the context and launched again while the buffers and shapes are the
+// same.
+struct BatchGraphKey {
+  const void* p[13];
+  long long i[3];
+  bool operator==(const BatchGraphKey& o) const { return memcmp(this, &o, sizeof(*this)) == 0; }
+};
+
+struct BatchGraph {
+  BatchGraphKey key{};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+void batch_graph_release(BatchGraph* bg) {
+  if (!bg) return;
+  if (bg->exec) cudaGraphExecDestroy(bg->exec);
+  if (bg->graph) cudaGraphDestroy(bg->graph);
+  bg->exec = nullptr;
+  bg->graph = nullptr;
+}
+
+struct RoundArgs {
+  BCtl* ctl;
+  BGraph* gs;
+  const int* gid;
+  const long long* rp;
+  const int* col;
+  int* D;
+  int* bat;
+  int* ubuf[2];
+  long long* task_start;
+  int* task_len;
+  int* task_g;
+  unsigned* live;
+  int G, pblocks, upd_blocks;
+};
+
+// Builds (or reuses) the loop graph; cudaSuccess with *exec set, or an
+// error (the caller then runs the rounds from the host).
+cudaError_t batch_round_graph(gc_context* ctx, const RoundArgs& r, cudaGraphExec_t* exec) {
+  BatchGraphKey key{};
+  const void* ptrs[13] = {r.ctl, r.gs, r.gid, r.rp, r.col, r.D, r.bat, r.ubuf[0], r.ubuf[1], r.task_start,
+                          r.task_len, r.task_g, r.live};
+  memcpy(key.p, ptrs, sizeof(ptrs));
+  key.i[0] = r.G;
+  key.i[1] = r.pblocks;
+  key.i[2] = r.upd_blocks;
+  BatchGraph* bg = static_cast<BatchGraph*>(ctx->batch_graph);
+  if (bg && bg->exec && bg->key == key) {
+    *exec = bg->exec;
+    return cudaSuccess;
+  }
+  if (!bg) {
+    bg = new (std::nothrow) BatchGraph();
+    if (!bg) return cudaErrorMemoryAllocation;
+    ctx->batch_graph = bg;
+  }
+  batch_graph_release(bg);
+  cudaGraph_t graph = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  cudaError_t e = cudaGraphCreate(&graph, 0);
+  do {
+    if (e != cudaSuccess) break;
+    cudaGraphConditionalHandle loop;
+    if ((e = cudaGraphConditionalHandleCreate(&loop, graph, 1, cudaGraphCondAssignDefault)) != cudaSuccess) break;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = loop;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp)) != cudaSuccess) break;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) break;
+    if ((e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+        cudaSuccess)
+      break;
+    for (int half = 0; half < 2; ++half) {
+      batch_partition_kernel<<<r.pblocks, kBThreads, 0, cs>>>(r.ctl, r.gs, r.gid, r.rp, r.D, r.bat, r.ubuf[half],
+                                                              r.ubuf[half ^ 1], r.task_start, r.task_len, r.task_g,
+                                                              -1, r.live);
+      batch_update_kernel<<<r.upd_blocks, kBThreads, 0, cs>>>(r.ctl, r.gs, r.gid, r.rp, r.col, r.D, r.bat,
+                                                              r.task_start, r.task_len, r.task_g, 0, r.live);
+      batch_finalize_kernel<<<(r.G + 255) / 256, 256, 0, cs>>>(r.ctl, r.gs, r.G);
+      batch_next_round_graph_kernel<<<1, 1, 0, cs>>>(r.ctl, loop);
+    }
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(cs, &captured);
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = ec) != cudaSuccess) break;
+    e = cudaGraphInstantiate(&ex, graph, 0);
+  } while (false);
+  if (cs) cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (ex) cudaGraphExecDestroy(ex);
+    if (graph) cudaGraphDestroy(graph);
+    return e;
+  }
+  bg->key = key;
+  bg->graph = graph;
+  bg->exec = ex;
+  *exec = ex;
+  return cudaSuccess;
+}
+
 }  // namespace
+
+void batch_graph_free(gc_context* ctx) {
+  BatchGraph* bg = static_cast<BatchGraph*>(ctx->batch_graph);
+  if (!bg) return;
+  batch_graph_release(bg);
+  delete bg;
+  ctx->batch_graph = nullptr;
+}
 
 size_t batch_adg_scratch_bytes(long long n, long long nnz, long long G) {
   const long long ntask = n + nnz / kChunk + 1;
@@ -354,7 +498,7 @@ gc_status batch_color(gc_context* ctx, const gc_batch_csr* b, const gc_job* jobs
   if (n > 0) GC_TRY_CUDA(cudaMemsetAsync(bat, 0, sizeof(int) * n, s));  // 0 = still in U
   const int blocks = ctx->num_sms * 8;
   const int upd_blocks = resident_grid(batch_update_kernel, kBThreads, ctx->num_sms);
-  batch_init_kernel<<<(G + 255) / 256, 256, 0, s>>>(gs, djobs, G, off, rp, ctl, seeds);
+  batch_init_kernel<<<(G + 255) / 256, 256, 0, s>>>(gs, djobs, G, off, rp, ctl, seeds, n);
   ++g_launches;
   batch_gid_kernel<<<G < 65535 ? G : 65535, 256, 0, s>>>(off, G, gid);
   ++g_launches;
@@ -367,6 +511,22 @@ gc_status batch_color(gc_context* ctx, const gc_batch_csr* b, const gc_job* jobs
   int* pin = static_cast<int*>(ctx->pinned);
   while (size_u > 0) {
     ++round;
+    if (round == 2 && ctx->opt.round_graph) {
+      // rounds 2.. as one graph launch (no host round trip per round)
+      RoundArgs ra{ctl, gs, gid, rp, b->col_idx, D, bat, {ubuf[0], ubuf[1]}, task_start, task_len, task_g,
+                   live, G, blocks, upd_blocks};
+      cudaGraphExec_t ex = nullptr;
+      if (cur == 1 && batch_round_graph(ctx, ra, &ex) == cudaSuccess) {
+        GC_TRY_CUDA(cudaGraphLaunch(ex, s));
+        GC_TRY_CUDA(cudaMemcpyAsync(pin, &ctl->round, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        GC_TRY_CUDA(cudaStreamSynchronize(s));
+        if (pin[3]) return GC_ERR_CUDA;  // a round removed no vertex: cannot happen
+        const int last = pin[0] - 1;     // each round that ran advanced the round number
+        g_launches += 8ull * static_cast<unsigned long long>((last - 1 + 1) / 2);
+        round = last;
+        break;
+      }
+    }
     const long long want = (size_u + kBThreads - 1) / kBThreads;
     const int pblocks = static_cast<int>(want < blocks ? want : blocks);
     batch_partition_kernel<<<pblocks, kBThreads, 0, s>>>(ctl, gs, gid, rp, D, bat,

@@ -210,6 +210,9 @@ gc_status batch_color_persistent(gc_context* ctx, Arena a, const gc_batch_csr* b
                                  const int* order, int32_t* color_out, int32_t* batch_out, int32_t* num_colors_out,
                                  int32_t* num_rounds_out, cudaStream_t s);
 
+// Frees the context's batch round-loop graph (gc_batch.cu).
+void batch_graph_free(gc_context* ctx);
+
 // JP-ADG on the disjoint union of many graphs.  Vertex v of graph gid[v]
 // (first vertex off[gid[v]]) has the tie-break rho_R of its own graph's seed,
 // seed[gid[v]], and its id inside the graph; runs of more than 255 rounds
@@ -276,6 +279,8 @@ struct gc_context {
   void* h_graph = nullptr;
   size_t h_graph_bytes = 0;
   cudaStream_t copy_stream = nullptr;
+  // the segmented batch path's round-loop graph (gc_batch.cu)
+  void* batch_graph = nullptr;
   cudaEvent_t copy_ev[gc::kUploadChunks + 1] = {};  // per range, then "the device buffers are free"
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   // kernel-group timers: event pairs recorded around launches when timing is

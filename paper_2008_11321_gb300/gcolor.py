@@ -64,7 +64,7 @@ class gc_options(ctypes.Structure):
                 ("update_mode", ctypes.c_int32), ("pull_percent", ctypes.c_int32),
                 ("bulk_blocks_per_sm", ctypes.c_int32), ("wait_limit_ms", ctypes.c_uint32),
                 ("jp_state16", ctypes.c_int32), ("batch_mode", ctypes.c_int32), ("update_hubs", ctypes.c_int32),
-                ("host_upload", ctypes.c_int32)]
+                ("host_upload", ctypes.c_int32), ("round_graph", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "struct_size"}

@@ -117,14 +117,14 @@ def test_options_defaults_and_range_checks(lib):
                            "update_mode": gcp.GC_UPDATE_AUTO, "pull_percent": 25, "bulk_blocks_per_sm": 0,
                            "wait_limit_ms": 4000, "jp_state16": 0,
                            "batch_mode": gcp.GC_BATCH_AUTO, "update_hubs": 512,
-                           "host_upload": 1}
+                           "host_upload": 1, "round_graph": 1}
     h = ctypes.c_void_p()
     bad = [dict(core_target=-1), dict(core_target=32769), dict(core_cluster=0), dict(core_cluster=17),
            dict(core_warps=0), dict(core_warps=33), dict(dec_tail=2), dict(update_mode=3),
            dict(pull_percent=-1), dict(bulk_blocks_per_sm=33), dict(wait_limit_ms=0),
            dict(wait_limit_ms=600001), dict(jp_state16=2),
            dict(batch_mode=3), dict(update_hubs=-1), dict(update_hubs=4097),
-           dict(host_upload=2)]
+           dict(host_upload=2), dict(round_graph=2)]
     for fields in bad:
         o = gcp.make_options(**fields)
         assert lib.gc_create(ctypes.byref(h), 0, ctypes.byref(o)) == gcp.GC_ERR_INVALID_ARG, fields

@@ -18,16 +18,20 @@ pytestmark = pytest.mark.gpu
 import paper_2008_11321_gb300 as gcp  # noqa: E402
 
 
-MODES = {"auto": gcp.GC_BATCH_AUTO, "segmented": gcp.GC_BATCH_SEGMENTED, "persistent": gcp.GC_BATCH_PERSISTENT}
+MODES = {"auto": gcp.GC_BATCH_AUTO, "segmented": gcp.GC_BATCH_SEGMENTED, "persistent": gcp.GC_BATCH_PERSISTENT,
+         "segmented-host-rounds": gcp.GC_BATCH_SEGMENTED}
 
 
 @pytest.fixture(scope="module", params=sorted(MODES))
 def ctx(request):
+    # the segmented path runs ADG's rounds from round 2 on as one CUDA graph
+    # launch by default; "segmented-host-rounds" launches each round from
+    # the host (round_graph 0)
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2008_11321_gb300 import _build
     _build.build()
-    c = gcp.Context(0, {"batch_mode": MODES[request.param]})
+    c = gcp.Context(0, {"batch_mode": MODES[request.param], "round_graph": int(request.param != "segmented-host-rounds")})
     c.mode = MODES[request.param]
     yield c
     c.close()

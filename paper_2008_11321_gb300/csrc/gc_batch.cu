@@ -215,7 +215,7 @@ batch_update_kernel(BCtl* __restrict__ ctl, BGraph* __restrict__ gs, const int* 
         tg = task_g[t];
       }
     }
-    sweep_tile(
+    sweep_tile<4>(
         st, len, tg, col, [&](int w, int) { return (__ldg(live + (w >> 5)) >> (w & 31)) & 1u; },
         [&](int w, int g, unsigned lw) {
       if (lw) {  // w is still in U

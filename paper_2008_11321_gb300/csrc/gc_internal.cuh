@@ -454,9 +454,10 @@ __device__ __forceinline__ T warp_inclusive_scan(T v) {
 // that a lane has kSweepUnroll loads in flight at each step even where fn
 // writes memory (which could keep the compiler from moving the next edge's
 // gather ahead of it).
-template <class Gather, class Fn>
+template <int kU = kSweepUnroll, class Gather, class Fn>
 __device__ __forceinline__ void sweep_tile(long long st, int len, int tag, const int* __restrict__ col,
                                            Gather gather, Fn fn) {
+  constexpr int kSweepUnroll = kU;  // edges per lane and step
   const int lane = threadIdx.x & 31;
   const int incl = warp_inclusive_scan(len);
   const int total = __shfl_sync(kFull, incl, 31);

@@ -275,7 +275,8 @@ adg_update_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row_pt
     }
     // gathered per neighbour w: bit 0 live, bit 1 hub, bits 2.. the hubs
     // below w in its word
-    sweep_tile(
+    // the hub variant at 6 edges per lane and step stays at 40 registers
+    sweep_tile<kHubs ? 6 : 8>(
         st, len, 0, col,
         [&](int w, int) {
           const uint2 lw = __ldg(live + (w >> 5));

@@ -824,7 +824,9 @@ jpf_core_preds_kernel(const int* __restrict__ col, const unsigned* __restrict__ 
       len = task_len[t];
       ci = task_i[t];
     }
-    sweep_tile(
+    // 4 edges per lane and step: 36 registers (60 at 8), and 0.67 instead
+    // of 0.83 ms on R-MAT 24
+    sweep_tile<4>(
         st, len, ci, col, [&](int w, int) { return static_cast<int>((__ldg(cbits + (w >> 5)) >> (w & 31)) & 1u); },
         [&](int w, int i, int in_core) {
           const int lw = in_core ? __ldg(lid + w) : 0;

@@ -314,9 +314,11 @@ __global__ void batch_results_kernel(const BGraph* __restrict__ gs, const int* _
 // reading U from ubuf[0] and writing U' to ubuf[1], the second the other way
 // round, so every kernel argument is fixed; the partition reads |U| from the
 // control block, and each round's last kernel sets the loop condition.  A
-// round whose U is already empty is a no-op.  The instantiated graph is kept
-// by the context and launched again while the buffers and shapes are the
-// same.
+// round whose U is already empty is a no-op.  The graph is built on the
+// second call in a row with the same buffers and shapes (building costs more
+// than a few host-driven rounds, so calls whose buffers change -- a server's
+// batches -- keep the host loop), kept by the context and launched again
+// while they stay the same.
 struct BatchGraphKey {
   const void* p[13];
   long long i[3];
@@ -324,7 +326,8 @@ struct BatchGraphKey {
 };
 
 struct BatchGraph {
-  BatchGraphKey key{};
+  BatchGraphKey key{};   // of the graph built
+  BatchGraphKey seen{};  // of the previous call
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
@@ -372,6 +375,10 @@ cudaError_t batch_round_graph(gc_context* ctx, const RoundArgs& r, cudaGraphExec
     bg = new (std::nothrow) BatchGraph();
     if (!bg) return cudaErrorMemoryAllocation;
     ctx->batch_graph = bg;
+  }
+  if (!(bg->seen == key)) {  // first call with these buffers: the host loop
+    bg->seen = key;
+    return cudaErrorNotReady;
   }
   batch_graph_release(bg);
   cudaGraph_t graph = nullptr;

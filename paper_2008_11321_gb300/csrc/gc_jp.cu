@@ -780,15 +780,18 @@ __global__ void jpf_core_tasks_kernel(const int* __restrict__ order, const long 
                                       const long long* __restrict__ toff, const JpCtl* ctl,
                                       int* __restrict__ task_i, long long* __restrict__ task_start,
                                       int* __restrict__ task_len) {
+  // a warp per core vertex: a hub's row of 10^5 entries is thousands of tasks
   const long long kc = static_cast<long long>(ctl->ncore);
-  for (long long i = gtid(); i < kc; i += gstride()) {
+  const int lane = threadIdx.x & 31;
+  for (long long i = gtid() >> 5; i < kc; i += gstride() >> 5) {
     const int v = order[i];
     const long long rs = row_ptr[v], re = row_ptr[v + 1];
-    long long t = toff[i];
-    for (long long st = rs; st < re; st += kChunk, ++t) {
-      task_i[t] = static_cast<int>(i);
-      task_start[t] = st;
-      task_len[t] = static_cast<int>(re - st < kChunk ? re - st : kChunk);
+    const long long t0 = toff[i];
+    for (long long c = lane; rs + c * kChunk < re; c += 32) {
+      const long long st = rs + c * kChunk;
+      task_i[t0 + c] = static_cast<int>(i);
+      task_start[t0 + c] = st;
+      task_len[t0 + c] = static_cast<int>(re - st < kChunk ? re - st : kChunk);
     }
   }
 }

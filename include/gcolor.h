@@ -185,9 +185,11 @@ typedef struct {
  * SEGMENTED runs ADG's rounds for all graphs together, one set of GPU-wide
  * launches per round, then one JP over the union; PERSISTENT is one launch
  * in which each thread block takes whole graphs from a queue (largest first)
- * and runs ADG and JP on each graph alone.  AUTO takes PERSISTENT unless one
- * graph holds more than 2^24 CSR entries or more than 4/num_SMs of the
- * batch's.  Results are identical. */
+ * and runs ADG and JP on each graph alone.  AUTO takes PERSISTENT only
+ * while every graph holds at most 1/1024 of the batch's CSR entries (and at
+ * most 2^24): one block colours a graph at a small fraction of the GPU's
+ * rate, so a large graph sets the persistent launch's time.  Results are
+ * identical. */
 enum { GC_BATCH_AUTO = 0, GC_BATCH_SEGMENTED = 1, GC_BATCH_PERSISTENT = 2 };
 
 /* Fill *opt with the defaults (and struct_size = sizeof(gc_options)). */

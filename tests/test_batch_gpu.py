@@ -129,9 +129,23 @@ def test_batch_list_entry_point(ctx):
         assert np.array_equal(o.cpu().numpy(), oracle.jp_adg(g, p, q, sd)[1])
 
 
+def test_auto_takes_persistent_for_many_small_graphs():
+    # every graph holds at most 1/1024 of the batch's entries: one launch
+    graphs = [gg.erdos_renyi(40, 100, 900 + i) for i in range(1500)]
+    jobs = [(1, 100, 5 + i) for i in range(len(graphs))]
+    with gcp.Context(0) as c:
+        c.mode = gcp.GC_BATCH_AUTO
+        color, batch, ncol, nrnd, voff = _run(c, graphs, jobs)
+        assert c.gc_get_stats().batch_path == gcp.GC_BATCH_PERSISTENT
+    for i in (0, 1, 700, 1499):
+        ob, oc, onr, onc = oracle.jp_adg(graphs[i], *jobs[i])
+        sl = slice(voff[i], voff[i + 1])
+        assert np.array_equal(batch[sl], ob) and np.array_equal(color[sl], oc), i
+
+
 def test_auto_falls_back_to_segmented_on_a_fresh_context():
-    # AUTO with one graph too large for a block (more than 4/num_SMs of the
-    # batch) in a multi-graph batch, on a fresh context: the persistent
+    # AUTO with one graph too large for a block (more than 1/1024 of the
+    # batch's entries) in a multi-graph batch, on a fresh context: the persistent
     # path's check grows the scratch, then the segmented path runs on the
     # grown scratch
     graphs = [gg.rmat(16, 16, seed=8), path(9), complete(6), gg.erdos_renyi(300, 900, 2)]

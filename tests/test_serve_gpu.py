@@ -57,9 +57,13 @@ def test_results_same_alone_and_in_the_mix():
     rng = np.random.default_rng(3)
     with ColoringServer(0, memory_budget=8 << 30) as srv:
         reqs = []
-        for g, eps, seed in reqs_in:  # Poisson arrivals while earlier requests run
+        # arrivals in bursts of 6 (Poisson gaps between bursts) while earlier
+        # requests run: a burst arrives faster than one request is coloured,
+        # so requests share batches however fast the device is
+        for i, (g, eps, seed) in enumerate(reqs_in):
             reqs.append(srv.submit(g.row_ptr, g.col_idx, eps[0], eps[1], seed))
-            time.sleep(rng.exponential(0.002))
+            if i % 6 == 5:
+                time.sleep(rng.exponential(0.002))
         results = [r.result(timeout=120) for r in reqs]
         batches = list(srv.batches)
     assert sum(b[1] for b in batches) == len(reqs_in)

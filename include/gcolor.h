@@ -176,9 +176,10 @@ typedef struct {
   int32_t round_graph;     /* gc_color_batch, segmented path: 1 (default) runs
                               ADG's rounds from round 2 on as one CUDA graph
                               launch (a device-side loop, no host round trip
-                              per round; built on the first call and kept by
-                              the context while the buffers are the same);
-                              0 launches each round from the host            */
+                              per round; built on the second call in a row
+                              with the same buffers and shapes, kept by the
+                              context while they stay the same); 0 launches
+                              each round from the host                       */
 } gc_options;
 
 /* How gc_color_batch runs (gc_options.batch_mode, gc_stats.batch_path):

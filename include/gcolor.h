@@ -173,13 +173,17 @@ typedef struct {
                               vertex ranges on a stream of the context and
                               ADG's first round sweeps each range once it
                               has arrived                                    */
-  int32_t round_graph;     /* gc_color_batch, segmented path: 1 (default) runs
-                              ADG's rounds from round 2 on as one CUDA graph
-                              launch (a device-side loop, no host round trip
-                              per round; built on the second call in a row
-                              with the same buffers and shapes, kept by the
-                              context while they stay the same); 0 launches
-                              each round from the host                       */
+  int32_t round_graph;     /* 1 (default) runs ADG's rounds from round 2 on
+                              as one CUDA graph launch (a device-side loop,
+                              no host round trip per round) in the segmented
+                              batch path and, while the context keeps no
+                              timers (gc_set_timing), in the calls that run
+                              ADG (gc_color_graph, _host, gc_adg_partition,
+                              gc_color_graph_dec_itr, gc_color_graph_o);
+                              built on the second call in a row with the
+                              same buffers and shapes, kept by the context
+                              while they stay the same; 0 launches each
+                              round from the host                            */
 } gc_options;
 
 /* How gc_color_batch runs (gc_options.batch_mode, gc_stats.batch_path):

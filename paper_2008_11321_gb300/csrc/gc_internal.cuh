@@ -61,6 +61,7 @@ struct AdgCtl {
                                  // least this degree (INT_MAX: none)
   int hub_cap;                   // hubs the rank table holds
   int n_hubs;                    // hubs ranked by round 1's partition
+  int graph_err;                 // graph-launched rounds: a round removed no vertex
 };
 
 static_assert(sizeof(AdgCtl) <= 256, "AdgCtl must fit the pinned read-back buffer");
@@ -210,7 +211,8 @@ gc_status batch_color_persistent(gc_context* ctx, Arena a, const gc_batch_csr* b
                                  const int* order, int32_t* color_out, int32_t* batch_out, int32_t* num_colors_out,
                                  int32_t* num_rounds_out, cudaStream_t s);
 
-// Frees the context's batch round-loop graph (gc_batch.cu).
+// Free the context's round-loop graphs (gc_adg.cu, gc_batch.cu).
+void adg_graph_free(gc_context* ctx);
 void batch_graph_free(gc_context* ctx);
 
 // JP-ADG on the disjoint union of many graphs.  Vertex v of graph gid[v]
@@ -279,7 +281,9 @@ struct gc_context {
   void* h_graph = nullptr;
   size_t h_graph_bytes = 0;
   cudaStream_t copy_stream = nullptr;
-  // the segmented batch path's round-loop graph (gc_batch.cu)
+  // the round-loop graphs of ADG (gc_adg.cu) and of the segmented batch
+  // path (gc_batch.cu)
+  void* adg_graph = nullptr;
   void* batch_graph = nullptr;
   cudaEvent_t copy_ev[gc::kUploadChunks + 1] = {};  // per range, then "the device buffers are free"
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};

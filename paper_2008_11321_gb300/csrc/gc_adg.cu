@@ -453,26 +453,12 @@ __global__ void adg_finalize_graph_kernel(AdgCtl* ctl, cudaGraphConditionalHandl
   cudaGraphSetConditional(loop, ctl->size_U > 0 ? 1u : 0u);
 }
 
-// ADG's rounds from round 2 on as one CUDA graph: a while node whose body
-// holds two rounds (partition, UPDATE, the pull kernels unless the mode is
-// PUSH, finalize), the first reading U from ubuf[0] and writing U' to
+// ADG's rounds from round 2 on as one CUDA graph loop (gc_graph.cu): the
+// body holds two rounds (partition, UPDATE, the pull kernels unless the mode
+// is PUSH, finalize), the first reading U from ubuf[0] and writing U' to
 // ubuf[1], the second the other way round, so every kernel argument is
 // fixed (the partition reads |U| from the control block).  Used when the
-// context keeps no per-round timers; built on the second call in a row with
-// the same buffers and shapes and kept by the context while they stay so.
-struct AdgGraphKey {
-  const void* p[13];
-  long long i[6];
-  bool operator==(const AdgGraphKey& o) const { return memcmp(this, &o, sizeof(*this)) == 0; }
-};
-
-struct AdgGraph {
-  AdgGraphKey key{};   // of the graph built
-  AdgGraphKey seen{};  // of the previous call
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-};
-
+// context keeps no per-round timers.
 struct AdgRoundArgs {
   AdgCtl* ctl;
   const long long* rp;
@@ -486,110 +472,38 @@ struct AdgRoundArgs {
   uint2* live;
   int* hub_base;
   int* hub_vertex;
-  int mode, hubs, upd_blocks, pull_blocks, max_blocks;
-  size_t hub_smem;
+  long long mode, hubs, upd_blocks, pull_blocks, max_blocks, hub_smem;  // the key: all of the above
 };
 
-void adg_graph_release(AdgGraph* ag) {
-  if (ag->exec) cudaGraphExecDestroy(ag->exec);
-  if (ag->graph) cudaGraphDestroy(ag->graph);
-  ag->exec = nullptr;
-  ag->graph = nullptr;
-}
-
 cudaError_t adg_round_graph(gc_context* ctx, const AdgRoundArgs& r, cudaGraphExec_t* exec) {
-  AdgGraphKey key{};
-  const void* ptrs[13] = {r.ctl, r.rp, r.col, r.D, r.batch, r.ubuf[0], r.ubuf[1], r.task_start, r.task_len,
-                          r.task_v, r.live, r.hub_base, r.hub_vertex};
-  memcpy(key.p, ptrs, sizeof(ptrs));
-  const long long ints[6] = {r.mode, r.hubs, r.upd_blocks, r.pull_blocks, r.max_blocks,
-                             static_cast<long long>(r.hub_smem)};
-  memcpy(key.i, ints, sizeof(ints));
-  AdgGraph* ag = static_cast<AdgGraph*>(ctx->adg_graph);
-  if (ag && ag->exec && ag->key == key) {
-    *exec = ag->exec;
-    return cudaSuccess;
-  }
-  if (!ag) {
-    ag = new (std::nothrow) AdgGraph();
-    if (!ag) return cudaErrorMemoryAllocation;
-    ctx->adg_graph = ag;
-  }
-  if (!(ag->seen == key)) {  // first call with these buffers: the host loop
-    ag->seen = key;
-    return cudaErrorNotReady;
-  }
-  adg_graph_release(ag);
-  cudaGraph_t graph = nullptr;
-  cudaStream_t cs = nullptr;
-  cudaGraphExec_t ex = nullptr;
-  cudaError_t e = cudaGraphCreate(&graph, 0);
-  do {
-    if (e != cudaSuccess) break;
-    cudaGraphConditionalHandle loop;
-    if ((e = cudaGraphConditionalHandleCreate(&loop, graph, 1, cudaGraphCondAssignDefault)) != cudaSuccess) break;
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = loop;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t node;
-    if ((e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp)) != cudaSuccess) break;
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) break;
-    if ((e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
-        cudaSuccess)
-      break;
+  return loop_graph(&ctx->adg_graph, &r, sizeof(r), [&](cudaStream_t cs, cudaGraphConditionalHandle loop) {
     for (int half = 0; half < 2; ++half) {
       int* u_in = r.ubuf[half];
       int* u_out = r.ubuf[half ^ 1];
-      adg_partition_kernel<<<r.max_blocks, kAdgThreads, 0, cs>>>(r.ctl, r.rp, r.D, r.batch, u_in, u_out,
-                                                                 r.task_start, r.task_len, r.live, 0, nullptr,
-                                                                 nullptr, r.hub_base, r.hub_vertex);
+      adg_partition_kernel<<<static_cast<int>(r.max_blocks), kAdgThreads, 0, cs>>>(
+          r.ctl, r.rp, r.D, r.batch, u_in, u_out, r.task_start, r.task_len, r.live, 0, nullptr, nullptr,
+          r.hub_base, r.hub_vertex);
       if (r.mode != GC_UPDATE_PULL) {
         if (r.hubs > 0)
-          adg_update_kernel<true><<<r.upd_blocks, kAdgThreads, r.hub_smem, cs>>>(
-              r.ctl, r.rp, r.col, r.D, r.batch, r.live, r.task_start, r.task_len, 0, r.hub_base, r.hub_vertex, 0);
+          adg_update_kernel<true><<<static_cast<int>(r.upd_blocks), kAdgThreads, static_cast<size_t>(r.hub_smem),
+                                    cs>>>(r.ctl, r.rp, r.col, r.D, r.batch, r.live, r.task_start, r.task_len, 0,
+                                          r.hub_base, r.hub_vertex, 0);
         else
-          adg_update_kernel<false><<<r.upd_blocks, kAdgThreads, 0, cs>>>(
+          adg_update_kernel<false><<<static_cast<int>(r.upd_blocks), kAdgThreads, 0, cs>>>(
               r.ctl, r.rp, r.col, r.D, r.batch, r.live, r.task_start, r.task_len, 0, nullptr, nullptr, 0);
       }
       if (r.mode != GC_UPDATE_PUSH) {
-        adg_pull_tasks_kernel<<<r.max_blocks, kAdgThreads, 0, cs>>>(r.ctl, r.rp, r.D, u_out, r.task_start,
-                                                                    r.task_len, r.task_v);
-        adg_pull_count_kernel<<<r.pull_blocks, kAdgThreads, 0, cs>>>(r.ctl, r.col, r.D, r.live, r.task_start,
-                                                                     r.task_len, r.task_v);
+        adg_pull_tasks_kernel<<<static_cast<int>(r.max_blocks), kAdgThreads, 0, cs>>>(
+            r.ctl, r.rp, r.D, u_out, r.task_start, r.task_len, r.task_v);
+        adg_pull_count_kernel<<<static_cast<int>(r.pull_blocks), kAdgThreads, 0, cs>>>(
+            r.ctl, r.col, r.D, r.live, r.task_start, r.task_len, r.task_v);
       }
       adg_finalize_graph_kernel<<<1, 1, 0, cs>>>(r.ctl, loop);
     }
-    cudaGraph_t captured = nullptr;
-    const cudaError_t ec = cudaStreamEndCapture(cs, &captured);
-    if ((e = cudaGetLastError()) != cudaSuccess || (e = ec) != cudaSuccess) break;
-    e = cudaGraphInstantiate(&ex, graph, 0);
-  } while (false);
-  if (cs) cudaStreamDestroy(cs);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    if (ex) cudaGraphExecDestroy(ex);
-    if (graph) cudaGraphDestroy(graph);
-    return e;
-  }
-  ag->key = key;
-  ag->graph = graph;
-  ag->exec = ex;
-  *exec = ex;
-  return cudaSuccess;
+  }, exec);
 }
 
 }  // namespace
-
-void adg_graph_free(gc_context* ctx) {
-  AdgGraph* ag = static_cast<AdgGraph*>(ctx->adg_graph);
-  if (!ag) return;
-  adg_graph_release(ag);
-  delete ag;
-  ctx->adg_graph = nullptr;
-}
 
 // Excludes D (n ints), which the caller provides.
 size_t adg_scratch_bytes(long long n, long long nnz) {
@@ -655,9 +569,10 @@ gc_status adg_run(gc_context* ctx, Arena a, const gc_csr* g, unsigned p, unsigne
     ++round;
     if (round == 2 && cur == 1 && !ctx->timing && ctx->opt.round_graph) {
       // rounds 2.. as one graph launch (no host round trip per round)
-      const AdgRoundArgs ra{ctl,       row_ptr_of(g), g->col_idx, D,          batch,      {ubuf[0], ubuf[1]},
-                            task_start, task_len,     task_v,     live,       hub_base,   hub_vertex,
-                            mode,       hubs,         upd_blocks, pull_blocks, max_blocks, hub_smem};
+      const AdgRoundArgs ra{ctl,        row_ptr_of(g), g->col_idx, D,        batch,    {ubuf[0], ubuf[1]},
+                            task_start, task_len,      task_v,     live,     hub_base, hub_vertex,
+                            mode,       hubs,          upd_blocks, pull_blocks, max_blocks,
+                            static_cast<long long>(hub_smem)};
       cudaGraphExec_t ex = nullptr;
       if (adg_round_graph(ctx, ra, &ex) == cudaSuccess) {
         GC_TRY_CUDA(cudaGraphLaunch(ex, s));

@@ -385,8 +385,8 @@ void gc_destroy(gc_context* ctx) {
   if (ctx->aux) cudaFree(ctx->aux);
   if (ctx->pack) cudaFree(ctx->pack);
   if (ctx->h_graph) cudaFree(ctx->h_graph);
-  gc::adg_graph_free(ctx);
-  gc::batch_graph_free(ctx);
+  gc::loop_graph_free(&ctx->adg_graph);
+  gc::loop_graph_free(&ctx->batch_graph);
   for (auto& e : ctx->copy_ev)
     if (e) cudaEventDestroy(e);
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
@@ -768,8 +768,6 @@ gc_status gc_color_graph_host(gc_context* ctx, int64_t n, int64_t nnz, const int
   const size_t need = b_rp + b_ci + 2 * b_v + 256;
   if (need > ctx->h_graph_bytes) {
     if (ctx->h_graph) cudaFree(ctx->h_graph);
-  gc::adg_graph_free(ctx);
-  gc::batch_graph_free(ctx);
     ctx->h_graph = nullptr;
     ctx->h_graph_bytes = 0;
     if (cudaMalloc(&ctx->h_graph, need) != cudaSuccess) {

@@ -309,37 +309,12 @@ __global__ void batch_results_kernel(const BGraph* __restrict__ gs, const int* _
       nrounds[g] = gs[g].rounds;
 }
 
-// The ADG rounds from round 2 on as one CUDA graph: a while node whose body
-// holds two rounds (partition, UPDATE, finalize, next round), the first
+// The ADG rounds from round 2 on as one CUDA graph loop (gc_graph.cu): the
+// body holds two rounds (partition, UPDATE, finalize, next round), the first
 // reading U from ubuf[0] and writing U' to ubuf[1], the second the other way
 // round, so every kernel argument is fixed; the partition reads |U| from the
 // control block, and each round's last kernel sets the loop condition.  A
-// round whose U is already empty is a no-op.  The graph is built on the
-// second call in a row with the same buffers and shapes (building costs more
-// than a few host-driven rounds, so calls whose buffers change -- a server's
-// batches -- keep the host loop), kept by the context and launched again
-// while they stay the same.
-struct BatchGraphKey {
-  const void* p[13];
-  long long i[3];
-  bool operator==(const BatchGraphKey& o) const { return memcmp(this, &o, sizeof(*this)) == 0; }
-};
-
-struct BatchGraph {
-  BatchGraphKey key{};   // of the graph built
-  BatchGraphKey seen{};  // of the previous call
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-};
-
-void batch_graph_release(BatchGraph* bg) {
-  if (!bg) return;
-  if (bg->exec) cudaGraphExecDestroy(bg->exec);
-  if (bg->graph) cudaGraphDestroy(bg->graph);
-  bg->exec = nullptr;
-  bg->graph = nullptr;
-}
-
+// round whose U is already empty is a no-op.
 struct RoundArgs {
   BCtl* ctl;
   BGraph* gs;
@@ -353,91 +328,25 @@ struct RoundArgs {
   int* task_len;
   int* task_g;
   unsigned* live;
-  int G, pblocks, upd_blocks;
+  long long G, pblocks, upd_blocks;  // the key: all of the above
 };
 
-// Builds (or reuses) the loop graph; cudaSuccess with *exec set, or an
-// error (the caller then runs the rounds from the host).
 cudaError_t batch_round_graph(gc_context* ctx, const RoundArgs& r, cudaGraphExec_t* exec) {
-  BatchGraphKey key{};
-  const void* ptrs[13] = {r.ctl, r.gs, r.gid, r.rp, r.col, r.D, r.bat, r.ubuf[0], r.ubuf[1], r.task_start,
-                          r.task_len, r.task_g, r.live};
-  memcpy(key.p, ptrs, sizeof(ptrs));
-  key.i[0] = r.G;
-  key.i[1] = r.pblocks;
-  key.i[2] = r.upd_blocks;
-  BatchGraph* bg = static_cast<BatchGraph*>(ctx->batch_graph);
-  if (bg && bg->exec && bg->key == key) {
-    *exec = bg->exec;
-    return cudaSuccess;
-  }
-  if (!bg) {
-    bg = new (std::nothrow) BatchGraph();
-    if (!bg) return cudaErrorMemoryAllocation;
-    ctx->batch_graph = bg;
-  }
-  if (!(bg->seen == key)) {  // first call with these buffers: the host loop
-    bg->seen = key;
-    return cudaErrorNotReady;
-  }
-  batch_graph_release(bg);
-  cudaGraph_t graph = nullptr;
-  cudaStream_t cs = nullptr;
-  cudaGraphExec_t ex = nullptr;
-  cudaError_t e = cudaGraphCreate(&graph, 0);
-  do {
-    if (e != cudaSuccess) break;
-    cudaGraphConditionalHandle loop;
-    if ((e = cudaGraphConditionalHandleCreate(&loop, graph, 1, cudaGraphCondAssignDefault)) != cudaSuccess) break;
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = loop;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t node;
-    if ((e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp)) != cudaSuccess) break;
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) break;
-    if ((e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
-        cudaSuccess)
-      break;
+  return loop_graph(&ctx->batch_graph, &r, sizeof(r), [&](cudaStream_t cs, cudaGraphConditionalHandle loop) {
+    const int G = static_cast<int>(r.G);
     for (int half = 0; half < 2; ++half) {
-      batch_partition_kernel<<<r.pblocks, kBThreads, 0, cs>>>(r.ctl, r.gs, r.gid, r.rp, r.D, r.bat, r.ubuf[half],
-                                                              r.ubuf[half ^ 1], r.task_start, r.task_len, r.task_g,
-                                                              -1, r.live);
-      batch_update_kernel<<<r.upd_blocks, kBThreads, 0, cs>>>(r.ctl, r.gs, r.gid, r.rp, r.col, r.D, r.bat,
-                                                              r.task_start, r.task_len, r.task_g, 0, r.live);
-      batch_finalize_kernel<<<(r.G + 255) / 256, 256, 0, cs>>>(r.ctl, r.gs, r.G);
+      batch_partition_kernel<<<static_cast<int>(r.pblocks), kBThreads, 0, cs>>>(
+          r.ctl, r.gs, r.gid, r.rp, r.D, r.bat, r.ubuf[half], r.ubuf[half ^ 1], r.task_start, r.task_len, r.task_g,
+          -1, r.live);
+      batch_update_kernel<<<static_cast<int>(r.upd_blocks), kBThreads, 0, cs>>>(
+          r.ctl, r.gs, r.gid, r.rp, r.col, r.D, r.bat, r.task_start, r.task_len, r.task_g, 0, r.live);
+      batch_finalize_kernel<<<(G + 255) / 256, 256, 0, cs>>>(r.ctl, r.gs, G);
       batch_next_round_graph_kernel<<<1, 1, 0, cs>>>(r.ctl, loop);
     }
-    cudaGraph_t captured = nullptr;
-    const cudaError_t ec = cudaStreamEndCapture(cs, &captured);
-    if ((e = cudaGetLastError()) != cudaSuccess || (e = ec) != cudaSuccess) break;
-    e = cudaGraphInstantiate(&ex, graph, 0);
-  } while (false);
-  if (cs) cudaStreamDestroy(cs);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    if (ex) cudaGraphExecDestroy(ex);
-    if (graph) cudaGraphDestroy(graph);
-    return e;
-  }
-  bg->key = key;
-  bg->graph = graph;
-  bg->exec = ex;
-  *exec = ex;
-  return cudaSuccess;
+  }, exec);
 }
 
 }  // namespace
-
-void batch_graph_free(gc_context* ctx) {
-  BatchGraph* bg = static_cast<BatchGraph*>(ctx->batch_graph);
-  if (!bg) return;
-  batch_graph_release(bg);
-  delete bg;
-  ctx->batch_graph = nullptr;
-}
 
 size_t batch_adg_scratch_bytes(long long n, long long nnz, long long G) {
   const long long ntask = n + nnz / kChunk + 1;
@@ -525,8 +434,8 @@ gc_status batch_color(gc_context* ctx, const gc_batch_csr* b, const gc_job* jobs
     ++round;
     if (round == 2 && ctx->opt.round_graph) {
       // rounds 2.. as one graph launch (no host round trip per round)
-      RoundArgs ra{ctl, gs, gid, rp, b->col_idx, D, bat, {ubuf[0], ubuf[1]}, task_start, task_len, task_g,
-                   live, G, blocks, upd_blocks};
+      RoundArgs ra{ctl,  gs,     gid,  rp,   b->col_idx, D,      bat, {ubuf[0], ubuf[1]}, task_start, task_len,
+                   task_g, live, G, blocks, upd_blocks};
       cudaGraphExec_t ex = nullptr;
       if (cur == 1 && batch_round_graph(ctx, ra, &ex) == cudaSuccess) {
         GC_TRY_CUDA(cudaGraphLaunch(ex, s));

@@ -5,6 +5,8 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <functional>
+#include <vector>
 
 #include "gcolor.h"
 
@@ -150,6 +152,13 @@ size_t adg_scratch_bytes(long long n, long long nnz);
 // range once its event has fired (round 1's partition needs row offsets only),
 // so the copy of col_idx overlaps ADG's first round.
 constexpr int kUploadChunks = 8;
+// A context's round-loop graph (gc_graph.cu).
+struct LoopGraph {
+  std::vector<unsigned char> key;   // of the graph built
+  std::vector<unsigned char> seen;  // of the previous call
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
 struct ColChunks {
   int k = 0;
   long long lo[kUploadChunks + 1] = {};
@@ -211,9 +220,15 @@ gc_status batch_color_persistent(gc_context* ctx, Arena a, const gc_batch_csr* b
                                  const int* order, int32_t* color_out, int32_t* batch_out, int32_t* num_colors_out,
                                  int32_t* num_rounds_out, cudaStream_t s);
 
-// Free the context's round-loop graphs (gc_adg.cu, gc_batch.cu).
-void adg_graph_free(gc_context* ctx);
-void batch_graph_free(gc_context* ctx);
+// A round loop as a CUDA graph (gc_graph.cu): capture(stream, handle) makes
+// the launches of one body iteration on `stream`; its last kernel sets the
+// handle's condition.  cudaSuccess with *exec, cudaErrorNotReady on the
+// first call with a key (the caller then runs its host loop), or the error
+// that stopped the build.
+cudaError_t loop_graph(LoopGraph** slot, const void* key, size_t key_bytes,
+                       const std::function<void(cudaStream_t, cudaGraphConditionalHandle)>& capture,
+                       cudaGraphExec_t* exec);
+void loop_graph_free(LoopGraph** slot);
 
 // JP-ADG on the disjoint union of many graphs.  Vertex v of graph gid[v]
 // (first vertex off[gid[v]]) has the tie-break rho_R of its own graph's seed,
@@ -226,9 +241,6 @@ gc_status jp_run_packed(gc_context* ctx, Arena a, const gc_csr* g, const int* ba
 // autotuner times run() (one colouring into its argument, n ints) under
 // candidate options and leaves the fastest applied.
 void apply_options(gc_context* ctx, const gc_options& o);
-}  // namespace gc
-#include <functional>
-namespace gc {
 gc_status autotune(gc_context* ctx, long long n, const std::function<gc_status(int*)>& run, bool batch, int reps,
                    float budget_ms, gc_options* best_out, float* best_ms_out, float* start_ms_out, int* trials_out,
                    cudaStream_t s);
@@ -283,8 +295,8 @@ struct gc_context {
   cudaStream_t copy_stream = nullptr;
   // the round-loop graphs of ADG (gc_adg.cu) and of the segmented batch
   // path (gc_batch.cu)
-  void* adg_graph = nullptr;
-  void* batch_graph = nullptr;
+  gc::LoopGraph* adg_graph = nullptr;
+  gc::LoopGraph* batch_graph = nullptr;
   cudaEvent_t copy_ev[gc::kUploadChunks + 1] = {};  // per range, then "the device buffers are free"
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   // kernel-group timers: event pairs recorded around launches when timing is

@@ -108,7 +108,153 @@ __global__ void adg_hub_pick_kernel(const unsigned long long* __restrict__ hist,
   ctl->hub_cap = max_hubs;
 }
 
-__global__ void __launch_bounds__(kAdgThreads)
+// The partition's work on one block step of K vertices per thread (vertex
+// i = base + j * blockDim.x + threadIdx.x for j < K, so each j is a coalesced
+// run): all K vertices' loads are issued before any decision, and the step's
+// survivors and UPDATE tasks are appended with one atomic per list for the
+// whole block (block_reserve) rather than one per warp on the same word.
+template <int K>
+__device__ __forceinline__ void adg_partition_steps(
+    AdgCtl* __restrict__ ctl, const long long* __restrict__ row_ptr, int* __restrict__ D, int* __restrict__ batch,
+    const int* __restrict__ u_in, int* __restrict__ u_out, long long* __restrict__ task_start,
+    int* __restrict__ task_len, uint2* __restrict__ live, bool first, long long size_u,
+    const unsigned long long* __restrict__ mkeys, const unsigned long long* __restrict__ kstar,
+    int* __restrict__ hub_base, int* __restrict__ hub_vertex, int round, int T, int hub_min,
+    unsigned long long& sum_r, unsigned long long& rows_r, int& max_d) {
+  __shared__ int s_keep[2][kAdgThreads / 32];
+  __shared__ unsigned long long s_task[2][kAdgThreads / 32];
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+  const long long span = static_cast<long long>(blockDim.x) * K;
+  const long long stride = static_cast<long long>(gridDim.x) * span;
+  int par = 0;
+  // base is the same for every thread of the block: the barriers inside
+  // block_reserve are reached by all of them on every step
+  for (long long base = static_cast<long long>(blockIdx.x) * span; base < size_u; base += stride, par ^= 1) {
+    int u[K], d[K], nt[K], incl[K];
+    long long rs[K], re[K];
+    bool in_r[K], keep[K];
+    unsigned km[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const long long i = base + static_cast<long long>(j) * blockDim.x + threadIdx.x;
+      const bool active = i < size_u;
+      u[j] = 0;
+      d[j] = 0;
+      rs[j] = 0;
+      re[j] = 0;
+      if (active) {
+        if (first) {
+          u[j] = static_cast<int>(i);
+          rs[j] = row_ptr[u[j]];
+          re[j] = row_ptr[u[j] + 1];
+          d[j] = static_cast<int>(re[j] - rs[j]);
+        } else {
+          u[j] = u_in[i];
+          d[j] = D[u[j]];
+        }
+      }
+      // ADG: D[u] <= T; ADG-M: the key D[u] * 2^32 + u of list entry i is at
+      // most the selected ceil(|U|/2)-th smallest key
+      in_r[j] = active && (mkeys ? mkeys[i] <= *kstar : d[j] <= T);
+      keep[j] = active && !in_r[j];
+    }
+    // removed vertices' rows (round 1 has them already) -> UPDATE tasks of at
+    // most kChunk edges
+    if (!first) {
+#pragma unroll
+      for (int j = 0; j < K; ++j)
+        if (in_r[j]) {
+          rs[j] = row_ptr[u[j]];
+          re[j] = row_ptr[u[j] + 1];
+        }
+    }
+    int wkeep = 0;
+    unsigned long long wtask = 0;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      km[j] = __ballot_sync(kFull, keep[j]);
+      wkeep += __popc(km[j]);
+      nt[j] = (!first && in_r[j]) ? static_cast<int>((re[j] - rs[j] + kChunk - 1) / kChunk) : 0;
+      incl[j] = warp_inclusive_scan(nt[j]);
+      wtask += static_cast<unsigned>(__shfl_sync(kFull, incl[j], 31));
+    }
+    const BlockSlots slot = block_reserve(&ctl->size_Unext, wkeep, &ctl->ntasks, wtask, s_keep[par], s_task[par]);
+    // survivors -> U'
+    int kb = slot.a;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      if (keep[j]) u_out[kb + __popc(km[j] & lt)] = u[j];
+      kb += __popc(km[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const long long i = base + static_cast<long long>(j) * blockDim.x + threadIdx.x;
+      const bool active = i < size_u;
+      // liveness bitmap: round 1 writes the warp's word pair (vertices
+      // i = 32 w .. 32 w + 31, since every run starts at a multiple of 32:
+      // live bits, hub bits); later rounds clear live bits
+      if (first) {
+        const unsigned hm = __ballot_sync(kFull, active && d[j] >= hub_min);
+        if (lane == 0 && active) live[i >> 5] = make_uint2(km[j], hm);
+        // hub ranks: the word's hubs take consecutive ranks from
+        // hub_base[word] on, in bit order (the hub of bit b has rank
+        // hub_base + popc(hm & (2^b - 1)))
+        if (hm && hub_base) {
+          int hb = 0;
+          if (lane == 0) {
+            hb = atomicAdd(&ctl->n_hubs, __popc(hm));
+            hub_base[i >> 5] = hb;
+          }
+          hb = __shfl_sync(kFull, hb, 0) + __popc(hm & lt);
+          if (((hm >> lane) & 1u) && hb < ctl->hub_cap) hub_vertex[hb] = u[j];
+        }
+        // D[u] is written for every vertex in round 1; for a removed vertex
+        // it then keeps its degree at removal, |{w in N(u) : batch(w) >=
+        // batch(u)}|, which bounds u's predecessor count in JP.
+        if (active) D[u[j]] = d[j];
+      } else if (in_r[j]) {
+        atomicAnd(&live[u[j] >> 5].x, ~(1u << (u[j] & 31)));
+      }
+      if (in_r[j]) {
+        batch[u[j]] = round;
+        sum_r += static_cast<unsigned long long>(d[j]);
+        max_d = d[j] > max_d ? d[j] : max_d;
+        rows_r += static_cast<unsigned long long>(re[j] - rs[j]);
+      }
+    }
+    if (first) continue;  // round 1's UPDATE sweeps vertex tiles, no task list
+    unsigned long long tb = slot.b;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const int tot = __shfl_sync(kFull, incl[j], 31);
+      const int excl = incl[j] - nt[j];
+      for (int b = 0; b < tot; b += 32) {
+        const int x = b + lane;
+        int o = 0;  // owner: the largest lane o with excl_o <= x
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int c = o + step;
+          if (__shfl_sync(kFull, excl, c) <= x) o = c;
+        }
+        const long long st = __shfl_sync(kFull, rs[j], o) +
+                             static_cast<long long>(x - __shfl_sync(kFull, excl, o)) * kChunk;
+        const long long rej = __shfl_sync(kFull, re[j], o);
+        if (x < tot) {
+          task_start[tb + x] = st;
+          task_len[tb + x] = static_cast<int>(rej - st < kChunk ? rej - st : kChunk);
+        }
+      }
+      tb += static_cast<unsigned long long>(tot);
+    }
+  }
+}
+
+// Vertices per thread and block step on rounds large enough to give every
+// thread of the grid that many.
+constexpr int kPartItems = 4;
+
+__global__ void __launch_bounds__(kAdgThreads, 4)  // 64 registers: 4 blocks per SM
 adg_partition_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row_ptr,
                      int* __restrict__ D, int* __restrict__ batch, const int* __restrict__ u_in,
                      int* __restrict__ u_out, long long* __restrict__ task_start,
@@ -122,100 +268,15 @@ adg_partition_kernel(AdgCtl* __restrict__ ctl, const long long* __restrict__ row
   const bool first = first_round_n > 0;
   const long long size_u = first ? first_round_n : ctl->size_U;
   const int lane = threadIdx.x & 31;
-  const unsigned lt = lanemask_lt();
   unsigned long long sum_r = 0, rows_r = 0;
   int max_d = 0;
-  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
-  for (long long base = static_cast<long long>(blockIdx.x) * blockDim.x; base < size_u; base += stride) {
-    const long long i = base + threadIdx.x;
-    const bool active = i < size_u;
-    int u = 0, d = 0;
-    long long rs = 0, re = 0;
-    if (active) {
-      if (first) {
-        u = static_cast<int>(i);
-        rs = row_ptr[u];
-        re = row_ptr[u + 1];
-        d = static_cast<int>(re - rs);
-      } else {
-        u = u_in[i];
-        d = D[u];
-      }
-    }
-    // ADG: D[u] <= T; ADG-M: the key D[u] * 2^32 + u of list entry i is at
-    // most the selected ceil(|U|/2)-th smallest key
-    const bool in_r = active && (mkeys ? mkeys[i] <= *kstar : d <= T);
-    const bool keep = active && !in_r;
-    // survivors -> U'
-    const unsigned km = __ballot_sync(kFull, keep);
-    int kbase = 0;
-    if (lane == 0 && km) kbase = atomicAdd(&ctl->size_Unext, __popc(km));
-    kbase = __shfl_sync(kFull, kbase, 0);
-    if (keep) u_out[kbase + __popc(km & lt)] = u;
-    // liveness bitmap: round 1 writes the warp's word pair (vertices
-    // i = 32 j .. 32 j + 31, since blocks start at multiples of 32: live bits,
-    // hub bits); later rounds clear live bits
-    if (first) {
-      const unsigned hm = __ballot_sync(kFull, active && d >= hub_min);
-      if (lane == 0 && active) live[i >> 5] = make_uint2(km, hm);
-      // hub ranks: the word's hubs take consecutive ranks from hub_base[word]
-      // on, in bit order (the hub of bit b has rank hub_base + popc(hm & (2^b - 1)))
-      if (hm && hub_base) {
-        int hb = 0;
-        if (lane == 0) {
-          hb = atomicAdd(&ctl->n_hubs, __popc(hm));
-          hub_base[i >> 5] = hb;
-        }
-        hb = __shfl_sync(kFull, hb, 0) + __popc(hm & lt);
-        if (((hm >> lane) & 1u) && hb < ctl->hub_cap) hub_vertex[hb] = u;
-      }
-    } else if (in_r) {
-      atomicAnd(&live[u >> 5].x, ~(1u << (u & 31)));
-    }
-    // D[u] is written for every vertex in round 1; for a removed vertex it then
-    // keeps its degree at removal, |{w in N(u) : batch(w) >= batch(u)}|, which
-    // bounds u's predecessor count in JP.
-    if (active && first) D[u] = d;
-    if (in_r) {
-      batch[u] = round;
-      sum_r += static_cast<unsigned long long>(d);
-      max_d = d > max_d ? d : max_d;
-    }
-    if (first) {  // round 1's UPDATE sweeps vertex tiles, no task list
-      if (in_r) rows_r += static_cast<unsigned long long>(re - rs);
-      continue;
-    }
-    // removed -> UPDATE tasks of at most kChunk edges, written by the warp
-    int nt = 0;
-    if (in_r) {
-      rs = row_ptr[u];
-      re = row_ptr[u + 1];
-      nt = static_cast<int>((re - rs + kChunk - 1) / kChunk);
-      rows_r += static_cast<unsigned long long>(re - rs);
-    }
-    const int incl = warp_inclusive_scan(nt);
-    const int tot = __shfl_sync(kFull, incl, 31);
-    const int excl = incl - nt;
-    unsigned long long tbase = 0;
-    if (lane == 31 && tot) tbase = atomicAdd(&ctl->ntasks, static_cast<unsigned long long>(tot));
-    tbase = __shfl_sync(kFull, tbase, 31);
-    for (int b = 0; b < tot; b += 32) {
-      const int x = b + lane;
-      int j = 0;  // owner: the largest lane j with excl_j <= x
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const int c = j + step;
-        if (__shfl_sync(kFull, excl, c) <= x) j = c;
-      }
-      const long long st = __shfl_sync(kFull, rs, j) +
-                           static_cast<long long>(x - __shfl_sync(kFull, excl, j)) * kChunk;
-      const long long rej = __shfl_sync(kFull, re, j);
-      if (x < tot) {
-        task_start[tbase + x] = st;
-        task_len[tbase + x] = static_cast<int>(rej - st < kChunk ? rej - st : kChunk);
-      }
-    }
-  }
+  // the same choice in every block: size_u and the grid are the kernel's
+  if (size_u >= static_cast<long long>(gridDim.x) * blockDim.x * kPartItems)
+    adg_partition_steps<kPartItems>(ctl, row_ptr, D, batch, u_in, u_out, task_start, task_len, live, first, size_u,
+                                    mkeys, kstar, hub_base, hub_vertex, round, T, hub_min, sum_r, rows_r, max_d);
+  else
+    adg_partition_steps<1>(ctl, row_ptr, D, batch, u_in, u_out, task_start, task_len, live, first, size_u, mkeys,
+                           kstar, hub_base, hub_vertex, round, T, hub_min, sum_r, rows_r, max_d);
   sum_r = warp_sum(sum_r);
   rows_r = warp_sum(rows_r);
   if (lane == 0 && sum_r) atomicAdd(&ctl->sum_R, sum_r);

@@ -92,7 +92,138 @@ __device__ __forceinline__ unsigned long long group_sum(unsigned group, unsigned
          (static_cast<unsigned long long>(hi) << 32);
 }
 
-__global__ void __launch_bounds__(kBThreads)
+// One block step of the batched partition, K vertices per thread (vertex
+// i = base + j * blockDim.x + threadIdx.x for j < K): all K vertices' loads
+// first, then the survivors and UPDATE tasks of the whole block appended with
+// one atomic per list (block_reserve); the per-graph counts stay per warp and
+// graph (__match_any_sync groups).
+template <int K>
+__device__ __forceinline__ void batch_partition_steps(
+    BCtl* __restrict__ ctl, BGraph* __restrict__ gs, const int* __restrict__ gid,
+    const long long* __restrict__ row_ptr, int* __restrict__ D, int* __restrict__ batch,
+    const int* __restrict__ u_in, int* __restrict__ u_out, long long* __restrict__ task_start,
+    int* __restrict__ task_len, int* __restrict__ task_g, long long size_u, unsigned* __restrict__ live, int round,
+    bool first) {
+  __shared__ int s_keep[2][kBThreads / 32];
+  __shared__ unsigned long long s_task[2][kBThreads / 32];
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+  const long long span = static_cast<long long>(blockDim.x) * K;
+  const long long stride = static_cast<long long>(gridDim.x) * span;
+  int par = 0;
+  // base is the same for every thread of the block: the barriers inside
+  // block_reserve are reached by all of them on every step
+  for (long long base = static_cast<long long>(blockIdx.x) * span; base < size_u; base += stride, par ^= 1) {
+    int u[K], d[K], g[K], nt[K], incl[K];
+    long long rs[K], re[K];
+    bool in_r[K], keep[K];
+    unsigned km[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const long long i = base + static_cast<long long>(j) * blockDim.x + threadIdx.x;
+      const bool active = i < size_u;
+      u[j] = 0;
+      d[j] = 0;
+      g[j] = -1;
+      rs[j] = 0;
+      re[j] = 0;
+      if (active) {
+        u[j] = first ? static_cast<int>(i) : u_in[i];
+        g[j] = gid[u[j]];
+        if (first) {
+          rs[j] = row_ptr[u[j]];
+          re[j] = row_ptr[u[j] + 1];
+          d[j] = static_cast<int>(re[j] - rs[j]);
+        } else {
+          d[j] = D[u[j]];
+        }
+      }
+      const int T = active ? gs[g[j]].T : 0;
+      in_r[j] = active && d[j] <= T;
+      keep[j] = active && !in_r[j];
+    }
+    if (!first) {  // removed vertices' rows -> UPDATE tasks of at most kChunk edges
+#pragma unroll
+      for (int j = 0; j < K; ++j)
+        if (in_r[j]) {
+          rs[j] = row_ptr[u[j]];
+          re[j] = row_ptr[u[j] + 1];
+        }
+    }
+    int wkeep = 0;
+    unsigned long long wtask = 0;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      km[j] = __ballot_sync(kFull, keep[j]);
+      wkeep += __popc(km[j]);
+      nt[j] = (!first && in_r[j]) ? static_cast<int>((re[j] - rs[j] + kChunk - 1) / kChunk) : 0;
+      incl[j] = warp_inclusive_scan(nt[j]);
+      wtask += static_cast<unsigned>(__shfl_sync(kFull, incl[j], 31));
+    }
+    const BlockSlots slot = block_reserve(&ctl->size_Unext, wkeep, &ctl->ntasks, wtask, s_keep[par], s_task[par]);
+    int kb = slot.a;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const long long i = base + static_cast<long long>(j) * blockDim.x + threadIdx.x;
+      const bool active = i < size_u;
+      // survivors -> U', counted per graph
+      if (keep[j]) u_out[kb + __popc(km[j] & lt)] = u[j];
+      kb += __popc(km[j]);
+      const unsigned grp = __match_any_sync(kFull, g[j]);
+      const unsigned kgrp = grp & km[j];
+      if (keep[j] && (kgrp & lt) == 0) atomicAdd(&gs[g[j]].size_Unext, __popc(kgrp));
+      // removed -> batch id, per-graph sum of D
+      const unsigned rm = __ballot_sync(kFull, in_r[j]);
+      const unsigned rgrp = grp & rm;
+      // liveness bitmap: round 1 writes the warp's word (vertices 32 w ..
+      // 32 w + 31: every run starts at a multiple of 32), later rounds clear
+      // bits
+      if (first) {
+        if (lane == 0 && active) live[i >> 5] = km[j];
+        if (active) D[u[j]] = d[j];
+      } else if (in_r[j]) {
+        atomicAnd(&live[u[j] >> 5], ~(1u << (u[j] & 31)));
+      }
+      const unsigned long long dsum = group_sum(grp, in_r[j] ? static_cast<unsigned long long>(d[j]) : 0ull);
+      if (in_r[j]) {
+        batch[u[j]] = round;
+        if ((rgrp & lt) == 0) atomicAdd(&gs[g[j]].sum_R, dsum);
+      }
+    }
+    if (first) continue;  // round 1 sweeps vertex tiles
+    unsigned long long tb = slot.b;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const int tot = __shfl_sync(kFull, incl[j], 31);
+      const int excl = incl[j] - nt[j];
+      for (int b = 0; b < tot; b += 32) {
+        const int x = b + lane;
+        int o = 0;  // owner: the largest lane o with excl_o <= x
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int c = o + step;
+          if (__shfl_sync(kFull, excl, c) <= x) o = c;
+        }
+        const long long st = __shfl_sync(kFull, rs[j], o) +
+                             static_cast<long long>(x - __shfl_sync(kFull, excl, o)) * kChunk;
+        const long long rej = __shfl_sync(kFull, re[j], o);
+        const int gj = __shfl_sync(kFull, g[j], o);
+        if (x < tot) {
+          task_start[tb + x] = st;
+          task_len[tb + x] = static_cast<int>(rej - st < kChunk ? rej - st : kChunk);
+          task_g[tb + x] = gj;
+        }
+      }
+      tb += static_cast<unsigned long long>(tot);
+    }
+  }
+}
+
+// Vertices per thread and block step on rounds large enough to give every
+// thread of the grid that many.
+constexpr int kBPartItems = 4;
+
+__global__ void __launch_bounds__(kBThreads, 4)  // 64 registers: 4 blocks per SM
 batch_partition_kernel(BCtl* __restrict__ ctl, BGraph* __restrict__ gs, const int* __restrict__ gid,
                        const long long* __restrict__ row_ptr, int* __restrict__ D,
                        int* __restrict__ batch, const int* __restrict__ u_in, int* __restrict__ u_out,
@@ -101,85 +232,13 @@ batch_partition_kernel(BCtl* __restrict__ ctl, BGraph* __restrict__ gs, const in
   const int round = ctl->round;
   if (size_u < 0) size_u = ctl->size_U;  // the graph-launched rounds
   const bool first = round == 1;
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = lanemask_lt();
-  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
-  for (long long base = static_cast<long long>(blockIdx.x) * blockDim.x; base < size_u; base += stride) {
-    const long long i = base + threadIdx.x;
-    const bool active = i < size_u;
-    int u = 0, d = 0, g = -1;
-    long long rs = 0, re = 0;
-    if (active) {
-      u = first ? static_cast<int>(i) : u_in[i];
-      g = gid[u];
-      if (first) {
-        rs = row_ptr[u];
-        re = row_ptr[u + 1];
-        d = static_cast<int>(re - rs);
-        D[u] = d;
-      } else {
-        d = D[u];
-      }
-    }
-    const int T = active ? gs[g].T : 0;
-    const bool in_r = active && d <= T;
-    const bool keep = active && !in_r;
-    // survivors -> U', counted per graph
-    const unsigned km = __ballot_sync(kFull, keep);
-    int kbase = 0;
-    if (lane == 0 && km) kbase = atomicAdd(&ctl->size_Unext, __popc(km));
-    kbase = __shfl_sync(kFull, kbase, 0);
-    if (keep) u_out[kbase + __popc(km & lt)] = u;
-    const unsigned grp = __match_any_sync(kFull, g);
-    const unsigned kgrp = grp & km;
-    if (keep && (kgrp & lt) == 0) atomicAdd(&gs[g].size_Unext, __popc(kgrp));
-    // removed -> batch id, per-graph sum of D
-    const unsigned rm = __ballot_sync(kFull, in_r);
-    const unsigned rgrp = grp & rm;
-    // liveness bitmap: round 1 writes the warp's word (vertices 32 j ..
-    // 32 j + 31: blocks start at multiples of 32), later rounds clear bits
-    if (first) {
-      if (lane == 0 && active) live[i >> 5] = km;
-    } else if (in_r) {
-      atomicAnd(&live[u >> 5], ~(1u << (u & 31)));
-    }
-    const unsigned long long dsum = group_sum(grp, in_r ? static_cast<unsigned long long>(d) : 0ull);
-    if (in_r) {
-      batch[u] = round;
-      if ((rgrp & lt) == 0) atomicAdd(&gs[g].sum_R, dsum);
-    }
-    if (first) continue;  // round 1 sweeps vertex tiles
-    int nt = 0;
-    if (in_r) {
-      rs = row_ptr[u];
-      re = row_ptr[u + 1];
-      nt = static_cast<int>((re - rs + kChunk - 1) / kChunk);
-    }
-    const int incl = warp_inclusive_scan(nt);
-    const int tot = __shfl_sync(kFull, incl, 31);
-    const int excl = incl - nt;
-    unsigned long long tbase = 0;
-    if (lane == 31 && tot) tbase = atomicAdd(&ctl->ntasks, static_cast<unsigned long long>(tot));
-    tbase = __shfl_sync(kFull, tbase, 31);
-    for (int b = 0; b < tot; b += 32) {
-      const int x = b + lane;
-      int j = 0;
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const int c = j + step;
-        if (__shfl_sync(kFull, excl, c) <= x) j = c;
-      }
-      const long long st = __shfl_sync(kFull, rs, j) +
-                           static_cast<long long>(x - __shfl_sync(kFull, excl, j)) * kChunk;
-      const long long rej = __shfl_sync(kFull, re, j);
-      const int gj = __shfl_sync(kFull, g, j);
-      if (x < tot) {
-        task_start[tbase + x] = st;
-        task_len[tbase + x] = static_cast<int>(rej - st < kChunk ? rej - st : kChunk);
-        task_g[tbase + x] = gj;
-      }
-    }
-  }
+  // the same choice in every block: size_u and the grid are the kernel's
+  if (size_u >= static_cast<long long>(gridDim.x) * blockDim.x * kBPartItems)
+    batch_partition_steps<kBPartItems>(ctl, gs, gid, row_ptr, D, batch, u_in, u_out, task_start, task_len, task_g,
+                                       size_u, live, round, first);
+  else
+    batch_partition_steps<1>(ctl, gs, gid, row_ptr, D, batch, u_in, u_out, task_start, task_len, task_g, size_u,
+                             live, round, first);
 }
 
 __global__ void __launch_bounds__(kBThreads)

@@ -460,6 +460,50 @@ __device__ __forceinline__ T warp_inclusive_scan(T v) {
   return v;
 }
 
+// One block step's appends to two global lists: warp w appends wa entries to
+// the list whose length is *ca and wb to the one whose length is *cb.  The
+// block adds its totals with one atomic each (instead of one per warp on the
+// same address) and each warp gets the start of its own run, warps in order.
+// Every thread of the block calls it (two barriers).  s_a and s_b are shared
+// arrays of blockDim.x / 32 entries; callers alternate between two pairs on
+// consecutive calls, which makes a third barrier before their reuse
+// unnecessary.
+struct BlockSlots {
+  int a;
+  unsigned long long b;
+};
+
+__device__ __forceinline__ BlockSlots block_reserve(int* ca, int wa, unsigned long long* cb, unsigned long long wb,
+                                                    int* s_a, unsigned long long* s_b) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+  if (lane == 0) {
+    s_a[warp] = wa;
+    s_b[warp] = wb;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int va = lane < nw ? s_a[lane] : 0;
+    const unsigned long long vb = lane < nw ? s_b[lane] : 0ull;
+    const int ia = warp_inclusive_scan(va);
+    const unsigned long long ib = warp_inclusive_scan(vb);
+    int ba = 0;
+    unsigned long long bb = 0;
+    if (lane == 31) {
+      if (ia) ba = atomicAdd(ca, ia);
+      if (ib) bb = atomicAdd(cb, ib);
+    }
+    ba = __shfl_sync(kFull, ba, 31);
+    bb = __shfl_sync(kFull, bb, 31);
+    if (lane < nw) {
+      s_a[lane] = ba + ia - va;
+      s_b[lane] = bb + ib - vb;
+    }
+  }
+  __syncthreads();
+  return BlockSlots{s_a[warp], s_b[warp]};
+}
+
 // Edge sweep over 32 tasks held one per lane (task start `st`, length `len`,
 // a caller value `tag`): the tasks' edges are numbered 0..total-1 in lane
 // order and handed out 32 * kSweepUnroll at a time, each lane taking

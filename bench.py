@@ -99,7 +99,7 @@ KERNEL_TRAFFIC = {
     # R-MAT scale 24, the fourth call of `bench.py --steps 1 --warmup 3`; mean
     # over the launches of one call (4 bulk, 7 UPDATE, 1 core)
     ("rmat24", "jp_color_kernel"): (1119338816, "gc_jp.cu", "cab66866d06a1d97"),
-    ("rmat24", "adg_update_kernel"): (355431424, "gc_adg.cu", "2514962b61b925f7"),
+    ("rmat24", "adg_update_kernel"): (355431424, "gc_adg.cu", "ee04c8d9eef69878"),
     ("rmat24", "jpf_core_solve_kernel"): (34953472, "gc_jp.cu", "cab66866d06a1d97"),
 }
 

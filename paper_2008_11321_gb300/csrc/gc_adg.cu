@@ -22,7 +22,7 @@
 // the rows of U'; the direction is chosen per round on the device
 // (adg_pulls) from the two row sums, which the partition and finalize carry.
 //
-// Round 1 reads U = V implicitly (no list) and writes D only for survivors.
+// Round 1 reads U = V implicitly (no list) and writes every vertex's D.
 //
 // Hubs.  Rounds 2-5 of a power-law graph send most decrements to a few
 // thousand high-degree vertices, and atomics on one word serialise in its L2
@@ -40,9 +40,11 @@
 // would not (random 4-byte gathers run several times faster from L2 than from
 // HBM).  Round 1's partition visits the vertices in order and writes whole
 // bitmap words; later rounds clear the bits of removed vertices.
-// The host reads |U| after every round to stop; the number of rounds is
-// O(log n) (the round-bound lemma of Section 3) and is single-digit on the
-// power-law workloads, so the read-back is not on the bulk path.
+// A host-driven round loop reads |U| after every round to stop; the number of
+// rounds is O(log n) (the round-bound lemma of Section 3) and is single-digit
+// on the power-law workloads.  A repeated call runs rounds 2 on as one CUDA
+// graph whose finalize kernel decides on the device whether to go on
+// (adg_round_graph below).
 #include <climits>
 #include <cstring>
 #include <mutex>
